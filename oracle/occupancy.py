@@ -1,0 +1,153 @@
+"""Occupancy phi(p) in FP64 for the oracle (test infrastructure only).
+
+Paper: an occupancy function phi: R^3 -> {0 (out), 1 (in)} (Sec. 3); neural
+occupancies are thresholded at the iso level to give binary labels (A.2.2).
+
+Readings (the paper is silent on these):
+  * The query point is rounded to FP32 before phi is evaluated, as every GPU
+    occupancy network consumes FP32 coordinates.  Both the oracle and the CUDA
+    path evaluate phi at the same FP32 point.
+  * Ties are "out": a point is inside only if occ > iso strictly.
+  * CSG: inside(prim) iff g_prim < 0.  Union is min, difference A \\ B is
+    max(g_A, -g_B); folded left to right in primitive order.  As booleans this
+    is ``in = in or in_p`` (union) and ``in = in and (g_p > 0)`` (difference).
+  * MLP: the decision is taken on the pre-sigmoid logit, z > logit(iso).
+
+Each evaluation also returns a *margin*: a distance-like measure of how far
+the decision is from flipping (world units for CSG, |occ - iso| for MLP).  The
+parity tests use it to flag decisions that finite precision could flip.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from paper_2409_13418_gb300.inputs import (CSGSource, MLPSource, OP_UNION, PRIM_AABB,
+                                           PRIM_CYLINDER, PRIM_OBOX, PRIM_SPHERE, PRIM_TORUS)
+
+
+def to_query(points: np.ndarray) -> np.ndarray:
+    """Round query points to FP32 and widen back to FP64."""
+    return np.asarray(points, np.float64).astype(np.float32).astype(np.float64)
+
+
+def prim_g(src: CSGSource, i: int, x: np.ndarray):
+    """Sign function g and margin of primitive ``i`` at FP64 points ``x`` (n, 3).
+
+    g < 0 inside, g > 0 outside.  Every operand is an FP32 value widened to
+    FP64; the operation order below is the definition of g.
+    """
+    t = int(src.types[i])
+    c = src.centers[i].astype(np.float64)
+    M = src.rot[i].astype(np.float64)
+    p = src.params[i].astype(np.float64)
+    dx = x[:, 0] - c[0]
+    dy = x[:, 1] - c[1]
+    dz = x[:, 2] - c[2]
+    if t == PRIM_SPHERE:
+        r = p[0]
+        g = ((dx * dx + dy * dy) + dz * dz) - r * r
+        return g, np.abs(g) / (2.0 * r)
+    if t == PRIM_AABB:
+        g = np.maximum(np.maximum(np.abs(dx) - p[0], np.abs(dy) - p[1]), np.abs(dz) - p[2])
+        return g, np.abs(g)
+    if t == PRIM_OBOX:
+        ls = [((M[k, 0] * dx + M[k, 1] * dy) + M[k, 2] * dz) for k in range(3)]
+        g = np.maximum(np.maximum(np.abs(ls[0]) - p[0], np.abs(ls[1]) - p[1]), np.abs(ls[2]) - p[2])
+        return g, np.abs(g)
+    ax = M[2]
+    tt = (ax[0] * dx + ax[1] * dy) + ax[2] * dz
+    d2 = (dx * dx + dy * dy) + dz * dz
+    if t == PRIM_CYLINDER:
+        r, hh = p[0], p[1]
+        radial = (d2 - tt * tt) - r * r
+        axial = np.abs(tt) - hh
+        g_r = radial / (2.0 * r)
+        g = np.maximum(g_r, axial)
+        return g, np.abs(g)
+    if t == PRIM_TORUS:
+        R, r = p[0], p[1]
+        q = (d2 + R * R) - r * r
+        g = q * q - (4.0 * R * R) * (d2 - tt * tt)
+        return g, np.abs(g) / (8.0 * R * R * r)
+    raise ValueError(f"unknown primitive type {t}")
+
+
+def csg_eval(src: CSGSource, points: np.ndarray):
+    """Labels (bool) and margins of a CSG source at ``points`` (n, 3)."""
+    x = to_query(points)
+    n = x.shape[0]
+    inside = np.zeros(n, bool)
+    margin = np.full(n, np.inf)
+    for i in range(src.n_prims):
+        g, m = prim_g(src, i, x)
+        if i == 0 or int(src.ops[i]) == OP_UNION:
+            inside = inside | (g < 0)
+        else:
+            inside = inside & (g > 0)
+        margin = np.minimum(margin, m)
+    return inside, margin
+
+
+def fourier_features(src: MLPSource, x: np.ndarray) -> np.ndarray:
+    """g(x) = [sin(2 pi B x), cos(2 pi B x)] in FP64."""
+    B = src.B.astype(np.float64)
+    u = x @ B.T
+    ang = 2.0 * math.pi * u
+    return np.concatenate([np.sin(ang), np.cos(ang)], axis=1)
+
+
+def mlp_f(src: MLPSource, x: np.ndarray, chunk: int = 32768) -> np.ndarray:
+    """The network output f(x) in FP64 (FP32 weights widened)."""
+    Ws = [w.astype(np.float64) for w in src.weights]
+    bs = [b.astype(np.float64) for b in src.biases]
+    out = np.empty(x.shape[0])
+    lat = None if src.latent is None else src.latent.astype(np.float64)
+    for s in range(0, x.shape[0], chunk):
+        xs = x[s:s + chunk]
+        h = fourier_features(src, xs)
+        if lat is not None:
+            h = np.concatenate([np.broadcast_to(lat, (xs.shape[0], lat.shape[0])), h], axis=1)
+        for li in range(len(Ws) - 1):
+            h = np.maximum(h @ Ws[li].T + bs[li], 0.0)
+        out[s:s + chunk] = (h @ Ws[-1].T + bs[-1])[:, 0]
+    return out
+
+
+def mlp_logit(src: MLPSource, points: np.ndarray) -> np.ndarray:
+    """z = scale * (radius - |x| + amp * f(x)), the envelope's pre-sigmoid logit."""
+    x = to_query(points)
+    r = np.sqrt((x[:, 0] * x[:, 0] + x[:, 1] * x[:, 1]) + x[:, 2] * x[:, 2])
+    return float(np.float32(src.env_scale)) * (
+        (float(np.float32(src.env_radius)) - r) + float(np.float32(src.env_amp)) * mlp_f(src, x))
+
+
+def mlp_eval(src: MLPSource, points: np.ndarray, iso: float = 0.5):
+    """Labels and margins |occ - iso| of an MLP source."""
+    z = mlp_logit(src, points)
+    t = math.log(iso / (1.0 - iso))
+    occ = 1.0 / (1.0 + np.exp(-z))
+    return z > t, np.abs(occ - iso)
+
+
+class Occupancy:
+    """Callable phi with query accounting: ``labels, margins = phi(points)``."""
+
+    def __init__(self, src, iso: float = 0.5):
+        self.src = src
+        self.iso = iso
+        self.queries = 0
+
+    def __call__(self, points: np.ndarray):
+        points = np.asarray(points, np.float64).reshape(-1, 3)
+        self.queries += points.shape[0]
+        if points.shape[0] == 0:
+            return np.zeros(0, bool), np.zeros(0)
+        if isinstance(self.src, CSGSource):
+            return csg_eval(self.src, points)
+        if isinstance(self.src, MLPSource):
+            return mlp_eval(self.src, points, self.iso)
+        if callable(self.src):
+            return self.src(to_query(points))
+        raise TypeError(type(self.src))
