@@ -1,0 +1,234 @@
+/*
+ * odc.h -- C ABI of the GB300 occupancy-based dual contouring (ODC) library.
+ *
+ * The library turns an occupancy function phi: R^3 -> {0 (out), 1 (in)} on a
+ * uniform grid over a box into a triangle mesh, following "Occupancy-Based
+ * Dual Contouring" (Hwang & Sung, SIGGRAPH Asia 2024): given phi and a grid
+ * over the space P, extract a mesh of the boundary surface (Sec. 3).  Every
+ * stage runs as a CUDA kernel for sm_103a on one GPU:
+ *   grid occupancy (Sec. 3) -> compaction of crossing edges, faces and cells
+ *   -> cycles per cell with the manifold fix (A.1.1) -> 1D binary search
+ *   (Sec. 5.1) -> 2D line-binary search (Sec. 5.2, A.1.3, A.1.4) -> normals
+ *   from 2D points (Sec. 5.3) -> one QEF 3D point per cycle (Eq. 2) -> quads
+ *   split by convex/concave analysis (Sec. 5.4, A.1.5).
+ *
+ * Conventions
+ *   - Grid: res[a] cells per axis; vertex coordinates x_i = fl32(lo + (hi -
+ *     lo) i / res) per axis, computed in double and rounded to float.
+ *   - phi is evaluated at the query point rounded to float32.  A point is
+ *     inside only if occ > iso strictly (ties are outside).
+ *   - Vertex id v = i + (res0+1) (j + (res1+1) k); edge and face ids are
+ *     3 v + a for the edge along axis a from vertex v and the face normal to
+ *     axis a whose lowest corner is v.
+ *   - Output vertices are float32 [n_verts][3] world coordinates; triangles
+ *     are int32 [n_tris][3], counter-clockwise seen from outside (A.1.5).
+ *     Vertices are the 3D points in cell order (cycles by increasing smallest
+ *     local edge), then the case-3 1D points in edge order; triangles are in
+ *     edge order.  The same input gives byte-identical output.
+ *
+ * Ownership
+ *   - A context owns one device, a stream (unless the caller passes one) and
+ *     a device memory arena that grows on demand up to ``mem_budget`` bytes.
+ *   - Source descriptors (primitives, weights) are HOST pointers; they are
+ *     copied to the device inside odc_extract.
+ *   - The mesh returned by odc_extract points into context memory; it stays
+ *     valid until the next odc_extract on the same context, odc_mesh_release
+ *     or odc_ctx_destroy.  odc_mesh_copy copies it into caller buffers.
+ *
+ * Errors
+ *   - Every call returns an odc_status; no exception or exit crosses the
+ *     ABI.  CUDA errors map to ODC_ERR_CUDA; odc_last_error() returns a
+ *     thread-local message for the last failing call on this thread.
+ *   - Invalid arguments (null pointers, res < 1 or res > 1024, lo >= hi,
+ *     steps_1d outside [1, 20], unknown primitive types, n_prims outside
+ *     [1, 4096], unsupported MLP shapes) return ODC_ERR_INVALID_ARG.
+ *   - Exceeding mem_budget returns ODC_ERR_OOM.
+ *   - Device-side waits are bounded; an expired wait returns ODC_ERR_TIMEOUT.
+ */
+#ifndef ODC_H
+#define ODC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ODC_OK = 0,
+    ODC_ERR_INVALID_ARG = 1,
+    ODC_ERR_OOM = 2,
+    ODC_ERR_CUDA = 3,
+    ODC_ERR_TIMEOUT = 4,
+    ODC_ERR_UNSUPPORTED = 5,
+    ODC_ERR_INTERNAL = 6
+} odc_status;
+
+typedef struct odc_ctx odc_ctx;
+
+/* Occupancy source kinds. */
+enum { ODC_SRC_CSG = 0, ODC_SRC_MLP = 1 };
+
+/* CSG primitive types and operations (Sec. 3: any phi; CSG is a synthetic
+ * stand-in for the paper's neural occupancies). */
+enum { ODC_PRIM_SPHERE = 0, ODC_PRIM_AABB = 1, ODC_PRIM_OBOX = 2,
+       ODC_PRIM_CYLINDER = 3, ODC_PRIM_TORUS = 4 };
+enum { ODC_OP_UNION = 0, ODC_OP_DIFFERENCE = 1 };
+
+/* One CSG primitive, 80 bytes.  d = x - center.
+ *   sphere:   params = [r]                 inside iff |d|^2 < r^2
+ *   aabb:     params = [ex, ey, ez]        inside iff |d_i| < e_i for all i
+ *   obox:     params = [ex, ey, ez]        l_i = rot[i] . d, inside iff |l_i| < e_i
+ *   cylinder: params = [r, hh], axis rot[2]  t = axis . d,
+ *             inside iff |d|^2 - t^2 < r^2 and |t| < hh
+ *   torus:    params = [R, r], axis rot[2]
+ *             inside iff (|d|^2 + R^2 - r^2)^2 < 4 R^2 (|d|^2 - t^2)
+ * The primitives are folded left to right: in = in || in_p (union) or
+ * in = in && out_p (difference, out_p strictly outside); prims[0].op is
+ * treated as a union. */
+typedef struct {
+    int32_t type;
+    int32_t op;
+    float center[3];
+    float rot[9];      /* row-major 3x3, rows are the local axes */
+    float params[4];
+    float pad[2];
+} odc_csg_prim;
+
+/* MLP precisions. */
+enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1 };
+
+/* Envelope MLP occupancy: occ(x) = sigmoid(env_scale (env_radius - |x| +
+ * env_amp f(x))), f(x) = W_L relu(... relu(W_0 [latent, g(x)] + b_0) ...) + b_L,
+ * g(x) = [sin(2 pi B x), cos(2 pi B x)].  All pointers are host float32
+ * row-major: B [n_freq][3], W_0 [hidden][latent_dim + 2 n_freq],
+ * W_1..W_{n_hidden-1} [hidden][hidden], W_{n_hidden} [1][hidden], biases
+ * b_l [rows of W_l].  Supported: n_freq = 64, hidden = 256, n_hidden = 4,
+ * latent_dim in {0, 128}.  With ODC_PREC_BF16 every decision whose BF16
+ * occupancy lies within ``band`` of iso is re-evaluated in FP32. */
+typedef struct {
+    int32_t n_freq;
+    int32_t hidden;
+    int32_t n_hidden;
+    int32_t latent_dim;
+    const float* B;
+    const float* W[8];
+    const float* b[8];
+    const float* latent;
+    float env_scale;
+    float env_radius;
+    float env_amp;
+    int32_t precision;
+    float band;
+    int32_t pad;
+} odc_mlp;
+
+typedef struct {
+    int32_t kind;                /* ODC_SRC_CSG or ODC_SRC_MLP */
+    int32_t n_prims;
+    const odc_csg_prim* prims;   /* host, n_prims records (CSG) */
+    const odc_mlp* mlp;          /* host (MLP) */
+} odc_source;
+
+typedef struct {
+    float lo[3];
+    float hi[3];
+    int32_t res[3];
+} odc_grid;
+
+/* Search parameters; the paper's values are iso 0.5, k = 15 at 128^3
+ * (Sec. 5.1), step 1 of the 2D search 4 samples + 11 bisections over
+ * 0.8 cell, step 2 3 samples + 12 bisections over sqrt(2)/2 cell (A.1.4). */
+typedef struct {
+    float iso;
+    int32_t steps_1d;
+    int32_t s2d_lin1, s2d_bin1;
+    float s2d_range1;
+    int32_t s2d_lin2, s2d_bin2;
+    float s2d_range2;
+    int32_t ic_split;            /* 1: IC quad splitting (A.1.5); 0: first diagonal */
+    int32_t reserved;
+} odc_params;
+
+typedef struct {
+    int64_t n_edges;             /* |E^S| crossing edges */
+    int64_t n_face_segs;         /* 2D points (one per face segment) */
+    int64_t n_cells;             /* |C^S| crossing cells */
+    int64_t n_verts3;            /* 3D points (cycles) */
+    int64_t n_case3;             /* quads split into 4 triangles */
+    int64_t n_flips;             /* faces flipped by the manifold fix */
+    int64_t fix_rounds;
+    int64_t n_queries;           /* occupancy evaluations on the main path */
+    int64_t n_requeries;         /* FP32 re-evaluations inside the band */
+    float stage_ms[8];           /* grid, compact, topology, 1D, 2D, QEF, quads, total */
+} odc_stats;
+
+typedef struct {
+    int64_t n_verts;
+    int64_t n_tris;
+    const float* d_verts;        /* device, context-owned */
+    const int32_t* d_tris;       /* device, context-owned */
+    odc_stats stats;
+} odc_mesh;
+
+/* Create a context on CUDA device ``device``; the arena may grow to
+ * ``mem_budget`` bytes (0 = no limit).  *out is NULL on failure. */
+odc_status odc_ctx_create(int device, size_t mem_budget, odc_ctx** out);
+
+/* Destroy a context and free its device memory.  NULL is accepted. */
+odc_status odc_ctx_destroy(odc_ctx* ctx);
+
+/* Run the whole ODC path for one shape.  ``cuda_stream`` is a cudaStream_t
+ * (NULL: the context's own stream).  Returns after the mesh is complete in
+ * device memory (the counts are read back once).  Sec. 3 problem statement;
+ * stages as listed at the top of this header. */
+odc_status odc_extract(odc_ctx* ctx, const odc_source* src, const odc_grid* grid,
+                       const odc_params* params, void* cuda_stream, odc_mesh* out);
+
+/* Copy a mesh into caller buffers: verts float[n_verts*3], tris
+ * int32[n_tris*3]; ``dst_on_device`` selects device or host destinations.
+ * Synchronous.  Either pointer may be NULL to skip it. */
+odc_status odc_mesh_copy(odc_ctx* ctx, const odc_mesh* mesh, float* verts, int32_t* tris,
+                         int dst_on_device);
+
+/* Mark the mesh's memory reusable (the next extract reuses it anyway). */
+odc_status odc_mesh_release(odc_ctx* ctx, odc_mesh* mesh);
+
+/* Intermediate buffers of the last extract, for parity checks.  Copies at
+ * most ``max_bytes`` of buffer ``what`` into host memory ``dst`` and stores
+ * the element count in *count and the element size in *elem_bytes:
+ *   ODC_DBG_LABELS     uint32 label bit rows [res2+1][res1+1][ceil((res0+1)/32)]
+ *   ODC_DBG_EDGES      uint32 crossing edge ids (sorted)
+ *   ODC_DBG_T          uint32 1D results T (odd; point = T / 2^(k+1) along the edge)
+ *   ODC_DBG_FACES      uint32 face ids of the 2D points (sorted with slots)
+ *   ODC_DBG_SLOTS      uint8 segment slot of each 2D point
+ *   ODC_DBG_FACE_PTS   float2 face-local (u, v) of each 2D point
+ *   ODC_DBG_FACE_FLAGS uint8 bit0: q == m, bit1: parallel lines
+ *   ODC_DBG_CELLS      uint32 crossing cell ids (sorted)
+ *   ODC_DBG_CONFIGS    uint8 cell configurations
+ *   ODC_DBG_CYCLES     uint64 per cell: 4-bit cycle index per local edge (0xF: none)
+ *   ODC_DBG_VLOCAL     float3 cell-local 3D points
+ *   ODC_DBG_QCASE      uint8 per crossing edge: 0 no quad, 1/2/3 split case
+ *   ODC_DBG_FLIPS      uint32 ids of faces flipped by the manifold fix (sorted)
+ */
+enum { ODC_DBG_LABELS = 0, ODC_DBG_EDGES, ODC_DBG_T, ODC_DBG_FACES, ODC_DBG_SLOTS,
+       ODC_DBG_FACE_PTS, ODC_DBG_FACE_FLAGS, ODC_DBG_CELLS, ODC_DBG_CONFIGS,
+       ODC_DBG_CYCLES, ODC_DBG_VLOCAL, ODC_DBG_QCASE, ODC_DBG_FLIPS, ODC_DBG_COUNT };
+odc_status odc_debug_copy(odc_ctx* ctx, int what, void* dst, size_t max_bytes,
+                          int64_t* count, int32_t* elem_bytes);
+
+/* Evaluate the occupancy of ``src`` at n points (host float[n][3]) on the
+ * device and return labels (host uint8[n]) and, for MLP sources, logits
+ * (host float[n], may be NULL).  ``precision`` overrides the MLP precision
+ * (-1 keeps the source's).  Sec. 3 / A.2.2 binary occupancy. */
+odc_status odc_eval_points(odc_ctx* ctx, const odc_source* src, const float* points, int64_t n,
+                           float iso, int precision, uint8_t* labels, float* logits);
+
+const char* odc_status_str(odc_status s);
+const char* odc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ODC_H */

@@ -51,7 +51,9 @@ def prim_g(src: CSGSource, i: int, x: np.ndarray):
         return g, np.abs(g) / (2.0 * r)
     if t == PRIM_AABB:
         g = np.maximum(np.maximum(np.abs(dx) - p[0], np.abs(dy) - p[1]), np.abs(dz) - p[2])
-        return g, np.abs(g)
+        # every operation above is exact for float32 operands, so a tie g == 0
+        # is decided identically ("out") in any precision: not a fragile decision
+        return g, np.where(g == 0.0, np.inf, np.abs(g))
     if t == PRIM_OBOX:
         ls = [((M[k, 0] * dx + M[k, 1] * dy) + M[k, 2] * dz) for k in range(3)]
         g = np.maximum(np.maximum(np.abs(ls[0]) - p[0], np.abs(ls[1]) - p[1]), np.abs(ls[2]) - p[2])

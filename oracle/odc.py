@@ -42,6 +42,43 @@ from .occupancy import Occupancy
 
 FACE_UV = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])   # face corners (u, v)
 
+def _fe_point(fe, t):
+    """Face-local (u, v) of the point at parameter t along face edge fe."""
+    u = np.where(fe == 1, 1.0, np.where(fe == 3, 0.0, t))
+    v = np.where(fe == 2, 1.0, np.where(fe == 0, 0.0, t))
+    return np.stack([u, v], axis=-1)
+
+
+FE_POINT = _fe_point
+
+
+def _seg_table():
+    """SEG[lab4, flip, slot] = (face edge 1, face edge 2) from topology.face_segments."""
+    t = np.full((16, 2, 2, 2), -1, np.int64)
+    for L in range(16):
+        for fl in (0, 1):
+            for s, (i, j) in enumerate(topo.face_segments([(L >> b) & 1 for b in range(4)], bool(fl))):
+                t[L, fl, s] = (i, j)
+    return t
+
+
+def _slot_table():
+    """SLOT[config, flip of face f, f, local edge] = segment slot holding the edge."""
+    t = np.zeros((256, 2, 6, 12), np.int64)
+    for cfg in range(256):
+        for fl in (0, 1):
+            for f in range(6):
+                for le in topo.face_edges(f):
+                    try:
+                        t[cfg, fl, f, le] = topo.face_slot_of_edge(cfg, fl << f, f, le)
+                    except ValueError:
+                        pass
+    return t
+
+
+SEG_TABLE = _seg_table()
+SLOT_TABLE = _slot_table()
+
 PAR_EPS = 1e-9       # relative parallel-line threshold of 2D step 3
 NORMAL_EPS = 1e-12   # degenerate-normal threshold (cell units^2)
 QEF_TRUNC = 0.01     # relative eigenvalue truncation
@@ -80,12 +117,18 @@ class Result:
 
 
 def grid_coords(grid):
-    """Per-axis FP32 grid coordinates x_i = fl32(lo + (hi - lo) i / N), widened."""
+    """Per-axis FP32 grid coordinates x_i = fl32(lo + (hi - lo) i / N), widened.
+
+    The box bounds are float32 values (they define the instance), widened to
+    double before the formula is evaluated.
+    """
     out = []
     for a in range(3):
         n = int(grid.res[a])
+        lo = float(np.float32(grid.lo[a]))
+        hi = float(np.float32(grid.hi[a]))
         i = np.arange(n + 1, dtype=np.float64)
-        out.append((grid.lo[a] + (grid.hi[a] - grid.lo[a]) * i / n).astype(np.float32).astype(np.float64))
+        out.append((lo + (hi - lo) * i / n).astype(np.float32).astype(np.float64))
     return out
 
 
@@ -378,46 +421,36 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     fslot = faces[:, 1]
     fi, fj, fk = geo.vijk(fv)
     fijk = np.stack([fi, fj, fk], axis=1)
-    P1 = np.zeros((F, 2))
-    P2 = np.zeros((F, 2))
-    in_w = np.zeros((F, 2))       # out-corner -> in-corner along the first segment edge
-    seg_margin = np.zeros(F)
-    seg_edges = np.zeros((F, 2), np.int64)
-    face_lab_cache = {}
-    for n in range(F):
-        fid = int(faces[n, 0])
-        a = int(fa[n])
-        labs4 = face_labels(fid)
-        face_lab_cache[fid] = labs4
-        segs = topo.face_segments(labs4, fid in flipped)
-        (s0, s1) = segs[int(fslot[n])]
-        v0 = fijk[n]
-        b, c = (a + 1) % 3, (a + 2) % 3
-        pts2 = []
-        for t, fe in enumerate((s0, s1)):
-            # global edge of face edge fe
-            if fe == 0:
-                g = 3 * geo.vid(*v0) + b
-            elif fe == 1:
-                g = 3 * geo.vid(*(v0 + _unit(b))) + c
-            elif fe == 2:
-                g = 3 * geo.vid(*(v0 + _unit(c))) + b
-            else:
-                g = 3 * geo.vid(*v0) + c
-            pi = edge_pos(g)
-            assert edges[pi] == g
-            seg_edges[n, t] = pi
-            tt = tau[pi]
-            pts2.append({0: (tt, 0.0), 1: (1.0, tt), 2: (tt, 1.0), 3: (0.0, tt)}[fe])
-        P1[n] = pts2[0]
-        P2[n] = pts2[1]
-        ca, cb = s0, (s0 + 1) % 4
-        if labs4[ca]:
-            in_w[n] = FACE_UV[ca] - FACE_UV[cb]
-        else:
-            in_w[n] = FACE_UV[cb] - FACE_UV[ca]
-    if F:
-        seg_margin = np.minimum(edge_margin[seg_edges[:, 0]], edge_margin[seg_edges[:, 1]])
+    fb = (fa + 1) % 3
+    fc = (fa + 2) % 3
+    EYE = np.eye(3, dtype=np.int64)
+    # face-corner labels in face order (u, v) = (0,0), (1,0), (1,1), (0,1)
+    lab4 = np.zeros((F, 4), bool)
+    for t, (du, dv) in enumerate(((0, 0), (1, 0), (1, 1), (0, 1))):
+        q = fijk + du * EYE[fb] + dv * EYE[fc]
+        lab4[:, t] = labels[q[:, 2], q[:, 1], q[:, 0]]
+    lab4i = lab4 @ np.array([1, 2, 4, 8])
+    fflip = np.isin(faces[:, 0], flips)
+    s0 = SEG_TABLE[lab4i, fflip.astype(np.int64), fslot, 0]
+    s1 = SEG_TABLE[lab4i, fflip.astype(np.int64), fslot, 1]
+
+    def face_edge_pos(fe):
+        """Index in ``edges`` of the global edge under face edge ``fe``."""
+        q = fijk + (fe == 1)[:, None] * EYE[fb] + (fe == 2)[:, None] * EYE[fc]
+        axis = np.where((fe == 0) | (fe == 2), fb, fc)
+        g = 3 * geo.vid(q[:, 0], q[:, 1], q[:, 2]) + axis
+        pi = np.searchsorted(edges, g)
+        assert np.all(edges[pi] == g)
+        return pi
+
+    seg_edges = np.stack([face_edge_pos(s0), face_edge_pos(s1)], axis=1) if F else np.zeros((0, 2), np.int64)
+    P1 = FE_POINT(s0, tau[seg_edges[:, 0]]) if F else np.zeros((0, 2))
+    P2 = FE_POINT(s1, tau[seg_edges[:, 1]]) if F else np.zeros((0, 2))
+    # out-corner -> in-corner along the first segment edge (face corners s0, s0+1)
+    ca, cb = s0, (s0 + 1) % 4
+    inA = lab4[np.arange(F), ca] if F else np.zeros(0, bool)
+    in_w = np.where(inA[:, None], FACE_UV[ca] - FACE_UV[cb], FACE_UV[cb] - FACE_UV[ca]) if F else np.zeros((0, 2))
+    seg_margin = np.minimum(edge_margin[seg_edges[:, 0]], edge_margin[seg_edges[:, 1]]) if F else np.zeros(0)
 
     def face_world(uv, sel):
         """World point of face-local (u, v) on the faces ``sel`` (index array)."""
@@ -502,79 +535,75 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
         near_par = act & (np.abs(det) <= 1e3 * PAR_EPS * np.linalg.norm(r1, axis=1) * np.linalg.norm(r2, axis=1))
         flags[near_par & ~par] |= 4
 
-    def face_pos(fid, slot):
-        return np.searchsorted(faces[:, 0] * 2 + faces[:, 1], fid * 2 + slot)
+    fkey = faces[:, 0] * 2 + faces[:, 1]
 
     # ---- normals (Sec. 5.3) and QEF 3D points (Eq. 2) --------------------------------
-    verts_local = np.zeros((V3, 3))
+    # every (crossing cell, crossing local edge) pair contributes one plane to
+    # the QEF of the cycle holding the edge
+    pc, ple = np.nonzero(cell_cyc >= 0)
+    K = pc.shape[0]
+    pvid = vbase[pc] + cell_cyc[pc, ple]
+    pa = ple // 4
+    po1, po2 = ple & 1, (ple >> 1) & 1
+    d0 = np.zeros((K, 3), np.int64)
+    d0[np.arange(K), (pa + 1) % 3] = po1
+    d0[np.arange(K), (pa + 2) % 3] = po2
+    cijk_all = np.stack([ci, cj, ck], axis=1)
+    pcell = cijk_all[pc]
+    q = pcell + d0
+    ppi = np.searchsorted(edges, 3 * geo.vid(q[:, 0], q[:, 1], q[:, 2]) + pa)
+    pe = d0.astype(np.float64)
+    pe[np.arange(K), pa] = tau[ppi]
+    mar = edge_margin[ppi].copy()
+    pflag = np.zeros(K, bool)
+    pfs = []
+    for f in (2 * ((pa + 1) % 3) + po1, 2 * ((pa + 2) % 3) + po2):   # the two faces holding the edge
+        fa_, s_ = f // 2, f % 2
+        fq = pcell + s_[:, None] * EYE[fa_]
+        gfid = 3 * geo.vid(fq[:, 0], fq[:, 1], fq[:, 2]) + fa_
+        slot = SLOT_TABLE[configs[pc], (cell_flipm[pc] >> f) & 1, f, ple]
+        fpi = np.searchsorted(fkey, gfid * 2 + slot)
+        assert np.all(fkey[fpi] == gfid * 2 + slot)
+        uv = pf[fpi]
+        p3 = np.zeros((K, 3))
+        p3[np.arange(K), fa_] = s_
+        p3[np.arange(K), (fa_ + 1) % 3] = uv[:, 0]
+        p3[np.arange(K), (fa_ + 2) % 3] = uv[:, 1]
+        pfs.append(p3)
+        mar = np.minimum(mar, face_margin[fpi])
+        pflag |= (flags[fpi] & 4) != 0
+    v1 = pfs[0] - pe
+    v2 = pfs[1] - pe
+    nrm = np.cross(v1, v2)
+    nn = np.linalg.norm(nrm, axis=1)
+    pflag |= (nn < 1e4 * NORMAL_EPS) | (nn < 1e-4 * np.linalg.norm(v1, axis=1) * np.linalg.norm(v2, axis=1))
+    keep = nn >= NORMAL_EPS
+    nh = np.zeros((K, 3))
+    nh[keep] = nrm[keep] / nn[keep, None]
+    A = np.zeros((V3, 3, 3))
+    bvec = np.zeros((V3, 3))
+    csum = np.zeros((V3, 3))
+    np.add.at(A, pvid, nh[:, :, None] * nh[:, None, :])
+    np.add.at(bvec, pvid, nh * np.einsum("ij,ij->i", nh, pe)[:, None])
+    np.add.at(csum, pvid, pe)
+    cnt = np.bincount(pvid, minlength=V3)
     vert_margin = np.full(V3, np.inf)
+    np.minimum.at(vert_margin, pvid, mar)
     vert_flag = np.zeros(V3, bool)
-    for n in range(C):
-        cfg_n = int(configs[n])
-        fm = int(cell_flipm[n])
-        cijk = np.array([ci[n], cj[n], ck[n]])
-        cyc = cell_cyc[n]
-        for cy in range(int(cell_ncyc[n])):
-            A = np.zeros((3, 3))
-            bvec = np.zeros(3)
-            pes = []
-            vid = int(vbase[n]) + cy
-            mar = np.inf
-            flag = False
-            for le in range(12):
-                if cyc[le] != cy:
-                    continue
-                a, o1, o2 = topo.edge_axis_offsets(le)
-                d0 = np.array(topo.edge_start(le))
-                gid = 3 * geo.vid(*(cijk + d0)) + a
-                pi = edge_pos(gid)
-                pe = d0.astype(np.float64)
-                pe[a] = tau[pi]
-                pes.append(pe)
-                mar = min(mar, edge_margin[pi])
-                pfs = []
-                for f in topo.edge_faces(le):
-                    fa_, s_ = f // 2, f % 2
-                    fq = cijk.copy()
-                    fq[fa_] += s_
-                    gfid = 3 * geo.vid(*fq) + fa_
-                    slot = topo.face_slot_of_edge(cfg_n, fm, f, le)
-                    fpi = face_pos(gfid, slot)
-                    assert faces[fpi, 0] == gfid and faces[fpi, 1] == slot
-                    uv = pf[fpi]
-                    p3 = np.zeros(3)
-                    p3[fa_] = s_
-                    p3[(fa_ + 1) % 3] = uv[0]
-                    p3[(fa_ + 2) % 3] = uv[1]
-                    pfs.append(p3)
-                    mar = min(mar, face_margin[fpi])
-                    if flags[fpi] & 4:
-                        flag = True
-                v1 = pfs[0] - pe
-                v2 = pfs[1] - pe
-                nrm = np.cross(v1, v2)
-                nn = np.linalg.norm(nrm)
-                if nn < 1e4 * NORMAL_EPS or nn < 1e-4 * np.linalg.norm(v1) * np.linalg.norm(v2):
-                    flag = True
-                if nn < NORMAL_EPS:
-                    continue
-                nh = nrm / nn
-                A += np.outer(nh, nh)
-                bvec += nh * np.dot(nh, pe)
-            cbar = np.mean(pes, axis=0)
-            lam, V = np.linalg.eigh(A)
-            lmax = lam.max()
-            x = cbar.copy()
-            if lmax > 0:
-                inv = np.zeros(3)
-                keep = lam >= QEF_TRUNC * lmax
-                inv[keep] = 1.0 / lam[keep]
-                if np.any(np.abs(lam / lmax - QEF_TRUNC) < 1e-6):
-                    flag = True
-                x = cbar + V @ (inv * (V.T @ (bvec - A @ cbar)))
-            verts_local[vid] = x
-            vert_margin[vid] = mar
-            vert_flag[vid] = flag
+    np.logical_or.at(vert_flag, pvid, pflag)
+    cbar = csum / np.maximum(cnt, 1)[:, None]
+    verts_local = cbar.copy()
+    if V3:
+        lam, V = np.linalg.eigh(A)
+        lmax = lam.max(axis=1)
+        pos = lmax > 0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ratio = lam / lmax[:, None]
+            inv = np.where((ratio >= QEF_TRUNC) & pos[:, None], 1.0 / lam, 0.0)
+            vert_flag |= pos & np.any(np.abs(ratio - QEF_TRUNC) < 1e-6, axis=1)
+        rhs = bvec - np.einsum("vij,vj->vi", A, cbar)
+        t = inv * np.einsum("vji,vj->vi", V, rhs)
+        verts_local = cbar + np.einsum("vij,vj->vi", V, t)
 
     cell_world0 = np.stack([X[0][ci], X[1][cj], X[2][ck]], axis=1) if C else np.zeros((0, 3))
     cell_span = np.stack([X[0][ci + 1] - X[0][ci], X[1][cj + 1] - X[1][cj], X[2][ck + 1] - X[2][ck]], axis=1) if C else np.zeros((0, 3))
@@ -582,66 +611,66 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     verts3 = cell_world0[vcell] + cell_span[vcell] * verts_local if V3 else np.zeros((0, 3))
 
     # ---- quads with IC splitting (Sec. 4, Sec. 5.4, A.1.5) --------------------------------
-    tris = []
-    extra = []
-    quad_edges, quad_case, quad_flag, quad_margin = [], [], [], []
-    cell_pos = {int(c): n for n, c in enumerate(cells)}
-    for n in range(E):
-        a = int(ea[n])
-        b, c = (a + 1) % 3, (a + 2) % 3
-        v = eijk[n]
-        if not (1 <= v[b] <= N[b] - 1 and 1 <= v[c] <= N[c] - 1):
-            continue
-        lower_in = bool(lab0[n])
-        order = quad_ring(a, lower_in)
-        vids, P = [], []
-        mar = edge_margin[n]
-        flag = False
-        for (db, dc) in order:
-            cc = v - db * _unit(b) - dc * _unit(c)
-            cn = cell_pos[int(geo.cid(*cc))]
-            le = topo.edge_index(a, db, dc)
-            cy = int(cell_cyc[cn, le])
-            vid = int(vbase[cn]) + cy
-            vids.append(vid)
-            P.append(verts_local[vid] - db * _unit(b) - dc * _unit(c))
-            mar = min(mar, vert_margin[vid])
-            flag |= bool(vert_flag[vid])
-        P = np.array(P)
-        p_in = np.zeros(3) if lower_in else _unit(a).astype(np.float64)
-        p_out = _unit(a).astype(np.float64) if lower_in else np.zeros(3)
-        case = 1
-        if ic_split:
-            conc = []
-            dets = []
-            for kq in range(4):
-                pk, pp, pn = P[kq], P[(kq - 1) % 4], P[(kq + 1) % 4]
-                d_out = np.dot(pk - p_out, np.cross(pp - p_out, pn - p_out))
-                d_in = np.dot(pk - p_in, np.cross(pp - p_in, pn - p_in))
-                dets += [d_out, d_in]
-                conc.append(d_out < 0 or d_in > 0)
-            ok1 = not (conc[1] or conc[3])
-            ok2 = not (conc[0] or conc[2])
-            case = 1 if ok1 else (2 if ok2 else 3)
-            if min(abs(t) for t in dets) < 1e-5:
-                flag = True
-        c1, c2, c3, c4 = vids
-        if case == 1:
-            tris += [(c1, c2, c3), (c1, c3, c4)]
-        elif case == 2:
-            tris += [(c1, c2, c4), (c2, c3, c4)]
-        else:
-            pe_id = V3 + len(extra)
-            pe = x_lo[n].copy()
-            pe[a] = x_lo[n, a] + span[n] * tau[n]
-            extra.append(pe)
-            tris += [(pe_id, c1, c2), (pe_id, c2, c3), (pe_id, c3, c4), (pe_id, c4, c1)]
-        quad_edges.append(n)
-        quad_case.append(case)
-        quad_flag.append(flag)
-        quad_margin.append(mar)
-    vertices = np.concatenate([verts3, np.array(extra).reshape(-1, 3)]) if (V3 or extra) else np.zeros((0, 3))
-    triangles = np.array(tris, np.int64).reshape(-1, 3)
+    eb, ec = (ea + 1) % 3, (ea + 2) % 3
+    ar = np.arange(E)
+    qsel = ((eijk[ar, eb] >= 1) & (eijk[ar, eb] <= np.array(N)[eb] - 1) &
+            (eijk[ar, ec] >= 1) & (eijk[ar, ec] <= np.array(N)[ec] - 1)) if E else np.zeros(0, bool)
+    qn = np.nonzero(qsel)[0]
+    Q = qn.shape[0]
+    qa, qb, qc = ea[qn], eb[qn], ec[qn]
+    lower_in = lab0[qn].astype(bool)
+    RING_IN = np.array([(0, 0), (1, 0), (1, 1), (0, 1)])
+    RING_OUT = np.array([(0, 0), (0, 1), (1, 1), (1, 0)])
+    vids = np.zeros((Q, 4), np.int64)
+    P = np.zeros((Q, 4, 3))
+    qmar = edge_margin[qn].copy()
+    qflag = np.zeros(Q, bool)
+    for kq in range(4):
+        db = np.where(lower_in, RING_IN[kq, 0], RING_OUT[kq, 0])
+        dc = np.where(lower_in, RING_IN[kq, 1], RING_OUT[kq, 1])
+        off = db[:, None] * EYE[qb] + dc[:, None] * EYE[qc]
+        cc = eijk[qn] - off
+        cpos = np.searchsorted(cells, geo.cid(cc[:, 0], cc[:, 1], cc[:, 2]))
+        le = 4 * qa + db + 2 * dc
+        vids[:, kq] = vbase[cpos] + cell_cyc[cpos, le]
+        P[:, kq] = verts_local[vids[:, kq]] - off
+        qmar = np.minimum(qmar, vert_margin[vids[:, kq]])
+        qflag |= vert_flag[vids[:, kq]]
+    p_in = np.where(lower_in[:, None], 0.0, EYE[qa].astype(np.float64))
+    p_out = np.where(lower_in[:, None], EYE[qa].astype(np.float64), 0.0)
+    case = np.ones(Q, np.int64)
+    if ic_split and Q:
+        conc = np.zeros((Q, 4), bool)
+        mindet = np.full(Q, np.inf)
+        for kq in range(4):
+            pk, pp, pn = P[:, kq], P[:, (kq - 1) % 4], P[:, (kq + 1) % 4]
+            d_out = np.einsum("ij,ij->i", pk - p_out, np.cross(pp - p_out, pn - p_out))
+            d_in = np.einsum("ij,ij->i", pk - p_in, np.cross(pp - p_in, pn - p_in))
+            conc[:, kq] = (d_out < 0) | (d_in > 0)
+            mindet = np.minimum(mindet, np.minimum(np.abs(d_out), np.abs(d_in)))
+        ok1 = ~(conc[:, 1] | conc[:, 3])
+        ok2 = ~(conc[:, 0] | conc[:, 2])
+        case = np.where(ok1, 1, np.where(ok2, 2, 3))
+        qflag |= mindet < 1e-5
+    is3 = case == 3
+    pe_id = V3 + np.cumsum(is3) - 1
+    c1, c2, c3, c4 = vids[:, 0], vids[:, 1], vids[:, 2], vids[:, 3]
+    tri4 = np.full((Q, 4, 3), -1, np.int64)
+    m1, m2 = case == 1, case == 2
+    tri4[m1, 0] = np.stack([c1, c2, c3], 1)[m1]
+    tri4[m1, 1] = np.stack([c1, c3, c4], 1)[m1]
+    tri4[m2, 0] = np.stack([c1, c2, c4], 1)[m2]
+    tri4[m2, 1] = np.stack([c2, c3, c4], 1)[m2]
+    tri4[is3, 0] = np.stack([pe_id, c1, c2], 1)[is3]
+    tri4[is3, 1] = np.stack([pe_id, c2, c3], 1)[is3]
+    tri4[is3, 2] = np.stack([pe_id, c3, c4], 1)[is3]
+    tri4[is3, 3] = np.stack([pe_id, c4, c1], 1)[is3]
+    triangles = tri4.reshape(-1, 3)
+    triangles = triangles[triangles[:, 0] >= 0]
+    extra = x_lo[qn[is3]].copy()
+    extra[np.arange(extra.shape[0]), ea[qn[is3]]] = x_lo[qn[is3], ea[qn[is3]]] + span[qn[is3]] * tau[qn[is3]]
+    vertices = np.concatenate([verts3, extra.reshape(-1, 3)])
+    quad_edges, quad_case, quad_flag, quad_margin = qn, case, qflag, qmar
 
     return Result(res=N, steps=k1, labels=labels, label_margin=label_margin,
                   edges=edges, T=T, edge_margin=edge_margin, faces=faces, face_pts=pf,
@@ -649,8 +678,8 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
                   configs=configs, cell_cyc=cell_cyc, cell_ncyc=cell_ncyc, vbase=vbase,
                   verts_local=verts_local, vert_margin=vert_margin, vert_flag=vert_flag,
                   vertices=vertices, triangles=triangles,
-                  quad_edges=np.array(quad_edges, np.int64), quad_case=np.array(quad_case, np.int64),
-                  quad_flag=np.array(quad_flag, bool), quad_margin=np.array(quad_margin),
+                  quad_edges=quad_edges.astype(np.int64), quad_case=quad_case.astype(np.int64),
+                  quad_flag=quad_flag.astype(bool), quad_margin=qmar,
                   queries=phi.queries,
-                  stats=dict(E=E, F=F, C=C, V3=V3, case3=len(extra), flips=len(flips),
+                  stats=dict(E=E, F=F, C=C, V3=V3, case3=int(is3.sum()), flips=len(flips),
                              fix_rounds=rounds, queries=phi.queries))

@@ -1,0 +1,536 @@
+// api.cu -- C ABI and host orchestration of the ODC path (include/odc.h).
+//
+// One extract runs every stage on one stream.  The host reads counts back
+// from the device twice (crossing counts to size the lists; final vertex and
+// triangle counts) plus once per manifold-fix round.  Device memory comes
+// from two arenas owned by the context: one sized by the grid, one by the
+// crossing counts; both grow on demand and are reused across calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/odc.h"
+#include "kernels.h"
+#include "mlp.h"
+#include "odc_internal.h"
+
+using namespace odc;
+
+namespace {
+
+thread_local std::string g_err;
+
+odc_status fail(odc_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define ODC_CK(call)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return fail(ODC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    void reset() { off = 0; }
+    void* take(size_t bytes) {
+        size_t o = (off + 255) & ~(size_t)255;
+        off = o + ((bytes + 255) & ~(size_t)255);
+        return base + o;
+    }
+};
+
+size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct odc_ctx {
+    int device = 0;
+    size_t budget = 0;
+    cudaStream_t own = nullptr;
+    Arena A, B, S;              // grid-sized, count-sized, source (prims / weights)
+    uint32_t* h_cnt = nullptr;  // pinned host counters
+    cudaEvent_t ev[9] = {};
+    MlpState* mlp = nullptr;
+    // last extract
+    GridDev g{};
+    int k = 0;
+    uint32_t E = 0, F = 0, C = 0, V3 = 0, NT = 0, N3 = 0, nflip = 0;
+    uint32_t *bits = nullptr, *flips = nullptr, *edges = nullptr, *T = nullptr, *faces = nullptr, *cells = nullptr;
+    uint8_t *slots = nullptr, *fflags = nullptr, *configs = nullptr, *qcase = nullptr;
+    float2* pf = nullptr;
+    unsigned long long* cycles = nullptr;
+    float3 *vlocal = nullptr, *vworld = nullptr;
+    int3* tris = nullptr;
+    size_t nw = 0;
+};
+
+static odc_status arena_ensure(odc_ctx* c, Arena& a, size_t need) {
+    if (need <= a.cap) {
+        a.reset();
+        return ODC_OK;
+    }
+    size_t others = c->A.cap + c->B.cap + c->S.cap - a.cap;
+    size_t want = std::max(need, a.cap + a.cap / 4);
+    if (c->budget && others + want > c->budget) {
+        want = need;
+        if (others + want > c->budget)
+            return fail(ODC_ERR_OOM, "device arena would exceed the context memory budget (" +
+                                         std::to_string(others + want) + " > " + std::to_string(c->budget) + " bytes)");
+    }
+    if (a.base) {
+        ODC_CK(cudaDeviceSynchronize());
+        ODC_CK(cudaFree(a.base));
+        a.base = nullptr;
+        a.cap = 0;
+    }
+    cudaError_t e = cudaMalloc((void**)&a.base, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ODC_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    a.cap = want;
+    a.reset();
+    return ODC_OK;
+}
+
+extern "C" {
+
+const char* odc_status_str(odc_status s) {
+    switch (s) {
+        case ODC_OK: return "ok";
+        case ODC_ERR_INVALID_ARG: return "invalid argument";
+        case ODC_ERR_OOM: return "out of memory";
+        case ODC_ERR_CUDA: return "CUDA error";
+        case ODC_ERR_TIMEOUT: return "timeout";
+        case ODC_ERR_UNSUPPORTED: return "unsupported";
+        case ODC_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char* odc_last_error(void) { return g_err.c_str(); }
+
+odc_status odc_ctx_create(int device, size_t mem_budget, odc_ctx** out) {
+    if (!out) return fail(ODC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    ODC_CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(ODC_ERR_INVALID_ARG, "no such CUDA device");
+    ODC_CK(cudaSetDevice(device));
+    odc_ctx* c = new odc_ctx();
+    c->device = device;
+    c->budget = mem_budget;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_cnt, 64 * sizeof(uint32_t));
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+    if (e != cudaSuccess) {
+        odc_ctx_destroy(c);
+        return fail(ODC_ERR_CUDA, std::string("context setup: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return ODC_OK;
+}
+
+odc_status odc_ctx_destroy(odc_ctx* c) {
+    if (!c) return ODC_OK;
+    cudaSetDevice(c->device);
+    if (c->own) cudaStreamSynchronize(c->own);
+    mlp_destroy(c->mlp);
+    for (Arena* a : {&c->A, &c->B, &c->S})
+        if (a->base) cudaFree(a->base);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+    return ODC_OK;
+}
+
+static odc_status check_source(const odc_source* src) {
+    if (!src) return fail(ODC_ERR_INVALID_ARG, "source is NULL");
+    if (src->kind == ODC_SRC_CSG) {
+        if (!src->prims) return fail(ODC_ERR_INVALID_ARG, "CSG source without primitives");
+        if (src->n_prims < 1 || src->n_prims > kMaxPrims) return fail(ODC_ERR_INVALID_ARG, "n_prims out of [1, 4096]");
+        for (int i = 0; i < src->n_prims; ++i) {
+            const odc_csg_prim& p = src->prims[i];
+            if (p.type < 0 || p.type > 4) return fail(ODC_ERR_INVALID_ARG, "unknown primitive type");
+            if (p.op != 0 && p.op != 1) return fail(ODC_ERR_INVALID_ARG, "unknown primitive op");
+        }
+        return ODC_OK;
+    }
+    if (src->kind == ODC_SRC_MLP) return mlp_check(src->mlp, &g_err);
+    return fail(ODC_ERR_INVALID_ARG, "unknown source kind");
+}
+
+// Upload a CSG source: primitives and per-primitive culling spheres.
+static odc_status upload_csg(odc_ctx* c, const odc_source* src, cudaStream_t st, PrimDev** d_prims,
+                             float4** d_cull) {
+    int n = src->n_prims;
+    std::vector<float4> cull(n);
+    for (int i = 0; i < n; ++i) {
+        const odc_csg_prim& p = src->prims[i];
+        double r;
+        switch (p.type) {
+            case ODC_PRIM_SPHERE: r = std::fabs((double)p.params[0]); break;
+            case ODC_PRIM_AABB:
+            case ODC_PRIM_OBOX:
+                r = std::sqrt((double)p.params[0] * p.params[0] + (double)p.params[1] * p.params[1] +
+                              (double)p.params[2] * p.params[2]);
+                if (p.type == ODC_PRIM_OBOX) {   // rows of rot may not be exactly unit
+                    double s = 0;
+                    for (int k = 0; k < 9; ++k) s = std::max(s, std::fabs((double)p.rot[k]));
+                    r *= std::max(1.0, 3.0 * s);
+                }
+                break;
+            case ODC_PRIM_CYLINDER: {
+                double an = std::sqrt((double)p.rot[6] * p.rot[6] + (double)p.rot[7] * p.rot[7] + (double)p.rot[8] * p.rot[8]);
+                r = std::sqrt((double)p.params[0] * p.params[0] + (double)p.params[1] * p.params[1]) * std::max(1.0, 1.0 / std::max(an, 1e-3)) * 1.01;
+                break;
+            }
+            default: {
+                double an = std::sqrt((double)p.rot[6] * p.rot[6] + (double)p.rot[7] * p.rot[7] + (double)p.rot[8] * p.rot[8]);
+                r = (std::fabs((double)p.params[0]) + std::fabs((double)p.params[1])) * std::max(1.0, 1.0 / std::max(an, 1e-3)) * 1.01;
+            }
+        }
+        double rr = r * (1.0 + 1e-4) + 1e-6;
+        cull[i] = make_float4(p.center[0], p.center[1], p.center[2], (float)(rr * rr));
+    }
+    size_t need = al(sizeof(PrimDev) * n) + al(sizeof(float4) * n);
+    odc_status s = arena_ensure(c, c->S, need);
+    if (s != ODC_OK) return s;
+    *d_prims = (PrimDev*)c->S.take(sizeof(PrimDev) * n);
+    *d_cull = (float4*)c->S.take(sizeof(float4) * n);
+    ODC_CK(cudaMemcpyAsync(*d_prims, src->prims, sizeof(PrimDev) * n, cudaMemcpyHostToDevice, st));
+    ODC_CK(cudaMemcpyAsync(*d_cull, cull.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, st));
+    return ODC_OK;
+}
+
+static void grid_coords(const odc_grid* grid, int a, std::vector<float>& X) {
+    int n = grid->res[a];
+    X.resize(n + 1);
+    for (int i = 0; i <= n; ++i)
+        X[i] = (float)((double)grid->lo[a] + ((double)grid->hi[a] - (double)grid->lo[a]) * (double)i / (double)n);
+}
+
+odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, const odc_params* prm,
+                       void* cuda_stream, odc_mesh* out) {
+    if (!c || !grid || !prm || !out) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    odc_status s = check_source(src);
+    if (s != ODC_OK) return s;
+    for (int a = 0; a < 3; ++a) {
+        if (grid->res[a] < 1 || grid->res[a] > kMaxRes) return fail(ODC_ERR_INVALID_ARG, "res out of [1, 1024]");
+        if (!(grid->lo[a] < grid->hi[a])) return fail(ODC_ERR_INVALID_ARG, "lo must be < hi");
+    }
+    if (prm->steps_1d < 1 || prm->steps_1d > 20) return fail(ODC_ERR_INVALID_ARG, "steps_1d out of [1, 20]");
+    if (prm->s2d_lin1 < 1 || prm->s2d_lin2 < 1 || prm->s2d_bin1 < 0 || prm->s2d_bin2 < 0 || prm->s2d_lin1 > 64 ||
+        prm->s2d_lin2 > 64 || prm->s2d_bin1 > 20 || prm->s2d_bin2 > 20 || !(prm->s2d_range1 > 0) ||
+        !(prm->s2d_range2 > 0))
+        return fail(ODC_ERR_INVALID_ARG, "2D search parameters out of range");
+    if (!(prm->iso > 0.0f && prm->iso < 1.0f)) return fail(ODC_ERR_INVALID_ARG, "iso must be in (0, 1)");
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    std::memset(out, 0, sizeof(*out));
+
+    // ---- source upload
+    PrimDev* d_prims = nullptr;
+    float4* d_cull = nullptr;
+    if (src->kind == ODC_SRC_CSG) {
+        s = upload_csg(c, src, st, &d_prims, &d_cull);
+        if (s != ODC_OK) return s;
+    } else {
+        s = mlp_prepare(&c->mlp, src->mlp, st, &g_err);
+        if (s != ODC_OK) return s;
+    }
+
+    // ---- grid-sized buffers
+    GridDev g{};
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = grid->res[a];
+        g.nv[a] = grid->res[a] + 1;
+    }
+    g.W = (g.nv[0] + 31) / 32;
+    size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
+    std::vector<float> Xh[3];
+    for (int a = 0; a < 3; ++a) grid_coords(grid, a, Xh[a]);
+    size_t nX = Xh[0].size() + Xh[1].size() + Xh[2].size();
+    size_t stmp = scan_tmp_elems(nw);
+    size_t needA = al(nX * 4) + al(nw * 4) + al(nw * sizeof(WordInfo)) + 6 * al(nw * 4) + al(3 * nw * 4) +
+                   al(stmp * 8) + al(64 * 8);
+    s = arena_ensure(c, c->A, needA);
+    if (s != ODC_OK) return s;
+    float* dX = (float*)c->A.take(nX * 4);
+    uint32_t* bits = (uint32_t*)c->A.take(nw * 4);
+    WordInfo* wi = (WordInfo*)c->A.take(nw * sizeof(WordInfo));
+    uint32_t* ce = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* cf = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* cc = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* ebase = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* fbase = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* cbase = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* flips = (uint32_t*)c->A.take(3 * nw * 4);
+    void* tmp = c->A.take(stmp * 8);
+    uint32_t* dcnt = (uint32_t*)c->A.take(64 * 8);
+    g.X[0] = dX;
+    g.X[1] = dX + Xh[0].size();
+    g.X[2] = dX + Xh[0].size() + Xh[1].size();
+    for (int a = 0; a < 3; ++a)
+        ODC_CK(cudaMemcpyAsync((void*)g.X[a], Xh[a].data(), Xh[a].size() * 4, cudaMemcpyHostToDevice, st));
+    ODC_CK(cudaMemsetAsync(flips, 0, 3 * nw * 4, st));
+    ODC_CK(cudaMemsetAsync(dcnt, 0, 64 * 8, st));
+
+    SearchParams sp{prm->steps_1d, prm->s2d_lin1, prm->s2d_bin1, prm->s2d_range1,
+                    prm->s2d_lin2, prm->s2d_bin2, prm->s2d_range2, prm->ic_split};
+    int64_t nq = 0, nrq = 0;
+
+    ODC_CK(cudaEventRecord(c->ev[0], st));
+    // ---- a1: grid occupancy
+    if (src->kind == ODC_SRC_CSG) {
+        launch_csg_grid(g, d_prims, d_cull, src->n_prims, bits, st);
+    } else {
+        s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &nrq, &g_err);
+        if (s != ODC_OK) return s;
+    }
+    nq += (int64_t)g.nv[0] * g.nv[1] * g.nv[2];
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaEventRecord(c->ev[1], st));
+    // ---- a2: compaction
+    launch_classify(g, bits, wi, ce, cf, cc, st);
+    exclusive_scan<uint32_t>(ce, ebase, nw, (uint32_t*)tmp, dcnt + 0, st);
+    exclusive_scan<uint32_t>(cf, fbase, nw, (uint32_t*)tmp, dcnt + 1, st);
+    exclusive_scan<uint32_t>(cc, cbase, nw, (uint32_t*)tmp, dcnt + 2, st);
+    ODC_CK(cudaMemcpyAsync(c->h_cnt, dcnt, 3 * 4, cudaMemcpyDeviceToHost, st));
+    ODC_CK(cudaStreamSynchronize(st));
+    ODC_CK(cudaGetLastError());
+    uint32_t E = c->h_cnt[0], F = c->h_cnt[1], C = c->h_cnt[2];
+
+    // ---- count-sized buffers
+    size_t stmpB = scan_tmp_elems(std::max<size_t>(std::max(E, C), 1));
+    size_t needB = 2 * al(E * 4ull) + al(F * 4ull) + 3 * al(F) + al(F * 8ull) + al(C * 4ull) + al(C) + al(C * 8ull) +
+                   2 * al(C * 4ull) + al(4ull * C * 12) + al((4ull * C + E) * 12) + al(E) + al(E * 16ull) +
+                   2 * al(E * 8ull) + al(4ull * E * 12) + al(stmpB * 8) + 1024;
+    s = arena_ensure(c, c->B, needB);
+    if (s != ODC_OK) return s;
+    uint32_t* edges = (uint32_t*)c->B.take(E * 4ull);
+    uint32_t* T = (uint32_t*)c->B.take(E * 4ull);
+    uint32_t* faces = (uint32_t*)c->B.take(F * 4ull);
+    uint8_t* slots = (uint8_t*)c->B.take(F);
+    uint8_t* fflags = (uint8_t*)c->B.take(F);
+    uint8_t* mark = (uint8_t*)c->B.take(F);
+    float2* pf = (float2*)c->B.take(F * 8ull);
+    uint32_t* cells = (uint32_t*)c->B.take(C * 4ull);
+    uint8_t* configs = (uint8_t*)c->B.take(C);
+    unsigned long long* cycles = (unsigned long long*)c->B.take(C * 8ull);
+    uint32_t* ncyc = (uint32_t*)c->B.take(C * 4ull);
+    uint32_t* vbase = (uint32_t*)c->B.take(C * 4ull);
+    float3* vlocal = (float3*)c->B.take(4ull * C * 12);
+    float3* vworld = (float3*)c->B.take((4ull * C + E) * 12);
+    uint8_t* qcase = (uint8_t*)c->B.take(E);
+    int4* qv = (int4*)c->B.take(E * 16ull);
+    unsigned long long* qcnt = (unsigned long long*)c->B.take(E * 8ull);
+    unsigned long long* qoff = (unsigned long long*)c->B.take(E * 8ull);
+    int3* tris = (int3*)c->B.take(4ull * E * 12);
+    void* tmpB = c->B.take(stmpB * 8);
+
+    launch_emit(g, bits, wi, ebase, fbase, cbase, edges, faces, slots, cells, configs, st);
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaEventRecord(c->ev[2], st));
+
+    // ---- a3: manifold fix rounds, cycles, 3D point ids
+    int rounds = 0;
+    uint32_t nflip = 0;
+    for (;;) {
+        ODC_CK(cudaMemsetAsync(dcnt + 8, 0, 4, st));
+        launch_manifold_mark(g, bits, flips, faces, slots, F, mark, dcnt + 8, st);
+        ODC_CK(cudaMemcpyAsync(c->h_cnt + 8, dcnt + 8, 4, cudaMemcpyDeviceToHost, st));
+        ODC_CK(cudaStreamSynchronize(st));
+        uint32_t marked = c->h_cnt[8];
+        if (!marked) break;
+        launch_manifold_apply(g, flips, faces, mark, F, st);
+        nflip += marked;   // faces flipped (each flip round toggles distinct faces)
+        if (++rounds > 64) return fail(ODC_ERR_INTERNAL, "manifold fix did not converge");
+    }
+    launch_cells(g, flips, cells, configs, C, cycles, ncyc, st);
+    exclusive_scan<uint32_t>(ncyc, vbase, C, (uint32_t*)tmpB, dcnt + 3, st);
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaEventRecord(c->ev[3], st));
+
+    // ---- a4: 1D search
+    if (src->kind == ODC_SRC_CSG) {
+        launch_bisect_csg(g, bits, edges, E, prm->steps_1d, d_prims, d_cull, src->n_prims, T, st);
+        nq += (int64_t)E * prm->steps_1d;
+    } else {
+        s = mlp_bisect(c->mlp, g, bits, edges, E, prm->steps_1d, prm->iso, T, st, &nq, &nrq, &g_err);
+        if (s != ODC_OK) return s;
+    }
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaEventRecord(c->ev[4], st));
+
+    // ---- a5: 2D search
+    if (src->kind == ODC_SRC_CSG) {
+        launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, src->n_prims, pf, fflags,
+                        st);
+    } else {
+        s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, st, &nq, &nrq,
+                      &g_err);
+        if (s != ODC_OK) return s;
+    }
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaEventRecord(c->ev[5], st));
+
+    // ---- a6, a7: normals and QEF
+    launch_qef(g, flips, wi, ebase, fbase, T, pf, cells, configs, cycles, vbase, C, prm->steps_1d, vlocal, vworld, st);
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaEventRecord(c->ev[6], st));
+
+    // ---- a8: quads with IC split
+    launch_quad_case(g, bits, wi, cbase, edges, E, cycles, vbase, vlocal, prm->ic_split, qcase, qv, qcnt, st);
+    exclusive_scan<unsigned long long>(qcnt, qoff, E, (unsigned long long*)tmpB, (unsigned long long*)(dcnt + 16), st);
+    launch_quad_emit(g, edges, T, E, prm->steps_1d, qcase, qv, qoff, dcnt + 3, vworld, tris, st);
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaEventRecord(c->ev[7], st));
+    ODC_CK(cudaMemcpyAsync(c->h_cnt + 16, dcnt, 24 * 4, cudaMemcpyDeviceToHost, st));
+    ODC_CK(cudaStreamSynchronize(st));
+    uint32_t V3 = c->h_cnt[16 + 3];
+    unsigned long long qt = ((unsigned long long)c->h_cnt[16 + 17] << 32) | c->h_cnt[16 + 16];
+    uint32_t NT = (uint32_t)(qt >> 32), N3 = (uint32_t)(qt & 0xffffffffu);
+
+    c->g = g;
+    c->k = prm->steps_1d;
+    c->E = E; c->F = F; c->C = C; c->V3 = V3; c->NT = NT; c->N3 = N3; c->nflip = nflip;
+    c->bits = bits; c->flips = flips; c->edges = edges; c->T = T; c->faces = faces; c->cells = cells;
+    c->slots = slots; c->fflags = fflags; c->configs = configs; c->qcase = qcase; c->pf = pf; c->cycles = cycles;
+    c->vlocal = vlocal; c->vworld = vworld; c->tris = tris; c->nw = nw;
+
+    out->n_verts = (int64_t)V3 + N3;
+    out->n_tris = NT;
+    out->d_verts = (const float*)vworld;
+    out->d_tris = (const int32_t*)tris;
+    odc_stats& S = out->stats;
+    S.n_edges = E; S.n_face_segs = F; S.n_cells = C; S.n_verts3 = V3; S.n_case3 = N3;
+    S.n_flips = nflip; S.fix_rounds = rounds; S.n_queries = nq; S.n_requeries = nrq;
+    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&S.stage_ms[i], c->ev[i], c->ev[i + 1]);
+    cudaEventElapsedTime(&S.stage_ms[7], c->ev[0], c->ev[7]);
+    return ODC_OK;
+}
+
+odc_status odc_mesh_copy(odc_ctx* c, const odc_mesh* m, float* verts, int32_t* tris, int dst_on_device) {
+    if (!c || !m) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    ODC_CK(cudaSetDevice(c->device));
+    cudaMemcpyKind k = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (verts && m->n_verts) ODC_CK(cudaMemcpyAsync(verts, m->d_verts, m->n_verts * 12, k, c->own));
+    if (tris && m->n_tris) ODC_CK(cudaMemcpyAsync(tris, m->d_tris, m->n_tris * 12, k, c->own));
+    ODC_CK(cudaStreamSynchronize(c->own));
+    return ODC_OK;
+}
+
+odc_status odc_mesh_release(odc_ctx* c, odc_mesh* m) {
+    if (!c || !m) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    m->d_verts = nullptr;
+    m->d_tris = nullptr;
+    m->n_verts = m->n_tris = 0;
+    return ODC_OK;
+}
+
+odc_status odc_debug_copy(odc_ctx* c, int what, void* dst, size_t max_bytes, int64_t* count, int32_t* elem_bytes) {
+    if (!c || !count || !elem_bytes) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    const void* p = nullptr;
+    int64_t n = 0;
+    int eb = 0;
+    std::vector<uint32_t> flipped;
+    switch (what) {
+        case ODC_DBG_LABELS: p = c->bits; n = (int64_t)c->nw; eb = 4; break;
+        case ODC_DBG_EDGES: p = c->edges; n = c->E; eb = 4; break;
+        case ODC_DBG_T: p = c->T; n = c->E; eb = 4; break;
+        case ODC_DBG_FACES: p = c->faces; n = c->F; eb = 4; break;
+        case ODC_DBG_SLOTS: p = c->slots; n = c->F; eb = 1; break;
+        case ODC_DBG_FACE_PTS: p = c->pf; n = c->F; eb = 8; break;
+        case ODC_DBG_FACE_FLAGS: p = c->fflags; n = c->F; eb = 1; break;
+        case ODC_DBG_CELLS: p = c->cells; n = c->C; eb = 4; break;
+        case ODC_DBG_CONFIGS: p = c->configs; n = c->C; eb = 1; break;
+        case ODC_DBG_CYCLES: p = c->cycles; n = c->C; eb = 8; break;
+        case ODC_DBG_VLOCAL: p = c->vlocal; n = c->V3; eb = 12; break;
+        case ODC_DBG_QCASE: p = c->qcase; n = c->E; eb = 1; break;
+        case ODC_DBG_FLIPS: {
+            // expand the flip bit planes into sorted face ids
+            std::vector<uint32_t> h(3 * c->nw);
+            if (c->nw) {
+                ODC_CK(cudaSetDevice(c->device));
+                ODC_CK(cudaMemcpy(h.data(), c->flips, h.size() * 4, cudaMemcpyDeviceToHost));
+            }
+            const GridDev& g = c->g;
+            for (int z = 0; z < g.nv[2]; ++z)
+                for (int y = 0; y < g.nv[1]; ++y)
+                    for (int w = 0; w < g.W; ++w)
+                        for (int a = 0; a < 3; ++a) {
+                            uint32_t bitsw = h[(((size_t)a * g.nv[2] + z) * g.nv[1] + y) * g.W + w];
+                            while (bitsw) {
+                                int l = __builtin_ctz(bitsw);
+                                bitsw &= bitsw - 1;
+                                uint32_t v = (uint32_t)(w * 32 + l) + (uint32_t)g.nv[0] * ((uint32_t)y + (uint32_t)g.nv[1] * z);
+                                flipped.push_back(3u * v + a);
+                            }
+                        }
+            std::sort(flipped.begin(), flipped.end());
+            *count = (int64_t)flipped.size();
+            *elem_bytes = 4;
+            if (dst) std::memcpy(dst, flipped.data(), std::min(max_bytes, flipped.size() * 4));
+            return ODC_OK;
+        }
+        default: return fail(ODC_ERR_INVALID_ARG, "unknown debug buffer");
+    }
+    *count = n;
+    *elem_bytes = eb;
+    if (dst && p && n) {
+        ODC_CK(cudaSetDevice(c->device));
+        ODC_CK(cudaMemcpy(dst, p, std::min(max_bytes, (size_t)n * eb), cudaMemcpyDeviceToHost));
+    }
+    return ODC_OK;
+}
+
+odc_status odc_eval_points(odc_ctx* c, const odc_source* src, const float* points, int64_t n, float iso,
+                           int precision, uint8_t* labels, float* logits) {
+    if (!c || !points || !labels || n < 0) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    odc_status s = check_source(src);
+    if (s != ODC_OK) return s;
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = c->own;
+    if (n == 0) return ODC_OK;
+    size_t need = al(n * 12) + al(n) + al(n * 4);
+    PrimDev* d_prims = nullptr;
+    float4* d_cull = nullptr;
+    if (src->kind == ODC_SRC_CSG) {
+        s = upload_csg(c, src, st, &d_prims, &d_cull);
+    } else {
+        s = mlp_prepare(&c->mlp, src->mlp, st, &g_err);
+    }
+    if (s != ODC_OK) return s;
+    s = arena_ensure(c, c->B, need);
+    if (s != ODC_OK) return s;
+    float3* dp = (float3*)c->B.take(n * 12);
+    uint8_t* dl = (uint8_t*)c->B.take(n);
+    float* dz = (float*)c->B.take(n * 4);
+    c->E = c->F = c->C = c->V3 = 0;   // the B arena no longer holds an extract
+    ODC_CK(cudaMemcpyAsync(dp, points, n * 12, cudaMemcpyHostToDevice, st));
+    if (src->kind == ODC_SRC_CSG) {
+        launch_csg_points(d_prims, d_cull, src->n_prims, dp, n, dl, st);
+    } else {
+        s = mlp_points(c->mlp, dp, n, iso, precision, dl, dz, st, &g_err);
+        if (s != ODC_OK) return s;
+    }
+    ODC_CK(cudaGetLastError());
+    ODC_CK(cudaMemcpyAsync(labels, dl, n, cudaMemcpyDeviceToHost, st));
+    if (logits && src->kind == ODC_SRC_MLP) ODC_CK(cudaMemcpyAsync(logits, dz, n * 4, cudaMemcpyDeviceToHost, st));
+    ODC_CK(cudaStreamSynchronize(st));
+    return ODC_OK;
+}
+
+}  // extern "C"

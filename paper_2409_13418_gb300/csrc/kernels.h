@@ -1,0 +1,55 @@
+// kernels.h -- host launchers of the ODC kernels (one translation unit each).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "odc_internal.h"
+
+namespace odc {
+
+// compact.cu
+size_t scan_tmp_elems(size_t n);
+template <typename T>
+void exclusive_scan(const T* in, T* out, size_t n, T* tmp, T* total, cudaStream_t st);
+void launch_csg_grid(const GridDev& g, const PrimDev* prims, const float4* cull, int n_prims, uint32_t* bits,
+                     cudaStream_t st);
+void launch_classify(const GridDev& g, const uint32_t* bits, WordInfo* wi, uint32_t* ce, uint32_t* cf, uint32_t* cc,
+                     cudaStream_t st);
+void launch_emit(const GridDev& g, const uint32_t* bits, const WordInfo* wi, const uint32_t* ebase,
+                 const uint32_t* fbase, const uint32_t* cbase, uint32_t* edges, uint32_t* faces, uint8_t* slots,
+                 uint32_t* cells, uint8_t* configs, cudaStream_t st);
+
+// topo.cu
+void launch_manifold_mark(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const uint32_t* faces,
+                          const uint8_t* slots, uint32_t nf, uint8_t* mark, uint32_t* counter, cudaStream_t st);
+void launch_manifold_apply(const GridDev& g, uint32_t* flips, const uint32_t* faces, const uint8_t* mark, uint32_t nf,
+                           cudaStream_t st);
+void launch_cells(const GridDev& g, const uint32_t* flips, const uint32_t* cells, const uint8_t* configs, uint32_t nc,
+                  unsigned long long* cyc, uint32_t* ncyc, cudaStream_t st);
+
+// search_csg.cu
+void launch_bisect_csg(const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
+                       const PrimDev* prims, const float4* cull, int n_prims, uint32_t* T, cudaStream_t st);
+void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
+                     const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
+                     uint32_t nf, const SearchParams& sp, const PrimDev* prims, const float4* cull, int n_prims,
+                     float2* pf, uint8_t* flags, cudaStream_t st);
+void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, const float3* pts, int64_t n,
+                       uint8_t* labels, cudaStream_t st);
+
+// qef.cu
+void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, const uint32_t* ebase,
+                const uint32_t* fbase, const uint32_t* T, const float2* pf, const uint32_t* cells,
+                const uint8_t* configs, const unsigned long long* cycles, const uint32_t* vbase, uint32_t nc, int k,
+                float3* vlocal, float3* vworld, cudaStream_t st);
+
+// quads.cu
+void launch_quad_case(const GridDev& g, const uint32_t* bits, const WordInfo* wi, const uint32_t* cbase,
+                      const uint32_t* edges, uint32_t ne, const unsigned long long* cycles, const uint32_t* vbase,
+                      const float3* vlocal, int ic_split, uint8_t* qcase, int4* qv, unsigned long long* cnt,
+                      cudaStream_t st);
+void launch_quad_emit(const GridDev& g, const uint32_t* edges, const uint32_t* T, uint32_t ne, int k,
+                      const uint8_t* qcase, const int4* qv, const unsigned long long* off, const uint32_t* v3tot,
+                      float3* vworld, int3* tris, cudaStream_t st);
+
+}  // namespace odc

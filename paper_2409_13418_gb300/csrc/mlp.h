@@ -1,0 +1,34 @@
+// mlp.h -- MLP occupancy (envelope MLP over Fourier features) on the device.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/odc.h"
+#include "odc_internal.h"
+
+namespace odc {
+
+struct MlpState;
+
+odc_status mlp_check(const odc_mlp* m, std::string* err);
+odc_status mlp_prepare(MlpState** st, const odc_mlp* m, cudaStream_t s, std::string* err);
+void mlp_destroy(MlpState* st);
+
+// Grid labels (a1): bit rows as in the CSG path.
+odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, cudaStream_t s, int64_t* nq,
+                    int64_t* nrq, std::string* err);
+// 1D search (a4) in k wavefronts over all crossing edges.
+odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
+                      float iso, uint32_t* T, cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err);
+// 2D search (a5) in wavefronts over all face segments.
+odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
+                     const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
+                     uint32_t nf, const SearchParams& sp, float iso, float2* pf, uint8_t* flags, cudaStream_t s,
+                     int64_t* nq, int64_t* nrq, std::string* err);
+// Labels (and logits) at explicit points.
+odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
+                      float* logits, cudaStream_t s, std::string* err);
+
+}  // namespace odc

@@ -1,0 +1,158 @@
+// search_csg.cu -- 1D and 2D point searches against a CSG occupancy, one
+// thread per crossing edge / face segment running its whole search in
+// registers (CSG queries cost tens of FMAs, so no batching is needed).
+//
+// 1D (Sec. 5.1): k bisections of the edge keeping ends of opposite labels;
+// the result is the midpoint of the final interval, stored as the odd integer
+// T of T / 2^(k+1).
+// 2D (Sec. 5.2, A.1.3, A.1.4): step 1 line-binary search from m along the
+// perpendicular towards the opposite label; if it never leaves m, p_f = m;
+// step 2 two line-binary searches from q parallel to l; step 3 intersects
+// (p_e1, q1) and (p_e2, q2).
+#include "kernels.h"
+#include "search.cuh"
+
+namespace odc {
+
+struct CsgOcc {
+    const PrimDev* prims;
+    const float4* cull;
+    int n;
+    __device__ __forceinline__ uint32_t operator()(float3 p) const { return csg_label(prims, cull, n, p.x, p.y, p.z); }
+};
+
+__global__ void k_bisect_csg(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ edges,
+                             uint32_t ne, int k, CsgOcc occ, uint32_t* __restrict__ T) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    uint32_t e = edges[i];
+    int p[3];
+    vid_xyz(g, e / 3u, &p[0], &p[1], &p[2]);
+    int a = (int)(e % 3u);
+    uint32_t lab0 = label_at(g, bits, p[0], p[1], p[2]);
+    float w[3] = {g.X[0][p[0]], g.X[1][p[1]], g.X[2][p[2]]};
+    uint32_t lo = 0;   // numerator of the low end over 2^s
+    for (int s = 0; s < k; ++s) {
+        uint32_t mid = 2u * lo + 1u;   // over 2^(s+1)
+        float u = (float)mid * __int_as_float((127 - (s + 1)) << 23);
+        w[a] = axis_world_ff(g.X[a], p[a], ff_make(u)).hi;
+        uint32_t lab = occ(make_float3(w[0], w[1], w[2]));
+        lo = (lab == lab0) ? mid : 2u * lo;
+    }
+    T[i] = 2u * lo + 1u;
+}
+
+// Line-binary search (A.1.3) from p along unit d: returns J of the near end.
+template <class Occ>
+__device__ __forceinline__ uint32_t lbs(const GridDev& g, const FaceSeg& F, const Occ& occ, ff2 p, ff2 d, float R,
+                                        int n, int b, uint32_t lab0) {
+    int first = n;
+    for (int i = 1; i <= n; ++i) {
+        ff s = lbs_param(R, (uint32_t)i << b, n, b);
+        if (occ(face_world2(g, F, ray_point(p, d, s))) != lab0) {
+            first = i;
+            break;
+        }
+    }
+    uint32_t Ja = (uint32_t)(first - 1) << b, Jc = (uint32_t)first << b;
+    for (int t = 0; t < b; ++t) {
+        uint32_t Jm = (Ja + Jc) >> 1;
+        ff s = lbs_param(R, Jm, n, b);
+        if (occ(face_world2(g, F, ray_point(p, d, s))) == lab0) Ja = Jm;
+        else Jc = Jm;
+    }
+    return Ja;
+}
+
+__device__ __forceinline__ void load_face(const GridDev& g, const uint32_t* bits, const uint32_t* flips,
+                                          const WordInfo* wi, const uint32_t* ebase, const uint32_t* T, int k,
+                                          uint32_t fid, int slot, FaceSeg& F) {
+    int x, y, z;
+    vid_xyz(g, fid / 3u, &x, &y, &z);
+    int a = (int)(fid % 3u);
+    int b = nxt3(a), c = prv3(a);
+    int lab4 = 0;
+    for (int i = 0; i < 4; ++i) {
+        int p[3] = {x, y, z};
+        if (i == 1 || i == 2) p[b] += 1;
+        if (i >= 2) p[c] += 1;
+        lab4 |= (int)label_at(g, bits, p[0], p[1], p[2]) << i;
+    }
+    int seg[2][2];
+    face_segments(lab4, flip_at(g, flips, a, x, y, z), seg);
+    int fe1 = seg[slot][0], fe2 = seg[slot][1];
+    F.a = a;
+    F.b = b;
+    F.c = c;
+    F.q[0] = x;
+    F.q[1] = y;
+    F.q[2] = z;
+    int ex, ey, ez, ea;
+    face_edge_global(F, fe1, &ex, &ey, &ez, &ea);
+    uint32_t T1 = T[edge_rank(g, wi, ebase, ex, ey, ez, ea)];
+    face_edge_global(F, fe2, &ex, &ey, &ez, &ea);
+    uint32_t T2 = T[edge_rank(g, wi, ebase, ex, ey, ez, ea)];
+    face_setup(F, a, x, y, z, lab4, fe1, fe2, T1, T2, k);
+}
+
+__global__ void k_face_csg(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ flips,
+                           const WordInfo* __restrict__ wi, const uint32_t* __restrict__ ebase,
+                           const uint32_t* __restrict__ T, const uint32_t* __restrict__ faces,
+                           const uint8_t* __restrict__ slots, uint32_t nf, SearchParams sp, CsgOcc occ,
+                           float2* __restrict__ pf, uint8_t* __restrict__ flags) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    FaceSeg F;
+    load_face(g, bits, flips, wi, ebase, T, sp.steps_1d, faces[i], slots[i], F);
+    uint32_t lab_m = occ(face_world2(g, F, F.m));
+    ff2 d = lab_m ? ff2{ff_neg(F.d.u), ff_neg(F.d.v)} : F.d;
+    int fl = 0;
+    uint32_t Jq = lbs(g, F, occ, F.m, d, sp.range1, sp.lin1, sp.bin1, lab_m);
+    float2 out;
+    if (Jq == 0) {
+        fl |= 1;
+        out = make_float2(F.m.u.hi, F.m.v.hi);
+    } else {
+        ff2 q = ray_point(F.m, d, lbs_param(sp.range1, Jq, sp.lin1, sp.bin1));
+        ff2 nu1 = {ff_neg(F.u1.u), ff_neg(F.u1.v)};
+        uint32_t J1 = lbs(g, F, occ, q, F.u1, sp.range2, sp.lin2, sp.bin2, lab_m);
+        uint32_t J2 = lbs(g, F, occ, q, nu1, sp.range2, sp.lin2, sp.bin2, lab_m);
+        ff2 q1 = ray_point(q, F.u1, lbs_param(sp.range2, J1, sp.lin2, sp.bin2));
+        ff2 q2 = ray_point(q, nu1, lbs_param(sp.range2, J2, sp.lin2, sp.bin2));
+        out = face_intersect(F, q1, q2, &fl);
+    }
+    pf[i] = out;
+    flags[i] = (uint8_t)fl;
+}
+
+__global__ void k_csg_points(CsgOcc occ, const float3* __restrict__ pts, int64_t n, uint8_t* __restrict__ labels) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    labels[i] = (uint8_t)occ(pts[i]);
+}
+
+void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, const float3* pts, int64_t n,
+                       uint8_t* labels, cudaStream_t st) {
+    if (n <= 0) return;
+    CsgOcc occ{prims, cull, n_prims};
+    k_csg_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(occ, pts, n, labels);
+}
+
+void launch_bisect_csg(const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
+                       const PrimDev* prims, const float4* cull, int n_prims, uint32_t* T, cudaStream_t st) {
+    if (!ne) return;
+    CsgOcc occ{prims, cull, n_prims};
+    k_bisect_csg<<<(ne + 127) / 128, 128, 0, st>>>(g, bits, edges, ne, k, occ, T);
+}
+
+void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
+                     const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
+                     uint32_t nf, const SearchParams& sp, const PrimDev* prims, const float4* cull, int n_prims,
+                     float2* pf, uint8_t* flags, cudaStream_t st) {
+    if (!nf) return;
+    CsgOcc occ{prims, cull, n_prims};
+    k_face_csg<<<(nf + 127) / 128, 128, 0, st>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp, occ, pf,
+                                                  flags);
+}
+
+}  // namespace odc

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of the ODC C ABI (include/odc.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+The library is loaded from this package directory; if it is missing this
+module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libodc.so")
+
+ODC_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
+          5: "unsupported", 6: "internal error"}
+SRC_CSG, SRC_MLP = 0, 1
+PREC_FP32, PREC_BF16 = 0, 1
+DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
+           cycles=9, vlocal=10, qcase=11, flips=12)
+_DBG_DTYPE = dict(labels=np.uint32, edges=np.uint32, T=np.uint32, faces=np.uint32, slots=np.uint8,
+                  face_pts=np.float32, face_flags=np.uint8, cells=np.uint32, configs=np.uint8,
+                  cycles=np.uint64, vlocal=np.float32, qcase=np.uint8, flips=np.uint32)
+_DBG_SHAPE = dict(face_pts=2, vlocal=3)
+
+
+class Prim(C.Structure):
+    _fields_ = [("type", C.c_int32), ("op", C.c_int32), ("center", C.c_float * 3), ("rot", C.c_float * 9),
+                ("params", C.c_float * 4), ("pad", C.c_float * 2)]
+
+
+class Mlp(C.Structure):
+    _fields_ = [("n_freq", C.c_int32), ("hidden", C.c_int32), ("n_hidden", C.c_int32), ("latent_dim", C.c_int32),
+                ("B", C.c_void_p), ("W", C.c_void_p * 8), ("b", C.c_void_p * 8), ("latent", C.c_void_p),
+                ("env_scale", C.c_float), ("env_radius", C.c_float), ("env_amp", C.c_float),
+                ("precision", C.c_int32), ("band", C.c_float), ("pad", C.c_int32)]
+
+
+class Source(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_prims", C.c_int32), ("prims", C.c_void_p), ("mlp", C.c_void_p)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("res", C.c_int32 * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("iso", C.c_float), ("steps_1d", C.c_int32), ("s2d_lin1", C.c_int32), ("s2d_bin1", C.c_int32),
+                ("s2d_range1", C.c_float), ("s2d_lin2", C.c_int32), ("s2d_bin2", C.c_int32),
+                ("s2d_range2", C.c_float), ("ic_split", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_edges", C.c_int64), ("n_face_segs", C.c_int64), ("n_cells", C.c_int64),
+                ("n_verts3", C.c_int64), ("n_case3", C.c_int64), ("n_flips", C.c_int64),
+                ("fix_rounds", C.c_int64), ("n_queries", C.c_int64), ("n_requeries", C.c_int64),
+                ("stage_ms", C.c_float * 8)]
+
+
+class MeshC(C.Structure):
+    _fields_ = [("n_verts", C.c_int64), ("n_tris", C.c_int64), ("d_verts", C.c_void_p), ("d_tris", C.c_void_p),
+                ("stats", Stats)]
+
+
+EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
+           "odc_debug_copy", "odc_eval_points", "odc_status_str", "odc_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libodc.so (build it first with ``paper_2409_13418_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (there is no fallback)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.odc_ctx_create.argtypes = [C.c_int, C.c_size_t, C.POINTER(P)]
+    lib.odc_ctx_destroy.argtypes = [P]
+    lib.odc_extract.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), P, C.POINTER(MeshC)]
+    lib.odc_mesh_copy.argtypes = [P, C.POINTER(MeshC), P, P, C.c_int]
+    lib.odc_mesh_release.argtypes = [P, C.POINTER(MeshC)]
+    lib.odc_debug_copy.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+    lib.odc_eval_points.argtypes = [P, C.POINTER(Source), P, C.c_int64, C.c_float, C.c_int, P, P]
+    lib.odc_status_str.restype = C.c_char_p
+    lib.odc_status_str.argtypes = [C.c_int]
+    lib.odc_last_error.restype = C.c_char_p
+    for f in ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
+              "odc_debug_copy", "odc_eval_points"]:
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class OdcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status):
+    if status != ODC_OK:
+        raise OdcError(status, _lib.odc_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class _SourceHolder:
+    """Keeps the numpy buffers behind a Source structure alive."""
+
+    def __init__(self, src, precision=None, band=None):
+        self.keep = []
+        self.src = Source()
+        if isinstance(src, I.CSGSource):
+            rec = np.zeros(src.n_prims, dtype=np.dtype([("type", "<i4"), ("op", "<i4"), ("center", "<f4", 3),
+                                                         ("rot", "<f4", 9), ("params", "<f4", 4),
+                                                         ("pad", "<f4", 2)]))
+            rec["type"] = src.types
+            rec["op"] = src.ops
+            rec["center"] = src.centers
+            rec["rot"] = src.rot.reshape(-1, 9)
+            rec["params"] = src.params
+            self.keep.append(rec)
+            self.src.kind = SRC_CSG
+            self.src.n_prims = src.n_prims
+            self.src.prims = _ptr(rec)
+        elif isinstance(src, I.MLPSource):
+            m = Mlp()
+            m.n_freq = src.n_freq
+            m.hidden = src.hidden
+            m.n_hidden = len(src.weights) - 1
+            m.latent_dim = 0 if src.latent is None else int(src.latent.shape[0])
+            B = np.ascontiguousarray(src.B, np.float32)
+            self.keep.append(B)
+            m.B = _ptr(B)
+            for i, (W, b) in enumerate(zip(src.weights, src.biases)):
+                W = np.ascontiguousarray(W, np.float32)
+                b = np.ascontiguousarray(b, np.float32)
+                self.keep += [W, b]
+                m.W[i] = _ptr(W)
+                m.b[i] = _ptr(b)
+            if src.latent is not None:
+                lat = np.ascontiguousarray(src.latent, np.float32)
+                self.keep.append(lat)
+                m.latent = _ptr(lat)
+            m.env_scale, m.env_radius, m.env_amp = src.env_scale, src.env_radius, src.env_amp
+            m.precision = PREC_FP32 if precision is None else precision
+            m.band = 1e-3 if band is None else band
+            self.keep.append(m)
+            self.src.kind = SRC_MLP
+            self.src.mlp = C.addressof(m)
+        else:
+            raise TypeError(type(src))
+
+
+def make_grid(grid: I.Grid) -> Grid:
+    g = Grid()
+    for a in range(3):
+        g.lo[a], g.hi[a], g.res[a] = grid.lo[a], grid.hi[a], int(grid.res[a])
+    return g
+
+
+def make_params(steps_1d=15, iso=0.5, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12,
+                range2=float(np.float32(np.sqrt(2.0) / 2.0)), ic_split=True) -> Params:
+    p = Params()
+    p.iso, p.steps_1d = iso, steps_1d
+    p.s2d_lin1, p.s2d_bin1, p.s2d_range1 = lin1, bin1, range1
+    p.s2d_lin2, p.s2d_bin2, p.s2d_range2 = lin2, bin2, range2
+    p.ic_split = int(bool(ic_split))
+    return p
+
+
+class Mesh:
+    def __init__(self, ctx, c: MeshC):
+        self.ctx = ctx
+        self.c = c
+        self.n_verts = int(c.n_verts)
+        self.n_tris = int(c.n_tris)
+        s = c.stats
+        self.stats = {f: getattr(s, f) for f, _ in Stats._fields_ if f != "stage_ms"}
+        self.stats["stage_ms"] = list(s.stage_ms)
+
+    def to_host(self):
+        v = np.empty((self.n_verts, 3), np.float32)
+        t = np.empty((self.n_tris, 3), np.int32)
+        _check(_lib.odc_mesh_copy(self.ctx.h, C.byref(self.c), _ptr(v), _ptr(t), 0))
+        return v, t
+
+    def copy_to(self, verts_ptr: int, tris_ptr: int, on_device: bool):
+        _check(_lib.odc_mesh_copy(self.ctx.h, C.byref(self.c), verts_ptr, tris_ptr, int(on_device)))
+
+
+class Context:
+    """An ODC context on one CUDA device (``odc_ctx``)."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0):
+        load()
+        h = C.c_void_p()
+        _check(_lib.odc_ctx_create(device, mem_budget, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.odc_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, **kw) -> Mesh:
+        holder = _SourceHolder(src, precision, band)
+        g = make_grid(grid)
+        p = make_params(steps_1d=steps_1d, **kw)
+        m = MeshC()
+        _check(_lib.odc_extract(self.h, C.byref(holder.src), C.byref(g), C.byref(p),
+                                stream if stream else None, C.byref(m)))
+        return Mesh(self, m)
+
+    def debug(self, what: str) -> np.ndarray:
+        n = C.c_int64()
+        eb = C.c_int32()
+        _check(_lib.odc_debug_copy(self.h, DBG[what], None, 0, C.byref(n), C.byref(eb)))
+        dt = np.dtype(_DBG_DTYPE[what])
+        k = _DBG_SHAPE.get(what, 1)
+        out = np.empty(int(n.value) * k, dt)
+        _check(_lib.odc_debug_copy(self.h, DBG[what], _ptr(out), out.nbytes, C.byref(n), C.byref(eb)))
+        return out.reshape(-1, k) if k > 1 else out
+
+    def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None):
+        holder = _SourceHolder(src, None if precision < 0 else precision, band)
+        pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
+        lab = np.empty(pts.shape[0], np.uint8)
+        z = np.empty(pts.shape[0], np.float32)
+        _check(_lib.odc_eval_points(self.h, C.byref(holder.src), _ptr(pts), pts.shape[0], iso, precision,
+                                    _ptr(lab), _ptr(z)))
+        return lab.astype(bool), z
