@@ -1,0 +1,287 @@
+"""Benchmark: ODC Mcells/s at 256^3 on the envelope-MLP occupancy workload.
+
+Workload (one step = one whole ODC extraction, every stage): 256^3 cells on
+[-1, 1]^3, occ(x) = sigmoid(20 (0.5 - |x| + 0.15 f(x))) with f a random
+Kaiming-initialised 64-frequency (sigma 4) Fourier-feature MLP, 4 x 256 ReLU,
+iso 0.5, 15 bisection steps, 2D search (4 + 11, 0.8) and (3 + 12, sqrt(2)/2).
+Synthetic seeded weights (the paper's trained networks are not available).
+
+``value`` times the device work of each step with CUDA events on the stream
+the library runs on, with the source already resident in HBM and L2 flushed
+(a 512 MiB write) between steps, outside the timed events.  ``e2e`` times the
+public C-ABI call with host source buffers and the mesh copied back to host.
+Under torchrun every rank extracts its own shape (replicas; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+RES = 256
+STEPS_1D = 15
+FP32_FMA_PER_SM_CLK = 128          # FP32 lanes per SM on GB300
+N_SM = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = []
+        mx = 0.0
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(seed: int = 0):
+    from paper_2409_13418_gb300 import inputs as I
+    return I.envelope_mlp(seed), I.cube_grid(RES)
+
+
+def cpu_sample(mlp, n_cells: int = 40):
+    """Oracle on an n^3-cell block of the same 256^3 grid crossing the surface shell."""
+    import numpy as np
+
+    from oracle import odc as oracle
+    from paper_2409_13418_gb300 import inputs as I
+    h = 2.0 / RES
+    i0 = (RES // 2 + 40, RES // 2 - n_cells // 2, RES // 2 - n_cells // 2)   # x in [0.31, 0.31 + n h]
+    lo = tuple(-1.0 + i0[a] * h for a in range(3))
+    hi = tuple(lo[a] + n_cells * h for a in range(3))
+    g = I.Grid(lo, hi, (n_cells, n_cells, n_cells))
+    t = time.perf_counter()
+    r = oracle.extract(mlp, g, steps_1d=STEPS_1D)
+    dt = time.perf_counter() - t
+    del np
+    return n_cells ** 3, dt, r.stats
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores, on a bounded sample per step."""
+    if rank != 0:
+        return
+    mlp, _ = workload(0)
+    for _ in range(args.warmup):
+        cpu_sample(mlp, args.cpu_cells)
+    tot_cells, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        c, dt, st = cpu_sample(mlp, args.cpu_cells)
+        tot_cells += c
+        tot_t += dt
+    v = tot_cells / tot_t / 1e6
+    cores = os.cpu_count()
+    line = {"metric": "ODC Mcells/s at 256^3", "value": v, "unit": "Mcells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"envelope MLP 256^3 (k={STEPS_1D}), sampled as a {args.cpu_cells}^3-cell block "
+                                   f"of the same grid crossing the surface shell"},
+            "cpu_baseline": {"value": v, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.cpu_cells}^3-cell block of the 256^3 grid per step"},
+            "e2e": {"value": v, "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--band", type=float, default=1e-3)
+    ap.add_argument("--cpu-cells", type=int, default=None,
+                    help="oracle sample block edge (default 40 for cpu_baseline, 32 per reference step)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        args.cpu_cells = args.cpu_cells or 32
+        run_reference(args, rank, world)
+        return
+    args.cpu_cells = args.cpu_cells or 40
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2409_13418_gb300 import build, odc
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    assert args.warmup >= 3 or os.environ.get("ODC_BENCH_ALLOW_SHORT"), "at least 3 warm-up steps"
+
+    prec = odc.PREC_BF16 if args.precision == "bf16" else odc.PREC_FP32
+    mlp, grid = workload(rank)
+    ctx = odc.Context(local)
+    ctx.upload(mlp, precision=prec, band=args.band)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        return ctx.extract(None, grid, steps_1d=STEPS_1D, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = odc.launch_total()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    mlp_ms, mlp_flops, mlp_launches, stats = 0.0, 0.0, 0, None
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        m = step()
+        ev[i][1].record(stream)
+        stats = m.stats
+        mlp_ms += stats["mlp_ms"]
+        mlp_flops += stats["mlp_flops"]
+        mlp_launches += stats["mlp_launches"]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = odc.launch_total() - l0
+    clocks = sampler.stop()
+    t_steps = sum(a.elapsed_time(b) for a, b in ev)          # ms, device time of K steps
+    t_local = torch.tensor([t_steps], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    t_max = float(t_local.item())
+    cells = float(RES ** 3)
+    value = cells * world * args.steps / (t_max * 1e-3) / 1e6
+
+    # e2e: host source buffers in, mesh copied back to host, wall clock
+    vbytes = tbytes = 0
+    h2d = sum(a.nbytes for a in [mlp.B] + mlp.weights + mlp.biases)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m = ctx.extract(mlp, grid, steps_1d=STEPS_1D, stream=stream.cuda_stream, precision=prec, band=args.band)
+        v, t = m.to_host()
+        vbytes, tbytes = v.nbytes, t.nbytes
+    torch.cuda.synchronize()
+    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e = cells * world * args.steps / float(t_e2e.item()) / 1e6
+
+    if rank == 0:
+        peaks, peak_src = _peaks()
+        achieved = mlp_flops / (mlp_ms * 1e-3) / 1e12 if mlp_ms > 0 else None
+        if prec == odc.PREC_FP32:
+            peak = N_SM * FP32_FMA_PER_SM_CLK * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": "k_mlp_fp32 (FP32 FMA pipe)", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock (unit counts)",
+                    "flops_per_launch": mlp_flops / max(1, mlp_launches)}
+        else:
+            peak = float(peaks["bf16_tflops_sustained"])
+            roof = {"bound": "tensor", "kernel": "k_mlp_tc (tcgen05 BF16)", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                    "peak_source": f"bf16_tflops_sustained of {peak_src}",
+                    "flops_per_launch": mlp_flops / max(1, mlp_launches)}
+        line = {"metric": "ODC Mcells/s at 256^3", "value": value, "unit": "Mcells/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == odc.PREC_FP32 else "bf16+f32",
+                "data": "synthetic (seeded random-init MLP weights)",
+                "config": {"workload": f"envelope MLP occupancy, {RES}^3 cells, k={STEPS_1D}, "
+                                       f"{args.precision}" + (f" band {args.band}" if prec == odc.PREC_BF16 else ""),
+                           "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) between steps",
+                           "edges": stats["n_edges"], "face_segs": stats["n_face_segs"],
+                           "queries": stats["n_queries"], "requeries_fp32": stats["n_requeries"],
+                           "stage_ms": [round(x, 3) for x in stats["stage_ms"]]},
+                "e2e": {"value": e2e, "unit": "Mcells/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(vbytes + tbytes)},
+                "gpu_launches": int(launches),
+                "roofline": roof,
+                "clocks": clocks}
+        if world == 1 and not args.no_cpu_baseline:
+            c, dt, st = cpu_sample(mlp, args.cpu_cells)
+            line["cpu_baseline"] = {"value": c / dt / 1e6, "unit": "Mcells/s", "cores": os.cpu_count(),
+                                    "kind": "oracle",
+                                    "sample": f"{args.cpu_cells}^3-cell block of the same 256^3 grid crossing the "
+                                              f"surface shell, FP64 numpy oracle"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -67,8 +67,9 @@ typedef enum {
 
 typedef struct odc_ctx odc_ctx;
 
-/* Occupancy source kinds. */
-enum { ODC_SRC_CSG = 0, ODC_SRC_MLP = 1 };
+/* Occupancy source kinds.  ODC_SRC_RESIDENT reuses the source last uploaded
+ * to the context (by odc_source_upload or a previous odc_extract). */
+enum { ODC_SRC_CSG = 0, ODC_SRC_MLP = 1, ODC_SRC_RESIDENT = 2 };
 
 /* CSG primitive types and operations (Sec. 3: any phi; CSG is a synthetic
  * stand-in for the paper's neural occupancies). */
@@ -162,6 +163,10 @@ typedef struct {
     int64_t n_queries;           /* occupancy evaluations on the main path */
     int64_t n_requeries;         /* FP32 re-evaluations inside the band */
     float stage_ms[8];           /* grid, compact, topology, 1D, 2D, QEF, quads, total */
+    double mlp_flops;            /* algorithmic FLOPs of the network launches (MLP sources) */
+    float mlp_ms;                /* CUDA-event time of the network launches */
+    int32_t n_launches;          /* kernel launches issued by this extract */
+    int64_t mlp_launches;        /* network kernel launches */
 } odc_stats;
 
 typedef struct {
@@ -185,6 +190,12 @@ odc_status odc_ctx_destroy(odc_ctx* ctx);
  * stages as listed at the top of this header. */
 odc_status odc_extract(odc_ctx* ctx, const odc_source* src, const odc_grid* grid,
                        const odc_params* params, void* cuda_stream, odc_mesh* out);
+
+/* Upload an occupancy source (host descriptors) to the context's device
+ * memory without extracting, so that later odc_extract calls with kind
+ * ODC_SRC_RESIDENT start from device-resident inputs.  Returns
+ * ODC_ERR_INVALID_ARG for a malformed source. */
+odc_status odc_source_upload(odc_ctx* ctx, const odc_source* src);
 
 /* Copy a mesh into caller buffers: verts float[n_verts*3], tris
  * int32[n_tris*3]; ``dst_on_device`` selects device or host destinations.
@@ -224,6 +235,10 @@ odc_status odc_debug_copy(odc_ctx* ctx, int what, void* dst, size_t max_bytes,
  * (-1 keeps the source's).  Sec. 3 / A.2.2 binary occupancy. */
 odc_status odc_eval_points(odc_ctx* ctx, const odc_source* src, const float* points, int64_t n,
                            float iso, int precision, uint8_t* labels, float* logits);
+
+/* Number of CUDA kernel launches the library has issued since it was loaded
+ * (all contexts and threads); lets a caller count the kernels of a region. */
+int64_t odc_launch_count(void);
 
 const char* odc_status_str(odc_status s);
 const char* odc_last_error(void);

@@ -60,6 +60,11 @@ struct odc_ctx {
     uint32_t* h_cnt = nullptr;  // pinned host counters
     cudaEvent_t ev[9] = {};
     MlpState* mlp = nullptr;
+    // resident source
+    int res_kind = -1;
+    int res_nprims = 0;
+    PrimDev* res_prims = nullptr;
+    float4* res_cull = nullptr;
     // last extract
     GridDev g{};
     int k = 0;
@@ -119,6 +124,8 @@ const char* odc_status_str(odc_status s) {
 
 const char* odc_last_error(void) { return g_err.c_str(); }
 
+int64_t odc_launch_count(void) { return (int64_t)launch_count(); }
+
 odc_status odc_ctx_create(int device, size_t mem_budget, odc_ctx** out) {
     if (!out) return fail(ODC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -157,6 +164,7 @@ odc_status odc_ctx_destroy(odc_ctx* c) {
 
 static odc_status check_source(const odc_source* src) {
     if (!src) return fail(ODC_ERR_INVALID_ARG, "source is NULL");
+    if (src->kind == ODC_SRC_RESIDENT) return ODC_OK;
     if (src->kind == ODC_SRC_CSG) {
         if (!src->prims) return fail(ODC_ERR_INVALID_ARG, "CSG source without primitives");
         if (src->n_prims < 1 || src->n_prims > kMaxPrims) return fail(ODC_ERR_INVALID_ARG, "n_prims out of [1, 4096]");
@@ -214,6 +222,21 @@ static odc_status upload_csg(odc_ctx* c, const odc_source* src, cudaStream_t st,
     return ODC_OK;
 }
 
+static odc_status upload_source(odc_ctx* c, const odc_source* src, cudaStream_t st) {
+    odc_status s;
+    c->res_kind = -1;
+    if (src->kind == ODC_SRC_CSG) {
+        s = upload_csg(c, src, st, &c->res_prims, &c->res_cull);
+        if (s != ODC_OK) return s;
+        c->res_nprims = src->n_prims;
+    } else {
+        s = mlp_prepare(&c->mlp, src->mlp, st, &g_err);
+        if (s != ODC_OK) return s;
+    }
+    c->res_kind = src->kind;
+    return ODC_OK;
+}
+
 static void grid_coords(const odc_grid* grid, int a, std::vector<float>& X) {
     int n = grid->res[a];
     X.resize(n + 1);
@@ -240,16 +263,17 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
     std::memset(out, 0, sizeof(*out));
 
-    // ---- source upload
-    PrimDev* d_prims = nullptr;
-    float4* d_cull = nullptr;
-    if (src->kind == ODC_SRC_CSG) {
-        s = upload_csg(c, src, st, &d_prims, &d_cull);
+    // ---- source upload (skipped for a resident source)
+    if (src->kind != ODC_SRC_RESIDENT) {
+        s = upload_source(c, src, st);
         if (s != ODC_OK) return s;
-    } else {
-        s = mlp_prepare(&c->mlp, src->mlp, st, &g_err);
-        if (s != ODC_OK) return s;
+    } else if (c->res_kind < 0) {
+        return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
     }
+    const int kind = c->res_kind;
+    PrimDev* d_prims = c->res_prims;
+    float4* d_cull = c->res_cull;
+    const int n_prims = c->res_nprims;
 
     // ---- grid-sized buffers
     GridDev g{};
@@ -291,10 +315,12 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
                     prm->s2d_lin2, prm->s2d_bin2, prm->s2d_range2, prm->ic_split};
     int64_t nq = 0, nrq = 0;
 
+    const long long launches0 = launch_count();
+    mlp_timing_begin(c->mlp);
     ODC_CK(cudaEventRecord(c->ev[0], st));
     // ---- a1: grid occupancy
-    if (src->kind == ODC_SRC_CSG) {
-        launch_csg_grid(g, d_prims, d_cull, src->n_prims, bits, st);
+    if (kind == ODC_SRC_CSG) {
+        launch_csg_grid(g, d_prims, d_cull, n_prims, bits, st);
     } else {
         s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &nrq, &g_err);
         if (s != ODC_OK) return s;
@@ -364,8 +390,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     ODC_CK(cudaEventRecord(c->ev[3], st));
 
     // ---- a4: 1D search
-    if (src->kind == ODC_SRC_CSG) {
-        launch_bisect_csg(g, bits, edges, E, prm->steps_1d, d_prims, d_cull, src->n_prims, T, st);
+    if (kind == ODC_SRC_CSG) {
+        launch_bisect_csg(g, bits, edges, E, prm->steps_1d, d_prims, d_cull, n_prims, T, st);
         nq += (int64_t)E * prm->steps_1d;
     } else {
         s = mlp_bisect(c->mlp, g, bits, edges, E, prm->steps_1d, prm->iso, T, st, &nq, &nrq, &g_err);
@@ -375,8 +401,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     ODC_CK(cudaEventRecord(c->ev[4], st));
 
     // ---- a5: 2D search
-    if (src->kind == ODC_SRC_CSG) {
-        launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, src->n_prims, pf, fflags,
+    if (kind == ODC_SRC_CSG) {
+        launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, n_prims, pf, fflags,
                         st);
     } else {
         s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, st, &nq, &nrq,
@@ -419,6 +445,20 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     S.n_flips = nflip; S.fix_rounds = rounds; S.n_queries = nq; S.n_requeries = nrq;
     for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&S.stage_ms[i], c->ev[i], c->ev[i + 1]);
     cudaEventElapsedTime(&S.stage_ms[7], c->ev[0], c->ev[7]);
+    S.n_launches = (int32_t)(launch_count() - launches0);
+    if (kind == ODC_SRC_MLP) mlp_timing_collect(c->mlp, &S.mlp_ms, &S.mlp_flops, &S.mlp_launches);
+    return ODC_OK;
+}
+
+odc_status odc_source_upload(odc_ctx* c, const odc_source* src) {
+    if (!c) return fail(ODC_ERR_INVALID_ARG, "NULL context");
+    if (src && src->kind == ODC_SRC_RESIDENT) return fail(ODC_ERR_INVALID_ARG, "cannot upload a resident source");
+    odc_status s = check_source(src);
+    if (s != ODC_OK) return s;
+    ODC_CK(cudaSetDevice(c->device));
+    s = upload_source(c, src, c->own);
+    if (s != ODC_OK) return s;
+    ODC_CK(cudaStreamSynchronize(c->own));
     return ODC_OK;
 }
 
@@ -505,14 +545,14 @@ odc_status odc_eval_points(odc_ctx* c, const odc_source* src, const float* point
     cudaStream_t st = c->own;
     if (n == 0) return ODC_OK;
     size_t need = al(n * 12) + al(n) + al(n * 4);
-    PrimDev* d_prims = nullptr;
-    float4* d_cull = nullptr;
-    if (src->kind == ODC_SRC_CSG) {
-        s = upload_csg(c, src, st, &d_prims, &d_cull);
-    } else {
-        s = mlp_prepare(&c->mlp, src->mlp, st, &g_err);
+    if (src->kind != ODC_SRC_RESIDENT) {
+        s = upload_source(c, src, st);
+        if (s != ODC_OK) return s;
+    } else if (c->res_kind < 0) {
+        return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
     }
-    if (s != ODC_OK) return s;
+    PrimDev* d_prims = c->res_prims;
+    float4* d_cull = c->res_cull;
     s = arena_ensure(c, c->B, need);
     if (s != ODC_OK) return s;
     float3* dp = (float3*)c->B.take(n * 12);
@@ -520,15 +560,15 @@ odc_status odc_eval_points(odc_ctx* c, const odc_source* src, const float* point
     float* dz = (float*)c->B.take(n * 4);
     c->E = c->F = c->C = c->V3 = 0;   // the B arena no longer holds an extract
     ODC_CK(cudaMemcpyAsync(dp, points, n * 12, cudaMemcpyHostToDevice, st));
-    if (src->kind == ODC_SRC_CSG) {
-        launch_csg_points(d_prims, d_cull, src->n_prims, dp, n, dl, st);
+    if (c->res_kind == ODC_SRC_CSG) {
+        launch_csg_points(d_prims, d_cull, c->res_nprims, dp, n, dl, st);
     } else {
         s = mlp_points(c->mlp, dp, n, iso, precision, dl, dz, st, &g_err);
         if (s != ODC_OK) return s;
     }
     ODC_CK(cudaGetLastError());
     ODC_CK(cudaMemcpyAsync(labels, dl, n, cudaMemcpyDeviceToHost, st));
-    if (logits && src->kind == ODC_SRC_MLP) ODC_CK(cudaMemcpyAsync(logits, dz, n * 4, cudaMemcpyDeviceToHost, st));
+    if (logits && c->res_kind == ODC_SRC_MLP) ODC_CK(cudaMemcpyAsync(logits, dz, n * 4, cudaMemcpyDeviceToHost, st));
     ODC_CK(cudaStreamSynchronize(st));
     return ODC_OK;
 }

@@ -10,7 +10,13 @@
 #include "kernels.h"
 #include "odc_device.cuh"
 
+#include <atomic>
+
 namespace odc {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- grid phi
 // One warp per label word: lane l evaluates vertex x = 32 w + l.  A primitive
@@ -234,9 +240,9 @@ void exclusive_scan(const T* in, T* out, size_t n, T* tmp, T* total, cudaStream_
         cudaMemsetAsync(total, 0, sizeof(T), st);
         return;
     }
-    k_scan_tiles<T><<<(unsigned)nt, kScanThreads, 0, st>>>(in, n, tmp);
-    k_scan_sums<T><<<1, kScanThreads, 0, st>>>(tmp, nt, total);
-    k_scan_apply<T><<<(unsigned)nt, kScanThreads, 0, st>>>(in, n, tmp, out);
+    k_scan_tiles<T><<<(unsigned)nt, kScanThreads, 0, st>>>(in, n, tmp); note_launch();
+    k_scan_sums<T><<<1, kScanThreads, 0, st>>>(tmp, nt, total); note_launch();
+    k_scan_apply<T><<<(unsigned)nt, kScanThreads, 0, st>>>(in, n, tmp, out); note_launch();
 }
 
 template void exclusive_scan<uint32_t>(const uint32_t*, uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
@@ -248,13 +254,13 @@ void launch_csg_grid(const GridDev& g, const PrimDev* prims, const float4* cull,
                      cudaStream_t st) {
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
     size_t threads = nw * 32;
-    k_csg_grid<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, prims, cull, n_prims, bits);
+    k_csg_grid<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, prims, cull, n_prims, bits); note_launch();
 }
 
 void launch_classify(const GridDev& g, const uint32_t* bits, WordInfo* wi, uint32_t* ce, uint32_t* cf, uint32_t* cc,
                      cudaStream_t st) {
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
-    k_classify<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(g, bits, wi, ce, cf, cc);
+    k_classify<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(g, bits, wi, ce, cf, cc); note_launch();
 }
 
 void launch_emit(const GridDev& g, const uint32_t* bits, const WordInfo* wi, const uint32_t* ebase,
@@ -263,7 +269,7 @@ void launch_emit(const GridDev& g, const uint32_t* bits, const WordInfo* wi, con
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
     size_t threads = nw * 32;
     k_emit<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, bits, wi, ebase, fbase, cbase, edges, faces, slots,
-                                                            cells, configs);
+                                                            cells, configs); note_launch();
 }
 
 }  // namespace odc

@@ -1,13 +1,426 @@
-// mlp.cu -- placeholder until the MLP occupancy kernels land.
+// mlp.cu -- envelope-MLP occupancy network on the device.
+//
+// f(x) = W5 relu(W4 relu(W3 relu(W2 relu(W1 g(x) + b1) + b2) + b3) + b4) + b5,
+// g(x) = [sin(2 pi B x), cos(2 pi B x)] (64 frequencies), z = scale (radius -
+// |x| + amp f(x)).  The FP32 path (this file) is the plain reference path of
+// the GPU: SIMT FMAs, register-tiled 64-query x 256-output tiles, the
+// Fourier phase B.x formed exactly in float-float and reduced to one period
+// before sincospi.  The BF16 tensor-core path lives in mlp_tc.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "mlp.h"
+#include "mlp_dev.cuh"
+#include "odc_device.cuh"
 
 namespace odc {
-struct MlpState {};
-odc_status mlp_check(const odc_mlp*, std::string* err) { *err = "MLP sources not built yet"; return ODC_ERR_UNSUPPORTED; }
-odc_status mlp_prepare(MlpState**, const odc_mlp*, cudaStream_t, std::string* err) { *err = "MLP"; return ODC_ERR_UNSUPPORTED; }
-void mlp_destroy(MlpState*) {}
-odc_status mlp_grid(MlpState*, const GridDev&, float, uint32_t*, cudaStream_t, int64_t*, int64_t*, std::string*) { return ODC_ERR_UNSUPPORTED; }
-odc_status mlp_bisect(MlpState*, const GridDev&, const uint32_t*, const uint32_t*, uint32_t, int, float, uint32_t*, cudaStream_t, int64_t*, int64_t*, std::string*) { return ODC_ERR_UNSUPPORTED; }
-odc_status mlp_faces(MlpState*, const GridDev&, const uint32_t*, const uint32_t*, const WordInfo*, const uint32_t*, const uint32_t*, const uint32_t*, const uint8_t*, uint32_t, const SearchParams&, float, float2*, uint8_t*, cudaStream_t, int64_t*, int64_t*, std::string*) { return ODC_ERR_UNSUPPORTED; }
-odc_status mlp_points(MlpState*, const float3*, int64_t, float, int, uint8_t*, float*, cudaStream_t, std::string*) { return ODC_ERR_UNSUPPORTED; }
+
+odc_status mlp_check(const odc_mlp* m, std::string* err) {
+    if (!m) { *err = "MLP source without descriptor"; return ODC_ERR_INVALID_ARG; }
+    if (m->n_freq != kNF || m->hidden != kH || m->n_hidden != kNL)
+        { *err = "MLP shape must be 64 frequencies, 4 hidden layers of 256"; return ODC_ERR_INVALID_ARG; }
+    if (m->latent_dim != 0 && m->latent_dim != 128) { *err = "latent_dim must be 0 or 128"; return ODC_ERR_INVALID_ARG; }
+    if (m->latent_dim && !m->latent) { *err = "latent pointer missing"; return ODC_ERR_INVALID_ARG; }
+    if (!m->B) { *err = "Fourier matrix missing"; return ODC_ERR_INVALID_ARG; }
+    for (int l = 0; l <= kNL; ++l)
+        if (!m->W[l] || !m->b[l]) { *err = "weight or bias pointer missing"; return ODC_ERR_INVALID_ARG; }
+    if (m->precision != ODC_PREC_FP32 && m->precision != ODC_PREC_BF16)
+        { *err = "precision must be FP32 or BF16"; return ODC_ERR_INVALID_ARG; }
+    if (m->precision == ODC_PREC_BF16 && !(m->band >= 0.0f && m->band < 0.5f))
+        { *err = "band must be in [0, 0.5)"; return ODC_ERR_INVALID_ARG; }
+    return ODC_OK;
+}
+
+float mlp_logit_threshold(float iso) { return (float)std::log((double)iso / (1.0 - (double)iso)); }
+
+int mlp_precision(const MlpState* st) { return st->precision; }
+
+#define MLP_CK(call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) { *err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+                                 return ODC_ERR_CUDA; }                                     \
+    } while (0)
+
+odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::string* err) {
+    if (st->scr_cap[slot] < bytes) {
+        if (st->scr[slot]) {
+            MLP_CK(cudaDeviceSynchronize());
+            cudaFree(st->scr[slot]);
+            st->scr[slot] = nullptr;
+            st->scr_cap[slot] = 0;
+        }
+        size_t want = bytes + bytes / 4 + 4096;
+        cudaError_t e = cudaMalloc(&st->scr[slot], want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *err = std::string("MLP scratch allocation failed: ") + cudaGetErrorString(e);
+            return ODC_ERR_OOM;
+        }
+        st->scr_cap[slot] = want;
+    }
+    *out = st->scr[slot];
+    return ODC_OK;
+}
+
+cudaEvent_t* mlp_ev_pair(MlpState* st) {
+    if (st->ev_used >= 256) return nullptr;
+    cudaEvent_t* p = &st->ev[2 * st->ev_used];
+    if (!p[0]) {
+        if (cudaEventCreate(&p[0]) != cudaSuccess || cudaEventCreate(&p[1]) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+    }
+    ++st->ev_used;
+    return p;
+}
+
+void mlp_timing_begin(MlpState* st) {
+    if (!st) return;
+    st->ev_used = 0;
+    st->flops = 0.0;
+    st->launches = 0;
+}
+
+void mlp_timing_collect(MlpState* st, float* ms, double* flops, int64_t* launches) {
+    *ms = 0.0f;
+    *flops = 0.0;
+    *launches = 0;
+    if (!st) return;
+    for (int i = 0; i < st->ev_used; ++i) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, st->ev[2 * i], st->ev[2 * i + 1]) == cudaSuccess) *ms += t;
+        else cudaGetLastError();
+    }
+    *flops = st->flops;
+    *launches = st->launches;
+}
+
+void mlp_destroy(MlpState* st) {
+    if (!st) return;
+    for (auto& e : st->ev)
+        if (e) cudaEventDestroy(e);
+    if (st->wblob) cudaFree(st->wblob);
+    for (int i = 0; i < kScratchSlots; ++i)
+        if (st->scr[i]) cudaFree(st->scr[i]);
+    mlp_tc_destroy(st);
+    delete st;
+}
+
+// Upload weights: FP32 transposed copies for the SIMT path (W^T [in][out]),
+// and the BF16 operand tiles of the tensor-core path.
+odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::string* err) {
+    odc_status r = mlp_check(m, err);
+    if (r != ODC_OK) return r;
+    if (!*pst) *pst = new MlpState();
+    MlpState* st = *pst;
+    st->precision = m->precision;
+    st->band = m->band;
+    // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
+    st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
+    st->scale = m->env_scale;
+    st->radius = m->env_radius;
+    st->amp = m->env_amp;
+    const int din = 2 * kNF + m->latent_dim;
+    std::vector<float> h(kBlobFloats, 0.0f);
+    // B
+    std::memcpy(&h[kOffB], m->B, sizeof(float) * kNF * 3);
+    // layer 0: fold a constant latent into the bias (its columns multiply a
+    // per-shape constant); W0^T for the Fourier columns only
+    {
+        const float* W = m->W[0];
+        for (int k = 0; k < 2 * kNF; ++k)
+            for (int n = 0; n < kH; ++n) h[kOffW[0] + (size_t)k * kH + n] = W[(size_t)n * din + m->latent_dim + k];
+        for (int n = 0; n < kH; ++n) {
+            double b = m->b[0][n];
+            for (int j = 0; j < m->latent_dim; ++j) b += (double)W[(size_t)n * din + j] * (double)m->latent[j];
+            h[kOffb[0] + n] = (float)b;
+        }
+    }
+    for (int l = 1; l < kNL; ++l) {
+        const float* W = m->W[l];
+        for (int k = 0; k < kH; ++k)
+            for (int n = 0; n < kH; ++n) h[kOffW[l] + (size_t)k * kH + n] = W[(size_t)n * kH + k];
+        std::memcpy(&h[kOffb[l]], m->b[l], sizeof(float) * kH);
+    }
+    std::memcpy(&h[kOffW[kNL]], m->W[kNL], sizeof(float) * kH);
+    h[kOffb[kNL]] = m->b[kNL][0];
+    if (!st->wblob) MLP_CK(cudaMalloc((void**)&st->wblob, sizeof(float) * kBlobFloats));
+    MLP_CK(cudaMemcpyAsync(st->wblob, h.data(), sizeof(float) * kBlobFloats, cudaMemcpyHostToDevice, s));
+    r = mlp_tc_prepare(st, h.data(), s, err);
+    if (r != ODC_OK) return r;
+    return ODC_OK;
+}
+
+// ----------------------------------------------------------- FP32 network
+constexpr int kTM = 64;           // queries per CTA
+constexpr int kThreads = 256;
+constexpr int kKC = 16;           // weight rows per staged chunk
+constexpr int kActStride = kH + 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// out[m][n] = relu(sum_k in[m][k] Wt[k][n] + b[n]) for the CTA's 64 queries.
+// Thread (tr, tc): rows tr*8..tr*8+7, columns tc*4..tc*4+3 and 128+tc*4..+3.
+__device__ __forceinline__ void dense_relu(const float* __restrict__ in, float* __restrict__ out, int K,
+                                           const float* __restrict__ Wt, const float* __restrict__ bias,
+                                           float* __restrict__ wbuf) {
+    const int tid = threadIdx.x, tr = tid >> 5, tc = tid & 31;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    const int nchunk = K / kKC;
+    auto stage = [&](int c, int buf) {
+        const float* src = Wt + (size_t)c * kKC * kH;
+        float* dst = wbuf + buf * kKC * kH;
+#pragma unroll
+        for (int r = 0; r < (kKC * kH / 4) / kThreads; ++r) {
+            int idx = (r * kThreads + tid) * 4;
+            cp_async16(dst + idx, src + idx);
+        }
+        cp_async_commit();
+    };
+    stage(0, 0);
+    for (int c = 0; c < nchunk; ++c) {
+        if (c + 1 < nchunk) {
+            stage(c + 1, (c + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float* w = wbuf + (c & 1) * kKC * kH;
+#pragma unroll
+        for (int kk = 0; kk < kKC; kk += 4) {
+            float4 a4[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                a4[i] = *reinterpret_cast<const float4*>(in + (tr * 8 + i) * kActStride + c * kKC + kk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float* wr = w + (kk + q) * kH;
+                float4 w0 = *reinterpret_cast<const float4*>(wr + tc * 4);
+                float4 w1 = *reinterpret_cast<const float4*>(wr + 128 + tc * 4);
+                float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float av = q == 0 ? a4[i].x : (q == 1 ? a4[i].y : (q == 2 ? a4[i].z : a4[i].w));
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av, wv[j], acc[i][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    float4 b0 = *reinterpret_cast<const float4*>(bias + tc * 4);
+    float4 b1 = *reinterpret_cast<const float4*>(bias + 128 + tc * 4);
+    float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float* o = out + (tr * 8 + i) * kActStride;
+        float4 v0 = make_float4(fmaxf(acc[i][0] + bv[0], 0.f), fmaxf(acc[i][1] + bv[1], 0.f),
+                                fmaxf(acc[i][2] + bv[2], 0.f), fmaxf(acc[i][3] + bv[3], 0.f));
+        float4 v1 = make_float4(fmaxf(acc[i][4] + bv[4], 0.f), fmaxf(acc[i][5] + bv[5], 0.f),
+                                fmaxf(acc[i][6] + bv[6], 0.f), fmaxf(acc[i][7] + bv[7], 0.f));
+        *reinterpret_cast<float4*>(o + tc * 4) = v0;
+        *reinterpret_cast<float4*>(o + 128 + tc * 4) = v1;
+    }
+    __syncthreads();
+}
+
+// Query points either from a list or from the grid in label-word order.
+struct QuerySrc {
+    const float3* pts;       // list mode when non-null
+    const int* idx;          // optional gather indices into pts
+    GridDev g;               // grid mode
+};
+
+__device__ __forceinline__ float3 query_point(const QuerySrc& Q, int64_t q) {
+    if (Q.pts) return Q.pts[Q.idx ? Q.idx[q] : q];
+    int64_t w = q >> 5;
+    int l = (int)(q & 31);
+    int xw = (int)(w % Q.g.W);
+    int64_t row = w / Q.g.W;
+    int y = (int)(row % Q.g.nv[1]);
+    int z = (int)(row / Q.g.nv[1]);
+    int x = min(xw * 32 + l, Q.g.nv[0] - 1);
+    return make_float3(Q.g.X[0][x], Q.g.X[1][y], Q.g.X[2][z]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n, float scale, float radius, float amp,
+               float* __restrict__ zout) {
+    extern __shared__ __align__(16) float sm[];
+    float* actA = sm;
+    float* actB = sm + kTM * kActStride;
+    float* wbuf = sm + 2 * kTM * kActStride;
+    __shared__ float3 xs[kTM];
+    __shared__ float part[kTM][4];
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kTM;
+    if (tid < kTM) {
+        int64_t q = base + tid;
+        xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const float* B = wb + kOffB;
+    for (int i = tid; i < kNF * kTM; i += kThreads) {
+        int j = i / kTM, m = i % kTM;
+        float3 x = xs[m];
+        float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], x);
+        actA[m * kActStride + j] = sc.x;
+        actA[m * kActStride + kNF + j] = sc.y;
+    }
+    __syncthreads();
+    dense_relu(actA, actB, 2 * kNF, wb + kOffW[0], wb + kOffb[0], wbuf);
+    dense_relu(actB, actA, kH, wb + kOffW[1], wb + kOffb[1], wbuf);
+    dense_relu(actA, actB, kH, wb + kOffW[2], wb + kOffb[2], wbuf);
+    dense_relu(actB, actA, kH, wb + kOffW[3], wb + kOffb[3], wbuf);
+    {
+        int m = tid >> 2, p = tid & 3;
+        const float* w5 = wb + kOffW[kNL];
+        float s = 0.0f;
+        for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(actA[m * kActStride + k], w5[k], s);
+        part[m][p] = s;
+    }
+    __syncthreads();
+    if (tid < kTM && base + tid < n) {
+        float f = ((part[tid][0] + part[tid][1]) + (part[tid][2] + part[tid][3])) + wb[kOffb[kNL]];
+        zout[base + tid] = envelope_logit(xs[tid], f, scale, radius, amp);
+    }
+}
+
+static size_t fp32_smem() { return sizeof(float) * (2 * kTM * kActStride + 2 * kKC * kH); }
+
+static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
+    if (n <= 0) return ODC_OK;
+    static bool attr = false;
+    if (!attr) {
+        MLP_CK(cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp32_smem()));
+        attr = true;
+    }
+    int64_t blocks = (n + kTM - 1) / kTM;
+    cudaEvent_t* ev = mlp_ev_pair(st);
+    if (ev) MLP_CK(cudaEventRecord(ev[0], s));
+    k_mlp_fp32<<<(unsigned)blocks, kThreads, fp32_smem(), s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z); note_launch();
+    if (ev) MLP_CK(cudaEventRecord(ev[1], s));
+    MLP_CK(cudaGetLastError());
+    int64_t real = n;
+    if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];   // grid mode: padding lanes excluded
+    st->flops += kFlopsPerQuery * (double)real;
+    st->launches += 1;
+    return ODC_OK;
+}
+
+// ------------------------------------------------------------ band re-eval
+__global__ void k_band_flag(const float* __restrict__ z, int64_t n, float zb, uint32_t* __restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = fabsf(z[i]) < zb ? 1u : 0u;
+}
+__global__ void k_band_gather(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ off, int64_t n,
+                              int* __restrict__ idx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) idx[off[i]] = (int)i;
+}
+__global__ void k_band_scatter(const int* __restrict__ idx, const uint32_t* __restrict__ cnt,
+                               const float* __restrict__ zr, float* __restrict__ z) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *cnt) z[idx[i]] = zr[i];
+}
+__global__ void k_grid_points(GridDev g, const int* __restrict__ idx, const uint32_t* __restrict__ cnt,
+                              float3* __restrict__ pts) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *cnt) return;
+    QuerySrc Q{nullptr, nullptr, g};
+    pts[i] = query_point(Q, idx[i]);
+}
+
+// Re-evaluate in FP32 every logit of z[0..n) whose magnitude is below the
+// band (A.2.2 binary decision at iso; the band makes the reduced-precision
+// decision equal the FP32 one).
+static odc_status band_reeval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, int64_t* nrq,
+                              std::string* err) {
+    void *pflag, *poff, *pidx, *ppts, *pz, *pcnt;
+    odc_status r;
+    if ((r = mlp_scratch(st, 4, n * 4 + 64, &pflag, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, 5, n * 4 + scan_tmp_elems(n) * 8 + 64, &poff, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, 6, n * 4 + 64, &pidx, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, 7, 64, &pcnt, err)) != ODC_OK) return r;
+    uint32_t* flag = (uint32_t*)pflag;
+    uint32_t* off = (uint32_t*)poff;
+    uint32_t* tmp = off + ((n + 63) / 64) * 64;
+    uint32_t* cnt = (uint32_t*)pcnt;
+    unsigned blocks = (unsigned)((n + 255) / 256);
+    k_band_flag<<<blocks, 256, 0, s>>>(z, n, st->zband, flag); note_launch();
+    exclusive_scan<uint32_t>(flag, off, (size_t)n, tmp, cnt, s);
+    k_band_gather<<<blocks, 256, 0, s>>>(flag, off, n, (int*)pidx); note_launch();
+    uint32_t hcnt = 0;
+    MLP_CK(cudaMemcpyAsync(&hcnt, cnt, 4, cudaMemcpyDeviceToHost, s));
+    MLP_CK(cudaStreamSynchronize(s));
+    *nrq += hcnt;
+    if (!hcnt) return ODC_OK;
+    if ((r = mlp_scratch(st, 8, (size_t)hcnt * 16 + 64, &ppts, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, 9, (size_t)hcnt * 4 + 64, &pz, err)) != ODC_OK) return r;
+    QuerySrc R;
+    if (Q.pts) {
+        R = QuerySrc{Q.pts, (const int*)pidx, Q.g};
+    } else {
+        k_grid_points<<<(hcnt + 255) / 256, 256, 0, s>>>(Q.g, (const int*)pidx, cnt, (float3*)ppts); note_launch();
+        R = QuerySrc{(const float3*)ppts, nullptr, Q.g};
+    }
+    if (Q.pts && Q.idx) { *err = "nested gather"; return ODC_ERR_INTERNAL; }
+    if ((r = launch_fp32(st, R, hcnt, (float*)pz, s, err)) != ODC_OK) return r;
+    k_band_scatter<<<(hcnt + 255) / 256, 256, 0, s>>>((const int*)pidx, cnt, (const float*)pz, z); note_launch();
+    MLP_CK(cudaGetLastError());
+    return ODC_OK;
+}
+
+static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int precision, cudaStream_t s,
+                       int64_t* nrq, std::string* err) {
+    if (precision < 0) precision = st->precision;
+    if (precision == ODC_PREC_FP32) return launch_fp32(st, Q, n, z, s, err);
+    odc_status r = mlp_tc_eval(st, Q.pts, Q.g, n, z, s, err);
+    if (r != ODC_OK) return r;
+    return band_reeval(st, Q, n, z, s, nrq, err);
+}
+
+odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
+                         int64_t* nrq, std::string* err) {
+    QuerySrc Q{pts, nullptr, GridDev{}};
+    return eval(st, Q, n, z, precision, s, nrq, err);
+}
+
+odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, int64_t* nrq, std::string* err) {
+    QuerySrc Q{nullptr, nullptr, g};
+    int64_t n = (int64_t)g.W * g.nv[1] * g.nv[2] * 32;
+    return eval(st, Q, n, z, -1, s, nrq, err);
+}
+
+__global__ void k_pts_labels(const float* __restrict__ z, int64_t n, float t, uint8_t* __restrict__ lab) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) lab[i] = z[i] > t ? 1 : 0;
+}
+
+odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
+                      float* logits, cudaStream_t s, std::string* err) {
+    int64_t nrq = 0;
+    odc_status r = mlp_eval_list(st, pts, n, logits, precision, s, &nrq, err);
+    if (r != ODC_OK) return r;
+    k_pts_labels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(logits, n, mlp_logit_threshold(iso), labels); note_launch();
+    MLP_CK(cudaGetLastError());
+    return ODC_OK;
+}
+
 }  // namespace odc

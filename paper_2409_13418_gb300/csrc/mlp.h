@@ -1,4 +1,9 @@
 // mlp.h -- MLP occupancy (envelope MLP over Fourier features) on the device.
+//
+// occ(x) = sigmoid(scale (radius - |x| + amp f(x))); decisions are taken on
+// the logit z = scale (radius - |x| + amp f(x)) against logit(iso).  The
+// searches batch their queries into wavefronts: one network evaluation per
+// search step over all active edges or face segments.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -16,6 +21,18 @@ odc_status mlp_check(const odc_mlp* m, std::string* err);
 odc_status mlp_prepare(MlpState** st, const odc_mlp* m, cudaStream_t s, std::string* err);
 void mlp_destroy(MlpState* st);
 
+// Device scratch owned by the MLP state (grows on demand, never shrinks).
+odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::string* err);
+
+// Logits at n explicit points.  With BF16 precision, every logit within the
+// band is recomputed in FP32 (counted in *nrq).
+odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
+                         int64_t* nrq, std::string* err);
+// Logits at the grid vertices in label-word order (query q -> word q/32, lane q%32).
+odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, int64_t* nrq, std::string* err);
+int mlp_precision(const MlpState* st);
+float mlp_logit_threshold(float iso);
+
 // Grid labels (a1): bit rows as in the CSG path.
 odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, cudaStream_t s, int64_t* nq,
                     int64_t* nrq, std::string* err);
@@ -27,6 +44,11 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
                      const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
                      uint32_t nf, const SearchParams& sp, float iso, float2* pf, uint8_t* flags, cudaStream_t s,
                      int64_t* nq, int64_t* nrq, std::string* err);
+// Start / finish the per-extract accounting of network launches: total
+// event-timed kernel milliseconds and algorithmic FLOPs.
+void mlp_timing_begin(MlpState* st);
+void mlp_timing_collect(MlpState* st, float* ms, double* flops, int64_t* launches);
+
 // Labels (and logits) at explicit points.
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
                       float* logits, cudaStream_t s, std::string* err);

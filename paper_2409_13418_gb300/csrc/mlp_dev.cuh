@@ -1,0 +1,98 @@
+// mlp_dev.cuh -- device layout and shared helpers of the MLP occupancy path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/odc.h"
+#include "odc_device.cuh"
+
+namespace odc {
+
+constexpr int kNF = 64;    // Fourier frequencies
+constexpr int kH = 256;    // hidden width
+constexpr int kNL = 4;     // hidden layers
+constexpr int kScratchSlots = 16;
+
+// FP32 weight blob (floats): B [64][3] (padded to 256), W_l^T [in][out] for
+// l = 0..3, w4 [256], biases b_0..b_3 [256], b_4 [1].
+struct BlobLayout {
+    static constexpr size_t B = 0;
+    static constexpr size_t W0 = 256;
+    static constexpr size_t W1 = W0 + 2 * kNF * kH;
+    static constexpr size_t W2 = W1 + kH * kH;
+    static constexpr size_t W3 = W2 + kH * kH;
+    static constexpr size_t W4 = W3 + kH * kH;
+    static constexpr size_t b0 = W4 + kH;
+    static constexpr size_t b1 = b0 + kH;
+    static constexpr size_t b2 = b1 + kH;
+    static constexpr size_t b3 = b2 + kH;
+    static constexpr size_t b4 = b3 + kH;
+    static constexpr size_t total = b4 + 64;
+};
+#define kOffB (BlobLayout::B)
+#define kBlobFloats (BlobLayout::total)
+__host__ __device__ constexpr size_t kOffW_(int l) {
+    return l == 0 ? BlobLayout::W0 : l == 1 ? BlobLayout::W1 : l == 2 ? BlobLayout::W2 : l == 3 ? BlobLayout::W3 : BlobLayout::W4;
+}
+__host__ __device__ constexpr size_t kOffb_(int l) {
+    return l == 0 ? BlobLayout::b0 : l == 1 ? BlobLayout::b1 : l == 2 ? BlobLayout::b2 : l == 3 ? BlobLayout::b3 : BlobLayout::b4;
+}
+// array-like accessors kOffW[l], kOffb[l]
+struct OffW { __host__ __device__ constexpr size_t operator[](int l) const { return kOffW_(l); } };
+struct Offb { __host__ __device__ constexpr size_t operator[](int l) const { return kOffb_(l); } };
+constexpr OffW kOffW{};
+constexpr Offb kOffb{};
+
+struct MlpTc;   // tensor-core path state (mlp_tc.cu)
+
+struct MlpState {
+    int precision = ODC_PREC_FP32;
+    float band = 1e-3f;
+    float zband = 0.004f;
+    float scale = 20.f, radius = 0.5f, amp = 0.15f;
+    float* wblob = nullptr;                 // FP32 weight blob (device)
+    void* scr[kScratchSlots] = {};
+    size_t scr_cap[kScratchSlots] = {};
+    MlpTc* tc = nullptr;
+    // per-launch CUDA events around the network kernels of one extract
+    cudaEvent_t ev[2 * 256] = {};
+    int ev_used = 0;
+    double flops = 0.0;         // algorithmic FLOPs of the network launches
+    int64_t launches = 0;
+};
+
+// Event pair around one network launch (none once 256 are in use).
+cudaEvent_t* mlp_ev_pair(MlpState* st);
+constexpr double kFlopsPerQuery = 2.0 * (2.0 * kNF * kH + 3.0 * kH * kH + kH);
+
+// Tensor-core path (mlp_tc.cu)
+odc_status mlp_tc_prepare(MlpState* st, const float* host_blob, cudaStream_t s, std::string* err);
+odc_status mlp_tc_eval(MlpState* st, const float3* pts, const GridDev& g, int64_t n, float* z, cudaStream_t s,
+                       std::string* err);
+void mlp_tc_destroy(MlpState* st);
+
+// [sin(2 pi u), cos(2 pi u)] with u = b . x formed exactly in float-float and
+// reduced to [-1/2, 1/2] turns before sincospi.
+__device__ __forceinline__ float2 fourier_sincos(float b0, float b1, float b2, float3 x) {
+    ff u = ff_add(ff_add(two_prod(b0, x.x), two_prod(b1, x.y)), two_prod(b2, x.z));
+    float k = rintf(u.hi);
+    float r = __fadd_rn(__fsub_rn(u.hi, k), u.lo);
+    float s, c;
+    sincospif(2.0f * r, &s, &c);
+    return make_float2(s, c);
+}
+
+// z = scale (radius - |x| + amp f)
+__device__ __forceinline__ float envelope_logit(float3 x, float f, float scale, float radius, float amp) {
+    float r = __fsqrt_rn(x.x * x.x + x.y * x.y + x.z * x.z);
+    return scale * ((radius - r) + amp * f);
+}
+
+// compact.cu
+size_t scan_tmp_elems(size_t n);
+template <typename T>
+void exclusive_scan(const T* in, T* out, size_t n, T* tmp, T* total, cudaStream_t st);
+
+}  // namespace odc

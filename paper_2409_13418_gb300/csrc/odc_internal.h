@@ -41,6 +41,10 @@ struct PrimDev {
 static_assert(sizeof(PrimDev) == 80, "PrimDev must match odc_csg_prim");
 
 // Search parameters (device copy of odc_params).
+// Kernel launches issued by the library (all streams, all contexts).
+void note_launch();
+long long launch_count();
+
 struct SearchParams {
     int steps_1d;
     int lin1, bin1;

@@ -135,8 +135,8 @@ void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, con
                 const uint32_t* fbase, const uint32_t* T, const float2* pf, const uint32_t* cells,
                 const uint8_t* configs, const unsigned long long* cycles, const uint32_t* vbase, uint32_t nc, int k,
                 float3* vlocal, float3* vworld, cudaStream_t st) {
-    if (nc) k_qef<<<(nc + 127) / 128, 128, 0, st>>>(g, flips, wi, ebase, fbase, T, pf, cells, configs, cycles, vbase,
-                                                   nc, k, vlocal, vworld);
+    if (nc) { k_qef<<<(nc + 127) / 128, 128, 0, st>>>(g, flips, wi, ebase, fbase, T, pf, cells, configs, cycles, vbase,
+                                                   nc, k, vlocal, vworld); note_launch(); }
 }
 
 }  // namespace odc

@@ -119,14 +119,14 @@ void launch_quad_case(const GridDev& g, const uint32_t* bits, const WordInfo* wi
                       const uint32_t* edges, uint32_t ne, const unsigned long long* cycles, const uint32_t* vbase,
                       const float3* vlocal, int ic_split, uint8_t* qcase, int4* qv, unsigned long long* cnt,
                       cudaStream_t st) {
-    if (ne) k_quad_case<<<(ne + 255) / 256, 256, 0, st>>>(g, bits, wi, cbase, edges, ne, cycles, vbase, vlocal,
-                                                         ic_split, qcase, qv, cnt);
+    if (ne) { k_quad_case<<<(ne + 255) / 256, 256, 0, st>>>(g, bits, wi, cbase, edges, ne, cycles, vbase, vlocal,
+                                                         ic_split, qcase, qv, cnt); note_launch(); }
 }
 
 void launch_quad_emit(const GridDev& g, const uint32_t* edges, const uint32_t* T, uint32_t ne, int k,
                       const uint8_t* qcase, const int4* qv, const unsigned long long* off,
                       const uint32_t* v3tot, float3* vworld, int3* tris, cudaStream_t st) {
-    if (ne) k_quad_emit<<<(ne + 255) / 256, 256, 0, st>>>(g, edges, T, ne, k, qcase, qv, off, v3tot, vworld, tris);
+    if (ne) { k_quad_emit<<<(ne + 255) / 256, 256, 0, st>>>(g, edges, T, ne, k, qcase, qv, off, v3tot, vworld, tris); note_launch(); }
 }
 
 }  // namespace odc

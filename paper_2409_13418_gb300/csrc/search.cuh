@@ -127,4 +127,37 @@ __device__ __forceinline__ float2 face_intersect(const FaceSeg& F, ff2 q1, ff2 q
     return make_float2(pf.u.hi, pf.v.hi);
 }
 
+// Load face segment (fid, slot): its corner labels and pairing, the two 1D
+// points from the 1D results T, and the search geometry.
+__device__ __forceinline__ void load_face(const GridDev& g, const uint32_t* bits, const uint32_t* flips,
+                                          const WordInfo* wi, const uint32_t* ebase, const uint32_t* T, int k,
+                                          uint32_t fid, int slot, FaceSeg& F) {
+    int x, y, z;
+    vid_xyz(g, fid / 3u, &x, &y, &z);
+    int a = (int)(fid % 3u);
+    int b = nxt3(a), c = prv3(a);
+    int lab4 = 0;
+    for (int i = 0; i < 4; ++i) {
+        int p[3] = {x, y, z};
+        if (i == 1 || i == 2) p[b] += 1;
+        if (i >= 2) p[c] += 1;
+        lab4 |= (int)label_at(g, bits, p[0], p[1], p[2]) << i;
+    }
+    int seg[2][2];
+    face_segments(lab4, flip_at(g, flips, a, x, y, z), seg);
+    int fe1 = seg[slot][0], fe2 = seg[slot][1];
+    F.a = a;
+    F.b = b;
+    F.c = c;
+    F.q[0] = x;
+    F.q[1] = y;
+    F.q[2] = z;
+    int ex, ey, ez, ea;
+    face_edge_global(F, fe1, &ex, &ey, &ez, &ea);
+    uint32_t T1 = T[edge_rank(g, wi, ebase, ex, ey, ez, ea)];
+    face_edge_global(F, fe2, &ex, &ey, &ez, &ea);
+    uint32_t T2 = T[edge_rank(g, wi, ebase, ex, ey, ez, ea)];
+    face_setup(F, a, x, y, z, lab4, fe1, fe2, T1, T2, k);
+}
+
 }  // namespace odc

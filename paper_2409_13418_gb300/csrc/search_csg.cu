@@ -64,37 +64,6 @@ __device__ __forceinline__ uint32_t lbs(const GridDev& g, const FaceSeg& F, cons
     return Ja;
 }
 
-__device__ __forceinline__ void load_face(const GridDev& g, const uint32_t* bits, const uint32_t* flips,
-                                          const WordInfo* wi, const uint32_t* ebase, const uint32_t* T, int k,
-                                          uint32_t fid, int slot, FaceSeg& F) {
-    int x, y, z;
-    vid_xyz(g, fid / 3u, &x, &y, &z);
-    int a = (int)(fid % 3u);
-    int b = nxt3(a), c = prv3(a);
-    int lab4 = 0;
-    for (int i = 0; i < 4; ++i) {
-        int p[3] = {x, y, z};
-        if (i == 1 || i == 2) p[b] += 1;
-        if (i >= 2) p[c] += 1;
-        lab4 |= (int)label_at(g, bits, p[0], p[1], p[2]) << i;
-    }
-    int seg[2][2];
-    face_segments(lab4, flip_at(g, flips, a, x, y, z), seg);
-    int fe1 = seg[slot][0], fe2 = seg[slot][1];
-    F.a = a;
-    F.b = b;
-    F.c = c;
-    F.q[0] = x;
-    F.q[1] = y;
-    F.q[2] = z;
-    int ex, ey, ez, ea;
-    face_edge_global(F, fe1, &ex, &ey, &ez, &ea);
-    uint32_t T1 = T[edge_rank(g, wi, ebase, ex, ey, ez, ea)];
-    face_edge_global(F, fe2, &ex, &ey, &ez, &ea);
-    uint32_t T2 = T[edge_rank(g, wi, ebase, ex, ey, ez, ea)];
-    face_setup(F, a, x, y, z, lab4, fe1, fe2, T1, T2, k);
-}
-
 __global__ void k_face_csg(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ flips,
                            const WordInfo* __restrict__ wi, const uint32_t* __restrict__ ebase,
                            const uint32_t* __restrict__ T, const uint32_t* __restrict__ faces,
@@ -135,14 +104,14 @@ void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, co
                        uint8_t* labels, cudaStream_t st) {
     if (n <= 0) return;
     CsgOcc occ{prims, cull, n_prims};
-    k_csg_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(occ, pts, n, labels);
+    k_csg_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(occ, pts, n, labels); note_launch();
 }
 
 void launch_bisect_csg(const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
                        const PrimDev* prims, const float4* cull, int n_prims, uint32_t* T, cudaStream_t st) {
     if (!ne) return;
     CsgOcc occ{prims, cull, n_prims};
-    k_bisect_csg<<<(ne + 127) / 128, 128, 0, st>>>(g, bits, edges, ne, k, occ, T);
+    k_bisect_csg<<<(ne + 127) / 128, 128, 0, st>>>(g, bits, edges, ne, k, occ, T); note_launch();
 }
 
 void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
@@ -152,7 +121,7 @@ void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* fli
     if (!nf) return;
     CsgOcc occ{prims, cull, n_prims};
     k_face_csg<<<(nf + 127) / 128, 128, 0, st>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp, occ, pf,
-                                                  flags);
+                                                  flags); note_launch();
 }
 
 }  // namespace odc

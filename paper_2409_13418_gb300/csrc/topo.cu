@@ -63,17 +63,17 @@ __global__ void k_cells(GridDev g, const uint32_t* __restrict__ flips, const uin
 
 void launch_manifold_mark(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const uint32_t* faces,
                           const uint8_t* slots, uint32_t nf, uint8_t* mark, uint32_t* counter, cudaStream_t st) {
-    if (nf) k_manifold_mark<<<(nf + 255) / 256, 256, 0, st>>>(g, bits, flips, faces, slots, nf, mark, counter);
+    if (nf) { k_manifold_mark<<<(nf + 255) / 256, 256, 0, st>>>(g, bits, flips, faces, slots, nf, mark, counter); note_launch(); }
 }
 
 void launch_manifold_apply(const GridDev& g, uint32_t* flips, const uint32_t* faces, const uint8_t* mark, uint32_t nf,
                            cudaStream_t st) {
-    if (nf) k_manifold_apply<<<(nf + 255) / 256, 256, 0, st>>>(g, flips, faces, mark, nf);
+    if (nf) { k_manifold_apply<<<(nf + 255) / 256, 256, 0, st>>>(g, flips, faces, mark, nf); note_launch(); }
 }
 
 void launch_cells(const GridDev& g, const uint32_t* flips, const uint32_t* cells, const uint8_t* configs, uint32_t nc,
                   unsigned long long* cyc, uint32_t* ncyc, cudaStream_t st) {
-    if (nc) k_cells<<<(nc + 255) / 256, 256, 0, st>>>(g, flips, cells, configs, nc, cyc, ncyc);
+    if (nc) { k_cells<<<(nc + 255) / 256, 256, 0, st>>>(g, flips, cells, configs, nc, cyc, ncyc); note_launch(); }
 }
 
 }  // namespace odc

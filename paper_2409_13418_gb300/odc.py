@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libodc.so")
 ODC_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
           5: "unsupported", 6: "internal error"}
-SRC_CSG, SRC_MLP = 0, 1
+SRC_CSG, SRC_MLP, SRC_RESIDENT = 0, 1, 2
 PREC_FP32, PREC_BF16 = 0, 1
 DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
            cycles=9, vlocal=10, qcase=11, flips=12)
@@ -59,7 +59,8 @@ class Stats(C.Structure):
     _fields_ = [("n_edges", C.c_int64), ("n_face_segs", C.c_int64), ("n_cells", C.c_int64),
                 ("n_verts3", C.c_int64), ("n_case3", C.c_int64), ("n_flips", C.c_int64),
                 ("fix_rounds", C.c_int64), ("n_queries", C.c_int64), ("n_requeries", C.c_int64),
-                ("stage_ms", C.c_float * 8)]
+                ("stage_ms", C.c_float * 8), ("mlp_flops", C.c_double), ("mlp_ms", C.c_float),
+                ("n_launches", C.c_int32), ("mlp_launches", C.c_int64)]
 
 
 class MeshC(C.Structure):
@@ -67,8 +68,13 @@ class MeshC(C.Structure):
                 ("stats", Stats)]
 
 
+def launch_total() -> int:
+    """Kernel launches issued by the library so far (all contexts)."""
+    return int(load().odc_launch_count())
+
+
 EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
-           "odc_debug_copy", "odc_eval_points", "odc_status_str", "odc_last_error"]
+           "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_status_str", "odc_last_error"]
 
 _lib = None
 
@@ -89,11 +95,14 @@ def load(path: str = LIB_PATH):
     lib.odc_mesh_release.argtypes = [P, C.POINTER(MeshC)]
     lib.odc_debug_copy.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
     lib.odc_eval_points.argtypes = [P, C.POINTER(Source), P, C.c_int64, C.c_float, C.c_int, P, P]
+    lib.odc_source_upload.argtypes = [P, C.POINTER(Source)]
+    lib.odc_launch_count.restype = C.c_int64
+    lib.odc_launch_count.argtypes = []
     lib.odc_status_str.restype = C.c_char_p
     lib.odc_status_str.argtypes = [C.c_int]
     lib.odc_last_error.restype = C.c_char_p
     for f in ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
-              "odc_debug_copy", "odc_eval_points"]:
+              "odc_debug_copy", "odc_eval_points", "odc_source_upload"]:
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -120,7 +129,9 @@ class _SourceHolder:
     def __init__(self, src, precision=None, band=None):
         self.keep = []
         self.src = Source()
-        if isinstance(src, I.CSGSource):
+        if src is None:
+            self.src.kind = SRC_RESIDENT
+        elif isinstance(src, I.CSGSource):
             rec = np.zeros(src.n_prims, dtype=np.dtype([("type", "<i4"), ("op", "<i4"), ("center", "<f4", 3),
                                                          ("rot", "<f4", 9), ("params", "<f4", 4),
                                                          ("pad", "<f4", 2)]))
@@ -225,7 +236,13 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
+    def upload(self, src, precision=None, band=None):
+        """Make ``src`` the context's resident source (``extract(None, ...)`` reuses it)."""
+        holder = _SourceHolder(src, precision, band)
+        _check(_lib.odc_source_upload(self.h, C.byref(holder.src)))
+
     def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, **kw) -> Mesh:
+        """Run ODC; ``src=None`` reuses the resident source."""
         holder = _SourceHolder(src, precision, band)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
