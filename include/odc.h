@@ -236,6 +236,31 @@ odc_status odc_debug_copy(odc_ctx* ctx, int what, void* dst, size_t max_bytes,
 odc_status odc_eval_points(odc_ctx* ctx, const odc_source* src, const float* points, int64_t n,
                            float iso, int precision, uint8_t* labels, float* logits);
 
+/* List the crossing edges of a label bitmask without allocating any memory.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc (inside a stream capture that must not gain allocation nodes,
+ * allocator-free hosts, plug-ins whose host owns all device memory).  It
+ * computes what the compaction stage of odc_extract computes for edges.
+ *   d_label_bits: device, uint32 label rows [res2+1][res1+1][ceil((res0+1)/32)]
+ *                 as returned for ODC_DBG_LABELS (bit x of word x/32 = vertex x).
+ *   res:          host, cells per axis (1..1024); the grid may hold at most
+ *                 520,000 label words (e.g. 240^3 cells: 464,648 words).
+ *   d_edges:      device, caller-owned, room for max_edges uint32 edge ids
+ *                 (3 v + a, ascending); ids beyond max_edges are not written.
+ *   d_count:      device uint32, receives the number of crossing edges.
+ *   h_count:      optional host uint32; when given, the call synchronises the
+ *                 stream, stores the count and returns ODC_ERR_OOM if it
+ *                 exceeds max_edges.
+ *   cuda_stream:  cudaStream_t (NULL: the legacy default stream).
+ * Scratch lives in a 4 MiB file-scope device array that every GPU loading
+ * the library keeps until exit.  The first call on each device looks up its
+ * address (make that first call before any stream capture).  All calls on a
+ * device share the array: calls that overlap on the GPU race.  Grids above
+ * the limit return ODC_ERR_INVALID_ARG; nothing is allocated on any path. */
+odc_status odc_compact_edges_noalloc(const uint32_t* d_label_bits, const int32_t res[3], uint32_t* d_edges,
+                                     uint32_t max_edges, uint32_t* d_count, uint32_t* h_count,
+                                     void* cuda_stream);
+
 /* Number of CUDA kernel launches the library has issued since it was loaded
  * (all contexts and threads); lets a caller count the kernels of a region. */
 int64_t odc_launch_count(void);

@@ -52,6 +52,8 @@ size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
+void odc::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct odc_ctx {
     int device = 0;
     size_t budget = 0;

@@ -4,7 +4,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace odc {
+
+// Message returned by odc_last_error() for the calling thread.
+void set_last_error(const std::string& msg);
 
 enum { PRIM_SPHERE = 0, PRIM_AABB = 1, PRIM_OBOX = 2, PRIM_CYLINDER = 3, PRIM_TORUS = 4 };
 enum { OP_UNION = 0, OP_DIFFERENCE = 1 };

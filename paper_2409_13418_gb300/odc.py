@@ -74,7 +74,8 @@ def launch_total() -> int:
 
 
 EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
-           "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_status_str", "odc_last_error"]
+           "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_compact_edges_noalloc", "odc_status_str",
+           "odc_last_error"]
 
 _lib = None
 
@@ -96,6 +97,9 @@ def load(path: str = LIB_PATH):
     lib.odc_debug_copy.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
     lib.odc_eval_points.argtypes = [P, C.POINTER(Source), P, C.c_int64, C.c_float, C.c_int, P, P]
     lib.odc_source_upload.argtypes = [P, C.POINTER(Source)]
+    lib.odc_compact_edges_noalloc.argtypes = [P, C.POINTER(C.c_int32), P, C.c_uint32, P,
+                                              C.POINTER(C.c_uint32), P]
+    lib.odc_compact_edges_noalloc.restype = C.c_int
     lib.odc_launch_count.restype = C.c_int64
     lib.odc_launch_count.argtypes = []
     lib.odc_status_str.restype = C.c_char_p
@@ -188,6 +192,19 @@ def make_params(steps_1d=15, iso=0.5, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=
     p.s2d_lin2, p.s2d_bin2, p.s2d_range2 = lin2, bin2, range2
     p.ic_split = int(bool(ic_split))
     return p
+
+
+def compact_edges_noalloc(d_label_bits: int, res, d_edges: int, max_edges: int, d_count: int,
+                          stream: int | None = None) -> int:
+    """Crossing edges of a device label bitmask with no allocation (odc_compact_edges_noalloc).
+
+    All pointers are device addresses owned by the caller; returns the edge
+    count (the call synchronises ``stream`` to read it back).
+    """
+    r = (C.c_int32 * 3)(*[int(x) for x in res])
+    h = C.c_uint32()
+    _check(load().odc_compact_edges_noalloc(d_label_bits, r, d_edges, max_edges, d_count, C.byref(h), stream))
+    return int(h.value)
 
 
 class Mesh:
