@@ -214,7 +214,8 @@ odc_status odc_mesh_release(odc_ctx* ctx, odc_mesh* mesh);
  *   ODC_DBG_T          uint32 1D results T (odd; point = T / 2^(k+1) along the edge)
  *   ODC_DBG_FACES      uint32 face ids of the 2D points (sorted with slots)
  *   ODC_DBG_SLOTS      uint8 segment slot of each 2D point
- *   ODC_DBG_FACE_PTS   float2 face-local (u, v) of each 2D point
+ *   ODC_DBG_FACE_PTS   float4 face-local 2D point as float-float pairs
+ *                      (u_hi, u_lo, v_hi, v_lo): u = u_hi + u_lo
  *   ODC_DBG_FACE_FLAGS uint8 bit0: q == m, bit1: parallel lines
  *   ODC_DBG_CELLS      uint32 crossing cell ids (sorted)
  *   ODC_DBG_CONFIGS    uint8 cell configurations
@@ -222,10 +223,15 @@ odc_status odc_mesh_release(odc_ctx* ctx, odc_mesh* mesh);
  *   ODC_DBG_VLOCAL     float3 cell-local 3D points
  *   ODC_DBG_QCASE      uint8 per crossing edge: 0 no quad, 1/2/3 split case
  *   ODC_DBG_FLIPS      uint32 ids of faces flipped by the manifold fix (sorted)
+ *   ODC_DBG_SEARCH     16 bytes per 2D point: uint32 Jq, J1, J2 (near-end
+ *                      parameters of the three line-binary searches, sample
+ *                      s = R J / (N 2^b)), uint8 label of m, uint8 found
+ *                      (bit0 step 1, bit1 ray r1, bit2 ray r2 met a label
+ *                      change in their linear phase), 2 pad bytes
  */
 enum { ODC_DBG_LABELS = 0, ODC_DBG_EDGES, ODC_DBG_T, ODC_DBG_FACES, ODC_DBG_SLOTS,
        ODC_DBG_FACE_PTS, ODC_DBG_FACE_FLAGS, ODC_DBG_CELLS, ODC_DBG_CONFIGS,
-       ODC_DBG_CYCLES, ODC_DBG_VLOCAL, ODC_DBG_QCASE, ODC_DBG_FLIPS, ODC_DBG_COUNT };
+       ODC_DBG_CYCLES, ODC_DBG_VLOCAL, ODC_DBG_QCASE, ODC_DBG_FLIPS, ODC_DBG_SEARCH, ODC_DBG_COUNT };
 odc_status odc_debug_copy(odc_ctx* ctx, int what, void* dst, size_t max_bytes,
                           int64_t* count, int32_t* elem_bytes);
 

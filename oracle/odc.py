@@ -114,6 +114,7 @@ class Result:
     quad_margin: np.ndarray
     queries: int = 0
     stats: dict = field(default_factory=dict)
+    search: dict = field(default_factory=dict)   # 2D decisions: Jq, J1, J2, lab_m, found
 
 
 def grid_coords(grid):
@@ -300,8 +301,18 @@ def topology_triangles(labels):
 
 
 def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12,
-            range2=float(np.float32(math.sqrt(2.0) / 2.0)), iso=0.5, ic_split=True) -> Result:
-    """Run ODC on ``src`` (a CSG/MLP source or a callable) over ``grid``."""
+            range2=float(np.float32(math.sqrt(2.0) / 2.0)), iso=0.5, ic_split=True,
+            replay=None, replay_margin=0.0) -> Result:
+    """Run ODC on ``src`` (a CSG/MLP source or a callable) over ``grid``.
+
+    ``replay`` (optional) supplies the search decisions of another
+    implementation instead of taking them from phi: ``T`` (1D results) and
+    the 2D decisions ``Jq, J1, J2, lab_m, found``.  Every replayed decision is
+    still checked against phi here: a replayed label that disagrees with phi
+    where phi's margin is at least ``replay_margin`` is a violation, counted
+    per element in ``stats['edge_violations']`` / ``stats['face_violations']``.
+    All geometry downstream is then computed from the replayed decisions.
+    """
     phi = Occupancy(src, iso)
     geo = _Geo(grid.res)
     N, NV = geo.N, geo.NV
@@ -401,13 +412,21 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
         edge_margin = np.minimum(edge_margin, label_margin[up[:, 2], up[:, 1], up[:, 0]])
     lo = np.zeros(E)
     width = 1.0
-    for _ in range(k1):
+    edge_viol = np.zeros(E, bool)
+    if replay is not None:
+        lo_rep = (np.asarray(replay["T"], np.int64) - 1) // 2      # k-bit low end of the final interval
+    for step in range(k1):
         mid = lo + width / 2.0
         q = x_lo.copy()
         q[np.arange(E), ea] = x_lo[np.arange(E), ea] + span * mid
         lab, mar = phi(q)
         edge_margin = np.minimum(edge_margin, mar)
-        lo = np.where(lab == lab0, mid, lo)
+        same = lab == lab0
+        if replay is not None:
+            rep_same = ((lo_rep >> (k1 - 1 - step)) & 1).astype(bool)
+            edge_viol |= (rep_same != same) & (mar >= replay_margin)
+            same = rep_same
+        lo = np.where(same, mid, lo)
         width /= 2.0
     T = (2 * np.round(lo * (1 << k1)).astype(np.int64) + 1) if E else np.zeros(0, np.int64)
     tau = T / float(1 << (k1 + 1))
@@ -469,55 +488,96 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
 
     face_margin = seg_margin.copy()
 
+    face_viol = np.zeros(F, bool)
+
     def query(uv, active):
         lab = np.zeros(F, bool)
+        mar_out = np.full(F, np.inf)
         if active.any():
             l, mar = phi(face_world(uv[active], np.nonzero(active)[0]))
             lab[active] = l
+            mar_out[active] = mar
             face_margin[active] = np.minimum(face_margin[active], mar)
-        return lab
+        return lab, mar_out
 
-    def lbs(p, d, R, n, b, lab0, active):
-        """Line-binary search (A.1.3); returns the integer J of the near end."""
+    def lbs(p, d, R, n, b, lab0, active, rep=None):
+        """Line-binary search (A.1.3); returns the integer J of the near end.
+
+        ``rep = (J, found)`` replays another run's result: the first line
+        sample with a label change is J // 2^b + 1 when ``found`` (else the
+        last sample keeps p's label), and the bits of J below 2^b are the
+        bisection decisions, most significant first (1: kept p's label).
+        """
+        nonlocal face_viol
         denom = float(n * (1 << b))
         first = np.full(F, n, np.int64)
         found = np.zeros(F, bool)
+        if rep is not None:
+            Jr, fr = np.asarray(rep[0], np.int64), np.asarray(rep[1], bool)
+            first_r = np.where(fr, (Jr >> b) + 1, n)
         for i in range(1, n + 1):
             s = R * (i * (1 << b)) / denom
-            act = active & ~found
-            lab = query(p + s * d, act)
-            hit = act & (lab != lab0)
+            if rep is None:
+                act = active & ~found
+                lab, _ = query(p + s * d, act)
+                hit = act & (lab != lab0)
+            else:
+                act = active & (i <= first_r)
+                lab, mar = query(p + s * d, act)
+                hit = act & (i == first_r) & fr
+                face_viol |= act & ((lab != lab0) != hit) & (mar >= replay_margin)
             first[hit] = i
             found |= hit
+        if rep is not None:
+            first = np.where(active, first_r, first)
         Ja = (first - 1) * (1 << b)
         Jc = first * (1 << b)
-        for _ in range(b):
+        for t in range(b):
             Jm = (Ja + Jc) // 2
             s = R * Jm.astype(np.float64) / denom
-            lab = query(p + s[:, None] * d, active)
+            lab, mar = query(p + s[:, None] * d, active)
             same = lab == lab0
+            if rep is not None:
+                rep_same = (((Jr - (first - 1) * (1 << b)) >> (b - 1 - t)) & 1).astype(bool)
+                face_viol |= active & (rep_same != same) & (mar >= replay_margin)
+                same = rep_same
             Ja = np.where(active & same, Jm, Ja)
             Jc = np.where(active & ~same, Jm, Jc)
+        lbs.found = found
         return Ja, denom
 
     flags = np.zeros(F, np.int64)
     pf = np.zeros((F, 2))
+    search = dict(Jq=np.zeros(0, np.int64), J1=np.zeros(0, np.int64), J2=np.zeros(0, np.int64),
+                  lab_m=np.zeros(0, bool), found=np.zeros(0, np.int64))
     if F:
         allf = np.ones(F, bool)
         m = (P1 + P2) / 2.0
-        lab_m = query(m, allf)
+        lab_m, mar_m = query(m, allf)
+        if replay is not None:
+            rlab = np.asarray(replay["lab_m"], bool)
+            face_viol |= (rlab != lab_m) & (mar_m >= replay_margin)
+            lab_m = rlab
+            rfound = np.asarray(replay["found"], np.int64)
         d0 = np.stack([-(P2[:, 1] - P1[:, 1]), P2[:, 0] - P1[:, 0]], axis=1)
         sig = np.sign(d0[:, 0] * in_w[:, 0] + d0[:, 1] * in_w[:, 1])
         d_in = sig[:, None] * d0 / np.linalg.norm(d0, axis=1)[:, None]
         d = np.where(lab_m[:, None], -d_in, d_in)
-        Jq, den1 = lbs(m, d, range1, lin1, bin1, lab_m, allf)
+        Jq, den1 = lbs(m, d, range1, lin1, bin1, lab_m, allf,
+                       None if replay is None else (replay["Jq"], rfound & 1))
+        found_bits = lbs.found.astype(np.int64)
         qm = Jq == 0
         flags[qm] |= 1
         q = m + (range1 * Jq.astype(np.float64) / den1)[:, None] * d
         act = ~qm
         u1 = (P1 - P2) / np.linalg.norm(P1 - P2, axis=1)[:, None]
-        J1, den2 = lbs(q, u1, range2, lin2, bin2, lab_m, act)
-        J2, _ = lbs(q, -u1, range2, lin2, bin2, lab_m, act)
+        J1, den2 = lbs(q, u1, range2, lin2, bin2, lab_m, act,
+                       None if replay is None else (replay["J1"], (rfound >> 1) & 1))
+        found_bits |= (lbs.found & act).astype(np.int64) << 1
+        J2, _ = lbs(q, -u1, range2, lin2, bin2, lab_m, act,
+                    None if replay is None else (replay["J2"], (rfound >> 2) & 1))
+        found_bits |= (lbs.found & act).astype(np.int64) << 2
+        search = dict(Jq=Jq, J1=np.where(act, J1, 0), J2=np.where(act, J2, 0), lab_m=lab_m, found=found_bits)
         q1 = q + (range2 * J1.astype(np.float64) / den2)[:, None] * u1
         q2 = q - (range2 * J2.astype(np.float64) / den2)[:, None] * u1
         r1 = q1 - P1
@@ -680,6 +740,7 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
                   vertices=vertices, triangles=triangles,
                   quad_edges=quad_edges.astype(np.int64), quad_case=quad_case.astype(np.int64),
                   quad_flag=quad_flag.astype(bool), quad_margin=qmar,
-                  queries=phi.queries,
+                  queries=phi.queries, search=search,
                   stats=dict(E=E, F=F, C=C, V3=V3, case3=int(is3.sum()), flips=len(flips),
-                             fix_rounds=rounds, queries=phi.queries))
+                             fix_rounds=rounds, queries=phi.queries,
+                             edge_violations=int(edge_viol.sum()), face_violations=int(face_viol.sum())))

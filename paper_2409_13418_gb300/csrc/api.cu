@@ -73,7 +73,8 @@ struct odc_ctx {
     uint32_t E = 0, F = 0, C = 0, V3 = 0, NT = 0, N3 = 0, nflip = 0;
     uint32_t *bits = nullptr, *flips = nullptr, *edges = nullptr, *T = nullptr, *faces = nullptr, *cells = nullptr;
     uint8_t *slots = nullptr, *fflags = nullptr, *configs = nullptr, *qcase = nullptr;
-    float2* pf = nullptr;
+    float4* pf = nullptr;
+    FaceDecisions* dec = nullptr;
     unsigned long long* cycles = nullptr;
     float3 *vlocal = nullptr, *vworld = nullptr;
     int3* tris = nullptr;
@@ -342,7 +343,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
 
     // ---- count-sized buffers
     size_t stmpB = scan_tmp_elems(std::max<size_t>(std::max(E, C), 1));
-    size_t needB = 2 * al(E * 4ull) + al(F * 4ull) + 3 * al(F) + al(F * 8ull) + al(C * 4ull) + al(C) + al(C * 8ull) +
+    size_t needB = 2 * al(E * 4ull) + al(F * 4ull) + 3 * al(F) + al(F * 16ull) + al(F * sizeof(FaceDecisions)) + al(C * 4ull) + al(C) + al(C * 8ull) +
                    2 * al(C * 4ull) + al(4ull * C * 12) + al((4ull * C + E) * 12) + al(E) + al(E * 16ull) +
                    2 * al(E * 8ull) + al(4ull * E * 12) + al(stmpB * 8) + 1024;
     s = arena_ensure(c, c->B, needB);
@@ -353,7 +354,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     uint8_t* slots = (uint8_t*)c->B.take(F);
     uint8_t* fflags = (uint8_t*)c->B.take(F);
     uint8_t* mark = (uint8_t*)c->B.take(F);
-    float2* pf = (float2*)c->B.take(F * 8ull);
+    float4* pf = (float4*)c->B.take(F * 16ull);
+    FaceDecisions* dec = (FaceDecisions*)c->B.take(F * sizeof(FaceDecisions));
     uint32_t* cells = (uint32_t*)c->B.take(C * 4ull);
     uint8_t* configs = (uint8_t*)c->B.take(C);
     unsigned long long* cycles = (unsigned long long*)c->B.take(C * 8ull);
@@ -405,10 +407,10 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     // ---- a5: 2D search
     if (kind == ODC_SRC_CSG) {
         launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, n_prims, pf, fflags,
-                        st);
+                        dec, st);
     } else {
-        s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, st, &nq, &nrq,
-                      &g_err);
+        s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, dec, st, &nq,
+                      &nrq, &g_err);
         if (s != ODC_OK) return s;
     }
     ODC_CK(cudaGetLastError());
@@ -435,7 +437,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     c->k = prm->steps_1d;
     c->E = E; c->F = F; c->C = C; c->V3 = V3; c->NT = NT; c->N3 = N3; c->nflip = nflip;
     c->bits = bits; c->flips = flips; c->edges = edges; c->T = T; c->faces = faces; c->cells = cells;
-    c->slots = slots; c->fflags = fflags; c->configs = configs; c->qcase = qcase; c->pf = pf; c->cycles = cycles;
+    c->slots = slots; c->fflags = fflags; c->configs = configs; c->qcase = qcase; c->pf = pf; c->dec = dec; c->cycles = cycles;
     c->vlocal = vlocal; c->vworld = vworld; c->tris = tris; c->nw = nw;
 
     out->n_verts = (int64_t)V3 + N3;
@@ -494,13 +496,14 @@ odc_status odc_debug_copy(odc_ctx* c, int what, void* dst, size_t max_bytes, int
         case ODC_DBG_T: p = c->T; n = c->E; eb = 4; break;
         case ODC_DBG_FACES: p = c->faces; n = c->F; eb = 4; break;
         case ODC_DBG_SLOTS: p = c->slots; n = c->F; eb = 1; break;
-        case ODC_DBG_FACE_PTS: p = c->pf; n = c->F; eb = 8; break;
+        case ODC_DBG_FACE_PTS: p = c->pf; n = c->F; eb = 16; break;
         case ODC_DBG_FACE_FLAGS: p = c->fflags; n = c->F; eb = 1; break;
         case ODC_DBG_CELLS: p = c->cells; n = c->C; eb = 4; break;
         case ODC_DBG_CONFIGS: p = c->configs; n = c->C; eb = 1; break;
         case ODC_DBG_CYCLES: p = c->cycles; n = c->C; eb = 8; break;
         case ODC_DBG_VLOCAL: p = c->vlocal; n = c->V3; eb = 12; break;
         case ODC_DBG_QCASE: p = c->qcase; n = c->E; eb = 1; break;
+        case ODC_DBG_SEARCH: p = c->dec; n = c->F; eb = (int)sizeof(FaceDecisions); break;
         case ODC_DBG_FLIPS: {
             // expand the flip bit planes into sorted face ids
             std::vector<uint32_t> h(3 * c->nw);

@@ -33,13 +33,13 @@ void launch_bisect_csg(const GridDev& g, const uint32_t* bits, const uint32_t* e
 void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
                      const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
                      uint32_t nf, const SearchParams& sp, const PrimDev* prims, const float4* cull, int n_prims,
-                     float2* pf, uint8_t* flags, cudaStream_t st);
+                     float4* pf, uint8_t* flags, FaceDecisions* dec, cudaStream_t st);
 void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, const float3* pts, int64_t n,
                        uint8_t* labels, cudaStream_t st);
 
 // qef.cu
 void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, const uint32_t* ebase,
-                const uint32_t* fbase, const uint32_t* T, const float2* pf, const uint32_t* cells,
+                const uint32_t* fbase, const uint32_t* T, const float4* pf, const uint32_t* cells,
                 const uint8_t* configs, const unsigned long long* cycles, const uint32_t* vbase, uint32_t nc, int k,
                 float3* vlocal, float3* vworld, cudaStream_t st);
 

@@ -42,8 +42,8 @@ odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, cons
 // 2D search (a5) in wavefronts over all face segments.
 odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
                      const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
-                     uint32_t nf, const SearchParams& sp, float iso, float2* pf, uint8_t* flags, cudaStream_t s,
-                     int64_t* nq, int64_t* nrq, std::string* err);
+                     uint32_t nf, const SearchParams& sp, float iso, float4* pf, uint8_t* flags, FaceDecisions* dec,
+                     cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err);
 // Start / finish the per-extract accounting of network launches: total
 // event-timed kernel milliseconds and algorithmic FLOPs.
 void mlp_timing_begin(MlpState* st);

@@ -50,6 +50,15 @@ static_assert(sizeof(PrimDev) == 80, "PrimDev must match odc_csg_prim");
 void note_launch();
 long long launch_count();
 
+// Decisions of one 2D search (exported for parity checks): the near-end
+// parameters J of the three line-binary searches, the label of m, and
+// whether each linear phase met a label change (bit0 step 1, bit1 ray r1,
+// bit2 ray r2).
+struct FaceDecisions {
+    uint32_t Jq, J1, J2;
+    uint8_t lab_m, found, pad0, pad1;
+};
+
 struct SearchParams {
     int steps_1d;
     int lin1, bin1;

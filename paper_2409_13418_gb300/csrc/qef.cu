@@ -2,10 +2,11 @@
 // cycle (Eq. 2), one thread per crossing cell.
 //
 // For every crossing edge e of a cycle, the two faces of the cell that hold
-// e each carry the 2D point of the segment through e; the plane through p_e
-// and those two points has normal n = (p_f1 - p_e) x (p_f2 - p_e) (float32,
-// cell-local units).  The QEF sum_e (n_e . (p - p_e))^2 is accumulated in
-// FP64 as A = sum n n^T, b = sum n (n . p_e) and solved about the mass point
+// e each carry the 2D point of the segment through e (stored float-float);
+// the plane through p_e and those two points has normal n = (p_f1 - p_e) x
+// (p_f2 - p_e) in cell-local units.  Each normal is a row of the QEF normal
+// matrix and is formed in FP64 with it: QEF sum_e (n_e . (p - p_e))^2 is
+// accumulated as A = sum n n^T, b = sum n (n . p_e) and solved about the mass point
 // c of the cycle's 1D points: p = c + A^+ (b - A c), with A^+ the
 // pseudo-inverse keeping eigenvalues >= 0.01 of the largest (cyclic Jacobi
 // eigen-decomposition, FP64, in registers).
@@ -53,7 +54,7 @@ __device__ __forceinline__ void jacobi3(double a[3][3], double V[3][3], double w
 
 __global__ void k_qef(GridDev g, const uint32_t* __restrict__ flips, const WordInfo* __restrict__ wi,
                       const uint32_t* __restrict__ ebase, const uint32_t* __restrict__ fbase,
-                      const uint32_t* __restrict__ T, const float2* __restrict__ pf, const uint32_t* __restrict__ cells,
+                      const uint32_t* __restrict__ T, const float4* __restrict__ pf, const uint32_t* __restrict__ cells,
                       const uint8_t* __restrict__ configs, const unsigned long long* __restrict__ cycles,
                       const uint32_t* __restrict__ vbase, uint32_t nc, int k, float3* __restrict__ vlocal,
                       float3* __restrict__ vworld) {
@@ -77,26 +78,27 @@ __global__ void k_qef(GridDev g, const uint32_t* __restrict__ flips, const WordI
             int d0 = edge_corner0(le);
             int o[3] = {d0 & 1, (d0 >> 1) & 1, (d0 >> 2) & 1};
             uint32_t te = T[edge_rank(g, wi, ebase, cp[0] + o[0], cp[1] + o[1], cp[2] + o[2], a)];
-            float pe[3] = {(float)o[0], (float)o[1], (float)o[2]};
-            pe[a] = (float)te * inv;
-            float pfs[2][3];
+            double pe[3] = {(double)o[0], (double)o[1], (double)o[2]};
+            pe[a] = (double)te * (double)inv;
+            double pfs[2][3];
             for (int s = 0; s < 2; ++s) {
                 int f = s == 0 ? edge_face0(le) : edge_face1(le);
                 int fa = f >> 1, fs = f & 1;
                 int q[3] = {cp[0], cp[1], cp[2]};
                 q[fa] += fs;
                 int slot = face_slot_of(cfg, fm, f, le);
-                float2 uv = pf[face_rank(g, wi, fbase, q[0], q[1], q[2], fa, slot)];
-                pfs[s][fa] = (float)fs;
-                pfs[s][nxt3(fa)] = uv.x;
-                pfs[s][prv3(fa)] = uv.y;
+                float4 uv = pf[face_rank(g, wi, fbase, q[0], q[1], q[2], fa, slot)];
+                pfs[s][fa] = (double)fs;
+                pfs[s][nxt3(fa)] = (double)uv.x + (double)uv.y;
+                pfs[s][prv3(fa)] = (double)uv.z + (double)uv.w;
             }
-            float v1[3] = {pfs[0][0] - pe[0], pfs[0][1] - pe[1], pfs[0][2] - pe[2]};
-            float v2[3] = {pfs[1][0] - pe[0], pfs[1][1] - pe[1], pfs[1][2] - pe[2]};
-            float n[3] = {v1[1] * v2[2] - v1[2] * v2[1], v1[2] * v2[0] - v1[0] * v2[2], v1[0] * v2[1] - v1[1] * v2[0]};
-            for (int j = 0; j < 3; ++j) cs[j] += (double)pe[j];
+            // the plane's normal is a row of the QEF normal matrix: formed in FP64
+            double v1[3] = {pfs[0][0] - pe[0], pfs[0][1] - pe[1], pfs[0][2] - pe[2]};
+            double v2[3] = {pfs[1][0] - pe[0], pfs[1][1] - pe[1], pfs[1][2] - pe[2]};
+            double n[3] = {v1[1] * v2[2] - v1[2] * v2[1], v1[2] * v2[0] - v1[0] * v2[2], v1[0] * v2[1] - v1[1] * v2[0]};
+            for (int j = 0; j < 3; ++j) cs[j] += pe[j];
             ++cnt;
-            double nn = sqrt((double)n[0] * n[0] + (double)n[1] * n[1] + (double)n[2] * n[2]);
+            double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
             if (nn < 1e-12) continue;   // degenerate plane: dropped
             double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
             double dp = nh[0] * pe[0] + nh[1] * pe[1] + nh[2] * pe[2];
@@ -132,7 +134,7 @@ __global__ void k_qef(GridDev g, const uint32_t* __restrict__ flips, const WordI
 }
 
 void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, const uint32_t* ebase,
-                const uint32_t* fbase, const uint32_t* T, const float2* pf, const uint32_t* cells,
+                const uint32_t* fbase, const uint32_t* T, const float4* pf, const uint32_t* cells,
                 const uint8_t* configs, const unsigned long long* cycles, const uint32_t* vbase, uint32_t nc, int k,
                 float3* vlocal, float3* vworld, cudaStream_t st) {
     if (nc) { k_qef<<<(nc + 127) / 128, 128, 0, st>>>(g, flips, wi, ebase, fbase, T, pf, cells, configs, cycles, vbase,

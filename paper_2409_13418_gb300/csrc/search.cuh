@@ -108,9 +108,12 @@ __device__ __forceinline__ void face_setup(FaceSeg& F, int a, int x, int y, int 
     F.u1 = {ff_div(e.u, el), ff_div(e.v, el)};
 }
 
+// A 2D point as stored: float-float (u.hi, u.lo, v.hi, v.lo).
+__device__ __forceinline__ float4 ff2_pack(ff2 p) { return make_float4(p.u.hi, p.u.lo, p.v.hi, p.v.lo); }
+
 // Step 3 of the 2D search: intersection of lines (p_e1, q1) and (p_e2, q2);
 // parallel lines give m.  Returns flags bit1 when parallel.
-__device__ __forceinline__ float2 face_intersect(const FaceSeg& F, ff2 q1, ff2 q2, int* flags) {
+__device__ __forceinline__ float4 face_intersect(const FaceSeg& F, ff2 q1, ff2 q2, int* flags) {
     ff2 P1 = {ff_make(F.p1.x), ff_make(F.p1.y)}, P2 = {ff_make(F.p2.x), ff_make(F.p2.y)};
     ff2 r1 = ff2_sub(q1, P1), r2 = ff2_sub(q2, P2);
     ff det = ff_sub(ff_mul(r1.u, r2.v), ff_mul(r1.v, r2.u));
@@ -119,12 +122,12 @@ __device__ __forceinline__ float2 face_intersect(const FaceSeg& F, ff2 q1, ff2 q
     float dh = fabsf(det.hi);
     if (dh * dh <= 1e-18f * n1 * n2) {
         *flags |= 2;
-        return make_float2(F.m.u.hi, F.m.v.hi);
+        return ff2_pack(F.m);
     }
     ff2 dp = ff2_sub(P2, P1);
     ff alpha = ff_div(ff_sub(ff_mul(dp.u, r2.v), ff_mul(dp.v, r2.u)), det);
     ff2 pf = ff2_add(P1, ff2_scale(r1, alpha));
-    return make_float2(pf.u.hi, pf.v.hi);
+    return ff2_pack(pf);
 }
 
 // Load face segment (fid, slot): its corner labels and pairing, the two 1D

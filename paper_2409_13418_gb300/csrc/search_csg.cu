@@ -45,12 +45,14 @@ __global__ void k_bisect_csg(GridDev g, const uint32_t* __restrict__ bits, const
 // Line-binary search (A.1.3) from p along unit d: returns J of the near end.
 template <class Occ>
 __device__ __forceinline__ uint32_t lbs(const GridDev& g, const FaceSeg& F, const Occ& occ, ff2 p, ff2 d, float R,
-                                        int n, int b, uint32_t lab0) {
+                                        int n, int b, uint32_t lab0, bool* found) {
     int first = n;
+    *found = false;
     for (int i = 1; i <= n; ++i) {
         ff s = lbs_param(R, (uint32_t)i << b, n, b);
         if (occ(face_world2(g, F, ray_point(p, d, s))) != lab0) {
             first = i;
+            *found = true;
             break;
         }
     }
@@ -68,7 +70,7 @@ __global__ void k_face_csg(GridDev g, const uint32_t* __restrict__ bits, const u
                            const WordInfo* __restrict__ wi, const uint32_t* __restrict__ ebase,
                            const uint32_t* __restrict__ T, const uint32_t* __restrict__ faces,
                            const uint8_t* __restrict__ slots, uint32_t nf, SearchParams sp, CsgOcc occ,
-                           float2* __restrict__ pf, uint8_t* __restrict__ flags) {
+                           float4* __restrict__ pf, uint8_t* __restrict__ flags, FaceDecisions* __restrict__ dec) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     FaceSeg F;
@@ -76,22 +78,32 @@ __global__ void k_face_csg(GridDev g, const uint32_t* __restrict__ bits, const u
     uint32_t lab_m = occ(face_world2(g, F, F.m));
     ff2 d = lab_m ? ff2{ff_neg(F.d.u), ff_neg(F.d.v)} : F.d;
     int fl = 0;
-    uint32_t Jq = lbs(g, F, occ, F.m, d, sp.range1, sp.lin1, sp.bin1, lab_m);
-    float2 out;
+    bool f0 = false, f1 = false, f2 = false;
+    uint32_t Jq = lbs(g, F, occ, F.m, d, sp.range1, sp.lin1, sp.bin1, lab_m, &f0);
+    uint32_t J1 = 0, J2 = 0;
+    float4 out;
     if (Jq == 0) {
         fl |= 1;
-        out = make_float2(F.m.u.hi, F.m.v.hi);
+        out = ff2_pack(F.m);
     } else {
         ff2 q = ray_point(F.m, d, lbs_param(sp.range1, Jq, sp.lin1, sp.bin1));
         ff2 nu1 = {ff_neg(F.u1.u), ff_neg(F.u1.v)};
-        uint32_t J1 = lbs(g, F, occ, q, F.u1, sp.range2, sp.lin2, sp.bin2, lab_m);
-        uint32_t J2 = lbs(g, F, occ, q, nu1, sp.range2, sp.lin2, sp.bin2, lab_m);
+        J1 = lbs(g, F, occ, q, F.u1, sp.range2, sp.lin2, sp.bin2, lab_m, &f1);
+        J2 = lbs(g, F, occ, q, nu1, sp.range2, sp.lin2, sp.bin2, lab_m, &f2);
         ff2 q1 = ray_point(q, F.u1, lbs_param(sp.range2, J1, sp.lin2, sp.bin2));
         ff2 q2 = ray_point(q, nu1, lbs_param(sp.range2, J2, sp.lin2, sp.bin2));
         out = face_intersect(F, q1, q2, &fl);
     }
     pf[i] = out;
     flags[i] = (uint8_t)fl;
+    FaceDecisions D;
+    D.Jq = Jq;
+    D.J1 = J1;
+    D.J2 = J2;
+    D.lab_m = (uint8_t)lab_m;
+    D.found = (uint8_t)(f0 | (f1 << 1) | (f2 << 2));
+    D.pad0 = D.pad1 = 0;
+    dec[i] = D;
 }
 
 __global__ void k_csg_points(CsgOcc occ, const float3* __restrict__ pts, int64_t n, uint8_t* __restrict__ labels) {
@@ -117,11 +129,11 @@ void launch_bisect_csg(const GridDev& g, const uint32_t* bits, const uint32_t* e
 void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
                      const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
                      uint32_t nf, const SearchParams& sp, const PrimDev* prims, const float4* cull, int n_prims,
-                     float2* pf, uint8_t* flags, cudaStream_t st) {
+                     float4* pf, uint8_t* flags, FaceDecisions* dec, cudaStream_t st) {
     if (!nf) return;
     CsgOcc occ{prims, cull, n_prims};
     k_face_csg<<<(nf + 127) / 128, 128, 0, st>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp, occ, pf,
-                                                  flags); note_launch();
+                                                  flags, dec); note_launch();
 }
 
 }  // namespace odc

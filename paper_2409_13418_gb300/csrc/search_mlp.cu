@@ -108,7 +108,7 @@ struct FaceSt {
     FaceSeg F;
     ff2 d;        // step-1 ray (oriented by the label of m)
     ff2 q;        // step-1 result
-    uint32_t lab_m, Ja, Jc, J1a, J1c, J2a, J2c, pad;
+    uint32_t lab_m, Ja, Jc, J1a, J1c, J2a, J2c, found;
 };
 
 __global__ void k_face_init(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ flips,
@@ -146,8 +146,9 @@ __global__ void k_face_lin1(GridDev g, uint32_t nf, const float* __restrict__ z,
     if (i >= nf) return;
     FaceSt& st = S[i];
     int first = sp.lin1;
+    st.found = 0;
     for (int j = 1; j <= sp.lin1; ++j)
-        if ((uint32_t)(z[(size_t)(j - 1) * nf + i] > t) != st.lab_m) { first = j; break; }
+        if ((uint32_t)(z[(size_t)(j - 1) * nf + i] > t) != st.lab_m) { first = j; st.found = 1; break; }
     st.Ja = (uint32_t)(first - 1) << sp.bin1;
     st.Jc = (uint32_t)first << sp.bin1;
     if (sp.bin1 > 0)
@@ -166,13 +167,20 @@ __global__ void k_face_bin1(GridDev g, uint32_t nf, const float* __restrict__ z,
 }
 
 // end of step 1: q == m gives p_f = m; else keep q and mark the face active
-__global__ void k_face_fin1(uint32_t nf, SearchParams sp, FaceSt* __restrict__ S, float2* __restrict__ pf,
-                            uint8_t* __restrict__ flags, uint32_t* __restrict__ active) {
+__global__ void k_face_fin1(uint32_t nf, SearchParams sp, FaceSt* __restrict__ S, float4* __restrict__ pf,
+                            uint8_t* __restrict__ flags, uint32_t* __restrict__ active, FaceDecisions* __restrict__ dec) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     FaceSt& st = S[i];
+    FaceDecisions D;
+    D.Jq = st.Ja;
+    D.J1 = D.J2 = 0;
+    D.lab_m = (uint8_t)st.lab_m;
+    D.found = (uint8_t)st.found;
+    D.pad0 = D.pad1 = 0;
+    dec[i] = D;
     if (st.Ja == 0) {
-        pf[i] = make_float2(st.F.m.u.hi, st.F.m.v.hi);
+        pf[i] = ff2_pack(st.F.m);
         flags[i] = 1;
         active[i] = 0;
     } else {
@@ -214,7 +222,11 @@ __global__ void k_face_lin2(GridDev g, const uint32_t* __restrict__ list, uint32
     for (int r = 0; r < 2; ++r) {
         int first = sp.lin2;
         for (int j = 1; j <= sp.lin2; ++j)
-            if ((uint32_t)(z[(size_t)(r * sp.lin2 + j - 1) * na + li] > t) != st.lab_m) { first = j; break; }
+            if ((uint32_t)(z[(size_t)(r * sp.lin2 + j - 1) * na + li] > t) != st.lab_m) {
+                first = j;
+                st.found |= 2u << r;
+                break;
+            }
         Ja[r] = (uint32_t)(first - 1) << sp.bin2;
         Jc[r] = (uint32_t)first << sp.bin2;
         if (sp.bin2 > 0)
@@ -241,11 +253,15 @@ __global__ void k_face_bin2(GridDev g, const uint32_t* __restrict__ list, uint32
 }
 
 __global__ void k_face_fin2(const uint32_t* __restrict__ list, uint32_t na, SearchParams sp,
-                            const FaceSt* __restrict__ S, float2* __restrict__ pf, uint8_t* __restrict__ flags) {
+                            const FaceSt* __restrict__ S, float4* __restrict__ pf, uint8_t* __restrict__ flags,
+                            FaceDecisions* __restrict__ dec) {
     uint32_t li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= na) return;
     uint32_t i = list[li];
     const FaceSt& st = S[i];
+    dec[i].J1 = st.J1a;
+    dec[i].J2 = st.J2a;
+    dec[i].found = (uint8_t)st.found;
     ff2 q1 = ray_point(st.q, ray2(st, 0), lbs_param(sp.range2, st.J1a, sp.lin2, sp.bin2));
     ff2 q2 = ray_point(st.q, ray2(st, 1), lbs_param(sp.range2, st.J2a, sp.lin2, sp.bin2));
     int fl = 0;
@@ -255,8 +271,8 @@ __global__ void k_face_fin2(const uint32_t* __restrict__ list, uint32_t na, Sear
 
 odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
                      const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
-                     uint32_t nf, const SearchParams& sp, float iso, float2* pf, uint8_t* flags, cudaStream_t s,
-                     int64_t* nq, int64_t* nrq, std::string* err) {
+                     uint32_t nf, const SearchParams& sp, float iso, float4* pf, uint8_t* flags, FaceDecisions* dec,
+                     cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err) {
     if (!nf) return ODC_OK;
     const float t = mlp_logit_threshold(iso);
     size_t nmax = (size_t)nf * std::max(sp.lin1, 2 * sp.lin2);
@@ -287,7 +303,7 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
         S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, nrq, err));
         k_face_bin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, b, S, pts); note_launch();
     }
-    k_face_fin1<<<nblk(nf), 256, 0, s>>>(nf, sp, S, pf, flags, act); note_launch();
+    k_face_fin1<<<nblk(nf), 256, 0, s>>>(nf, sp, S, pf, flags, act, dec); note_launch();
     *nq += (int64_t)nf * (1 + sp.lin1 + sp.bin1);
     // faces still active after step 1
     exclusive_scan<uint32_t>(act, off, nf, tmp, cnt, s);
@@ -305,7 +321,7 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
         S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2, z, -1, s, nrq, err));
         k_face_bin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, b, S, pts); note_launch();
     }
-    k_face_fin2<<<nblk(na, 128), 128, 0, s>>>(list, na, sp, S, pf, flags); note_launch();
+    k_face_fin2<<<nblk(na, 128), 128, 0, s>>>(list, na, sp, S, pf, flags, dec); note_launch();
     S_CK(cudaGetLastError());
     *nq += (int64_t)na * 2 * (sp.lin2 + sp.bin2);
     return ODC_OK;

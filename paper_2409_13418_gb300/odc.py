@@ -22,11 +22,11 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
 SRC_CSG, SRC_MLP, SRC_RESIDENT = 0, 1, 2
 PREC_FP32, PREC_BF16 = 0, 1
 DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
-           cycles=9, vlocal=10, qcase=11, flips=12)
+           cycles=9, vlocal=10, qcase=11, flips=12, search=13)
 _DBG_DTYPE = dict(labels=np.uint32, edges=np.uint32, T=np.uint32, faces=np.uint32, slots=np.uint8,
                   face_pts=np.float32, face_flags=np.uint8, cells=np.uint32, configs=np.uint8,
-                  cycles=np.uint64, vlocal=np.float32, qcase=np.uint8, flips=np.uint32)
-_DBG_SHAPE = dict(face_pts=2, vlocal=3)
+                  cycles=np.uint64, vlocal=np.float32, qcase=np.uint8, flips=np.uint32, search=np.uint32)
+_DBG_SHAPE = dict(face_pts=4, vlocal=3, search=4)
 
 
 class Prim(C.Structure):
@@ -267,6 +267,18 @@ class Context:
         _check(_lib.odc_extract(self.h, C.byref(holder.src), C.byref(g), C.byref(p),
                                 stream if stream else None, C.byref(m)))
         return Mesh(self, m)
+
+    def face_points(self) -> np.ndarray:
+        """2D points of the last extract as float64 (u, v) (stored float-float)."""
+        r = self.debug("face_pts").astype(np.float64)
+        return np.stack([r[:, 0] + r[:, 1], r[:, 2] + r[:, 3]], axis=1)
+
+    def search_decisions(self) -> dict:
+        """2D search decisions of the last extract: Jq, J1, J2, lab_m, found."""
+        raw = self.debug("search")
+        b = raw[:, 3].copy().view(np.uint8).reshape(-1, 4)
+        return dict(Jq=raw[:, 0].astype(np.int64), J1=raw[:, 1].astype(np.int64), J2=raw[:, 2].astype(np.int64),
+                    lab_m=b[:, 0].astype(bool), found=b[:, 1].astype(np.int64))
 
     def debug(self, what: str) -> np.ndarray:
         n = C.c_int64()

@@ -58,7 +58,7 @@ def compare(ctx, mesh, ref, margin_eps=1e-12):
     assert not bad.any(), f"{int(bad.sum())} unflagged 1D results differ"
 
     # 2D points
-    pf = ctx.debug("face_pts").astype(np.float64)
+    pf = ctx.face_points()
     fflag = (ref.face_margin < margin_eps) | ((ref.face_flags & 4) != 0)
     rep["face_flagged"] = int(fflag.sum())
     gflags = ctx.debug("face_flags").astype(np.int64)

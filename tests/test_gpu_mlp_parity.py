@@ -1,9 +1,19 @@
-"""GPU-vs-oracle parity of the MLP occupancy path (FP32 network).
+"""GPU-vs-oracle parity of the MLP occupancy path, by decision replay.
 
-The FP32 network differs from the FP64 oracle by rounding only; every
-decision whose oracle margin |occ - 0.5| is below MARGIN (2e-5, i.e. |z| <
-8e-5, an order of magnitude above the measured FP32 logit error) is flagged,
-and elements fed by a flagged decision are excluded from the strict checks.
+Every ODC search ends next to the iso-surface, so its last decisions sit
+where the FP32 network (GPU) and the FP64 network (oracle) can legitimately
+disagree: the measured FP32 logit error is below 7e-6 (test below), while the
+logits at the final bisection steps are ~1e-4.  The comparison therefore
+splits what is unique from what is a valid choice:
+
+  * grid labels, crossing lists, configurations, flips, cycles: bit-exact;
+  * every search decision the GPU took (1D results T, 2D line-binary
+    results, labels of m) is replayed through the oracle and checked against
+    its FP64 label wherever the FP64 margin |occ - 0.5| >= MARGIN (2e-5, i.e.
+    |z| >= 8e-5, an order of magnitude above the FP32 error): no violation;
+  * given those decisions, everything downstream (2D points, normals, QEF 3D
+    points, quad splits, triangles) is unique: 2D points within 1e-5, 3D
+    points within 1e-4 cell, split cases and triangles bit-exact.
 """
 import numpy as np
 import pytest
@@ -39,19 +49,36 @@ def test_fp32_logits_match_fp64(ctx, mlp):
     zr = mlp_logit(mlp, pts.astype(np.float64))
     err = np.abs(z.astype(np.float64) - zr)
     print("max |z_fp32 - z_fp64|", err.max(), "median", np.median(err))
-    assert err.max() < 8e-5
-    sure = np.abs(zr) > 8e-5
+    assert err.max() < 2e-5
+    sure = np.abs(zr) > 2e-5
     assert np.array_equal(lab[sure], (zr > 0)[sure])
 
 
+def replay_parity(ctx, src, grid, k, precision=0, band=None):
+    mesh = ctx.extract(src, grid, steps_1d=k, precision=precision, band=band)
+    T = ctx.debug("T").astype(np.int64)
+    dec = ctx.search_decisions()
+    ref = oracle.extract(src, grid, steps_1d=k, replay=dict(T=T, **dec), replay_margin=MARGIN)
+    assert ref.stats["edge_violations"] == 0, ref.stats
+    assert ref.stats["face_violations"] == 0, ref.stats
+    rep, verts, tris = compare(ctx, mesh, ref, margin_eps=0.0)
+    own = oracle.extract(src, grid, steps_1d=k)
+    rep["T_choices_differing_from_fp64"] = int(np.sum(own.T != T)) if own.T.shape == T.shape else None
+    return mesh, ref, rep, verts, tris
+
+
 @pytest.mark.parametrize("n", [24, 40])
-def test_fp32_extract_parity(ctx, mlp, n):
-    g = I.cube_grid(n)
-    ref = oracle.extract(mlp, g, steps_1d=15)
-    mesh = ctx.extract(mlp, g, steps_1d=15)
-    rep, verts, tris = compare(ctx, mesh, ref, margin_eps=MARGIN)
+def test_fp32_extract_replay_parity(ctx, mlp, n):
+    mesh, ref, rep, verts, tris = replay_parity(ctx, mlp, I.cube_grid(n), 15)
     print(n, rep, ref.stats, mesh.stats)
+    assert rep["vert_max_err"] < 1e-4
     assert meshcheck.check_closed_manifold(tris)["ok"]
+
+
+def test_ragged_grid_replay_parity(ctx, mlp):
+    g = I.Grid((-0.71, -0.8, -0.66), (0.69, 0.75, 0.7), (37, 29, 33))
+    mesh, ref, rep, verts, tris = replay_parity(ctx, mlp, g, 12)
+    assert rep["vert_max_err"] < 1e-4
 
 
 def test_resident_source_gives_same_mesh(ctx, mlp):
@@ -60,3 +87,10 @@ def test_resident_source_gives_same_mesh(ctx, mlp):
     ctx.upload(mlp)
     v2, t2 = ctx.extract(None, g, steps_1d=12).to_host()
     assert np.array_equal(t1, t2) and np.array_equal(v1, v2)
+
+
+def test_csg_replay_parity_agrees_with_direct(ctx):
+    # the replay check also holds on the exact CSG path (no decision differs)
+    src = I.random_csg(3, n_prims=24)
+    mesh, ref, rep, verts, tris = replay_parity(ctx, src, I.cube_grid(48), 12)
+    assert rep["T_choices_differing_from_fp64"] == 0

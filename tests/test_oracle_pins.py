@@ -336,3 +336,25 @@ def test_query_points_are_fp32_rounded():
     # e + 1e-12 rounds to e itself (on the boundary: out); e - 1e-8 (more than
     # half an FP32 ulp of 0.1) rounds below e
     assert list(lab) == [False, True]
+
+
+def test_replay_of_own_decisions_is_exact_and_detects_planted_errors():
+    """Replaying the oracle's own decisions reproduces it with no violation;
+    a planted wrong decision (one flipped bisection bit, one flipped label of
+    m) is reported as a violation."""
+    src = I.random_csg(6, n_prims=10)
+    g = I.cube_grid(20)
+    r = odc.extract(src, g, steps_1d=10)
+    rep = dict(T=r.T, **r.search)
+    r2 = odc.extract(src, g, steps_1d=10, replay=rep, replay_margin=1e-12)
+    assert r2.stats["edge_violations"] == 0 and r2.stats["face_violations"] == 0
+    assert np.array_equal(r2.triangles, r.triangles)
+    assert np.array_equal(r2.face_pts, r.face_pts) and np.array_equal(r2.verts_local, r.verts_local)
+    bad = dict(rep)
+    bad["T"] = r.T.copy()
+    bad["T"][5] ^= 1 << 6                      # flip one bisection decision
+    bad["lab_m"] = r.search["lab_m"].copy()
+    bad["lab_m"][7] = ~bad["lab_m"][7]         # flip the label of one midpoint
+    r3 = odc.extract(src, g, steps_1d=10, replay=bad, replay_margin=1e-12)
+    assert r3.stats["edge_violations"] == 1
+    assert r3.stats["face_violations"] >= 1
