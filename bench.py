@@ -151,8 +151,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
-    ap.add_argument("--band", type=float, default=1e-3)
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16")
+    ap.add_argument("--band", type=float, default=0.02,
+                    help="|occ - 0.5| band re-evaluated in FP32 (covers the measured BF16 logit error)")
     ap.add_argument("--cpu-cells", type=int, default=None,
                     help="oracle sample block edge (default 40 for cpu_baseline, 32 per reference step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -201,6 +202,7 @@ def main():
     if world > 1:
         dist.barrier()
     mlp_ms, mlp_flops, mlp_launches, stats = 0.0, 0.0, 0, None
+    tc_ms, tc_flops, tc_launches = 0.0, 0.0, 0
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
@@ -210,6 +212,9 @@ def main():
         mlp_ms += stats["mlp_ms"]
         mlp_flops += stats["mlp_flops"]
         mlp_launches += stats["mlp_launches"]
+        tc_ms += stats["tc_ms"]
+        tc_flops += stats["tc_flops"]
+        tc_launches += stats["tc_launches"]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -242,19 +247,26 @@ def main():
 
     if rank == 0:
         peaks, peak_src = _peaks()
-        achieved = mlp_flops / (mlp_ms * 1e-3) / 1e12 if mlp_ms > 0 else None
-        if prec == odc.PREC_FP32:
-            peak = N_SM * FP32_FMA_PER_SM_CLK * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-            roof = {"bound": "alu", "kernel": "k_mlp_fp32 (FP32 FMA pipe)", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock (unit counts)",
-                    "flops_per_launch": mlp_flops / max(1, mlp_launches)}
-        else:
-            peak = float(peaks["bf16_tflops_sustained"])
-            roof = {"bound": "tensor", "kernel": "k_mlp_tc (tcgen05 BF16)", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
-                    "peak_source": f"bf16_tflops_sustained of {peak_src}",
-                    "flops_per_launch": mlp_flops / max(1, mlp_launches)}
+        fp32_peak = N_SM * FP32_FMA_PER_SM_CLK * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        tc_peak = float(peaks["bf16_tflops_sustained"])
+        rows = []
+        if mlp_launches:
+            a = mlp_flops / (mlp_ms * 1e-3) / 1e12
+            rows.append({"bound": "alu", "kernel": "k_mlp_fp32 (FP32 SIMT network; the plain path and the band "
+                                                   "re-evaluation)", "achieved": a, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": a / fp32_peak, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock (unit counts)",
+                         "ms_per_step": mlp_ms / args.steps, "flops_per_launch": mlp_flops / mlp_launches})
+        if tc_launches:
+            a = tc_flops / (tc_ms * 1e-3) / 1e12
+            rows.append({"bound": "tensor", "kernel": "k_mlp_tc (tcgen05 BF16 network)", "achieved": a,
+                         "peak": tc_peak, "unit": "TFLOP/s", "frac": a / tc_peak, "traffic": None,
+                         "peak_source": f"bf16_tflops_sustained, {peak_src}",
+                         "ms_per_step": tc_ms / args.steps, "flops_per_launch": tc_flops / tc_launches})
+        rows.sort(key=lambda r: -r["ms_per_step"])
+        roof = dict(rows[0])
+        if len(rows) > 1:
+            roof["other_kernels"] = rows[1:]
         line = {"metric": "ODC Mcells/s at 256^3", "value": value, "unit": "Mcells/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -163,10 +163,14 @@ typedef struct {
     int64_t n_queries;           /* occupancy evaluations on the main path */
     int64_t n_requeries;         /* FP32 re-evaluations inside the band */
     float stage_ms[8];           /* grid, compact, topology, 1D, 2D, QEF, quads, total */
-    double mlp_flops;            /* algorithmic FLOPs of the network launches (MLP sources) */
-    float mlp_ms;                /* CUDA-event time of the network launches */
+    double mlp_flops;            /* algorithmic FLOPs of the FP32 (SIMT) network launches */
+    float mlp_ms;                /* CUDA-event time of the FP32 network launches */
     int32_t n_launches;          /* kernel launches issued by this extract */
-    int64_t mlp_launches;        /* network kernel launches */
+    int64_t mlp_launches;        /* FP32 network launches */
+    double tc_flops;             /* algorithmic FLOPs of the BF16 tensor-core network launches */
+    float tc_ms;                 /* CUDA-event time of the tensor-core network launches */
+    int32_t pad_;
+    int64_t tc_launches;         /* tensor-core network launches */
 } odc_stats;
 
 typedef struct {

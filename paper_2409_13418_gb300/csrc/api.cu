@@ -450,7 +450,10 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&S.stage_ms[i], c->ev[i], c->ev[i + 1]);
     cudaEventElapsedTime(&S.stage_ms[7], c->ev[0], c->ev[7]);
     S.n_launches = (int32_t)(launch_count() - launches0);
-    if (kind == ODC_SRC_MLP) mlp_timing_collect(c->mlp, &S.mlp_ms, &S.mlp_flops, &S.mlp_launches);
+    if (kind == ODC_SRC_MLP) {
+        mlp_timing_collect(c->mlp, 0, &S.mlp_ms, &S.mlp_flops, &S.mlp_launches);
+        mlp_timing_collect(c->mlp, 1, &S.tc_ms, &S.tc_flops, &S.tc_launches);
+    }
     return ODC_OK;
 }
 

@@ -66,8 +66,9 @@ odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::st
     return ODC_OK;
 }
 
-cudaEvent_t* mlp_ev_pair(MlpState* st) {
+cudaEvent_t* mlp_ev_pair(MlpState* st, int kind) {
     if (st->ev_used >= 256) return nullptr;
+    st->ev_kind[st->ev_used] = kind;
     cudaEvent_t* p = &st->ev[2 * st->ev_used];
     if (!p[0]) {
         if (cudaEventCreate(&p[0]) != cudaSuccess || cudaEventCreate(&p[1]) != cudaSuccess) {
@@ -82,22 +83,23 @@ cudaEvent_t* mlp_ev_pair(MlpState* st) {
 void mlp_timing_begin(MlpState* st) {
     if (!st) return;
     st->ev_used = 0;
-    st->flops = 0.0;
-    st->launches = 0;
+    st->flops[0] = st->flops[1] = 0.0;
+    st->launches[0] = st->launches[1] = 0;
 }
 
-void mlp_timing_collect(MlpState* st, float* ms, double* flops, int64_t* launches) {
+void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_t* launches) {
     *ms = 0.0f;
     *flops = 0.0;
     *launches = 0;
     if (!st) return;
     for (int i = 0; i < st->ev_used; ++i) {
+        if (st->ev_kind[i] != kind) continue;
         float t = 0.0f;
         if (cudaEventElapsedTime(&t, st->ev[2 * i], st->ev[2 * i + 1]) == cudaSuccess) *ms += t;
         else cudaGetLastError();
     }
-    *flops = st->flops;
-    *launches = st->launches;
+    *flops = st->flops[kind];
+    *launches = st->launches[kind];
 }
 
 void mlp_destroy(MlpState* st) {
@@ -240,25 +242,6 @@ __device__ __forceinline__ void dense_relu(const float* __restrict__ in, float* 
     __syncthreads();
 }
 
-// Query points either from a list or from the grid in label-word order.
-struct QuerySrc {
-    const float3* pts;       // list mode when non-null
-    const int* idx;          // optional gather indices into pts
-    GridDev g;               // grid mode
-};
-
-__device__ __forceinline__ float3 query_point(const QuerySrc& Q, int64_t q) {
-    if (Q.pts) return Q.pts[Q.idx ? Q.idx[q] : q];
-    int64_t w = q >> 5;
-    int l = (int)(q & 31);
-    int xw = (int)(w % Q.g.W);
-    int64_t row = w / Q.g.W;
-    int y = (int)(row % Q.g.nv[1]);
-    int z = (int)(row / Q.g.nv[1]);
-    int x = min(xw * 32 + l, Q.g.nv[0] - 1);
-    return make_float3(Q.g.X[0][x], Q.g.X[1][y], Q.g.X[2][z]);
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n, float scale, float radius, float amp,
                float* __restrict__ zout) {
@@ -312,15 +295,15 @@ static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float*
         attr = true;
     }
     int64_t blocks = (n + kTM - 1) / kTM;
-    cudaEvent_t* ev = mlp_ev_pair(st);
+    cudaEvent_t* ev = mlp_ev_pair(st, 0);
     if (ev) MLP_CK(cudaEventRecord(ev[0], s));
     k_mlp_fp32<<<(unsigned)blocks, kThreads, fp32_smem(), s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z); note_launch();
     if (ev) MLP_CK(cudaEventRecord(ev[1], s));
     MLP_CK(cudaGetLastError());
     int64_t real = n;
     if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];   // grid mode: padding lanes excluded
-    st->flops += kFlopsPerQuery * (double)real;
-    st->launches += 1;
+    st->flops[0] += kFlopsPerQuery * (double)real;
+    st->launches[0] += 1;
     return ODC_OK;
 }
 
@@ -369,6 +352,7 @@ static odc_status band_reeval(MlpState* st, const QuerySrc& Q, int64_t n, float*
     uint32_t hcnt = 0;
     MLP_CK(cudaMemcpyAsync(&hcnt, cnt, 4, cudaMemcpyDeviceToHost, s));
     MLP_CK(cudaStreamSynchronize(s));
+    if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
     *nrq += hcnt;
     if (!hcnt) return ODC_OK;
     if ((r = mlp_scratch(st, 8, (size_t)hcnt * 16 + 64, &ppts, err)) != ODC_OK) return r;
@@ -391,7 +375,7 @@ static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int
                        int64_t* nrq, std::string* err) {
     if (precision < 0) precision = st->precision;
     if (precision == ODC_PREC_FP32) return launch_fp32(st, Q, n, z, s, err);
-    odc_status r = mlp_tc_eval(st, Q.pts, Q.g, n, z, s, err);
+    odc_status r = mlp_tc_eval(st, Q, n, z, s, err);
     if (r != ODC_OK) return r;
     return band_reeval(st, Q, n, z, s, nrq, err);
 }

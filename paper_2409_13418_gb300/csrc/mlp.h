@@ -47,7 +47,8 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
 // Start / finish the per-extract accounting of network launches: total
 // event-timed kernel milliseconds and algorithmic FLOPs.
 void mlp_timing_begin(MlpState* st);
-void mlp_timing_collect(MlpState* st, float* ms, double* flops, int64_t* launches);
+// Per kind (0: FP32 SIMT network, 1: tensor-core network).
+void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_t* launches);
 
 // Labels (and logits) at explicit points.
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,

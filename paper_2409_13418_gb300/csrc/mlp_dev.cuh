@@ -58,20 +58,23 @@ struct MlpState {
     MlpTc* tc = nullptr;
     // per-launch CUDA events around the network kernels of one extract
     cudaEvent_t ev[2 * 256] = {};
+    int ev_kind[256] = {};      // 0: FP32 network, 1: tensor-core network
     int ev_used = 0;
-    double flops = 0.0;         // algorithmic FLOPs of the network launches
-    int64_t launches = 0;
+    double flops[2] = {0.0, 0.0};   // algorithmic FLOPs of the network launches, per kind
+    int64_t launches[2] = {0, 0};
 };
 
-// Event pair around one network launch (none once 256 are in use).
-cudaEvent_t* mlp_ev_pair(MlpState* st);
+// Event pair around one network launch of the given kind (none once 256 are in use).
+cudaEvent_t* mlp_ev_pair(MlpState* st, int kind);
 constexpr double kFlopsPerQuery = 2.0 * (2.0 * kNF * kH + 3.0 * kH * kH + kH);
 
 // Tensor-core path (mlp_tc.cu)
 odc_status mlp_tc_prepare(MlpState* st, const float* host_blob, cudaStream_t s, std::string* err);
-odc_status mlp_tc_eval(MlpState* st, const float3* pts, const GridDev& g, int64_t n, float* z, cudaStream_t s,
-                       std::string* err);
+struct QuerySrc;
+odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 void mlp_tc_destroy(MlpState* st);
+// ODC_ERR_TIMEOUT if a tensor-core launch since the last check hit a bounded wait.
+odc_status mlp_tc_check(MlpState* st, std::string* err);
 
 // [sin(2 pi u), cos(2 pi u)] with u = b . x formed exactly in float-float and
 // reduced to [-1/2, 1/2] turns before sincospi.
@@ -88,6 +91,25 @@ __device__ __forceinline__ float2 fourier_sincos(float b0, float b1, float b2, f
 __device__ __forceinline__ float envelope_logit(float3 x, float f, float scale, float radius, float amp) {
     float r = __fsqrt_rn(x.x * x.x + x.y * x.y + x.z * x.z);
     return scale * ((radius - r) + amp * f);
+}
+
+// Query points either from a list or from the grid in label-word order.
+struct QuerySrc {
+    const float3* pts;       // list mode when non-null
+    const int* idx;          // optional gather indices into pts
+    GridDev g;               // grid mode
+};
+
+__device__ __forceinline__ float3 query_point(const QuerySrc& Q, int64_t q) {
+    if (Q.pts) return Q.pts[Q.idx ? Q.idx[q] : q];
+    int64_t w = q >> 5;
+    int l = (int)(q & 31);
+    int xw = (int)(w % Q.g.W);
+    int64_t row = w / Q.g.W;
+    int y = (int)(row % Q.g.nv[1]);
+    int z = (int)(row / Q.g.nv[1]);
+    int x = min(xw * 32 + l, Q.g.nv[0] - 1);
+    return make_float3(Q.g.X[0][x], Q.g.X[1][y], Q.g.X[2][z]);
 }
 
 // compact.cu

@@ -1,13 +1,492 @@
-// mlp_tc.cu -- BF16 tensor-core (tcgen05) path of the MLP occupancy network.
+// mlp_tc.cu -- BF16 tensor-core path of the occupancy network (tcgen05 + TMA).
+//
+// One persistent CTA per SM evaluates 256 queries at a time as two M = 128
+// sub-tiles.  Per hidden layer the 256 x K weight matrix streams from L2 by
+// TMA in K = 32 slices (SWIZZLE_64B, 16 KB) through a 5-stage ring; one thread
+// issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M 128, N 256, K 16)
+// for both sub-tiles on every slice, so each weight byte serves 256 queries.
+// The two 128 x 256 FP32 accumulators live in TMEM (512 columns).  Eight
+// epilogue warps read them back with tcgen05.ld, add the bias, apply ReLU,
+// round to BF16 and write the next layer's A operand (K-major, SWIZZLE_128B)
+// into shared memory in place; after the last hidden layer they fold the
+// 256 -> 1 output layer and the envelope into the logit z.  The Fourier
+// features (float-float phase, sincospi) are computed by the same warps.
+//
+// Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
+// CTA raises an error flag, stops issuing work, waits (bounded) for its TMA
+// loads in flight, frees its TMEM and exits, and the host reports
+// ODC_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "mlp.h"
 #include "mlp_dev.cuh"
 
 namespace odc {
-struct MlpTc {};
-odc_status mlp_tc_prepare(MlpState*, const float*, cudaStream_t, std::string*) { return ODC_OK; }
-odc_status mlp_tc_eval(MlpState*, const float3*, const GridDev&, int64_t, float*, cudaStream_t, std::string* err) {
-    *err = "BF16 path not built yet";
-    return ODC_ERR_UNSUPPORTED;
+
+namespace tc {
+
+constexpr int kTileM = 128;                 // rows per sub-tile (UMMA M)
+constexpr int kSub = 2;                     // sub-tiles per CTA tile
+constexpr int kRows = kTileM * kSub;        // queries per CTA tile
+constexpr int kKC = 32;                     // K per weight slice
+constexpr int kStages = 5;
+constexpr int kSliceBytes = kH * kKC * 2;   // 16 KB
+constexpr int kABytes = kTileM * kH * 2;    // 64 KB per sub-tile
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr uint32_t kTmemCols = 512;
+constexpr size_t kSmemBytes = 1024 + kSub * kABytes + kStages * kSliceBytes + 256;
+constexpr int kChunks0 = 2 * kNF / kKC;     // layer 0: K = 128
+constexpr int kChunksH = kH / kKC;          // layers 1..3: K = 256
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+// ---------------------------------------------------------------- PTX
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
 }
-void mlp_tc_destroy(MlpState*) {}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity ``parity``; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+    if (mbar_try(b, parity)) return true;
+    unsigned long long t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(b, parity)) return true;
+        if ((i & 255) == 0) {
+            if (*abort) return false;
+            if (gtimer() - t0 > kWaitNs) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(su32(dst)), "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, swizzled (LBO unused), SBO =
+// byte distance between 8-row groups, descriptor version 1 (bits 46-47)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo, uint32_t layout) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)layout << 61;
+    return d;
+}
+constexpr uint32_t kLayoutSW128 = 2, kLayoutSW64 = 4;
+
+// instruction descriptor: D F32, A/B BF16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Byte offset of element (row r, k) in a K-major SWIZZLE_128B operand of K
+// extent 256: four 64-column chunks of 128 rows x 128 B; 16-byte unit u of
+// row r sits at unit u ^ (r % 8).
+__device__ __forceinline__ uint32_t a_offset(int r, int k) {
+    int chunk = k >> 6, b = (k & 63) * 2;
+    int u = (b >> 4) ^ (r & 7);
+    return (uint32_t)(chunk * (kTileM * 128) + (r >> 3) * 1024 + (r & 7) * 128 + u * 16 + (b & 15));
+}
+
+struct TcParams {
+    const float* wblob;     // FP32 blob: B, biases, w4 (BlobLayout)
+    QuerySrc Q;
+    int64_t n;
+    float scale, radius, amp;
+    float* z;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mlp_tc(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
+             const __grid_constant__ CUtensorMap m2, const __grid_constant__ CUtensorMap m3, TcParams P) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* A = sm;                                   // kSub x 64 KB
+    uint8_t* Bring = sm + kSub * kABytes;              // kStages x 16 KB
+    uint64_t* bars = (uint64_t*)(Bring + kStages * kSliceBytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* acc_full = bars + 2 * kStages;
+    uint64_t* act_ready = bars + 2 * kStages + 1;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 2);
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (P.n + kRows - 1) / kRows;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(act_ready, kEpiWarps);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&m0) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&m1) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&m2) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&m3) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int l = 0; l < kNL && ok; ++l) {
+                    const CUtensorMap* map = l == 0 ? &m0 : l == 1 ? &m1 : l == 2 ? &m2 : &m3;
+                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    for (int c = 0; c < nck; ++c) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort)) { ok = false; break; }
+                        mbar_expect_tx(&full[stage], kSliceBytes);
+                        tma_load_2d(Bring + stage * kSliceBytes, map, c * kKC, 0, &full[stage]);
+                        ++issued;
+                        if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    }
+                }
+            }
+            // drain: every issued slice must land before the CTA exits
+            for (int s = 0; s < kStages; ++s) {
+                // the last use of each stage completed phase (number of uses - 1) & 1
+                uint32_t uses = issued / kStages + (issued % kStages > (uint32_t)s ? 1 : 0);
+                if (uses) {
+                    unsigned long long t0 = gtimer();
+                    while (!mbar_try(&full[s], (uses - 1) & 1) && gtimer() - t0 < kWaitNs) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, act_phase = 0;
+            bool ok = true;
+            const uint32_t a_base = su32(A), b_base = su32(Bring);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int l = 0; l < kNL && ok; ++l) {
+                    if (!mbar_wait(act_ready, act_phase, abort)) { ok = false; break; }
+                    act_phase ^= 1;
+                    tc_fence_after();
+                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    for (int c = 0; c < nck; ++c) {
+                        if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                        tc_fence_after();
+                        for (int s = 0; s < kSub; ++s) {
+#pragma unroll
+                            for (int kk = 0; kk < kKC / 16; ++kk) {
+                                int kg = c * kKC + kk * 16;
+                                uint32_t aaddr = a_base + s * kABytes + (kg >> 6) * (kTileM * 128) + (kg & 63) * 2;
+                                uint32_t baddr = b_base + stage * kSliceBytes + kk * 32;
+                                umma(tmem + s * kH, sdesc(aaddr, 1024, kLayoutSW128), sdesc(baddr, 512, kLayoutSW64),
+                                     (c | kk) != 0);
+                            }
+                        }
+                        umma_commit(&empty[stage]);
+                        if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    }
+                    if (ok) umma_commit(acc_full);
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        const int e = warp - 2;                 // 0..7
+        const int sub = e >> 2;                 // sub-tile
+        const int quad = warp & 3;              // TMEM lane quarter this warp may access
+        const int r = quad * 32 + lane;         // row within the sub-tile
+        uint8_t* As = A + sub * kABytes;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sub * kH);
+        const float* Bf = P.wblob + kOffB;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t q = t * kRows + sub * kTileM + r;
+            const bool valid = q < P.n;
+            float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
+            // Fourier features -> A[:, 0:128]
+            for (int j = 0; j < kNF; j += 8) {
+                float s[8], cs[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float2 v = fourier_sincos(__ldg(Bf + 3 * (j + i)), __ldg(Bf + 3 * (j + i) + 1),
+                                              __ldg(Bf + 3 * (j + i) + 2), x);
+                    s[i] = v.x;
+                    cs[i] = v.y;
+                }
+                uint4 ps = make_uint4(pack_bf16(s[0], s[1]), pack_bf16(s[2], s[3]), pack_bf16(s[4], s[5]),
+                                      pack_bf16(s[6], s[7]));
+                uint4 pc = make_uint4(pack_bf16(cs[0], cs[1]), pack_bf16(cs[2], cs[3]), pack_bf16(cs[4], cs[5]),
+                                      pack_bf16(cs[6], cs[7]));
+                *reinterpret_cast<uint4*>(As + a_offset(r, j)) = ps;
+                *reinterpret_cast<uint4*>(As + a_offset(r, kNF + j)) = pc;
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(act_ready);
+            for (int l = 0; l < kNL; ++l) {
+                // every lane waits; the warp proceeds only if all lanes saw the phase
+                bool got = mbar_wait(acc_full, acc_phase, abort);
+                if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+                acc_phase ^= 1;
+                tc_fence_after();
+                const float* bias = P.wblob + kOffb_(l);
+                if (l < kNL - 1) {
+                    for (int cb = 0; cb < kH / 32; ++cb) {
+                        float v[32];
+                        tmem_ld32(trow + cb * 32, v);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float h[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) h[i] = fmaxf(v[u * 8 + i] + __ldg(bias + cb * 32 + u * 8 + i), 0.f);
+                            uint4 p = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
+                                                 pack_bf16(h[6], h[7]));
+                            *reinterpret_cast<uint4*>(As + a_offset(r, cb * 32 + u * 8)) = p;
+                        }
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(act_ready);
+                } else {
+                    const float* w4 = P.wblob + kOffW_(kNL);
+                    float f = 0.0f;
+                    for (int cb = 0; cb < kH / 32; ++cb) {
+                        float v[32];
+                        tmem_ld32(trow + cb * 32, v);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            f = fmaf(fmaxf(v[i] + __ldg(bias + cb * 32 + i), 0.f), __ldg(w4 + cb * 32 + i), f);
+                    }
+                    tc_fence_before();
+                    f += __ldg(P.wblob + kOffb_(kNL));
+                    if (valid) P.z[q] = envelope_logit(x, f, P.scale, P.radius, P.amp);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+    if (threadIdx.x == 0 && *abort) atomicExch(P.err, 1);
+}
+
+}  // namespace tc
+
+struct MlpTc {
+    __nv_bfloat16* w = nullptr;     // W_l as BF16 [256][K_l], l = 0..3
+    CUtensorMap maps[4];
+    int* err = nullptr;
+    int sms = 0;
+    bool ready = false;
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn(std::string* err) {
+    static EncodeTiledFn fn = nullptr;
+    if (fn) return fn;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+        cudaGetLastError();
+        *err = "cuTensorMapEncodeTiled is unavailable";
+        return nullptr;
+    }
+    fn = (EncodeTiledFn)p;
+    return fn;
+}
+
+odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::string* err) {
+    if (!st->tc) st->tc = new MlpTc();
+    MlpTc* T = st->tc;
+    const size_t K[4] = {2 * kNF, kH, kH, kH};
+    size_t total = 0;
+    for (int l = 0; l < 4; ++l) total += (size_t)kH * K[l];
+    std::vector<__nv_bfloat16> h(total);
+    size_t off = 0;
+    size_t offs[4];
+    for (int l = 0; l < 4; ++l) {
+        offs[l] = off;
+        const float* Wt = hb + kOffW[l];   // [K][256]
+        for (int n = 0; n < kH; ++n)
+            for (size_t k = 0; k < K[l]; ++k) h[off + (size_t)n * K[l] + k] = __float2bfloat16_rn(Wt[k * kH + n]);
+        off += (size_t)kH * K[l];
+    }
+    if (!T->w) {
+        if (cudaMalloc((void**)&T->w, total * sizeof(__nv_bfloat16)) != cudaSuccess ||
+            cudaMalloc((void**)&T->err, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            *err = "tensor-core weight allocation failed";
+            return ODC_ERR_OOM;
+        }
+    }
+    if (cudaMemcpyAsync(T->w, h.data(), total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        *err = "tensor-core weight upload failed";
+        return ODC_ERR_CUDA;
+    }
+    EncodeTiledFn fn = encode_fn(err);
+    if (!fn) return ODC_ERR_UNSUPPORTED;
+    for (int l = 0; l < 4; ++l) {
+        cuuint64_t gdim[2] = {(cuuint64_t)K[l], (cuuint64_t)kH};
+        cuuint64_t gstride[1] = {(cuuint64_t)K[l] * 2};
+        cuuint32_t box[2] = {(cuuint32_t)tc::kKC, (cuuint32_t)kH};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = fn(&T->maps[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)(T->w + offs[l]), gdim, gstride, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *err = "cuTensorMapEncodeTiled failed for layer " + std::to_string(l);
+            return ODC_ERR_CUDA;
+        }
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        *err = "cannot reserve shared memory for the tensor-core kernel";
+        return ODC_ERR_CUDA;
+    }
+    T->ready = true;
+    return ODC_OK;
+}
+
+odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
+    if (n <= 0) return ODC_OK;
+    MlpTc* T = st->tc;
+    if (!T || !T->ready) {
+        *err = "tensor-core path not prepared";
+        return ODC_ERR_INTERNAL;
+    }
+    int64_t tiles = (n + tc::kRows - 1) / tc::kRows;
+    int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err};
+    cudaEvent_t* ev = mlp_ev_pair(st, 1);
+    if (ev) cudaEventRecord(ev[0], s);
+    tc::k_mlp_tc<<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2], T->maps[3], P);
+    note_launch();
+    if (ev) cudaEventRecord(ev[1], s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("k_mlp_tc launch: ") + cudaGetErrorString(e);
+        return ODC_ERR_CUDA;
+    }
+    int64_t real = n;
+    if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];
+    st->flops[1] += kFlopsPerQuery * (double)real;
+    st->launches[1] += 1;
+    return ODC_OK;
+}
+
+odc_status mlp_tc_check(MlpState* st, std::string* err) {
+    if (!st || !st->tc || !st->tc->err) return ODC_OK;
+    int h = 0;
+    if (cudaMemcpy(&h, st->tc->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        *err = "cannot read the tensor-core error flag";
+        return ODC_ERR_CUDA;
+    }
+    if (h) {
+        cudaMemset(st->tc->err, 0, sizeof(int));
+        *err = "tensor-core kernel: a pipeline wait expired";
+        return ODC_ERR_TIMEOUT;
+    }
+    return ODC_OK;
+}
+
+void mlp_tc_destroy(MlpState* st) {
+    if (!st || !st->tc) return;
+    if (st->tc->w) cudaFree(st->tc->w);
+    if (st->tc->err) cudaFree(st->tc->err);
+    delete st->tc;
+    st->tc = nullptr;
+}
+
 }  // namespace odc

@@ -60,7 +60,8 @@ class Stats(C.Structure):
                 ("n_verts3", C.c_int64), ("n_case3", C.c_int64), ("n_flips", C.c_int64),
                 ("fix_rounds", C.c_int64), ("n_queries", C.c_int64), ("n_requeries", C.c_int64),
                 ("stage_ms", C.c_float * 8), ("mlp_flops", C.c_double), ("mlp_ms", C.c_float),
-                ("n_launches", C.c_int32), ("mlp_launches", C.c_int64)]
+                ("n_launches", C.c_int32), ("mlp_launches", C.c_int64), ("tc_flops", C.c_double),
+                ("tc_ms", C.c_float), ("pad_", C.c_int32), ("tc_launches", C.c_int64)]
 
 
 class MeshC(C.Structure):
