@@ -96,6 +96,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(value: float, dist=None, device="cpu") -> float:
+    """Max of ``value`` over all ranks (identity without a process group)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(cells: float, world: int, steps: int, t_ms: float) -> float:
+    """Whole-job Mcells/s: every rank processed ``steps`` grids of ``cells`` cells in ``t_ms``."""
+    return cells * world * steps / (t_ms * 1e-3) / 1e6
+
+
 def workload(seed: int = 0):
     from paper_2409_13418_gb300 import inputs as I
     return I.envelope_mlp(seed), I.cube_grid(RES)
@@ -221,12 +235,9 @@ def main():
     launches = odc.launch_total() - l0
     clocks = sampler.stop()
     t_steps = sum(a.elapsed_time(b) for a, b in ev)          # ms, device time of K steps
-    t_local = torch.tensor([t_steps], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max = float(t_local.item())
+    t_max = reduce_max(t_steps, dist, "cuda")
     cells = float(RES ** 3)
-    value = cells * world * args.steps / (t_max * 1e-3) / 1e6
+    value = throughput(cells, world, args.steps, t_max)
 
     # e2e: host source buffers in, mesh copied back to host, wall clock
     vbytes = tbytes = 0
@@ -240,10 +251,8 @@ def main():
         v, t = m.to_host()
         vbytes, tbytes = v.nbytes, t.nbytes
     torch.cuda.synchronize()
-    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e = cells * world * args.steps / float(t_e2e.item()) / 1e6
+    t_e2e = reduce_max((time.perf_counter() - t0) * 1e3, dist, "cuda")
+    e2e = throughput(cells, world, args.steps, t_e2e)
 
     if rank == 0:
         peaks, peak_src = _peaks()
