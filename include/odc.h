@@ -97,8 +97,9 @@ typedef struct {
     float pad[2];
 } odc_csg_prim;
 
-/* MLP precisions. */
-enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1 };
+/* MLP precisions.  ODC_PREC_SPLIT (odc_eval_points only) evaluates every
+ * point with the split-FP16 tensor-core network, without band handling. */
+enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2 };
 
 /* Envelope MLP occupancy: occ(x) = sigmoid(env_scale (env_radius - |x| +
  * env_amp f(x))), f(x) = W_L relu(... relu(W_0 [latent, g(x)] + b_0) ...) + b_L,
@@ -107,7 +108,14 @@ enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1 };
  * W_1..W_{n_hidden-1} [hidden][hidden], W_{n_hidden} [1][hidden], biases
  * b_l [rows of W_l].  Supported: n_freq = 64, hidden = 256, n_hidden = 4,
  * latent_dim in {0, 128}.  With ODC_PREC_BF16 every decision whose BF16
- * occupancy lies within ``band`` of iso is re-evaluated in FP32. */
+ * occupancy lies within ``band`` of iso is re-evaluated so that its sign
+ * equals the FP32 plain path's: first by a split-precision tensor-core pass
+ * (operands split into FP16 hi + lo, three products per layer, FP32
+ * accumulation), then, for the logits still within ``split_zmargin`` of the
+ * threshold (0: the default 1e-4, three times the measured split-tier logit
+ * error of 3.2e-5), by the FP32 network; ``no_split`` nonzero sends every
+ * band decision to the FP32 network directly.  A band of 0.03 (|z| < 0.12)
+ * covers the measured BF16 logit error (0.063) twice over. */
 typedef struct {
     int32_t n_freq;
     int32_t hidden;
@@ -122,7 +130,9 @@ typedef struct {
     float env_amp;
     int32_t precision;
     float band;
-    int32_t pad;
+    int32_t no_split;
+    float split_zmargin;
+    int32_t reserved;
 } odc_mlp;
 
 typedef struct {
@@ -161,7 +171,7 @@ typedef struct {
     int64_t n_flips;             /* faces flipped by the manifold fix */
     int64_t fix_rounds;
     int64_t n_queries;           /* occupancy evaluations on the main path */
-    int64_t n_requeries;         /* FP32 re-evaluations inside the band */
+    int64_t n_requeries;         /* FP32 (SIMT) re-evaluations of band decisions */
     float stage_ms[8];           /* grid, compact, topology, 1D, 2D, QEF, quads, total */
     double mlp_flops;            /* algorithmic FLOPs of the FP32 (SIMT) network launches */
     float mlp_ms;                /* CUDA-event time of the FP32 network launches */
@@ -171,6 +181,11 @@ typedef struct {
     float tc_ms;                 /* CUDA-event time of the tensor-core network launches */
     int32_t pad_;
     int64_t tc_launches;         /* tensor-core network launches */
+    double split_flops;          /* tensor-pipe FLOPs of the split-FP16 re-evaluation (3 products) */
+    float split_ms;              /* CUDA-event time of the split-FP16 launches */
+    int32_t pad2_;
+    int64_t split_launches;
+    int64_t n_split;             /* band decisions re-evaluated by the split-FP16 tier */
 } odc_stats;
 
 typedef struct {

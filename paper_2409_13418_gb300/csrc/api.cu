@@ -453,6 +453,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     if (kind == ODC_SRC_MLP) {
         mlp_timing_collect(c->mlp, 0, &S.mlp_ms, &S.mlp_flops, &S.mlp_launches);
         mlp_timing_collect(c->mlp, 1, &S.tc_ms, &S.tc_flops, &S.tc_launches);
+        mlp_timing_collect(c->mlp, 2, &S.split_ms, &S.split_flops, &S.split_launches);
+        S.n_split = mlp_split_count(c->mlp);
     }
     return ODC_OK;
 }

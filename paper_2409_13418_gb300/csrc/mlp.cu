@@ -31,12 +31,14 @@ odc_status mlp_check(const odc_mlp* m, std::string* err) {
         { *err = "precision must be FP32 or BF16"; return ODC_ERR_INVALID_ARG; }
     if (m->precision == ODC_PREC_BF16 && !(m->band >= 0.0f && m->band < 0.5f))
         { *err = "band must be in [0, 0.5)"; return ODC_ERR_INVALID_ARG; }
+    if (!(m->split_zmargin >= 0.0f)) { *err = "split_zmargin must be >= 0"; return ODC_ERR_INVALID_ARG; }
     return ODC_OK;
 }
 
 float mlp_logit_threshold(float iso) { return (float)std::log((double)iso / (1.0 - (double)iso)); }
 
 int mlp_precision(const MlpState* st) { return st->precision; }
+int64_t mlp_split_count(const MlpState* st) { return st ? st->n_split : 0; }
 
 #define MLP_CK(call)                                                                        \
     do {                                                                                    \
@@ -83,8 +85,9 @@ cudaEvent_t* mlp_ev_pair(MlpState* st, int kind) {
 void mlp_timing_begin(MlpState* st) {
     if (!st) return;
     st->ev_used = 0;
-    st->flops[0] = st->flops[1] = 0.0;
-    st->launches[0] = st->launches[1] = 0;
+    st->flops[0] = st->flops[1] = st->flops[2] = 0.0;
+    st->launches[0] = st->launches[1] = st->launches[2] = 0;
+    st->n_split = 0;
 }
 
 void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_t* launches) {
@@ -122,6 +125,8 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     MlpState* st = *pst;
     st->precision = m->precision;
     st->band = m->band;
+    st->split = m->no_split ? 0 : 1;
+    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 1e-4f;
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
     st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
     st->scale = m->env_scale;
@@ -330,43 +335,83 @@ __global__ void k_grid_points(GridDev g, const int* __restrict__ idx, const uint
     pts[i] = query_point(Q, idx[i]);
 }
 
-// Re-evaluate in FP32 every logit of z[0..n) whose magnitude is below the
-// band (A.2.2 binary decision at iso; the band makes the reduced-precision
-// decision equal the FP32 one).
-static odc_status band_reeval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, int64_t* nrq,
-                              std::string* err) {
-    void *pflag, *poff, *pidx, *ppts, *pz, *pcnt;
+__global__ void k_gather_pts(const float3* __restrict__ pts, const int* __restrict__ idx,
+                             const uint32_t* __restrict__ cnt, float3* __restrict__ out) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < *cnt) out[i] = pts[idx[i]];
+}
+
+// Indices of z[0..n) with |z| < thr, in increasing order (scratch slots
+// base..base+3); the count is read back to the host.
+static odc_status band_list(MlpState* st, const float* z, int64_t n, float thr, int base, int** idx,
+                            uint32_t** dcnt, uint32_t* hcnt, cudaStream_t s, std::string* err) {
+    void *pflag, *poff, *pidx, *pcnt;
     odc_status r;
-    if ((r = mlp_scratch(st, 4, n * 4 + 64, &pflag, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, 5, n * 4 + scan_tmp_elems(n) * 8 + 64, &poff, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, 6, n * 4 + 64, &pidx, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, 7, 64, &pcnt, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, base, n * 4 + 64, &pflag, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, base + 1, n * 4 + scan_tmp_elems(n) * 8 + 64, &poff, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, base + 2, n * 4 + 64, &pidx, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, base + 3, 64, &pcnt, err)) != ODC_OK) return r;
     uint32_t* flag = (uint32_t*)pflag;
     uint32_t* off = (uint32_t*)poff;
     uint32_t* tmp = off + ((n + 63) / 64) * 64;
-    uint32_t* cnt = (uint32_t*)pcnt;
     unsigned blocks = (unsigned)((n + 255) / 256);
-    k_band_flag<<<blocks, 256, 0, s>>>(z, n, st->zband, flag); note_launch();
-    exclusive_scan<uint32_t>(flag, off, (size_t)n, tmp, cnt, s);
+    k_band_flag<<<blocks, 256, 0, s>>>(z, n, thr, flag); note_launch();
+    exclusive_scan<uint32_t>(flag, off, (size_t)n, tmp, (uint32_t*)pcnt, s);
     k_band_gather<<<blocks, 256, 0, s>>>(flag, off, n, (int*)pidx); note_launch();
-    uint32_t hcnt = 0;
-    MLP_CK(cudaMemcpyAsync(&hcnt, cnt, 4, cudaMemcpyDeviceToHost, s));
+    MLP_CK(cudaMemcpyAsync(hcnt, pcnt, 4, cudaMemcpyDeviceToHost, s));
     MLP_CK(cudaStreamSynchronize(s));
+    *idx = (int*)pidx;
+    *dcnt = (uint32_t*)pcnt;
+    return ODC_OK;
+}
+
+// Band re-evaluation (A.2.2 binary decision at iso): every logit of z[0..n)
+// with |z| below the band is recomputed so that its sign equals the FP32
+// plain path's.  Tier 1: the split-FP16 tensor-core network (measured error
+// below zsplit / 3); tier 2: the FP32 SIMT network for the logits still within
+// zsplit.  Without the split tier every band logit goes to FP32 directly.
+static odc_status band_reeval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, int64_t* nrq,
+                              std::string* err) {
+    odc_status r;
+    int* idx1;
+    uint32_t *dcnt1, n1 = 0;
+    if ((r = band_list(st, z, n, st->zband, 4, &idx1, &dcnt1, &n1, s, err)) != ODC_OK) return r;
     if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
-    *nrq += hcnt;
-    if (!hcnt) return ODC_OK;
-    if ((r = mlp_scratch(st, 8, (size_t)hcnt * 16 + 64, &ppts, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, 9, (size_t)hcnt * 4 + 64, &pz, err)) != ODC_OK) return r;
-    QuerySrc R;
+    if (!n1) return ODC_OK;
+    void *ppts, *pz1;
+    if ((r = mlp_scratch(st, 8, (size_t)n1 * 12 + 64, &ppts, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, 9, (size_t)n1 * 4 + 64, &pz1, err)) != ODC_OK) return r;
+    float3* pts1 = (float3*)ppts;
+    float* z1 = (float*)pz1;
     if (Q.pts) {
-        R = QuerySrc{Q.pts, (const int*)pidx, Q.g};
+        if (Q.idx) { *err = "nested gather"; return ODC_ERR_INTERNAL; }
+        k_gather_pts<<<(n1 + 255) / 256, 256, 0, s>>>(Q.pts, idx1, dcnt1, pts1); note_launch();
     } else {
-        k_grid_points<<<(hcnt + 255) / 256, 256, 0, s>>>(Q.g, (const int*)pidx, cnt, (float3*)ppts); note_launch();
-        R = QuerySrc{(const float3*)ppts, nullptr, Q.g};
+        k_grid_points<<<(n1 + 255) / 256, 256, 0, s>>>(Q.g, idx1, dcnt1, pts1); note_launch();
     }
-    if (Q.pts && Q.idx) { *err = "nested gather"; return ODC_ERR_INTERNAL; }
-    if ((r = launch_fp32(st, R, hcnt, (float*)pz, s, err)) != ODC_OK) return r;
-    k_band_scatter<<<(hcnt + 255) / 256, 256, 0, s>>>((const int*)pidx, cnt, (const float*)pz, z); note_launch();
+    QuerySrc L1{pts1, nullptr, Q.g};
+    if (st->split) {
+        if ((r = mlp_tc3_eval(st, L1, n1, z1, s, err)) != ODC_OK) return r;
+        st->n_split += n1;
+        int* idx2;
+        uint32_t *dcnt2, n2 = 0;
+        if ((r = band_list(st, z1, n1, st->zsplit, 16, &idx2, &dcnt2, &n2, s, err)) != ODC_OK) return r;
+        if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
+        *nrq += n2;
+        if (n2) {
+            void *ppts2, *pz2;
+            if ((r = mlp_scratch(st, 20, (size_t)n2 * 12 + 64, &ppts2, err)) != ODC_OK) return r;
+            if ((r = mlp_scratch(st, 21, (size_t)n2 * 4 + 64, &pz2, err)) != ODC_OK) return r;
+            k_gather_pts<<<(n2 + 255) / 256, 256, 0, s>>>(pts1, idx2, dcnt2, (float3*)ppts2); note_launch();
+            QuerySrc L2{(const float3*)ppts2, nullptr, Q.g};
+            if ((r = launch_fp32(st, L2, n2, (float*)pz2, s, err)) != ODC_OK) return r;
+            k_band_scatter<<<(n2 + 255) / 256, 256, 0, s>>>(idx2, dcnt2, (const float*)pz2, z1); note_launch();
+        }
+    } else {
+        *nrq += n1;
+        if ((r = launch_fp32(st, L1, n1, z1, s, err)) != ODC_OK) return r;
+    }
+    k_band_scatter<<<(n1 + 255) / 256, 256, 0, s>>>(idx1, dcnt1, z1, z); note_launch();
     MLP_CK(cudaGetLastError());
     return ODC_OK;
 }
@@ -375,6 +420,7 @@ static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int
                        int64_t* nrq, std::string* err) {
     if (precision < 0) precision = st->precision;
     if (precision == ODC_PREC_FP32) return launch_fp32(st, Q, n, z, s, err);
+    if (precision == ODC_PREC_SPLIT) return mlp_tc3_eval(st, Q, n, z, s, err);
     odc_status r = mlp_tc_eval(st, Q, n, z, s, err);
     if (r != ODC_OK) return r;
     return band_reeval(st, Q, n, z, s, nrq, err);

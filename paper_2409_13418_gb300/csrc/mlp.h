@@ -50,6 +50,8 @@ void mlp_timing_begin(MlpState* st);
 // Per kind (0: FP32 SIMT network, 1: tensor-core network).
 void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_t* launches);
 
+int64_t mlp_split_count(const MlpState* st);
+
 // Labels (and logits) at explicit points.
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
                       float* logits, cudaStream_t s, std::string* err);

@@ -13,7 +13,7 @@ namespace odc {
 constexpr int kNF = 64;    // Fourier frequencies
 constexpr int kH = 256;    // hidden width
 constexpr int kNL = 4;     // hidden layers
-constexpr int kScratchSlots = 16;
+constexpr int kScratchSlots = 24;
 
 // FP32 weight blob (floats): B [64][3] (padded to 256), W_l^T [in][out] for
 // l = 0..3, w4 [256], biases b_0..b_3 [256], b_4 [1].
@@ -58,10 +58,13 @@ struct MlpState {
     MlpTc* tc = nullptr;
     // per-launch CUDA events around the network kernels of one extract
     cudaEvent_t ev[2 * 256] = {};
-    int ev_kind[256] = {};      // 0: FP32 network, 1: tensor-core network
+    int ev_kind[256] = {};      // 0: FP32 network, 1: BF16 tensor-core network, 2: split-FP16 network
     int ev_used = 0;
-    double flops[2] = {0.0, 0.0};   // algorithmic FLOPs of the network launches, per kind
-    int64_t launches[2] = {0, 0};
+    double flops[3] = {0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
+    int64_t launches[3] = {0, 0, 0};
+    int split = 1;              // use the split-FP16 tier for band re-evaluation
+    int64_t n_split = 0;        // queries re-evaluated by the split-FP16 tier in this extract
+    float zsplit = 1e-4f;       // |z| below which a split-tier decision is re-taken in FP32
 };
 
 // Event pair around one network launch of the given kind (none once 256 are in use).
@@ -75,6 +78,8 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
 void mlp_tc_destroy(MlpState* st);
 // ODC_ERR_TIMEOUT if a tensor-core launch since the last check hit a bounded wait.
 odc_status mlp_tc_check(MlpState* st, std::string* err);
+// Split-BF16 network (three BF16 products per layer, FP32 accumulation).
+odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 
 // [sin(2 pi u), cos(2 pi u)] with u = b . x formed exactly in float-float and
 // reduced to [-1/2, 1/2] turns before sincospi.

@@ -18,9 +18,11 @@
 // ODC_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -162,6 +164,7 @@ struct TcParams {
     float scale, radius, amp;
     float* z;
     int* err;
+    float wscale_inv[4];    // split path: 2^-s_l undoing the weight scale of layer l
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -353,11 +356,239 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && *abort) atomicExch(P.err, 1);
 }
 
+
+// ------------------------------------------------------------------------
+// Split-FP16 variant (FP32-class accuracy on the tensor pipe).  Every FP32
+// activation a and scaled weight w 2^s is split into hi = fp16(v) and lo =
+// fp16(v - hi) (22 significant bits); each layer accumulates A_hi W_hi +
+// A_lo W_hi + A_hi W_lo in FP32, where every product is exact and the dropped
+// A_lo W_lo term is ~2^-22 relative, and the epilogue undoes the 2^s weight
+// scale exactly.  An activation beyond the FP16 range marks its query (logit
+// 0) so that the FP32 tier re-evaluates it.  One 128-query tile per CTA:
+// A_hi and A_lo (64 KB each), a 3-stage ring of (W_hi, W_lo) K = 32 slices
+// (32 KB), 256 TMEM columns, four epilogue warps.
+constexpr int kStages3 = 3;
+constexpr int kEpiWarps3 = 4;
+constexpr int kThreads3 = 32 * (2 + kEpiWarps3);
+constexpr uint32_t kTmemCols3 = 256;
+constexpr size_t kSmemBytes3 = 1024 + 2 * kABytes + kStages3 * 2 * kSliceBytes + 256;
+
+constexpr float kF16Safe = 30000.0f;      // activations kept well inside the FP16 range
+// instruction descriptor: D F32, A/B F16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(kIdescF16), "r"(acc));
+}
+
+__device__ __forceinline__ void store_split8(uint8_t* Ahi, uint8_t* Alo, uint32_t off, const float* v) {
+    __align__(16) __half h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        h[i] = __float2half_rn(v[i]);
+        l[i] = __float2half_rn(v[i] - __half2float(h[i]));
+    }
+    *reinterpret_cast<uint4*>(Ahi + off) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(Alo + off) = *reinterpret_cast<const uint4*>(l);
+}
+
+__global__ void __launch_bounds__(kThreads3, 1)
+    k_mlp_tc3(const __grid_constant__ CUtensorMap h0, const __grid_constant__ CUtensorMap h1,
+              const __grid_constant__ CUtensorMap h2, const __grid_constant__ CUtensorMap h3,
+              const __grid_constant__ CUtensorMap l0, const __grid_constant__ CUtensorMap l1,
+              const __grid_constant__ CUtensorMap l2, const __grid_constant__ CUtensorMap l3, TcParams P) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* Ahi = sm;
+    uint8_t* Alo = sm + kABytes;
+    uint8_t* Bring = sm + 2 * kABytes;                 // stage s: hi slice, then lo slice
+    uint64_t* bars = (uint64_t*)(Bring + kStages3 * 2 * kSliceBytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages3;
+    uint64_t* acc_full = bars + 2 * kStages3;
+    uint64_t* act_ready = bars + 2 * kStages3 + 1;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages3 + 2);
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (P.n + kTileM - 1) / kTileM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages3; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(act_ready, kEpiWarps3);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kTmemCols3));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, issued = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int l = 0; l < kNL && ok; ++l) {
+                    const CUtensorMap* mh = l == 0 ? &h0 : l == 1 ? &h1 : l == 2 ? &h2 : &h3;
+                    const CUtensorMap* ml = l == 0 ? &l0 : l == 1 ? &l1 : l == 2 ? &l2 : &l3;
+                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    for (int c = 0; c < nck; ++c) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort)) { ok = false; break; }
+                        mbar_expect_tx(&full[stage], 2 * kSliceBytes);
+                        uint8_t* dst = Bring + stage * 2 * kSliceBytes;
+                        tma_load_2d(dst, mh, c * kKC, 0, &full[stage]);
+                        tma_load_2d(dst + kSliceBytes, ml, c * kKC, 0, &full[stage]);
+                        ++issued;
+                        if (++stage == kStages3) { stage = 0; phase ^= 1; }
+                    }
+                }
+            }
+            for (int s = 0; s < kStages3; ++s) {
+                uint32_t uses = issued / kStages3 + (issued % kStages3 > (uint32_t)s ? 1 : 0);
+                if (uses) {
+                    unsigned long long t0 = gtimer();
+                    while (!mbar_try(&full[s], (uses - 1) & 1) && gtimer() - t0 < kWaitNs) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0, act_phase = 0;
+            bool ok = true;
+            const uint32_t ahi = su32(Ahi), alo = su32(Alo), b_base = su32(Bring);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int l = 0; l < kNL && ok; ++l) {
+                    if (!mbar_wait(act_ready, act_phase, abort)) { ok = false; break; }
+                    act_phase ^= 1;
+                    tc_fence_after();
+                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    for (int c = 0; c < nck; ++c) {
+                        if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                        tc_fence_after();
+#pragma unroll
+                        for (int kk = 0; kk < kKC / 16; ++kk) {
+                            int kg = c * kKC + kk * 16;
+                            uint32_t aoff = (kg >> 6) * (kTileM * 128) + (kg & 63) * 2;
+                            uint32_t bh = b_base + stage * 2 * kSliceBytes + kk * 32;
+                            uint64_t dah = sdesc(ahi + aoff, 1024, kLayoutSW128);
+                            uint64_t dal = sdesc(alo + aoff, 1024, kLayoutSW128);
+                            uint64_t dbh = sdesc(bh, 512, kLayoutSW64);
+                            uint64_t dbl = sdesc(bh + kSliceBytes, 512, kLayoutSW64);
+                            umma_f16(tmem, dah, dbh, (c | kk) != 0);
+                            umma_f16(tmem, dal, dbh, 1);
+                            umma_f16(tmem, dah, dbl, 1);
+                        }
+                        umma_commit(&empty[stage]);
+                        if (++stage == kStages3) { stage = 0; phase ^= 1; }
+                    }
+                    if (ok) umma_commit(acc_full);
+                }
+            }
+        }
+    } else {
+        const int quad = warp & 3;
+        const int r = quad * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+        const float* Bf = P.wblob + kOffB;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t q = t * kTileM + r;
+            const bool valid = q < P.n;
+            bool range_ok = true;
+            float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
+            for (int j = 0; j < kNF; j += 8) {
+                float sv[8], cv[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float2 v = fourier_sincos(__ldg(Bf + 3 * (j + i)), __ldg(Bf + 3 * (j + i) + 1),
+                                              __ldg(Bf + 3 * (j + i) + 2), x);
+                    sv[i] = v.x;
+                    cv[i] = v.y;
+                }
+                store_split8(Ahi, Alo, a_offset(r, j), sv);
+                store_split8(Ahi, Alo, a_offset(r, kNF + j), cv);
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(act_ready);
+            for (int l = 0; l < kNL; ++l) {
+                bool got = mbar_wait(acc_full, acc_phase, abort);
+                if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+                acc_phase ^= 1;
+                tc_fence_after();
+                const float* bias = P.wblob + kOffb_(l);
+                const float unscale = P.wscale_inv[l];
+                if (l < kNL - 1) {
+                    for (int cb = 0; cb < kH / 32; ++cb) {
+                        float v[32];
+                        tmem_ld32(trow + cb * 32, v);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            float h[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                h[i] = fmaxf(fmaf(v[u * 8 + i], unscale, __ldg(bias + cb * 32 + u * 8 + i)), 0.f);
+                                range_ok &= h[i] < kF16Safe;
+                                h[i] = fminf(h[i], kF16Safe);
+                            }
+                            store_split8(Ahi, Alo, a_offset(r, cb * 32 + u * 8), h);
+                        }
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(act_ready);
+                } else {
+                    const float* w4 = P.wblob + kOffW_(kNL);
+                    float f = 0.0f;
+                    for (int cb = 0; cb < kH / 32; ++cb) {
+                        float v[32];
+                        tmem_ld32(trow + cb * 32, v);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            f = fmaf(fmaxf(fmaf(v[i], unscale, __ldg(bias + cb * 32 + i)), 0.f), __ldg(w4 + cb * 32 + i),
+                                     f);
+                    }
+                    tc_fence_before();
+                    f += __ldg(P.wblob + kOffb_(kNL));
+                    // an activation out of FP16 range sends the query to the FP32 tier (|z| = 0)
+                    if (valid) P.z[q] = range_ok ? envelope_logit(x, f, P.scale, P.radius, P.amp) : 0.0f;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols3));
+    }
+    if (threadIdx.x == 0 && *abort) atomicExch(P.err, 1);
+}
+
 }  // namespace tc
 
 struct MlpTc {
     __nv_bfloat16* w = nullptr;     // W_l as BF16 [256][K_l], l = 0..3
-    CUtensorMap maps[4];
+    __half* w16 = nullptr;          // split path: fp16 hi parts of W_l 2^s_l, then the lo parts
+    CUtensorMap maps[4];            // BF16 weights
+    CUtensorMap maps_hi[4];         // split path hi parts
+    CUtensorMap maps_lo[4];         // split path lo parts
+    float wscale_inv[4];
     int* err = nullptr;
     int sms = 0;
     bool ready = false;
@@ -389,17 +620,32 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     size_t total = 0;
     for (int l = 0; l < 4; ++l) total += (size_t)kH * K[l];
     std::vector<__nv_bfloat16> h(total);
+    std::vector<__half> h16(2 * total);
     size_t off = 0;
     size_t offs[4];
     for (int l = 0; l < 4; ++l) {
         offs[l] = off;
         const float* Wt = hb + kOffW[l];   // [K][256]
+        float wmax = 0.0f;
+        for (size_t i = 0; i < K[l] * kH; ++i) wmax = std::max(wmax, std::fabs(Wt[i]));
+        // largest power of two keeping |w| 2^s below 2^14 (FP16 max 65504)
+        int sexp = 0;
+        while (sexp < 24 && wmax * std::ldexp(1.0f, sexp + 1) < 16384.0f) ++sexp;
+        T->wscale_inv[l] = std::ldexp(1.0f, -sexp);
         for (int n = 0; n < kH; ++n)
-            for (size_t k = 0; k < K[l]; ++k) h[off + (size_t)n * K[l] + k] = __float2bfloat16_rn(Wt[k * kH + n]);
+            for (size_t k = 0; k < K[l]; ++k) {
+                float w = Wt[k * kH + n];
+                h[off + (size_t)n * K[l] + k] = __float2bfloat16_rn(w);
+                float ws = std::ldexp(w, sexp);
+                __half hi = __float2half_rn(ws);
+                h16[off + (size_t)n * K[l] + k] = hi;
+                h16[total + off + (size_t)n * K[l] + k] = __float2half_rn(ws - __half2float(hi));
+            }
         off += (size_t)kH * K[l];
     }
     if (!T->w) {
         if (cudaMalloc((void**)&T->w, total * sizeof(__nv_bfloat16)) != cudaSuccess ||
+            cudaMalloc((void**)&T->w16, 2 * total * sizeof(__half)) != cudaSuccess ||
             cudaMalloc((void**)&T->err, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             *err = "tensor-core weight allocation failed";
@@ -407,6 +653,7 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
         }
     }
     if (cudaMemcpyAsync(T->w, h.data(), total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(T->w16, h16.data(), 2 * total * sizeof(__half), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         *err = "tensor-core weight upload failed";
         return ODC_ERR_CUDA;
@@ -421,6 +668,14 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
         CUresult r = fn(&T->maps[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)(T->w + offs[l]), gdim, gstride, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = fn(&T->maps_hi[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + offs[l]), gdim, gstride, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = fn(&T->maps_lo[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + total + offs[l]), gdim,
+                   gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             *err = "cuTensorMapEncodeTiled failed for layer " + std::to_string(l);
             return ODC_ERR_CUDA;
@@ -430,7 +685,9 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
-        cudaSuccess) {
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_mlp_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes3) !=
+            cudaSuccess) {
         cudaGetLastError();
         *err = "cannot reserve shared memory for the tensor-core kernel";
         return ODC_ERR_CUDA;
@@ -448,7 +705,7 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
     }
     int64_t tiles = (n + tc::kRows - 1) / tc::kRows;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err};
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {1.f, 1.f, 1.f, 1.f}};
     cudaEvent_t* ev = mlp_ev_pair(st, 1);
     if (ev) cudaEventRecord(ev[0], s);
     tc::k_mlp_tc<<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2], T->maps[3], P);
@@ -463,6 +720,34 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
     if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];
     st->flops[1] += kFlopsPerQuery * (double)real;
     st->launches[1] += 1;
+    return ODC_OK;
+}
+
+odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
+    if (n <= 0) return ODC_OK;
+    MlpTc* T = st->tc;
+    if (!T || !T->ready) {
+        *err = "tensor-core path not prepared";
+        return ODC_ERR_INTERNAL;
+    }
+    int64_t tiles = (n + tc::kTileM - 1) / tc::kTileM;
+    int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {}};
+    for (int l = 0; l < 4; ++l) P.wscale_inv[l] = T->wscale_inv[l];
+    cudaEvent_t* ev = mlp_ev_pair(st, 2);
+    if (ev) cudaEventRecord(ev[0], s);
+    tc::k_mlp_tc3<<<grid, tc::kThreads3, tc::kSmemBytes3, s>>>(T->maps_hi[0], T->maps_hi[1], T->maps_hi[2], T->maps_hi[3],
+                                                             T->maps_lo[0], T->maps_lo[1], T->maps_lo[2],
+                                                             T->maps_lo[3], P);
+    note_launch();
+    if (ev) cudaEventRecord(ev[1], s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        *err = std::string("k_mlp_tc3 launch: ") + cudaGetErrorString(e);
+        return ODC_ERR_CUDA;
+    }
+    st->flops[2] += 3.0 * kFlopsPerQuery * (double)n;   // three products per layer
+    st->launches[2] += 1;
     return ODC_OK;
 }
 
@@ -484,6 +769,7 @@ odc_status mlp_tc_check(MlpState* st, std::string* err) {
 void mlp_tc_destroy(MlpState* st) {
     if (!st || !st->tc) return;
     if (st->tc->w) cudaFree(st->tc->w);
+    if (st->tc->w16) cudaFree(st->tc->w16);
     if (st->tc->err) cudaFree(st->tc->err);
     delete st->tc;
     st->tc = nullptr;

@@ -20,7 +20,7 @@ ODC_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
           5: "unsupported", 6: "internal error"}
 SRC_CSG, SRC_MLP, SRC_RESIDENT = 0, 1, 2
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_SPLIT = 0, 1, 2
 DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
            cycles=9, vlocal=10, qcase=11, flips=12, search=13)
 _DBG_DTYPE = dict(labels=np.uint32, edges=np.uint32, T=np.uint32, faces=np.uint32, slots=np.uint8,
@@ -38,7 +38,8 @@ class Mlp(C.Structure):
     _fields_ = [("n_freq", C.c_int32), ("hidden", C.c_int32), ("n_hidden", C.c_int32), ("latent_dim", C.c_int32),
                 ("B", C.c_void_p), ("W", C.c_void_p * 8), ("b", C.c_void_p * 8), ("latent", C.c_void_p),
                 ("env_scale", C.c_float), ("env_radius", C.c_float), ("env_amp", C.c_float),
-                ("precision", C.c_int32), ("band", C.c_float), ("pad", C.c_int32)]
+                ("precision", C.c_int32), ("band", C.c_float), ("no_split", C.c_int32),
+                ("split_zmargin", C.c_float), ("reserved", C.c_int32)]
 
 
 class Source(C.Structure):
@@ -61,7 +62,9 @@ class Stats(C.Structure):
                 ("fix_rounds", C.c_int64), ("n_queries", C.c_int64), ("n_requeries", C.c_int64),
                 ("stage_ms", C.c_float * 8), ("mlp_flops", C.c_double), ("mlp_ms", C.c_float),
                 ("n_launches", C.c_int32), ("mlp_launches", C.c_int64), ("tc_flops", C.c_double),
-                ("tc_ms", C.c_float), ("pad_", C.c_int32), ("tc_launches", C.c_int64)]
+                ("tc_ms", C.c_float), ("pad_", C.c_int32), ("tc_launches", C.c_int64),
+                ("split_flops", C.c_double), ("split_ms", C.c_float), ("pad2_", C.c_int32),
+                ("split_launches", C.c_int64), ("n_split", C.c_int64)]
 
 
 class MeshC(C.Structure):
@@ -131,7 +134,7 @@ def _ptr(a: np.ndarray) -> int:
 class _SourceHolder:
     """Keeps the numpy buffers behind a Source structure alive."""
 
-    def __init__(self, src, precision=None, band=None):
+    def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0):
         self.keep = []
         self.src = Source()
         if src is None:
@@ -170,7 +173,9 @@ class _SourceHolder:
                 m.latent = _ptr(lat)
             m.env_scale, m.env_radius, m.env_amp = src.env_scale, src.env_radius, src.env_amp
             m.precision = PREC_FP32 if precision is None else precision
-            m.band = 1e-3 if band is None else band
+            m.band = 0.03 if band is None else band
+            m.no_split = 0 if split else 1
+            m.split_zmargin = split_zmargin
             self.keep.append(m)
             self.src.kind = SRC_MLP
             self.src.mlp = C.addressof(m)
@@ -254,14 +259,15 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def upload(self, src, precision=None, band=None):
+    def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0):
         """Make ``src`` the context's resident source (``extract(None, ...)`` reuses it)."""
-        holder = _SourceHolder(src, precision, band)
+        holder = _SourceHolder(src, precision, band, split, split_zmargin)
         _check(_lib.odc_source_upload(self.h, C.byref(holder.src)))
 
-    def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, **kw) -> Mesh:
+    def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, split=True,
+                split_zmargin=0.0, **kw) -> Mesh:
         """Run ODC; ``src=None`` reuses the resident source."""
-        holder = _SourceHolder(src, precision, band)
+        holder = _SourceHolder(src, precision, band, split, split_zmargin)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
         m = MeshC()
@@ -291,8 +297,8 @@ class Context:
         _check(_lib.odc_debug_copy(self.h, DBG[what], _ptr(out), out.nbytes, C.byref(n), C.byref(eb)))
         return out.reshape(-1, k) if k > 1 else out
 
-    def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None):
-        holder = _SourceHolder(src, None if precision < 0 else precision, band)
+    def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None, split=True):
+        holder = _SourceHolder(src, None if precision < 0 else min(precision, PREC_BF16), band, split)
         pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
         lab = np.empty(pts.shape[0], np.uint8)
         z = np.empty(pts.shape[0], np.float32)
