@@ -43,7 +43,8 @@ constexpr int kABytes = kTileM * kH * 2;    // 64 KB per sub-tile
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr uint32_t kTmemCols = 512;
-constexpr size_t kSmemBytes = 1024 + kSub * kABytes + kStages * kSliceBytes + 256;
+constexpr int kParamFloats = 4 * kH + kH + 4 + 3 * kNF;      // biases, w4, b4 (padded), Fourier B
+constexpr size_t kSmemBytes = 1024 + kSub * kABytes + kStages * kSliceBytes + 256 + kParamFloats * 4;
 constexpr int kChunks0 = 2 * kNF / kKC;     // layer 0: K = 128
 constexpr int kChunksH = kH / kKC;          // layers 1..3: K = 256
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
@@ -181,6 +182,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* act_ready = bars + 2 * kStages + 1;
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
+    float* sp = (float*)((uint8_t*)bars + 256);        // biases [4][256], w4 [256], b4, Fourier B [64][3]
+    for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sp[i] = P.wblob[kOffb_(i / kH) + (i % kH)];
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) sp[4 * kH + i] = P.wblob[kOffW_(kNL) + i];
+    if (threadIdx.x == 0) sp[5 * kH] = P.wblob[kOffb_(kNL)];
+    for (int i = threadIdx.x; i < 3 * kNF; i += blockDim.x) sp[5 * kH + 4 + i] = P.wblob[kOffB + i];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = (P.n + kRows - 1) / kRows;
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = quad * 32 + lane;         // row within the sub-tile
         uint8_t* As = A + sub * kABytes;
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sub * kH);
-        const float* Bf = P.wblob + kOffB;
+        const float* Bf = sp + 5 * kH + 4;
         uint32_t acc_phase = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -291,8 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float s[8], cs[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    float2 v = fourier_sincos(__ldg(Bf + 3 * (j + i)), __ldg(Bf + 3 * (j + i) + 1),
-                                              __ldg(Bf + 3 * (j + i) + 2), x);
+                    float2 v = fourier_sincos(Bf[3 * (j + i)], Bf[3 * (j + i) + 1], Bf[3 * (j + i) + 2], x);
                     s[i] = v.x;
                     cs[i] = v.y;
                 }
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 acc_phase ^= 1;
                 tc_fence_after();
-                const float* bias = P.wblob + kOffb_(l);
+                const float* bias = sp + l * kH;
                 if (l < kNL - 1) {
                     for (int cb = 0; cb < kH / 32; ++cb) {
                         float v[32];
@@ -320,8 +325,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             float h[8];
+                            const float4 b0 = *reinterpret_cast<const float4*>(bias + cb * 32 + u * 8);
+                            const float4 b1 = *reinterpret_cast<const float4*>(bias + cb * 32 + u * 8 + 4);
+                            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) h[i] = fmaxf(v[u * 8 + i] + __ldg(bias + cb * 32 + u * 8 + i), 0.f);
+                            for (int i = 0; i < 8; ++i) h[i] = fmaxf(v[u * 8 + i] + bb[i], 0.f);
                             uint4 p = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
                                                  pack_bf16(h[6], h[7]));
                             *reinterpret_cast<uint4*>(As + a_offset(r, cb * 32 + u * 8)) = p;
@@ -332,17 +340,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(act_ready);
                 } else {
-                    const float* w4 = P.wblob + kOffW_(kNL);
+                    const float* w4 = sp + 4 * kH;
                     float f = 0.0f;
                     for (int cb = 0; cb < kH / 32; ++cb) {
                         float v[32];
                         tmem_ld32(trow + cb * 32, v);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            f = fmaf(fmaxf(v[i] + __ldg(bias + cb * 32 + i), 0.f), __ldg(w4 + cb * 32 + i), f);
+                        for (int i = 0; i < 32; i += 4) {
+                            const float4 b = *reinterpret_cast<const float4*>(bias + cb * 32 + i);
+                            const float4 w = *reinterpret_cast<const float4*>(w4 + cb * 32 + i);
+                            f = fmaf(fmaxf(v[i] + b.x, 0.f), w.x, f);
+                            f = fmaf(fmaxf(v[i + 1] + b.y, 0.f), w.y, f);
+                            f = fmaf(fmaxf(v[i + 2] + b.z, 0.f), w.z, f);
+                            f = fmaf(fmaxf(v[i + 3] + b.w, 0.f), w.w, f);
+                        }
                     }
                     tc_fence_before();
-                    f += __ldg(P.wblob + kOffb_(kNL));
+                    f += sp[5 * kH];
                     if (valid) P.z[q] = envelope_logit(x, f, P.scale, P.radius, P.amp);
                 }
             }
