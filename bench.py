@@ -296,7 +296,9 @@ def main():
                                        f"{args.precision}" + (f" band {args.band}" if prec == odc.PREC_BF16 else ""),
                            "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) between steps",
                            "edges": stats["n_edges"], "face_segs": stats["n_face_segs"],
-                           "queries": stats["n_queries"], "requeries_split_fp16": stats["n_split"],
+                           "queries": stats["n_queries"],
+                           "bf16_pass_queries": int(round(stats["tc_flops"] / 459264.0)),
+                           "requeries_split_fp16": stats["n_split"],
                            "requeries_fp32": stats["n_requeries"],
                            "stage_ms": [round(x, 3) for x in stats["stage_ms"]]},
                 "e2e": {"value": e2e, "unit": "Mcells/s", "h2d_bytes_per_step": int(h2d),

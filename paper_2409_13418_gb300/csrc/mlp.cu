@@ -164,9 +164,16 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
 }
 
 // ----------------------------------------------------------- FP32 network
-constexpr int kTM = 64;           // queries per CTA
-constexpr int kThreads = 256;
-constexpr int kKC = 16;           // weight rows per staged chunk
+#ifndef ODC_FP32_WARPS
+#define ODC_FP32_WARPS 12
+#endif
+constexpr int kWarps = ODC_FP32_WARPS;   // one warp per 8 queries of the tile
+constexpr int kTM = 8 * kWarps;          // queries per CTA
+constexpr int kThreads = 32 * kWarps;
+#ifndef ODC_FP32_KC
+#define ODC_FP32_KC 32
+#endif
+constexpr int kKC = ODC_FP32_KC;         // weight rows per staged chunk
 constexpr int kActStride = kH + 4;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -177,11 +184,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// out[m][n] = relu(sum_k in[m][k] Wt[k][n] + b[n]) for the CTA's 64 queries.
-// Thread (tr, tc): rows tr*8..tr*8+7, columns tc*4..tc*4+3 and 128+tc*4..+3.
-__device__ __forceinline__ void dense_relu(const float* __restrict__ in, float* __restrict__ out, int K,
-                                           const float* __restrict__ Wt, const float* __restrict__ bias,
-                                           float* __restrict__ wbuf) {
+// act[m][n] = relu(sum_k act[m][k] Wt[k][n] + b[n]) for the CTA's kTM queries,
+// in place.  Thread (tr, tc): rows tr*8..tr*8+7, columns tc*4..tc*4+3 and
+// 128+tc*4..+3.  The sums live in registers until every k has been read; the
+// last chunk ends with a barrier before the epilogue overwrites the tile.
+__device__ __forceinline__ void dense_relu(float* act, int K, const float* __restrict__ Wt,
+                                           const float* __restrict__ bias, float* __restrict__ wbuf) {
     const int tid = threadIdx.x, tr = tid >> 5, tc = tid & 31;
     float acc[8][8];
 #pragma unroll
@@ -193,10 +201,7 @@ __device__ __forceinline__ void dense_relu(const float* __restrict__ in, float* 
         const float* src = Wt + (size_t)c * kKC * kH;
         float* dst = wbuf + buf * kKC * kH;
 #pragma unroll
-        for (int r = 0; r < (kKC * kH / 4) / kThreads; ++r) {
-            int idx = (r * kThreads + tid) * 4;
-            cp_async16(dst + idx, src + idx);
-        }
+        for (int v = tid; v < kKC * kH / 4; v += kThreads) cp_async16(dst + 4 * v, src + 4 * v);
         cp_async_commit();
     };
     stage(0, 0);
@@ -214,7 +219,7 @@ __device__ __forceinline__ void dense_relu(const float* __restrict__ in, float* 
             float4 a4[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                a4[i] = *reinterpret_cast<const float4*>(in + (tr * 8 + i) * kActStride + c * kKC + kk);
+                a4[i] = *reinterpret_cast<const float4*>(act + (tr * 8 + i) * kActStride + c * kKC + kk);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float* wr = w + (kk + q) * kH;
@@ -236,7 +241,7 @@ __device__ __forceinline__ void dense_relu(const float* __restrict__ in, float* 
     float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        float* o = out + (tr * 8 + i) * kActStride;
+        float* o = act + (tr * 8 + i) * kActStride;
         float4 v0 = make_float4(fmaxf(acc[i][0] + bv[0], 0.f), fmaxf(acc[i][1] + bv[1], 0.f),
                                 fmaxf(acc[i][2] + bv[2], 0.f), fmaxf(acc[i][3] + bv[3], 0.f));
         float4 v1 = make_float4(fmaxf(acc[i][4] + bv[4], 0.f), fmaxf(acc[i][5] + bv[5], 0.f),
@@ -251,9 +256,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n, float scale, float radius, float amp,
                float* __restrict__ zout) {
     extern __shared__ __align__(16) float sm[];
-    float* actA = sm;
-    float* actB = sm + kTM * kActStride;
-    float* wbuf = sm + 2 * kTM * kActStride;
+    float* act = sm;                         // [kTM][kActStride], layers run in place
+    float* wbuf = sm + kTM * kActStride;     // two staged weight chunks
     __shared__ float3 xs[kTM];
     __shared__ float part[kTM][4];
     const int tid = threadIdx.x;
@@ -266,21 +270,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float* B = wb + kOffB;
     for (int i = tid; i < kNF * kTM; i += kThreads) {
         int j = i / kTM, m = i % kTM;
-        float3 x = xs[m];
-        float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], x);
-        actA[m * kActStride + j] = sc.x;
-        actA[m * kActStride + kNF + j] = sc.y;
+        float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
+        act[m * kActStride + j] = sc.x;
+        act[m * kActStride + kNF + j] = sc.y;
     }
     __syncthreads();
-    dense_relu(actA, actB, 2 * kNF, wb + kOffW[0], wb + kOffb[0], wbuf);
-    dense_relu(actB, actA, kH, wb + kOffW[1], wb + kOffb[1], wbuf);
-    dense_relu(actA, actB, kH, wb + kOffW[2], wb + kOffb[2], wbuf);
-    dense_relu(actB, actA, kH, wb + kOffW[3], wb + kOffb[3], wbuf);
+    for (int l = 0; l < kNL; ++l) dense_relu(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
     {
         int m = tid >> 2, p = tid & 3;
         const float* w5 = wb + kOffW[kNL];
         float s = 0.0f;
-        for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(actA[m * kActStride + k], w5[k], s);
+        for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[m * kActStride + k], w5[k], s);
         part[m][p] = s;
     }
     __syncthreads();
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-static size_t fp32_smem() { return sizeof(float) * (2 * kTM * kActStride + 2 * kKC * kH); }
+static size_t fp32_smem() { return sizeof(float) * (kTM * kActStride + 2 * kKC * kH); }
 
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
     if (n <= 0) return ODC_OK;
@@ -313,9 +313,28 @@ static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float*
 }
 
 // ------------------------------------------------------------ band re-eval
-__global__ void k_band_flag(const float* __restrict__ z, int64_t n, float zb, uint32_t* __restrict__ flag) {
+// Tier of every query: 0 = BF16 tensor-core pass first, 1 = split-FP16 pass
+// first, 2 = FP32 directly.  hint[i] estimates |z_i - zt| (from the logits
+// around the query in its search); no hint routes to the BF16 pass.
+__global__ void k_route(const float* __restrict__ hint, int64_t n, float zs, float zb, int split,
+                        uint8_t* __restrict__ r) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = fabsf(z[i]) < zb ? 1u : 0u;
+    if (i >= n) return;
+    float h = hint ? hint[i] : INFINITY;
+    r[i] = h < zs ? 2 : (h < zb ? (split ? 1 : 2) : 0);
+}
+// Queries of tier `from` whose logit lies within thr of t move to tier `to`;
+// flag = the queries now in tier `to`.
+__global__ void k_tier_flag(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr,
+                            uint8_t* __restrict__ r, uint32_t* __restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int ri = r[i];
+    if (ri == from && fabsf(z[i] - t) < thr) {
+        ri = to;
+        r[i] = (uint8_t)to;
+    }
+    flag[i] = ri == to ? 1u : 0u;
 }
 __global__ void k_band_gather(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ off, int64_t n,
                               int* __restrict__ idx) {
@@ -341,21 +360,21 @@ __global__ void k_gather_pts(const float3* __restrict__ pts, const int* __restri
     if (i < *cnt) out[i] = pts[idx[i]];
 }
 
-// Indices of z[0..n) with |z| < thr, in increasing order (scratch slots
-// base..base+3); the count is read back to the host.
-static odc_status band_list(MlpState* st, const float* z, int64_t n, float thr, int base, int** idx,
-                            uint32_t** dcnt, uint32_t* hcnt, cudaStream_t s, std::string* err) {
+// Indices of the queries of tier `to` after promotion (see k_tier_flag), in
+// increasing order (scratch slots base..base+3); the count is read back.
+static odc_status tier_list(MlpState* st, const float* z, int64_t n, uint8_t* r, int from, int to, float thr,
+                            int base, int** idx, uint32_t** dcnt, uint32_t* hcnt, cudaStream_t s, std::string* err) {
     void *pflag, *poff, *pidx, *pcnt;
-    odc_status r;
-    if ((r = mlp_scratch(st, base, n * 4 + 64, &pflag, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, base + 1, n * 4 + scan_tmp_elems(n) * 8 + 64, &poff, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, base + 2, n * 4 + 64, &pidx, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, base + 3, 64, &pcnt, err)) != ODC_OK) return r;
+    odc_status rc;
+    if ((rc = mlp_scratch(st, base, n * 4 + 64, &pflag, err)) != ODC_OK) return rc;
+    if ((rc = mlp_scratch(st, base + 1, n * 4 + scan_tmp_elems(n) * 8 + 64, &poff, err)) != ODC_OK) return rc;
+    if ((rc = mlp_scratch(st, base + 2, n * 4 + 64, &pidx, err)) != ODC_OK) return rc;
+    if ((rc = mlp_scratch(st, base + 3, 64, &pcnt, err)) != ODC_OK) return rc;
     uint32_t* flag = (uint32_t*)pflag;
     uint32_t* off = (uint32_t*)poff;
     uint32_t* tmp = off + ((n + 63) / 64) * 64;
     unsigned blocks = (unsigned)((n + 255) / 256);
-    k_band_flag<<<blocks, 256, 0, s>>>(z, n, thr, flag); note_launch();
+    k_tier_flag<<<blocks, 256, 0, s>>>(z, n, st->zt, from, to, thr, r, flag); note_launch();
     exclusive_scan<uint32_t>(flag, off, (size_t)n, tmp, (uint32_t*)pcnt, s);
     k_band_gather<<<blocks, 256, 0, s>>>(flag, off, n, (int*)pidx); note_launch();
     MLP_CK(cudaMemcpyAsync(hcnt, pcnt, 4, cudaMemcpyDeviceToHost, s));
@@ -365,77 +384,108 @@ static odc_status band_list(MlpState* st, const float* z, int64_t n, float thr, 
     return ODC_OK;
 }
 
-// Band re-evaluation (A.2.2 binary decision at iso): every logit of z[0..n)
-// with |z| below the band is recomputed so that its sign equals the FP32
-// plain path's.  Tier 1: the split-FP16 tensor-core network (measured error
-// below zsplit / 3); tier 2: the FP32 SIMT network for the logits still within
-// zsplit.  Without the split tier every band logit goes to FP32 directly.
-static odc_status band_reeval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, int64_t* nrq,
-                              std::string* err) {
-    odc_status r;
-    int* idx1;
-    uint32_t *dcnt1, n1 = 0;
-    if ((r = band_list(st, z, n, st->zband, 4, &idx1, &dcnt1, &n1, s, err)) != ODC_OK) return r;
-    if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
-    if (!n1) return ODC_OK;
-    void *ppts, *pz1;
-    if ((r = mlp_scratch(st, 8, (size_t)n1 * 12 + 64, &ppts, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, 9, (size_t)n1 * 4 + 64, &pz1, err)) != ODC_OK) return r;
-    float3* pts1 = (float3*)ppts;
-    float* z1 = (float*)pz1;
+// Points of the listed queries (scratch slot ps).
+static odc_status gather_points(MlpState* st, const QuerySrc& Q, const int* idx, const uint32_t* dcnt, uint32_t m,
+                                int ps, float3** out, cudaStream_t s, std::string* err) {
+    void* p;
+    odc_status rc;
+    if ((rc = mlp_scratch(st, ps, (size_t)m * 12 + 64, &p, err)) != ODC_OK) return rc;
+    if (Q.idx) { *err = "nested gather"; return ODC_ERR_INTERNAL; }
     if (Q.pts) {
-        if (Q.idx) { *err = "nested gather"; return ODC_ERR_INTERNAL; }
-        k_gather_pts<<<(n1 + 255) / 256, 256, 0, s>>>(Q.pts, idx1, dcnt1, pts1); note_launch();
+        k_gather_pts<<<(m + 255) / 256, 256, 0, s>>>(Q.pts, idx, dcnt, (float3*)p); note_launch();
     } else {
-        k_grid_points<<<(n1 + 255) / 256, 256, 0, s>>>(Q.g, idx1, dcnt1, pts1); note_launch();
+        k_grid_points<<<(m + 255) / 256, 256, 0, s>>>(Q.g, idx, dcnt, (float3*)p); note_launch();
     }
-    QuerySrc L1{pts1, nullptr, Q.g};
-    if (st->split) {
-        if ((r = mlp_tc3_eval(st, L1, n1, z1, s, err)) != ODC_OK) return r;
-        st->n_split += n1;
-        int* idx2;
-        uint32_t *dcnt2, n2 = 0;
-        if ((r = band_list(st, z1, n1, st->zsplit, 16, &idx2, &dcnt2, &n2, s, err)) != ODC_OK) return r;
-        if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
-        *nrq += n2;
-        if (n2) {
-            void *ppts2, *pz2;
-            if ((r = mlp_scratch(st, 20, (size_t)n2 * 12 + 64, &ppts2, err)) != ODC_OK) return r;
-            if ((r = mlp_scratch(st, 21, (size_t)n2 * 4 + 64, &pz2, err)) != ODC_OK) return r;
-            k_gather_pts<<<(n2 + 255) / 256, 256, 0, s>>>(pts1, idx2, dcnt2, (float3*)ppts2); note_launch();
-            QuerySrc L2{(const float3*)ppts2, nullptr, Q.g};
-            if ((r = launch_fp32(st, L2, n2, (float*)pz2, s, err)) != ODC_OK) return r;
-            k_band_scatter<<<(n2 + 255) / 256, 256, 0, s>>>(idx2, dcnt2, (const float*)pz2, z1); note_launch();
+    *out = (float3*)p;
+    return ODC_OK;
+}
+
+// Tiered evaluation (A.2.2 binary decision at iso): the sign of every logit
+// equals the FP32 plain path's.  A logit of the BF16 pass is kept only
+// outside the band |z - zt| >= zband; the split-FP16 tensor-core network
+// (measured error below zsplit / 3) re-takes the band and keeps |z - zt| >=
+// zsplit; the FP32 SIMT network takes the rest.  Without the split tier the
+// whole band goes to FP32.  With hints, queries predicted inside the band
+// (or inside zsplit) start at the split (or FP32) tier: the tiers' acceptance
+// rules are unchanged, so only the cost depends on the hints.
+static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float* z, const float* hint, cudaStream_t s,
+                              int64_t* nrq, std::string* err) {
+    odc_status r;
+    void* pr;
+    if ((r = mlp_scratch(st, 24, (size_t)n + 64, &pr, err)) != ODC_OK) return r;
+    uint8_t* route = (uint8_t*)pr;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_route<<<blocks, 256, 0, s>>>(hint, n, st->zsplit, st->zband, st->split, route); note_launch();
+    if (!hint) {
+        if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
+    } else {
+        int* idx0;
+        uint32_t *dc0, n0 = 0;
+        if ((r = tier_list(st, z, n, route, -1, 0, 0.0f, 28, &idx0, &dc0, &n0, s, err)) != ODC_OK) return r;
+        if (n0) {
+            float3* p0;
+            void* pz0;
+            if ((r = gather_points(st, Q, idx0, dc0, n0, 32, &p0, s, err)) != ODC_OK) return r;
+            if ((r = mlp_scratch(st, 33, (size_t)n0 * 4 + 64, &pz0, err)) != ODC_OK) return r;
+            QuerySrc L0{p0, nullptr, Q.g};
+            if ((r = mlp_tc_eval(st, L0, n0, (float*)pz0, s, err)) != ODC_OK) return r;
+            k_band_scatter<<<(n0 + 255) / 256, 256, 0, s>>>(idx0, dc0, (const float*)pz0, z); note_launch();
         }
-    } else {
-        *nrq += n1;
-        if ((r = launch_fp32(st, L1, n1, z1, s, err)) != ODC_OK) return r;
     }
-    k_band_scatter<<<(n1 + 255) / 256, 256, 0, s>>>(idx1, dcnt1, z1, z); note_launch();
+    if (st->split) {
+        int* idx1;
+        uint32_t *dc1, n1 = 0;
+        if ((r = tier_list(st, z, n, route, 0, 1, st->zband, 4, &idx1, &dc1, &n1, s, err)) != ODC_OK) return r;
+        if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
+        if (n1) {
+            float3* p1;
+            void* pz1;
+            if ((r = gather_points(st, Q, idx1, dc1, n1, 8, &p1, s, err)) != ODC_OK) return r;
+            if ((r = mlp_scratch(st, 9, (size_t)n1 * 4 + 64, &pz1, err)) != ODC_OK) return r;
+            QuerySrc L1{p1, nullptr, Q.g};
+            if ((r = mlp_tc3_eval(st, L1, n1, (float*)pz1, s, err)) != ODC_OK) return r;
+            k_band_scatter<<<(n1 + 255) / 256, 256, 0, s>>>(idx1, dc1, (const float*)pz1, z); note_launch();
+            st->n_split += n1;
+        }
+    }
+    int* idx2;
+    uint32_t *dc2, n2 = 0;
+    const int from = st->split ? 1 : 0;
+    const float thr = st->split ? st->zsplit : st->zband;
+    if ((r = tier_list(st, z, n, route, from, 2, thr, 16, &idx2, &dc2, &n2, s, err)) != ODC_OK) return r;
+    if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
+    *nrq += n2;
+    if (n2) {
+        float3* p2;
+        void* pz2;
+        if ((r = gather_points(st, Q, idx2, dc2, n2, 20, &p2, s, err)) != ODC_OK) return r;
+        if ((r = mlp_scratch(st, 21, (size_t)n2 * 4 + 64, &pz2, err)) != ODC_OK) return r;
+        QuerySrc L2{p2, nullptr, Q.g};
+        if ((r = launch_fp32(st, L2, n2, (float*)pz2, s, err)) != ODC_OK) return r;
+        k_band_scatter<<<(n2 + 255) / 256, 256, 0, s>>>(idx2, dc2, (const float*)pz2, z); note_launch();
+    }
     MLP_CK(cudaGetLastError());
     return ODC_OK;
 }
 
-static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int precision, cudaStream_t s,
-                       int64_t* nrq, std::string* err) {
+static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int precision, const float* hint,
+                       cudaStream_t s, int64_t* nrq, std::string* err) {
     if (precision < 0) precision = st->precision;
     if (precision == ODC_PREC_FP32) return launch_fp32(st, Q, n, z, s, err);
     if (precision == ODC_PREC_SPLIT) return mlp_tc3_eval(st, Q, n, z, s, err);
-    odc_status r = mlp_tc_eval(st, Q, n, z, s, err);
-    if (r != ODC_OK) return r;
-    return band_reeval(st, Q, n, z, s, nrq, err);
+    return eval_tiered(st, Q, n, z, hint, s, nrq, err);
 }
 
 odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
-                         int64_t* nrq, std::string* err) {
+                         int64_t* nrq, std::string* err, const float* hint) {
     QuerySrc Q{pts, nullptr, GridDev{}};
-    return eval(st, Q, n, z, precision, s, nrq, err);
+    return eval(st, Q, n, z, precision, hint, s, nrq, err);
 }
 
 odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, int64_t* nrq, std::string* err) {
     QuerySrc Q{nullptr, nullptr, g};
     int64_t n = (int64_t)g.W * g.nv[1] * g.nv[2] * 32;
-    return eval(st, Q, n, z, -1, s, nrq, err);
+    return eval(st, Q, n, z, -1, nullptr, s, nrq, err);
 }
 
 __global__ void k_pts_labels(const float* __restrict__ z, int64_t n, float t, uint8_t* __restrict__ lab) {
@@ -446,6 +496,7 @@ __global__ void k_pts_labels(const float* __restrict__ z, int64_t n, float t, ui
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
                       float* logits, cudaStream_t s, std::string* err) {
     int64_t nrq = 0;
+    st->zt = mlp_logit_threshold(iso);
     odc_status r = mlp_eval_list(st, pts, n, logits, precision, s, &nrq, err);
     if (r != ODC_OK) return r;
     k_pts_labels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(logits, n, mlp_logit_threshold(iso), labels); note_launch();

@@ -25,9 +25,12 @@ void mlp_destroy(MlpState* st);
 odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::string* err);
 
 // Logits at n explicit points.  With BF16 precision, every logit within the
-// band is recomputed in FP32 (counted in *nrq).
+// band is re-taken by the split-FP16 and FP32 tiers (FP32 ones counted in
+// *nrq).  hint (device, n floats, optional): an estimate of |z - logit(iso)|
+// per query that lets predicted band queries skip the BF16 pass; it changes
+// the cost, never a decision.
 odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
-                         int64_t* nrq, std::string* err);
+                         int64_t* nrq, std::string* err, const float* hint = nullptr);
 // Logits at the grid vertices in label-word order (query q -> word q/32, lane q%32).
 odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, int64_t* nrq, std::string* err);
 int mlp_precision(const MlpState* st);

@@ -13,7 +13,7 @@ namespace odc {
 constexpr int kNF = 64;    // Fourier frequencies
 constexpr int kH = 256;    // hidden width
 constexpr int kNL = 4;     // hidden layers
-constexpr int kScratchSlots = 24;
+constexpr int kScratchSlots = 40;
 
 // FP32 weight blob (floats): B [64][3] (padded to 256), W_l^T [in][out] for
 // l = 0..3, w4 [256], biases b_0..b_3 [256], b_4 [1].
@@ -64,7 +64,9 @@ struct MlpState {
     int64_t launches[3] = {0, 0, 0};
     int split = 1;              // use the split-FP16 tier for band re-evaluation
     int64_t n_split = 0;        // queries re-evaluated by the split-FP16 tier in this extract
-    float zsplit = 1e-4f;       // |z| below which a split-tier decision is re-taken in FP32
+    float zsplit = 1e-4f;       // |z - zt| below which a split-tier decision is re-taken in FP32
+    float zt = 0.0f;            // decision threshold logit(iso) of the current extract
+    const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
 };
 
 // Event pair around one network launch of the given kind (none once 256 are in use).

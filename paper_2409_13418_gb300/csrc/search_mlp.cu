@@ -45,12 +45,29 @@ odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, c
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
     void* pz;
     S_TRY(mlp_scratch(st, 0, nw * 32 * 4, &pz, err));
+    st->zt = mlp_logit_threshold(iso);
+    st->zgrid = (const float*)pz;
     S_TRY(mlp_eval_grid(st, g, (float*)pz, s, nrq, err));
     k_pack_labels<<<nblk(nw * 32), 256, 0, s>>>(g, (const float*)pz, mlp_logit_threshold(iso), bits); note_launch();
     S_CK(cudaGetLastError());
     (void)nq;
     return ODC_OK;
 }
+
+// Routing hint for the midpoint of a bracket whose ends have logits za, zc
+// (see mlp_eval_list): the linear prediction |(za + zc)/2 - t| plus a quarter
+// of the bracket's logit span for curvature, plus the error of the tier an
+// end's logit may come from (BF16 outside the band, split-FP16 outside zs).
+__device__ __forceinline__ float bracket_hint(float za, float zc, float t, float zb, float zs) {
+    float da = fabsf(za - t), dc = fabsf(zc - t);
+    float dm = fmaxf(da, dc);
+    float e = dm >= zb ? 0.07f : (dm >= zs ? 4e-5f : 0.0f);
+    return fabsf(0.5f * (za + zc) - t) + 0.25f * fabsf(zc - za) + e;
+}
+
+struct HintPar {
+    float t, zb, zs;
+};
 
 // ------------------------------------------------------------------- 1D
 __global__ void k_bis_gen(GridDev g, const uint32_t* __restrict__ edges, uint32_t ne, int s,
@@ -68,20 +85,47 @@ __global__ void k_bis_gen(GridDev g, const uint32_t* __restrict__ edges, uint32_
     pts[i] = make_float3(w[0], w[1], w[2]);
 }
 
+__device__ __forceinline__ size_t grid_query(const GridDev& g, int x, int y, int z) {
+    return (((size_t)z * g.nv[1] + y) * g.W + (x >> 5)) * 32 + (x & 31);
+}
+
+// Logits at both ends of every crossing edge (from the grid pass) and the
+// routing hint of the first midpoint.
+__global__ void k_bis_init(GridDev g, const uint32_t* __restrict__ edges, uint32_t ne, const float* __restrict__ zg,
+                           HintPar hp, float2* __restrict__ zac, float* __restrict__ hint) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    uint32_t e = edges[i];
+    int p[3];
+    vid_xyz(g, e / 3u, &p[0], &p[1], &p[2]);
+    float za = zg[grid_query(g, p[0], p[1], p[2])];
+    p[e % 3u] += 1;
+    float zc = zg[grid_query(g, p[0], p[1], p[2])];
+    zac[i] = make_float2(za, zc);
+    hint[i] = bracket_hint(za, zc, hp.t, hp.zb, hp.zs);
+}
+
 __global__ void k_bis_upd(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ edges,
                           uint32_t ne, const float* __restrict__ z, float t, uint32_t* __restrict__ lo, int last,
-                          uint32_t* __restrict__ T) {
+                          uint32_t* __restrict__ T, HintPar hp, float2* __restrict__ zac, float* __restrict__ hint) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     uint32_t e = edges[i];
     int p[3];
     vid_xyz(g, e / 3u, &p[0], &p[1], &p[2]);
     uint32_t lab0 = label_at(g, bits, p[0], p[1], p[2]);
-    uint32_t lab = z[i] > t;
+    float zm = z[i];
+    uint32_t lab = zm > t;
     uint32_t l = lo[i], mid = 2u * l + 1u;
     l = (lab == lab0) ? mid : 2u * l;
     lo[i] = l;
     if (last) T[i] = 2u * l + 1u;
+    if (hint) {
+        float2 b = zac[i];
+        if (lab == lab0) b.x = zm; else b.y = zm;
+        zac[i] = b;
+        hint[i] = bracket_hint(b.x, b.y, hp.t, hp.zb, hp.zs);
+    }
 }
 
 odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
@@ -93,10 +137,23 @@ odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, cons
     S_TRY(mlp_scratch(st, 3, ne * 4ull, &pz, err));
     S_CK(cudaMemsetAsync(plo, 0, ne * 4ull, s));
     float t = mlp_logit_threshold(iso);
+    st->zt = t;
+    HintPar hp{t, st->zband, st->zsplit};
+    float2* zac = nullptr;
+    float* hint = nullptr;
+    if (mlp_precision(st) == ODC_PREC_BF16 && st->zgrid) {
+        void *pzac, *ph;
+        S_TRY(mlp_scratch(st, 34, ne * 8ull, &pzac, err));
+        S_TRY(mlp_scratch(st, 35, ne * 4ull, &ph, err));
+        zac = (float2*)pzac;
+        hint = (float*)ph;
+        k_bis_init<<<nblk(ne), 256, 0, s>>>(g, edges, ne, st->zgrid, hp, zac, hint); note_launch();
+    }
     for (int step = 0; step < k; ++step) {
         k_bis_gen<<<nblk(ne), 256, 0, s>>>(g, edges, ne, step, (const uint32_t*)plo, (float3*)ppts); note_launch();
-        S_TRY(mlp_eval_list(st, (const float3*)ppts, ne, (float*)pz, -1, s, nrq, err));
-        k_bis_upd<<<nblk(ne), 256, 0, s>>>(g, bits, edges, ne, (const float*)pz, t, (uint32_t*)plo, step == k - 1, T); note_launch();
+        S_TRY(mlp_eval_list(st, (const float3*)ppts, ne, (float*)pz, -1, s, nrq, err, hint));
+        k_bis_upd<<<nblk(ne), 256, 0, s>>>(g, bits, edges, ne, (const float*)pz, t, (uint32_t*)plo, step == k - 1, T,
+                                           hp, zac, hint); note_launch();
         S_CK(cudaGetLastError());
     }
     *nq += (int64_t)ne * k;
@@ -109,6 +166,9 @@ struct FaceSt {
     ff2 d;        // step-1 ray (oriented by the label of m)
     ff2 q;        // step-1 result
     uint32_t lab_m, Ja, Jc, J1a, J1c, J2a, J2c, found;
+    float zm;               // logit at m
+    float za, zc;           // logits at the step-1 bracket ends (Ja, Jc)
+    float z1a, z1c, z2a, z2c;   // logits at the step-2 bracket ends of both rays
 };
 
 __global__ void k_face_init(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ flips,
@@ -132,6 +192,7 @@ __global__ void k_face_m(GridDev g, uint32_t nf, const float* __restrict__ z, fl
     FaceSt& st = S[i];
     uint32_t lab_m = z[i] > t;
     st.lab_m = lab_m;
+    st.zm = z[i];
     ff2 d = lab_m ? ff2{ff_neg(st.F.d.u), ff_neg(st.F.d.v)} : st.F.d;
     st.d = d;
     for (int j = 1; j <= sp.lin1; ++j)
@@ -141,7 +202,7 @@ __global__ void k_face_m(GridDev g, uint32_t nf, const float* __restrict__ z, fl
 
 // first line sample whose label differs -> bracket; first bisection query
 __global__ void k_face_lin1(GridDev g, uint32_t nf, const float* __restrict__ z, float t, SearchParams sp,
-                            FaceSt* __restrict__ S, float3* __restrict__ pts) {
+                            FaceSt* __restrict__ S, float3* __restrict__ pts, HintPar hp, float* __restrict__ hint) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     FaceSt& st = S[i];
@@ -151,19 +212,26 @@ __global__ void k_face_lin1(GridDev g, uint32_t nf, const float* __restrict__ z,
         if ((uint32_t)(z[(size_t)(j - 1) * nf + i] > t) != st.lab_m) { first = j; st.found = 1; break; }
     st.Ja = (uint32_t)(first - 1) << sp.bin1;
     st.Jc = (uint32_t)first << sp.bin1;
-    if (sp.bin1 > 0)
+    st.za = first > 1 ? z[(size_t)(first - 2) * nf + i] : st.zm;
+    st.zc = z[(size_t)(first - 1) * nf + i];
+    if (sp.bin1 > 0) {
         pts[i] = face_world2(g, st.F, ray_point(st.F.m, st.d, lbs_param(sp.range1, (st.Ja + st.Jc) >> 1, sp.lin1, sp.bin1)));
+        if (hint) hint[i] = bracket_hint(st.za, st.zc, hp.t, hp.zb, hp.zs);
+    }
 }
 
 __global__ void k_face_bin1(GridDev g, uint32_t nf, const float* __restrict__ z, float t, SearchParams sp, int step,
-                            FaceSt* __restrict__ S, float3* __restrict__ pts) {
+                            FaceSt* __restrict__ S, float3* __restrict__ pts, HintPar hp, float* __restrict__ hint) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     FaceSt& st = S[i];
     uint32_t Jm = (st.Ja + st.Jc) >> 1;
-    if ((uint32_t)(z[i] > t) == st.lab_m) st.Ja = Jm; else st.Jc = Jm;
-    if (step + 1 < sp.bin1)
+    float zm = z[i];
+    if ((uint32_t)(zm > t) == st.lab_m) { st.Ja = Jm; st.za = zm; } else { st.Jc = Jm; st.zc = zm; }
+    if (step + 1 < sp.bin1) {
         pts[i] = face_world2(g, st.F, ray_point(st.F.m, st.d, lbs_param(sp.range1, (st.Ja + st.Jc) >> 1, sp.lin1, sp.bin1)));
+        if (hint) hint[i] = bracket_hint(st.za, st.zc, hp.t, hp.zb, hp.zs);
+    }
 }
 
 // end of step 1: q == m gives p_f = m; else keep q and mark the face active
@@ -214,11 +282,13 @@ __global__ void k_face_lin2_gen(GridDev g, const uint32_t* __restrict__ list, ui
 }
 
 __global__ void k_face_lin2(GridDev g, const uint32_t* __restrict__ list, uint32_t na, const float* __restrict__ z,
-                            float t, SearchParams sp, FaceSt* __restrict__ S, float3* __restrict__ pts) {
+                            float t, SearchParams sp, FaceSt* __restrict__ S, float3* __restrict__ pts, HintPar hp,
+                            float* __restrict__ hint) {
     uint32_t li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= na) return;
     FaceSt& st = S[list[li]];
     uint32_t Ja[2], Jc[2];
+    float za[2], zc[2];
     for (int r = 0; r < 2; ++r) {
         int first = sp.lin2;
         for (int j = 1; j <= sp.lin2; ++j)
@@ -229,26 +299,38 @@ __global__ void k_face_lin2(GridDev g, const uint32_t* __restrict__ list, uint32
             }
         Ja[r] = (uint32_t)(first - 1) << sp.bin2;
         Jc[r] = (uint32_t)first << sp.bin2;
-        if (sp.bin2 > 0)
+        // the rays start at q, the step-1 bracket end Ja, whose logit is za
+        za[r] = first > 1 ? z[(size_t)(r * sp.lin2 + first - 2) * na + li] : st.za;
+        zc[r] = z[(size_t)(r * sp.lin2 + first - 1) * na + li];
+        if (sp.bin2 > 0) {
             pts[(size_t)r * na + li] =
                 face_world2(g, st.F, ray_point(st.q, ray2(st, r), lbs_param(sp.range2, (Ja[r] + Jc[r]) >> 1, sp.lin2, sp.bin2)));
+            if (hint) hint[(size_t)r * na + li] = bracket_hint(za[r], zc[r], hp.t, hp.zb, hp.zs);
+        }
     }
     st.J1a = Ja[0]; st.J1c = Jc[0]; st.J2a = Ja[1]; st.J2c = Jc[1];
+    st.z1a = za[0]; st.z1c = zc[0]; st.z2a = za[1]; st.z2c = zc[1];
 }
 
 __global__ void k_face_bin2(GridDev g, const uint32_t* __restrict__ list, uint32_t na, const float* __restrict__ z,
-                            float t, SearchParams sp, int step, FaceSt* __restrict__ S, float3* __restrict__ pts) {
+                            float t, SearchParams sp, int step, FaceSt* __restrict__ S, float3* __restrict__ pts,
+                            HintPar hp, float* __restrict__ hint) {
     uint32_t li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= na) return;
     FaceSt& st = S[list[li]];
     uint32_t* Ja[2] = {&st.J1a, &st.J2a};
     uint32_t* Jc[2] = {&st.J1c, &st.J2c};
+    float* za[2] = {&st.z1a, &st.z2a};
+    float* zc[2] = {&st.z1c, &st.z2c};
     for (int r = 0; r < 2; ++r) {
         uint32_t Jm = (*Ja[r] + *Jc[r]) >> 1;
-        if ((uint32_t)(z[(size_t)r * na + li] > t) == st.lab_m) *Ja[r] = Jm; else *Jc[r] = Jm;
-        if (step + 1 < sp.bin2)
+        float zm = z[(size_t)r * na + li];
+        if ((uint32_t)(zm > t) == st.lab_m) { *Ja[r] = Jm; *za[r] = zm; } else { *Jc[r] = Jm; *zc[r] = zm; }
+        if (step + 1 < sp.bin2) {
             pts[(size_t)r * na + li] =
                 face_world2(g, st.F, ray_point(st.q, ray2(st, r), lbs_param(sp.range2, (*Ja[r] + *Jc[r]) >> 1, sp.lin2, sp.bin2)));
+            if (hint) hint[(size_t)r * na + li] = bracket_hint(*za[r], *zc[r], hp.t, hp.zb, hp.zs);
+        }
     }
 }
 
@@ -275,7 +357,15 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
                      cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err) {
     if (!nf) return ODC_OK;
     const float t = mlp_logit_threshold(iso);
+    st->zt = t;
+    const HintPar hp{t, st->zband, st->zsplit};
     size_t nmax = (size_t)nf * std::max(sp.lin1, 2 * sp.lin2);
+    float* hint = nullptr;
+    if (mlp_precision(st) == ODC_PREC_BF16) {
+        void* ph;
+        S_TRY(mlp_scratch(st, 36, (size_t)nf * 2 * 4, &ph, err));
+        hint = (float*)ph;
+    }
     void *pS, *ppts, *pz, *pact, *poff, *plist, *pcnt;
     S_TRY(mlp_scratch(st, 10, (size_t)nf * sizeof(FaceSt), &pS, err));
     S_TRY(mlp_scratch(st, 2, nmax * 12, &ppts, err));
@@ -298,10 +388,10 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
     S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, nrq, err));
     k_face_m<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, S, pts); note_launch();
     S_TRY(mlp_eval_list(st, pts, (int64_t)nf * sp.lin1, z, -1, s, nrq, err));
-    k_face_lin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, S, pts); note_launch();
+    k_face_lin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, S, pts, hp, hint); note_launch();
     for (int b = 0; b < sp.bin1; ++b) {
-        S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, nrq, err));
-        k_face_bin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, b, S, pts); note_launch();
+        S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, nrq, err, hint));
+        k_face_bin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, b, S, pts, hp, hint); note_launch();
     }
     k_face_fin1<<<nblk(nf), 256, 0, s>>>(nf, sp, S, pf, flags, act, dec); note_launch();
     *nq += (int64_t)nf * (1 + sp.lin1 + sp.bin1);
@@ -316,10 +406,10 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
     // step 2: both rays from q, then step 3
     k_face_lin2_gen<<<nblk(na, 128), 128, 0, s>>>(g, list, na, sp, S, pts); note_launch();
     S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2 * sp.lin2, z, -1, s, nrq, err));
-    k_face_lin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, S, pts); note_launch();
+    k_face_lin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, S, pts, hp, hint); note_launch();
     for (int b = 0; b < sp.bin2; ++b) {
-        S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2, z, -1, s, nrq, err));
-        k_face_bin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, b, S, pts); note_launch();
+        S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2, z, -1, s, nrq, err, hint));
+        k_face_bin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, b, S, pts, hp, hint); note_launch();
     }
     k_face_fin2<<<nblk(na, 128), 128, 0, s>>>(list, na, sp, S, pf, flags, dec); note_launch();
     S_CK(cudaGetLastError());

@@ -148,6 +148,26 @@ def test_bf16_extract_equals_fp32_plain_path(ctx, mlp, n, split):
     assert m16.stats["n_requeries"] > 0
 
 
+@pytest.mark.parametrize("iso", [0.3, 0.7])
+def test_bf16_extract_equals_fp32_plain_path_off_half_iso(ctx, mlp, iso):
+    """The band and the split margin are measured from logit(iso), not from 0."""
+    g = I.cube_grid(56)
+    v32, t32 = ctx.extract(mlp, g, steps_1d=15, precision=0, iso=iso).to_host()
+    T32, d32 = ctx.debug("T"), ctx.search_decisions()
+    m16 = ctx.extract(mlp, g, steps_1d=15, precision=1, band=BF16_BAND, iso=iso)
+    v16, t16 = m16.to_host()
+    assert np.array_equal(ctx.debug("T"), T32)
+    d16 = ctx.search_decisions()
+    for k in d32:
+        assert np.array_equal(d16[k], d32[k]), k
+    assert np.array_equal(t16, t32) and np.array_equal(v16, v32)
+    rng = np.random.default_rng(5)
+    pts = rng.uniform(-1, 1, (200000, 3)).astype(np.float32)
+    l16, _ = ctx.eval_points(mlp, pts, iso=iso, precision=1, band=BF16_BAND)
+    l32, _ = ctx.eval_points(mlp, pts, iso=iso, precision=0)
+    assert np.array_equal(l16, l32)
+
+
 def test_bf16_extract_replay_parity(ctx, mlp):
     mesh, ref, rep, verts, tris = replay_parity(ctx, mlp, I.cube_grid(32), 15, precision=1, band=BF16_BAND)
     assert rep["vert_max_err"] < 1e-4
