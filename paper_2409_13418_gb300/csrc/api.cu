@@ -316,16 +316,16 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
 
     SearchParams sp{prm->steps_1d, prm->s2d_lin1, prm->s2d_bin1, prm->s2d_range1,
                     prm->s2d_lin2, prm->s2d_bin2, prm->s2d_range2, prm->ic_split};
-    int64_t nq = 0, nrq = 0;
+    int64_t nq = 0;
 
     const long long launches0 = launch_count();
-    mlp_timing_begin(c->mlp);
+    mlp_timing_begin(c->mlp, st);
     ODC_CK(cudaEventRecord(c->ev[0], st));
     // ---- a1: grid occupancy
     if (kind == ODC_SRC_CSG) {
         launch_csg_grid(g, d_prims, d_cull, n_prims, bits, st);
     } else {
-        s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &nrq, &g_err);
+        s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &g_err);
         if (s != ODC_OK) return s;
     }
     nq += (int64_t)g.nv[0] * g.nv[1] * g.nv[2];
@@ -398,7 +398,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         launch_bisect_csg(g, bits, edges, E, prm->steps_1d, d_prims, d_cull, n_prims, T, st);
         nq += (int64_t)E * prm->steps_1d;
     } else {
-        s = mlp_bisect(c->mlp, g, bits, edges, E, prm->steps_1d, prm->iso, T, st, &nq, &nrq, &g_err);
+        s = mlp_bisect(c->mlp, g, bits, edges, E, prm->steps_1d, prm->iso, T, st, &nq, &g_err);
         if (s != ODC_OK) return s;
     }
     ODC_CK(cudaGetLastError());
@@ -410,7 +410,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
                         dec, st);
     } else {
         s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, dec, st, &nq,
-                      &nrq, &g_err);
+                      &g_err);
         if (s != ODC_OK) return s;
     }
     ODC_CK(cudaGetLastError());
@@ -446,11 +446,13 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     out->d_tris = (const int32_t*)tris;
     odc_stats& S = out->stats;
     S.n_edges = E; S.n_face_segs = F; S.n_cells = C; S.n_verts3 = V3; S.n_case3 = N3;
-    S.n_flips = nflip; S.fix_rounds = rounds; S.n_queries = nq; S.n_requeries = nrq;
+    S.n_flips = nflip; S.fix_rounds = rounds; S.n_queries = nq; S.n_requeries = 0;
     for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&S.stage_ms[i], c->ev[i], c->ev[i + 1]);
     cudaEventElapsedTime(&S.stage_ms[7], c->ev[0], c->ev[7]);
     S.n_launches = (int32_t)(launch_count() - launches0);
     if (kind == ODC_SRC_MLP) {
+        mlp_timing_finish(c->mlp, st);
+        S.n_requeries = mlp_fp32_requery_count(c->mlp);
         mlp_timing_collect(c->mlp, 0, &S.mlp_ms, &S.mlp_flops, &S.mlp_launches);
         mlp_timing_collect(c->mlp, 1, &S.tc_ms, &S.tc_flops, &S.tc_launches);
         mlp_timing_collect(c->mlp, 2, &S.split_ms, &S.split_flops, &S.split_launches);

@@ -8,6 +8,7 @@
 // before sincospi.  The BF16 tensor-core path lives in mlp_tc.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -38,7 +39,8 @@ odc_status mlp_check(const odc_mlp* m, std::string* err) {
 float mlp_logit_threshold(float iso) { return (float)std::log((double)iso / (1.0 - (double)iso)); }
 
 int mlp_precision(const MlpState* st) { return st->precision; }
-int64_t mlp_split_count(const MlpState* st) { return st ? st->n_split : 0; }
+int64_t mlp_split_count(const MlpState* st) { return st ? (int64_t)st->hq[1] : 0; }
+int64_t mlp_fp32_requery_count(const MlpState* st) { return st ? (int64_t)st->hq[2] : 0; }
 
 #define MLP_CK(call)                                                                        \
     do {                                                                                    \
@@ -82,12 +84,22 @@ cudaEvent_t* mlp_ev_pair(MlpState* st, int kind) {
     return p;
 }
 
-void mlp_timing_begin(MlpState* st) {
+void mlp_timing_begin(MlpState* st, cudaStream_t s) {
     if (!st) return;
     st->ev_used = 0;
     st->flops[0] = st->flops[1] = st->flops[2] = 0.0;
     st->launches[0] = st->launches[1] = st->launches[2] = 0;
-    st->n_split = 0;
+    for (auto& v : st->hq) v = 0;
+    if (st->dq) cudaMemsetAsync(st->dq, 0, 4 * sizeof(unsigned long long), s);
+}
+
+void mlp_timing_finish(MlpState* st, cudaStream_t s) {
+    if (!st || !st->dq) return;
+    if (cudaMemcpyAsync(st->hq, st->dq, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        for (auto& v : st->hq) v = 0;
+    }
 }
 
 void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_t* launches) {
@@ -101,7 +113,9 @@ void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_
         if (cudaEventElapsedTime(&t, st->ev[2 * i], st->ev[2 * i + 1]) == cudaSuccess) *ms += t;
         else cudaGetLastError();
     }
-    *flops = st->flops[kind];
+    // device-sized lists: hq[0] BF16, hq[1] split-FP16 (three products), hq[2] FP32
+    const double dev = kind == 0 ? (double)st->hq[2] : kind == 1 ? (double)st->hq[0] : 3.0 * (double)st->hq[1];
+    *flops = st->flops[kind] + kFlopsPerQuery * dev;
     *launches = st->launches[kind];
 }
 
@@ -110,6 +124,7 @@ void mlp_destroy(MlpState* st) {
     for (auto& e : st->ev)
         if (e) cudaEventDestroy(e);
     if (st->wblob) cudaFree(st->wblob);
+    if (st->dq) cudaFree(st->dq);
     for (int i = 0; i < kScratchSlots; ++i)
         if (st->scr[i]) cudaFree(st->scr[i]);
     mlp_tc_destroy(st);
@@ -123,6 +138,12 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     if (r != ODC_OK) return r;
     if (!*pst) *pst = new MlpState();
     MlpState* st = *pst;
+    if (!st->sms) {
+        int dev = 0;
+        MLP_CK(cudaGetDevice(&dev));
+        MLP_CK(cudaDeviceGetAttribute(&st->sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    if (!st->dq) MLP_CK(cudaMalloc((void**)&st->dq, 8 * sizeof(unsigned long long)));
     st->precision = m->precision;
     st->band = m->band;
     st->split = m->no_split ? 0 : 1;
@@ -252,8 +273,10 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
     __syncthreads();
 }
 
+// Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// of min(n, *Q.cnt) queries (the tile loop is uniform within a CTA).
 __global__ void __launch_bounds__(kThreads, 1)
-    k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n, float scale, float radius, float amp,
+    k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n_max, float scale, float radius, float amp,
                float* __restrict__ zout) {
     extern __shared__ __align__(16) float sm[];
     float* act = sm;                         // [kTM][kActStride], layers run in place
@@ -261,37 +284,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ float3 xs[kTM];
     __shared__ float part[kTM][4];
     const int tid = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * kTM;
-    if (tid < kTM) {
-        int64_t q = base + tid;
-        xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
-    }
-    __syncthreads();
+    const int64_t n = query_count(Q, n_max);
     const float* B = wb + kOffB;
-    for (int i = tid; i < kNF * kTM; i += kThreads) {
-        int j = i / kTM, m = i % kTM;
-        float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
-        act[m * kActStride + j] = sc.x;
-        act[m * kActStride + kNF + j] = sc.y;
-    }
-    __syncthreads();
-    for (int l = 0; l < kNL; ++l) dense_relu(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
-    {
-        int m = tid >> 2, p = tid & 3;
-        const float* w5 = wb + kOffW[kNL];
-        float s = 0.0f;
-        for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[m * kActStride + k], w5[k], s);
-        part[m][p] = s;
-    }
-    __syncthreads();
-    if (tid < kTM && base + tid < n) {
-        float f = ((part[tid][0] + part[tid][1]) + (part[tid][2] + part[tid][3])) + wb[kOffb[kNL]];
-        zout[base + tid] = envelope_logit(xs[tid], f, scale, radius, amp);
+    for (int64_t base = (int64_t)blockIdx.x * kTM; base < n; base += (int64_t)gridDim.x * kTM) {
+        if (tid < kTM) {
+            int64_t q = base + tid;
+            xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        for (int i = tid; i < kNF * kTM; i += kThreads) {
+            int j = i / kTM, m = i % kTM;
+            float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
+            act[m * kActStride + j] = sc.x;
+            act[m * kActStride + kNF + j] = sc.y;
+        }
+        __syncthreads();
+        for (int l = 0; l < kNL; ++l) dense_relu(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
+        {
+            int m = tid >> 2, p = tid & 3;
+            const float* w5 = wb + kOffW[kNL];
+            float s = 0.0f;
+            for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[m * kActStride + k], w5[k], s);
+            part[m][p] = s;
+        }
+        __syncthreads();
+        if (tid < kTM && base + tid < n) {
+            float f = ((part[tid][0] + part[tid][1]) + (part[tid][2] + part[tid][3])) + wb[kOffb[kNL]];
+            zout[query_index(Q, base + tid)] = envelope_logit(xs[tid], f, scale, radius, amp);
+        }
     }
 }
 
 static size_t fp32_smem() { return sizeof(float) * (kTM * kActStride + 2 * kKC * kH); }
 
+// n is the query count, or with Q.cnt its upper bound (the count is then
+// accumulated on the device for the FLOP accounting).
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
     if (n <= 0) return ODC_OK;
     static bool attr = false;
@@ -299,15 +326,18 @@ static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float*
         MLP_CK(cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp32_smem()));
         attr = true;
     }
-    int64_t blocks = (n + kTM - 1) / kTM;
+    int64_t tiles = (n + kTM - 1) / kTM;
+    unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)std::max(st->sms, 1));
     cudaEvent_t* ev = mlp_ev_pair(st, 0);
     if (ev) MLP_CK(cudaEventRecord(ev[0], s));
-    k_mlp_fp32<<<(unsigned)blocks, kThreads, fp32_smem(), s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z); note_launch();
+    k_mlp_fp32<<<grid, kThreads, fp32_smem(), s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z); note_launch();
     if (ev) MLP_CK(cudaEventRecord(ev[1], s));
     MLP_CK(cudaGetLastError());
-    int64_t real = n;
-    if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];   // grid mode: padding lanes excluded
-    st->flops[0] += kFlopsPerQuery * (double)real;
+    if (!Q.cnt) {
+        int64_t real = n;
+        if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];   // grid mode: padding lanes excluded
+        st->flops[0] += kFlopsPerQuery * (double)real;
+    }
     st->launches[0] += 1;
     return ODC_OK;
 }
@@ -324,80 +354,33 @@ __global__ void k_route(const float* __restrict__ hint, int64_t n, float zs, flo
     r[i] = h < zs ? 2 : (h < zb ? (split ? 1 : 2) : 0);
 }
 // Queries of tier `from` whose logit lies within thr of t move to tier `to`;
-// flag = the queries now in tier `to`.
-__global__ void k_tier_flag(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr,
-                            uint8_t* __restrict__ r, uint32_t* __restrict__ flag) {
+// the queries now in tier `to` are appended to list (one atomic per warp:
+// the list order varies between runs, the logits written back through it do
+// not) and counted in *cnt and *total.
+__global__ void k_tier_list(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr,
+                            uint8_t* __restrict__ r, int* __restrict__ list, unsigned long long* __restrict__ cnt,
+                            unsigned long long* __restrict__ total) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int ri = r[i];
-    if (ri == from && fabsf(z[i] - t) < thr) {
-        ri = to;
-        r[i] = (uint8_t)to;
+    const int lane = threadIdx.x & 31;
+    bool f = false;
+    if (i < n) {
+        int ri = r[i];
+        if (ri == from && fabsf(z[i] - t) < thr) {
+            ri = to;
+            r[i] = (uint8_t)to;
+        }
+        f = ri == to;
     }
-    flag[i] = ri == to ? 1u : 0u;
-}
-__global__ void k_band_gather(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ off, int64_t n,
-                              int* __restrict__ idx) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && flag[i]) idx[off[i]] = (int)i;
-}
-__global__ void k_band_scatter(const int* __restrict__ idx, const uint32_t* __restrict__ cnt,
-                               const float* __restrict__ zr, float* __restrict__ z) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < *cnt) z[idx[i]] = zr[i];
-}
-__global__ void k_grid_points(GridDev g, const int* __restrict__ idx, const uint32_t* __restrict__ cnt,
-                              float3* __restrict__ pts) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *cnt) return;
-    QuerySrc Q{nullptr, nullptr, g};
-    pts[i] = query_point(Q, idx[i]);
-}
-
-__global__ void k_gather_pts(const float3* __restrict__ pts, const int* __restrict__ idx,
-                             const uint32_t* __restrict__ cnt, float3* __restrict__ out) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < *cnt) out[i] = pts[idx[i]];
-}
-
-// Indices of the queries of tier `to` after promotion (see k_tier_flag), in
-// increasing order (scratch slots base..base+3); the count is read back.
-static odc_status tier_list(MlpState* st, const float* z, int64_t n, uint8_t* r, int from, int to, float thr,
-                            int base, int** idx, uint32_t** dcnt, uint32_t* hcnt, cudaStream_t s, std::string* err) {
-    void *pflag, *poff, *pidx, *pcnt;
-    odc_status rc;
-    if ((rc = mlp_scratch(st, base, n * 4 + 64, &pflag, err)) != ODC_OK) return rc;
-    if ((rc = mlp_scratch(st, base + 1, n * 4 + scan_tmp_elems(n) * 8 + 64, &poff, err)) != ODC_OK) return rc;
-    if ((rc = mlp_scratch(st, base + 2, n * 4 + 64, &pidx, err)) != ODC_OK) return rc;
-    if ((rc = mlp_scratch(st, base + 3, 64, &pcnt, err)) != ODC_OK) return rc;
-    uint32_t* flag = (uint32_t*)pflag;
-    uint32_t* off = (uint32_t*)poff;
-    uint32_t* tmp = off + ((n + 63) / 64) * 64;
-    unsigned blocks = (unsigned)((n + 255) / 256);
-    k_tier_flag<<<blocks, 256, 0, s>>>(z, n, st->zt, from, to, thr, r, flag); note_launch();
-    exclusive_scan<uint32_t>(flag, off, (size_t)n, tmp, (uint32_t*)pcnt, s);
-    k_band_gather<<<blocks, 256, 0, s>>>(flag, off, n, (int*)pidx); note_launch();
-    MLP_CK(cudaMemcpyAsync(hcnt, pcnt, 4, cudaMemcpyDeviceToHost, s));
-    MLP_CK(cudaStreamSynchronize(s));
-    *idx = (int*)pidx;
-    *dcnt = (uint32_t*)pcnt;
-    return ODC_OK;
-}
-
-// Points of the listed queries (scratch slot ps).
-static odc_status gather_points(MlpState* st, const QuerySrc& Q, const int* idx, const uint32_t* dcnt, uint32_t m,
-                                int ps, float3** out, cudaStream_t s, std::string* err) {
-    void* p;
-    odc_status rc;
-    if ((rc = mlp_scratch(st, ps, (size_t)m * 12 + 64, &p, err)) != ODC_OK) return rc;
-    if (Q.idx) { *err = "nested gather"; return ODC_ERR_INTERNAL; }
-    if (Q.pts) {
-        k_gather_pts<<<(m + 255) / 256, 256, 0, s>>>(Q.pts, idx, dcnt, (float3*)p); note_launch();
-    } else {
-        k_grid_points<<<(m + 255) / 256, 256, 0, s>>>(Q.g, idx, dcnt, (float3*)p); note_launch();
+    const uint32_t b = __ballot_sync(0xffffffffu, f);
+    if (!b) return;
+    const int leader = __ffs(b) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) {
+        base = atomicAdd(cnt, (unsigned long long)__popc(b));
+        atomicAdd(total, (unsigned long long)__popc(b));
     }
-    *out = (float3*)p;
-    return ODC_OK;
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (f) list[base + __popc(b & ((1u << lane) - 1u))] = (int)i;
 }
 
 // Tiered evaluation (A.2.2 binary decision at iso): the sign of every logit
@@ -407,85 +390,62 @@ static odc_status gather_points(MlpState* st, const QuerySrc& Q, const int* idx,
 // zsplit; the FP32 SIMT network takes the rest.  Without the split tier the
 // whole band goes to FP32.  With hints, queries predicted inside the band
 // (or inside zsplit) start at the split (or FP32) tier: the tiers' acceptance
-// rules are unchanged, so only the cost depends on the hints.
+// rules are unchanged, so only the cost depends on the hints.  Each tier's
+// list is built and consumed on the device (its size stays there), so the
+// evaluation needs no host round trip.
 static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float* z, const float* hint, cudaStream_t s,
-                              int64_t* nrq, std::string* err) {
+                              std::string* err) {
     odc_status r;
-    void* pr;
+    void *pr, *pl0, *pl1, *pl2;
     if ((r = mlp_scratch(st, 24, (size_t)n + 64, &pr, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, 25, (size_t)n * 4 + 64, &pl1, err)) != ODC_OK) return r;
+    if ((r = mlp_scratch(st, 26, (size_t)n * 4 + 64, &pl2, err)) != ODC_OK) return r;
+    if (Q.idx) { *err = "nested query index"; return ODC_ERR_INTERNAL; }
     uint8_t* route = (uint8_t*)pr;
+    unsigned long long* cnt = st->dq + 4;
     const unsigned blocks = (unsigned)((n + 255) / 256);
+    MLP_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
     k_route<<<blocks, 256, 0, s>>>(hint, n, st->zsplit, st->zband, st->split, route); note_launch();
     if (!hint) {
         if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
     } else {
-        int* idx0;
-        uint32_t *dc0, n0 = 0;
-        if ((r = tier_list(st, z, n, route, -1, 0, 0.0f, 28, &idx0, &dc0, &n0, s, err)) != ODC_OK) return r;
-        if (n0) {
-            float3* p0;
-            void* pz0;
-            if ((r = gather_points(st, Q, idx0, dc0, n0, 32, &p0, s, err)) != ODC_OK) return r;
-            if ((r = mlp_scratch(st, 33, (size_t)n0 * 4 + 64, &pz0, err)) != ODC_OK) return r;
-            QuerySrc L0{p0, nullptr, Q.g};
-            if ((r = mlp_tc_eval(st, L0, n0, (float*)pz0, s, err)) != ODC_OK) return r;
-            k_band_scatter<<<(n0 + 255) / 256, 256, 0, s>>>(idx0, dc0, (const float*)pz0, z); note_launch();
-        }
+        if ((r = mlp_scratch(st, 27, (size_t)n * 4 + 64, &pl0, err)) != ODC_OK) return r;
+        k_tier_list<<<blocks, 256, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, route, (int*)pl0, cnt + 0, st->dq + 0); note_launch();
+        QuerySrc L0{Q.pts, (const int*)pl0, Q.g, cnt + 0};
+        if ((r = mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK) return r;
     }
     if (st->split) {
-        int* idx1;
-        uint32_t *dc1, n1 = 0;
-        if ((r = tier_list(st, z, n, route, 0, 1, st->zband, 4, &idx1, &dc1, &n1, s, err)) != ODC_OK) return r;
-        if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
-        if (n1) {
-            float3* p1;
-            void* pz1;
-            if ((r = gather_points(st, Q, idx1, dc1, n1, 8, &p1, s, err)) != ODC_OK) return r;
-            if ((r = mlp_scratch(st, 9, (size_t)n1 * 4 + 64, &pz1, err)) != ODC_OK) return r;
-            QuerySrc L1{p1, nullptr, Q.g};
-            if ((r = mlp_tc3_eval(st, L1, n1, (float*)pz1, s, err)) != ODC_OK) return r;
-            k_band_scatter<<<(n1 + 255) / 256, 256, 0, s>>>(idx1, dc1, (const float*)pz1, z); note_launch();
-            st->n_split += n1;
-        }
+        k_tier_list<<<blocks, 256, 0, s>>>(z, n, st->zt, 0, 1, st->zband, route, (int*)pl1, cnt + 1, st->dq + 1); note_launch();
+        QuerySrc L1{Q.pts, (const int*)pl1, Q.g, cnt + 1};
+        if ((r = mlp_tc3_eval(st, L1, n, z, s, err)) != ODC_OK) return r;
     }
-    int* idx2;
-    uint32_t *dc2, n2 = 0;
     const int from = st->split ? 1 : 0;
     const float thr = st->split ? st->zsplit : st->zband;
-    if ((r = tier_list(st, z, n, route, from, 2, thr, 16, &idx2, &dc2, &n2, s, err)) != ODC_OK) return r;
-    if ((r = mlp_tc_check(st, err)) != ODC_OK) return r;
-    *nrq += n2;
-    if (n2) {
-        float3* p2;
-        void* pz2;
-        if ((r = gather_points(st, Q, idx2, dc2, n2, 20, &p2, s, err)) != ODC_OK) return r;
-        if ((r = mlp_scratch(st, 21, (size_t)n2 * 4 + 64, &pz2, err)) != ODC_OK) return r;
-        QuerySrc L2{p2, nullptr, Q.g};
-        if ((r = launch_fp32(st, L2, n2, (float*)pz2, s, err)) != ODC_OK) return r;
-        k_band_scatter<<<(n2 + 255) / 256, 256, 0, s>>>(idx2, dc2, (const float*)pz2, z); note_launch();
-    }
+    k_tier_list<<<blocks, 256, 0, s>>>(z, n, st->zt, from, 2, thr, route, (int*)pl2, cnt + 2, st->dq + 2); note_launch();
+    QuerySrc L2{Q.pts, (const int*)pl2, Q.g, cnt + 2};
+    if ((r = launch_fp32(st, L2, n, z, s, err)) != ODC_OK) return r;
     MLP_CK(cudaGetLastError());
     return ODC_OK;
 }
 
 static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int precision, const float* hint,
-                       cudaStream_t s, int64_t* nrq, std::string* err) {
+                       cudaStream_t s, std::string* err) {
     if (precision < 0) precision = st->precision;
     if (precision == ODC_PREC_FP32) return launch_fp32(st, Q, n, z, s, err);
     if (precision == ODC_PREC_SPLIT) return mlp_tc3_eval(st, Q, n, z, s, err);
-    return eval_tiered(st, Q, n, z, hint, s, nrq, err);
+    return eval_tiered(st, Q, n, z, hint, s, err);
 }
 
 odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
-                         int64_t* nrq, std::string* err, const float* hint) {
-    QuerySrc Q{pts, nullptr, GridDev{}};
-    return eval(st, Q, n, z, precision, hint, s, nrq, err);
+                         std::string* err, const float* hint) {
+    QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
+    return eval(st, Q, n, z, precision, hint, s, err);
 }
 
-odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, int64_t* nrq, std::string* err) {
-    QuerySrc Q{nullptr, nullptr, g};
+odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, std::string* err) {
+    QuerySrc Q{nullptr, nullptr, g, nullptr};
     int64_t n = (int64_t)g.W * g.nv[1] * g.nv[2] * 32;
-    return eval(st, Q, n, z, -1, nullptr, s, nrq, err);
+    return eval(st, Q, n, z, -1, nullptr, s, err);
 }
 
 __global__ void k_pts_labels(const float* __restrict__ z, int64_t n, float t, uint8_t* __restrict__ lab) {
@@ -495,13 +455,12 @@ __global__ void k_pts_labels(const float* __restrict__ z, int64_t n, float t, ui
 
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
                       float* logits, cudaStream_t s, std::string* err) {
-    int64_t nrq = 0;
     st->zt = mlp_logit_threshold(iso);
-    odc_status r = mlp_eval_list(st, pts, n, logits, precision, s, &nrq, err);
+    odc_status r = mlp_eval_list(st, pts, n, logits, precision, s, err);
     if (r != ODC_OK) return r;
     k_pts_labels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(logits, n, mlp_logit_threshold(iso), labels); note_launch();
     MLP_CK(cudaGetLastError());
-    return ODC_OK;
+    return mlp_tc_check(st, s, err);
 }
 
 }  // namespace odc

@@ -25,35 +25,39 @@ void mlp_destroy(MlpState* st);
 odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::string* err);
 
 // Logits at n explicit points.  With BF16 precision, every logit within the
-// band is re-taken by the split-FP16 and FP32 tiers (FP32 ones counted in
-// *nrq).  hint (device, n floats, optional): an estimate of |z - logit(iso)|
+// band is re-taken by the split-FP16 and FP32 tiers (counted on the device,
+// see mlp_timing_finish).  hint (device, n floats, optional): an estimate of |z - logit(iso)|
 // per query that lets predicted band queries skip the BF16 pass; it changes
 // the cost, never a decision.
 odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
-                         int64_t* nrq, std::string* err, const float* hint = nullptr);
+                         std::string* err, const float* hint = nullptr);
 // Logits at the grid vertices in label-word order (query q -> word q/32, lane q%32).
-odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, int64_t* nrq, std::string* err);
+odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, std::string* err);
 int mlp_precision(const MlpState* st);
 float mlp_logit_threshold(float iso);
 
 // Grid labels (a1): bit rows as in the CSG path.
 odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, cudaStream_t s, int64_t* nq,
-                    int64_t* nrq, std::string* err);
+                    std::string* err);
 // 1D search (a4) in k wavefronts over all crossing edges.
 odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
-                      float iso, uint32_t* T, cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err);
+                      float iso, uint32_t* T, cudaStream_t s, int64_t* nq, std::string* err);
 // 2D search (a5) in wavefronts over all face segments.
 odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
                      const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
                      uint32_t nf, const SearchParams& sp, float iso, float4* pf, uint8_t* flags, FaceDecisions* dec,
-                     cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err);
+                     cudaStream_t s, int64_t* nq, std::string* err);
 // Start / finish the per-extract accounting of network launches: total
 // event-timed kernel milliseconds and algorithmic FLOPs.
-void mlp_timing_begin(MlpState* st);
+void mlp_timing_begin(MlpState* st, cudaStream_t s);
+// Reads the device-side query counters (synchronises the stream).
+void mlp_timing_finish(MlpState* st, cudaStream_t s);
 // Per kind (0: FP32 SIMT network, 1: tensor-core network).
 void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_t* launches);
 
+// Queries re-taken by the split-FP16 and by the FP32 tier (after mlp_timing_finish).
 int64_t mlp_split_count(const MlpState* st);
+int64_t mlp_fp32_requery_count(const MlpState* st);
 
 // Labels (and logits) at explicit points.
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,

@@ -46,6 +46,7 @@ constexpr OffW kOffW{};
 constexpr Offb kOffb{};
 
 struct MlpTc;   // tensor-core path state (mlp_tc.cu)
+constexpr int kMaxTimedLaunches = 512;
 
 struct MlpState {
     int precision = ODC_PREC_FP32;
@@ -57,19 +58,24 @@ struct MlpState {
     size_t scr_cap[kScratchSlots] = {};
     MlpTc* tc = nullptr;
     // per-launch CUDA events around the network kernels of one extract
-    cudaEvent_t ev[2 * 256] = {};
-    int ev_kind[256] = {};      // 0: FP32 network, 1: BF16 tensor-core network, 2: split-FP16 network
+    cudaEvent_t ev[2 * kMaxTimedLaunches] = {};
+    int ev_kind[kMaxTimedLaunches] = {};   // 0: FP32 network, 1: BF16 tensor-core network, 2: split-FP16 network
     int ev_used = 0;
     double flops[3] = {0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
     int64_t launches[3] = {0, 0, 0};
     int split = 1;              // use the split-FP16 tier for band re-evaluation
-    int64_t n_split = 0;        // queries re-evaluated by the split-FP16 tier in this extract
     float zsplit = 1e-4f;       // |z - zt| below which a split-tier decision is re-taken in FP32
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
+    int sms = 0;                // SM count of the device
+    // device counters: [0..2] queries evaluated from device-sized lists by the
+    // BF16, split-FP16 and FP32 networks since mlp_timing_begin; [4..7] the
+    // list sizes of the current evaluation (tiers 0..2)
+    unsigned long long* dq = nullptr;
+    unsigned long long hq[4] = {0, 0, 0, 0};   // host copy of dq[0..3] (mlp_timing_finish)
 };
 
-// Event pair around one network launch of the given kind (none once 256 are in use).
+// Event pair around one network launch of the given kind (none once all are in use).
 cudaEvent_t* mlp_ev_pair(MlpState* st, int kind);
 constexpr double kFlopsPerQuery = 2.0 * (2.0 * kNF * kH + 3.0 * kH * kH + kH);
 
@@ -79,7 +85,7 @@ struct QuerySrc;
 odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 void mlp_tc_destroy(MlpState* st);
 // ODC_ERR_TIMEOUT if a tensor-core launch since the last check hit a bounded wait.
-odc_status mlp_tc_check(MlpState* st, std::string* err);
+odc_status mlp_tc_check(MlpState* st, cudaStream_t s, std::string* err);
 // Split-BF16 network (three BF16 products per layer, FP32 accumulation).
 odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 
@@ -101,14 +107,24 @@ __device__ __forceinline__ float envelope_logit(float3 x, float f, float scale, 
 }
 
 // Query points either from a list or from the grid in label-word order.
+// With idx, query q of a launch is query idx[q] of the source and its logit
+// goes to z[idx[q]]; with cnt, the launch covers min(n, *cnt) queries (a
+// device-side list size, so the host needs no count).
 struct QuerySrc {
     const float3* pts;       // list mode when non-null
-    const int* idx;          // optional gather indices into pts
+    const int* idx;          // optional indices into the source (and the output)
     GridDev g;               // grid mode
+    const unsigned long long* cnt;   // optional device-side query count
 };
 
-__device__ __forceinline__ float3 query_point(const QuerySrc& Q, int64_t q) {
-    if (Q.pts) return Q.pts[Q.idx ? Q.idx[q] : q];
+__device__ __forceinline__ int64_t query_count(const QuerySrc& Q, int64_t n) {
+    return Q.cnt ? min(n, (int64_t)*Q.cnt) : n;
+}
+__device__ __forceinline__ int64_t query_index(const QuerySrc& Q, int64_t q) { return Q.idx ? Q.idx[q] : q; }
+
+__device__ __forceinline__ float3 query_point(const QuerySrc& Q, int64_t q0) {
+    const int64_t q = query_index(Q, q0);
+    if (Q.pts) return Q.pts[q];
     int64_t w = q >> 5;
     int l = (int)(q & 31);
     int xw = (int)(w % Q.g.W);

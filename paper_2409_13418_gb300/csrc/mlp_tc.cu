@@ -166,6 +166,7 @@ struct TcParams {
     float* z;
     int* err;
     float wscale_inv[4];    // split path: 2^-s_l undoing the weight scale of layer l
+    float zt;               // split path: logit written for an out-of-range query (forces re-evaluation)
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -189,7 +190,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = threadIdx.x; i < 3 * kNF; i += blockDim.x) sp[5 * kH + 4 + i] = P.wblob[kOffB + i];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = (P.n + kRows - 1) / kRows;
+    const int64_t n = query_count(P.Q, P.n);
+    const int64_t ntiles = (n + kRows - 1) / kRows;
+    if ((int64_t)blockIdx.x >= ntiles) return;   // uniform per CTA, before any barrier or TMEM use
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int64_t q = t * kRows + sub * kTileM + r;
-            const bool valid = q < P.n;
+            const bool valid = q < n;
             float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
             // Fourier features -> A[:, 0:128]
             for (int j = 0; j < kNF; j += 8) {
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_before();
                     f += sp[5 * kH];
-                    if (valid) P.z[q] = envelope_logit(x, f, P.scale, P.radius, P.amp);
+                    if (valid) P.z[query_index(P.Q, q)] = envelope_logit(x, f, P.scale, P.radius, P.amp);
                 }
             }
         }
@@ -428,7 +431,9 @@ __global__ void __launch_bounds__(kThreads3, 1)
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = (P.n + kTileM - 1) / kTileM;
+    const int64_t n = query_count(P.Q, P.n);
+    const int64_t ntiles = (n + kTileM - 1) / kTileM;
+    if ((int64_t)blockIdx.x >= ntiles) return;   // uniform per CTA, before any barrier or TMEM use
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages3; ++s) {
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int64_t q = t * kTileM + r;
-            const bool valid = q < P.n;
+            const bool valid = q < n;
             bool range_ok = true;
             float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
             for (int j = 0; j < kNF; j += 8) {
@@ -581,7 +586,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
                     tc_fence_before();
                     f += __ldg(P.wblob + kOffb_(kNL));
                     // an activation out of FP16 range sends the query to the FP32 tier (|z| = 0)
-                    if (valid) P.z[q] = range_ok ? envelope_logit(x, f, P.scale, P.radius, P.amp) : 0.0f;
+                    if (valid) P.z[query_index(P.Q, q)] = range_ok ? envelope_logit(x, f, P.scale, P.radius, P.amp) : P.zt;
                 }
             }
         }
@@ -719,7 +724,7 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
     }
     int64_t tiles = (n + tc::kRows - 1) / tc::kRows;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {1.f, 1.f, 1.f, 1.f}};
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {1.f, 1.f, 1.f, 1.f}, st->zt};
     cudaEvent_t* ev = mlp_ev_pair(st, 1);
     if (ev) cudaEventRecord(ev[0], s);
     tc::k_mlp_tc<<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2], T->maps[3], P);
@@ -730,9 +735,11 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
         *err = std::string("k_mlp_tc launch: ") + cudaGetErrorString(e);
         return ODC_ERR_CUDA;
     }
-    int64_t real = n;
-    if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];
-    st->flops[1] += kFlopsPerQuery * (double)real;
+    if (!Q.cnt) {   // device-sized lists are counted on the device
+        int64_t real = n;
+        if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];
+        st->flops[1] += kFlopsPerQuery * (double)real;
+    }
     st->launches[1] += 1;
     return ODC_OK;
 }
@@ -746,7 +753,7 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
     }
     int64_t tiles = (n + tc::kTileM - 1) / tc::kTileM;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {}};
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {}, st->zt};
     for (int l = 0; l < 4; ++l) P.wscale_inv[l] = T->wscale_inv[l];
     cudaEvent_t* ev = mlp_ev_pair(st, 2);
     if (ev) cudaEventRecord(ev[0], s);
@@ -760,20 +767,21 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
         *err = std::string("k_mlp_tc3 launch: ") + cudaGetErrorString(e);
         return ODC_ERR_CUDA;
     }
-    st->flops[2] += 3.0 * kFlopsPerQuery * (double)n;   // three products per layer
+    if (!Q.cnt) st->flops[2] += 3.0 * kFlopsPerQuery * (double)n;   // three products per layer
     st->launches[2] += 1;
     return ODC_OK;
 }
 
-odc_status mlp_tc_check(MlpState* st, std::string* err) {
+odc_status mlp_tc_check(MlpState* st, cudaStream_t s, std::string* err) {
     if (!st || !st->tc || !st->tc->err) return ODC_OK;
     int h = 0;
-    if (cudaMemcpy(&h, st->tc->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpyAsync(&h, st->tc->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
         *err = "cannot read the tensor-core error flag";
         return ODC_ERR_CUDA;
     }
     if (h) {
-        cudaMemset(st->tc->err, 0, sizeof(int));
+        cudaMemsetAsync(st->tc->err, 0, sizeof(int), s);
         *err = "tensor-core kernel: a pipeline wait expired";
         return ODC_ERR_TIMEOUT;
     }

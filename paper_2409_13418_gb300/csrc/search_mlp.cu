@@ -41,17 +41,17 @@ __global__ void k_pack_labels(GridDev g, const float* __restrict__ z, float t, u
 }
 
 odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, cudaStream_t s, int64_t* nq,
-                    int64_t* nrq, std::string* err) {
+                    std::string* err) {
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
     void* pz;
     S_TRY(mlp_scratch(st, 0, nw * 32 * 4, &pz, err));
     st->zt = mlp_logit_threshold(iso);
     st->zgrid = (const float*)pz;
-    S_TRY(mlp_eval_grid(st, g, (float*)pz, s, nrq, err));
+    S_TRY(mlp_eval_grid(st, g, (float*)pz, s, err));
     k_pack_labels<<<nblk(nw * 32), 256, 0, s>>>(g, (const float*)pz, mlp_logit_threshold(iso), bits); note_launch();
     S_CK(cudaGetLastError());
     (void)nq;
-    return ODC_OK;
+    return mlp_tc_check(st, s, err);
 }
 
 // Routing hint for the midpoint of a bracket whose ends have logits za, zc
@@ -129,7 +129,7 @@ __global__ void k_bis_upd(GridDev g, const uint32_t* __restrict__ bits, const ui
 }
 
 odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
-                      float iso, uint32_t* T, cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err) {
+                      float iso, uint32_t* T, cudaStream_t s, int64_t* nq, std::string* err) {
     if (!ne) return ODC_OK;
     void *plo, *ppts, *pz;
     S_TRY(mlp_scratch(st, 1, ne * 4ull, &plo, err));
@@ -151,13 +151,13 @@ odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, cons
     }
     for (int step = 0; step < k; ++step) {
         k_bis_gen<<<nblk(ne), 256, 0, s>>>(g, edges, ne, step, (const uint32_t*)plo, (float3*)ppts); note_launch();
-        S_TRY(mlp_eval_list(st, (const float3*)ppts, ne, (float*)pz, -1, s, nrq, err, hint));
+        S_TRY(mlp_eval_list(st, (const float3*)ppts, ne, (float*)pz, -1, s, err, hint));
         k_bis_upd<<<nblk(ne), 256, 0, s>>>(g, bits, edges, ne, (const float*)pz, t, (uint32_t*)plo, step == k - 1, T,
                                            hp, zac, hint); note_launch();
         S_CK(cudaGetLastError());
     }
     *nq += (int64_t)ne * k;
-    return ODC_OK;
+    return mlp_tc_check(st, s, err);
 }
 
 // ------------------------------------------------------------------- 2D
@@ -354,7 +354,7 @@ __global__ void k_face_fin2(const uint32_t* __restrict__ list, uint32_t na, Sear
 odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
                      const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
                      uint32_t nf, const SearchParams& sp, float iso, float4* pf, uint8_t* flags, FaceDecisions* dec,
-                     cudaStream_t s, int64_t* nq, int64_t* nrq, std::string* err) {
+                     cudaStream_t s, int64_t* nq, std::string* err) {
     if (!nf) return ODC_OK;
     const float t = mlp_logit_threshold(iso);
     st->zt = t;
@@ -385,12 +385,12 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
 
     // step 1: m, line samples, bisections
     k_face_init<<<nblk(nf, 128), 128, 0, s>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp.steps_1d, S, pts); note_launch();
-    S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, nrq, err));
+    S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, err));
     k_face_m<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, S, pts); note_launch();
-    S_TRY(mlp_eval_list(st, pts, (int64_t)nf * sp.lin1, z, -1, s, nrq, err));
+    S_TRY(mlp_eval_list(st, pts, (int64_t)nf * sp.lin1, z, -1, s, err));
     k_face_lin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, S, pts, hp, hint); note_launch();
     for (int b = 0; b < sp.bin1; ++b) {
-        S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, nrq, err, hint));
+        S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, err, hint));
         k_face_bin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, b, S, pts, hp, hint); note_launch();
     }
     k_face_fin1<<<nblk(nf), 256, 0, s>>>(nf, sp, S, pf, flags, act, dec); note_launch();
@@ -402,19 +402,20 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
     S_CK(cudaMemcpyAsync(&na, cnt, 4, cudaMemcpyDeviceToHost, s));
     S_CK(cudaStreamSynchronize(s));
     S_CK(cudaGetLastError());
+    S_TRY(mlp_tc_check(st, s, err));
     if (!na) return ODC_OK;
     // step 2: both rays from q, then step 3
     k_face_lin2_gen<<<nblk(na, 128), 128, 0, s>>>(g, list, na, sp, S, pts); note_launch();
-    S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2 * sp.lin2, z, -1, s, nrq, err));
+    S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2 * sp.lin2, z, -1, s, err));
     k_face_lin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, S, pts, hp, hint); note_launch();
     for (int b = 0; b < sp.bin2; ++b) {
-        S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2, z, -1, s, nrq, err, hint));
+        S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2, z, -1, s, err, hint));
         k_face_bin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, b, S, pts, hp, hint); note_launch();
     }
     k_face_fin2<<<nblk(na, 128), 128, 0, s>>>(list, na, sp, S, pf, flags, dec); note_launch();
     S_CK(cudaGetLastError());
     *nq += (int64_t)na * 2 * (sp.lin2 + sp.bin2);
-    return ODC_OK;
+    return mlp_tc_check(st, s, err);
 }
 
 }  // namespace odc
