@@ -159,6 +159,73 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serve_arm(odc, I, net, trace, slots, precision, budget):
+    """Replays an arrival trace through the request loop: a submitter thread
+    submits each request at its arrival time, the caller collects them.
+    Returns latencies (s), per-request cells and the makespan."""
+    srv = odc.Server(0, slots=slots, mem_budget=budget, host_copy=False)
+    try:
+        # warm-up: every slot grows its arenas for the largest resolution once
+        top = max(r for _, r, _ in trace)
+        ids = [srv.submit(I.with_latent(net, 10 ** 6 + k), I.cube_grid(top), steps_1d=STEPS_1D,
+                          precision=precision) for k in range(slots)]
+        for i in ids:
+            assert srv.poll(i)["status"] == 0
+            srv.release(i)
+        ids = [None] * len(trace)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for k, (t, res, seed) in enumerate(trace):
+                d = t0 + t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids[k] = srv.submit(I.with_latent(net, seed), I.cube_grid(res), steps_1d=STEPS_1D,
+                                    precision=precision)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, cells, t_first, t_last, bad = [], [], None, None, 0
+        for k in range(len(trace)):
+            while ids[k] is None:
+                time.sleep(0.0005)
+            r = srv.poll(ids[k])
+            bad += r["status"] != 0
+            lat.append(r["t_end"] - r["t_submit"])
+            cells.append(trace[k][1] ** 3)
+            t_first = r["t_submit"] if t_first is None else min(t_first, r["t_submit"])
+            t_last = r["t_end"] if t_last is None else max(t_last, r["t_end"])
+            srv.release(ids[k])
+        th.join()
+    finally:
+        srv.close()
+    return lat, cells, t_last - t_first, bad
+
+
+def serve_bench(odc, I, seconds: float, slots: int):
+    """Serving workload: Poisson arrivals at 40 req/s for ``seconds``, cube
+    resolutions {64, 128, 256, 512} with weights 0.4/0.3/0.2/0.1, each request
+    a latent-conditioned envelope MLP (one network, a 128-d latent per shape),
+    150 GB admission budget.  Our loop (``slots`` slots, BF16 tiered) against
+    plain one-request-at-a-time GPU ODC (one slot, FIFO, FP32 plain network)."""
+    import numpy as np
+    net = I.envelope_mlp(11, latent_dim=128)
+    trace = I.serving_trace(5, 40.0, seconds)
+    budget = 150 * 10 ** 9
+    out = {"workload": f"Poisson 40 req/s for {seconds:g} s ({len(trace)} requests), cube res "
+                       "{64,128,256,512} w 0.4/0.3/0.2/0.1, latent-conditioned envelope MLP (128-d latent), "
+                       f"k={STEPS_1D}, 150 GB budget; latency = completion - submission (server clock)"}
+    for name, sl, prec in (("ours", slots, odc.PREC_BF16), ("plain_fifo_fp32", 1, odc.PREC_FP32)):
+        lat, cells, span, bad = serve_arm(odc, I, net, trace, sl, prec, budget)
+        lat = np.asarray(lat)
+        out[name] = {"slots": sl, "precision": "bf16 tiered" if prec == odc.PREC_BF16 else "fp32 plain",
+                     "requests": len(lat), "failed": int(bad),
+                     "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                     "mean_s": float(lat.mean()), "makespan_s": span,
+                     "throughput_req_s": len(lat) / span, "throughput_mcells_s": float(np.sum(cells)) / span / 1e6}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,6 +238,9 @@ def main():
     ap.add_argument("--cpu-cells", type=int, default=None,
                     help="oracle sample block edge (default 40 for cpu_baseline, 32 per reference step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0,
+                    help="length of the serving arrival trace (0: skip the serving comparison)")
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -251,7 +321,8 @@ def main():
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        m = ctx.extract(mlp, grid, steps_1d=STEPS_1D, stream=stream.cuda_stream, precision=prec, band=args.band)
+        m = ctx.extract(mlp, grid, steps_1d=STEPS_1D, stream=stream.cuda_stream, precision=prec, band=args.band,
+                        reupload=True)
         v, t = m.to_host()
         vbytes, tbytes = v.nbytes, t.nbytes
     torch.cuda.synchronize()
@@ -306,6 +377,10 @@ def main():
                 "gpu_launches": int(launches),
                 "roofline": roof,
                 "clocks": clocks}
+        if world == 1 and args.serve_seconds > 0:
+            ctx.close()
+            from paper_2409_13418_gb300 import inputs as I
+            line["serving"] = serve_bench(odc, I, args.serve_seconds, args.serve_slots)
         if world == 1 and not args.no_cpu_baseline:
             c, dt, st = cpu_sample(mlp, args.cpu_cells)
             line["cpu_baseline"] = {"value": c / dt / 1e6, "unit": "Mcells/s", "cores": os.cpu_count(),

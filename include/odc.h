@@ -132,8 +132,12 @@ typedef struct {
     float band;
     int32_t no_split;
     float split_zmargin;
-    int32_t reserved;
+    int32_t flags;               /* ODC_MLP_REUPLOAD: prepare and upload the weights even when the
+                                    context already holds the same ones (by default a context that
+                                    holds the same B, W and b only refreshes the latent's folded bias) */
 } odc_mlp;
+
+enum { ODC_MLP_REUPLOAD = 1 };
 
 typedef struct {
     int32_t kind;                /* ODC_SRC_CSG or ODC_SRC_MLP */
@@ -260,6 +264,56 @@ odc_status odc_debug_copy(odc_ctx* ctx, int what, void* dst, size_t max_bytes,
  * (-1 keeps the source's).  Sec. 3 / A.2.2 binary occupancy. */
 odc_status odc_eval_points(odc_ctx* ctx, const odc_source* src, const float* points, int64_t n,
                            float iso, int precision, uint8_t* labels, float* logits);
+
+/* ---- Request loop ---------------------------------------------------------
+ * A server meshes requests of any grid size as they arrive.  Up to ``slots``
+ * requests are on the GPU at once, each on its own stream with its own
+ * context (device arenas, network weights), so their kernels and host round
+ * trips overlap on the device.  Requests are admitted in arrival order when a
+ * slot is free and the estimated device memory of the admitted requests plus
+ * the results not yet released stays within ``mem_budget``.  Each request runs
+ * exactly the odc_extract path, so its mesh is byte-identical whether it runs
+ * alone or among others.  The paper meshes one shape per call (Sec. 3); the
+ * loop is this library's serving layer around that call. */
+typedef struct odc_server odc_server;
+
+typedef struct {
+    int32_t device;
+    int32_t slots;               /* requests on the GPU at once, 1..64 */
+    size_t mem_budget;           /* bytes over admitted requests and held results; 0 = no limit */
+    int32_t host_copy;           /* nonzero: results also carry host copies of the mesh */
+    int32_t reserved;
+} odc_server_config;
+
+typedef struct {
+    odc_status status;           /* the request's own result (ODC_OK or its error) */
+    int32_t slot;                /* slot that ran it */
+    odc_mesh mesh;               /* device buffers owned by the server until odc_result_release */
+    const float* h_verts;        /* host copies when host_copy is set (same lifetime), else NULL */
+    const int32_t* h_tris;
+    double t_submit, t_start, t_end;   /* seconds on the server's monotonic clock */
+    uint64_t est_bytes;          /* device memory charged to the request at admission */
+} odc_result;
+
+/* Create a server (one context and one worker thread per slot). */
+odc_status odc_server_create(const odc_server_config* cfg, odc_server** out);
+/* Finish every queued and admitted request, then free everything, including
+ * unreleased results.  NULL is accepted. */
+odc_status odc_server_destroy(odc_server* srv);
+/* Queue one request.  The source (primitives or weights and latent), grid and
+ * parameters are copied: the caller may reuse its buffers at once.
+ * ODC_SRC_RESIDENT is rejected (ODC_ERR_INVALID_ARG), as are arguments
+ * odc_extract would reject.  *req_id identifies the request. */
+odc_status odc_submit(odc_server* srv, const odc_source* src, const odc_grid* grid, const odc_params* prm,
+                      uint64_t* req_id);
+/* Wait up to timeout_ms milliseconds (negative: no limit) for a request.
+ * ODC_ERR_TIMEOUT: not finished yet; ODC_ERR_INVALID_ARG: unknown id.
+ * Otherwise *out describes the finished request (its own status inside). */
+odc_status odc_poll(odc_server* srv, uint64_t req_id, int32_t timeout_ms, odc_result* out);
+/* Free a finished request's result buffers and forget the request. */
+odc_status odc_result_release(odc_server* srv, uint64_t req_id);
+/* Seconds on the server's monotonic clock (the time base of odc_result). */
+double odc_server_clock(const odc_server* srv);
 
 /* List the crossing edges of a label bitmask without allocating any memory.
  * The paper has no counterpart: this serves callers that cannot call

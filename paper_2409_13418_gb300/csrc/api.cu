@@ -81,7 +81,10 @@ struct odc_ctx {
     size_t nw = 0;
 };
 
-static odc_status arena_ensure(odc_ctx* c, Arena& a, size_t need) {
+// Grow an arena (stream-ordered: the old block is freed and the new one
+// allocated on the stream that uses them, so growth never waits for work of
+// other streams or contexts).
+static odc_status arena_ensure(odc_ctx* c, Arena& a, size_t need, cudaStream_t st) {
     if (need <= a.cap) {
         a.reset();
         return ODC_OK;
@@ -95,12 +98,11 @@ static odc_status arena_ensure(odc_ctx* c, Arena& a, size_t need) {
                                          std::to_string(others + want) + " > " + std::to_string(c->budget) + " bytes)");
     }
     if (a.base) {
-        ODC_CK(cudaDeviceSynchronize());
-        ODC_CK(cudaFree(a.base));
+        ODC_CK(cudaFreeAsync(a.base, st));
         a.base = nullptr;
         a.cap = 0;
     }
-    cudaError_t e = cudaMalloc((void**)&a.base, want);
+    cudaError_t e = cudaMallocAsync((void**)&a.base, want, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ODC_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
@@ -153,7 +155,7 @@ odc_status odc_ctx_create(int device, size_t mem_budget, odc_ctx** out) {
 odc_status odc_ctx_destroy(odc_ctx* c) {
     if (!c) return ODC_OK;
     cudaSetDevice(c->device);
-    if (c->own) cudaStreamSynchronize(c->own);
+    cudaDeviceSynchronize();   // arenas may still be in use on a caller's stream
     mlp_destroy(c->mlp);
     for (Arena* a : {&c->A, &c->B, &c->S})
         if (a->base) cudaFree(a->base);
@@ -216,7 +218,7 @@ static odc_status upload_csg(odc_ctx* c, const odc_source* src, cudaStream_t st,
         cull[i] = make_float4(p.center[0], p.center[1], p.center[2], (float)(rr * rr));
     }
     size_t need = al(sizeof(PrimDev) * n) + al(sizeof(float4) * n);
-    odc_status s = arena_ensure(c, c->S, need);
+    odc_status s = arena_ensure(c, c->S, need, st);
     if (s != ODC_OK) return s;
     *d_prims = (PrimDev*)c->S.take(sizeof(PrimDev) * n);
     *d_cull = (float4*)c->S.take(sizeof(float4) * n);
@@ -292,7 +294,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     size_t stmp = scan_tmp_elems(nw);
     size_t needA = al(nX * 4) + al(nw * 4) + al(nw * sizeof(WordInfo)) + 6 * al(nw * 4) + al(3 * nw * 4) +
                    al(stmp * 8) + al(64 * 8);
-    s = arena_ensure(c, c->A, needA);
+    s = arena_ensure(c, c->A, needA, st);
     if (s != ODC_OK) return s;
     float* dX = (float*)c->A.take(nX * 4);
     uint32_t* bits = (uint32_t*)c->A.take(nw * 4);
@@ -346,7 +348,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     size_t needB = 2 * al(E * 4ull) + al(F * 4ull) + 3 * al(F) + al(F * 16ull) + al(F * sizeof(FaceDecisions)) + al(C * 4ull) + al(C) + al(C * 8ull) +
                    2 * al(C * 4ull) + al(4ull * C * 12) + al((4ull * C + E) * 12) + al(E) + al(E * 16ull) +
                    2 * al(E * 8ull) + al(4ull * E * 12) + al(stmpB * 8) + 1024;
-    s = arena_ensure(c, c->B, needB);
+    s = arena_ensure(c, c->B, needB, st);
     if (s != ODC_OK) return s;
     uint32_t* edges = (uint32_t*)c->B.take(E * 4ull);
     uint32_t* T = (uint32_t*)c->B.take(E * 4ull);
@@ -565,7 +567,7 @@ odc_status odc_eval_points(odc_ctx* c, const odc_source* src, const float* point
     }
     PrimDev* d_prims = c->res_prims;
     float4* d_cull = c->res_cull;
-    s = arena_ensure(c, c->B, need);
+    s = arena_ensure(c, c->B, need, st);
     if (s != ODC_OK) return s;
     float3* dp = (float3*)c->B.take(n * 12);
     uint8_t* dl = (uint8_t*)c->B.take(n);

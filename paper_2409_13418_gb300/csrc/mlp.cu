@@ -51,14 +51,15 @@ int64_t mlp_fp32_requery_count(const MlpState* st) { return st ? (int64_t)st->hq
 
 odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::string* err) {
     if (st->scr_cap[slot] < bytes) {
+        // stream-ordered on the stream of the current call: growth waits for
+        // no other stream or context
         if (st->scr[slot]) {
-            MLP_CK(cudaDeviceSynchronize());
-            cudaFree(st->scr[slot]);
+            MLP_CK(cudaFreeAsync(st->scr[slot], st->stream));
             st->scr[slot] = nullptr;
             st->scr_cap[slot] = 0;
         }
         size_t want = bytes + bytes / 4 + 4096;
-        cudaError_t e = cudaMalloc(&st->scr[slot], want);
+        cudaError_t e = cudaMallocAsync(&st->scr[slot], want, st->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             *err = std::string("MLP scratch allocation failed: ") + cudaGetErrorString(e);
@@ -131,6 +132,8 @@ void mlp_destroy(MlpState* st) {
     delete st;
 }
 
+static odc_status fp32_kernel_setup(std::string* err);
+
 // Upload weights: FP32 transposed copies for the SIMT path (W^T [in][out]),
 // and the BF16 operand tiles of the tensor-core path.
 odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::string* err) {
@@ -138,12 +141,17 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     if (r != ODC_OK) return r;
     if (!*pst) *pst = new MlpState();
     MlpState* st = *pst;
+    st->stream = s;
     if (!st->sms) {
         int dev = 0;
         MLP_CK(cudaGetDevice(&dev));
         MLP_CK(cudaDeviceGetAttribute(&st->sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    if (!st->dq) MLP_CK(cudaMalloc((void**)&st->dq, 8 * sizeof(unsigned long long)));
+    if (!st->dq) {
+        MLP_CK(cudaMalloc((void**)&st->dq, 8 * sizeof(unsigned long long)));
+        odc_status r0 = fp32_kernel_setup(err);
+        if (r0 != ODC_OK) return r0;
+    }
     st->precision = m->precision;
     st->band = m->band;
     st->split = m->no_split ? 0 : 1;
@@ -154,6 +162,30 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->radius = m->env_radius;
     st->amp = m->env_amp;
     const int din = 2 * kNF + m->latent_dim;
+    // Weights already on the device (same B, W, b; only the latent may
+    // differ, as for latent-conditioned shapes of one network): refresh the
+    // folded first-layer bias and keep everything else.
+    std::vector<float> key;
+    key.reserve(kBlobFloats + (size_t)kH * m->latent_dim + 8);
+    key.push_back((float)m->latent_dim);
+    key.insert(key.end(), m->B, m->B + kNF * 3);
+    for (int l = 0; l <= kNL; ++l) {
+        size_t rows = l == kNL ? 1 : kH, cols = l == 0 ? (size_t)din : kH;
+        key.insert(key.end(), m->W[l], m->W[l] + rows * cols);
+        key.insert(key.end(), m->b[l], m->b[l] + rows);
+    }
+    if (st->wblob && !(m->flags & ODC_MLP_REUPLOAD) && key == st->wkey) {
+        std::vector<float> b0(kH);
+        for (int n = 0; n < kH; ++n) {
+            double b = m->b[0][n];
+            for (int j = 0; j < m->latent_dim; ++j) b += (double)m->W[0][(size_t)n * din + j] * (double)m->latent[j];
+            b0[n] = (float)b;
+        }
+        MLP_CK(cudaMemcpyAsync(st->wblob + kOffb[0], b0.data(), sizeof(float) * kH, cudaMemcpyHostToDevice, s));
+        MLP_CK(cudaStreamSynchronize(s));   // b0 is a host temporary
+        return ODC_OK;
+    }
+    st->wkey.clear();   // set again once the upload below has succeeded
     std::vector<float> h(kBlobFloats, 0.0f);
     // B
     std::memcpy(&h[kOffB], m->B, sizeof(float) * kNF * 3);
@@ -181,6 +213,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     MLP_CK(cudaMemcpyAsync(st->wblob, h.data(), sizeof(float) * kBlobFloats, cudaMemcpyHostToDevice, s));
     r = mlp_tc_prepare(st, h.data(), s, err);
     if (r != ODC_OK) return r;
+    st->wkey.swap(key);
     return ODC_OK;
 }
 
@@ -317,15 +350,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 static size_t fp32_smem() { return sizeof(float) * (kTM * kActStride + 2 * kKC * kH); }
 
+static odc_status fp32_kernel_setup(std::string* err) {
+    MLP_CK(cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp32_smem()));
+    return ODC_OK;
+}
+
 // n is the query count, or with Q.cnt its upper bound (the count is then
 // accumulated on the device for the FLOP accounting).
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
     if (n <= 0) return ODC_OK;
-    static bool attr = false;
-    if (!attr) {
-        MLP_CK(cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp32_smem()));
-        attr = true;
-    }
     int64_t tiles = (n + kTM - 1) / kTM;
     unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)std::max(st->sms, 1));
     cudaEvent_t* ev = mlp_ev_pair(st, 0);
@@ -456,6 +489,7 @@ __global__ void k_pts_labels(const float* __restrict__ z, int64_t n, float t, ui
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
                       float* logits, cudaStream_t s, std::string* err) {
     st->zt = mlp_logit_threshold(iso);
+    st->stream = s;
     odc_status r = mlp_eval_list(st, pts, n, logits, precision, s, err);
     if (r != ODC_OK) return r;
     k_pts_labels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(logits, n, mlp_logit_threshold(iso), labels); note_launch();

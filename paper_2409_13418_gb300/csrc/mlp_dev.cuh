@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/odc.h"
 #include "odc_device.cuh"
@@ -54,6 +55,7 @@ struct MlpState {
     float zband = 0.004f;
     float scale = 20.f, radius = 0.5f, amp = 0.15f;
     float* wblob = nullptr;                 // FP32 weight blob (device)
+    std::vector<float> wkey;                // host copy of the uploaded B, W, b (all but the latent)
     void* scr[kScratchSlots] = {};
     size_t scr_cap[kScratchSlots] = {};
     MlpTc* tc = nullptr;
@@ -68,6 +70,7 @@ struct MlpState {
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     int sms = 0;                // SM count of the device
+    cudaStream_t stream = nullptr;   // stream of the current call (scratch growth is ordered on it)
     // device counters: [0..2] queries evaluated from device-sized lists by the
     // BF16, split-FP16 and FP32 networks since mlp_timing_begin; [4..7] the
     // list sizes of the current evaluation (tiers 0..2)

@@ -44,6 +44,7 @@ odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, c
                     std::string* err) {
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
     void* pz;
+    st->stream = s;
     S_TRY(mlp_scratch(st, 0, nw * 32 * 4, &pz, err));
     st->zt = mlp_logit_threshold(iso);
     st->zgrid = (const float*)pz;
@@ -131,6 +132,7 @@ __global__ void k_bis_upd(GridDev g, const uint32_t* __restrict__ bits, const ui
 odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
                       float iso, uint32_t* T, cudaStream_t s, int64_t* nq, std::string* err) {
     if (!ne) return ODC_OK;
+    st->stream = s;
     void *plo, *ppts, *pz;
     S_TRY(mlp_scratch(st, 1, ne * 4ull, &plo, err));
     S_TRY(mlp_scratch(st, 2, ne * 12ull, &ppts, err));
@@ -356,6 +358,7 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
                      uint32_t nf, const SearchParams& sp, float iso, float4* pf, uint8_t* flags, FaceDecisions* dec,
                      cudaStream_t s, int64_t* nq, std::string* err) {
     if (!nf) return ODC_OK;
+    st->stream = s;
     const float t = mlp_logit_threshold(iso);
     st->zt = t;
     const HintPar hp{t, st->zband, st->zsplit};

@@ -261,6 +261,32 @@ def envelope_mlp(seed: int = 0, n_freq: int = 64, sigma: float = 4.0, hidden: in
                      name=f"mlp_seed{seed}")
 
 
+def with_latent(src: MLPSource, seed: int) -> MLPSource:
+    """The same network with a fresh latent ~ N(0, I) (latent-conditioned shapes)."""
+    if src.latent is None:
+        raise ValueError("the network takes no latent")
+    lat = np.random.default_rng(seed).standard_normal(src.latent.shape[0]).astype(np.float32)
+    return MLPSource(B=src.B, weights=src.weights, biases=src.biases, env_scale=src.env_scale,
+                     env_radius=src.env_radius, env_amp=src.env_amp, latent=lat, name=f"{src.name}_lat{seed}")
+
+
+def serving_trace(seed: int, rate: float, duration: float, res_choices=(64, 128, 256, 512),
+                  res_weights=(0.4, 0.3, 0.2, 0.1)):
+    """Poisson arrivals at ``rate`` per second over ``duration`` seconds; each
+    request draws a cube resolution from ``res_choices`` with ``res_weights``
+    and a latent seed.  Returns a list of (arrival time s, resolution, latent seed)."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    p = np.asarray(res_weights, np.float64)
+    p = p / p.sum()
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return out
+        res = int(rng.choice(np.asarray(res_choices), p=p))
+        out.append((t, res, int(rng.integers(1, 2 ** 31))))
+
+
 @dataclass
 class Grid:
     lo: tuple = (-1.0, -1.0, -1.0)

@@ -21,6 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4
           5: "unsupported", 6: "internal error"}
 SRC_CSG, SRC_MLP, SRC_RESIDENT = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_SPLIT = 0, 1, 2
+MLP_REUPLOAD = 1
 DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
            cycles=9, vlocal=10, qcase=11, flips=12, search=13)
 _DBG_DTYPE = dict(labels=np.uint32, edges=np.uint32, T=np.uint32, faces=np.uint32, slots=np.uint8,
@@ -39,7 +40,7 @@ class Mlp(C.Structure):
                 ("B", C.c_void_p), ("W", C.c_void_p * 8), ("b", C.c_void_p * 8), ("latent", C.c_void_p),
                 ("env_scale", C.c_float), ("env_radius", C.c_float), ("env_amp", C.c_float),
                 ("precision", C.c_int32), ("band", C.c_float), ("no_split", C.c_int32),
-                ("split_zmargin", C.c_float), ("reserved", C.c_int32)]
+                ("split_zmargin", C.c_float), ("flags", C.c_int32)]
 
 
 class Source(C.Structure):
@@ -72,6 +73,17 @@ class MeshC(C.Structure):
                 ("stats", Stats)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("mem_budget", C.c_size_t), ("host_copy", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class ResultC(C.Structure):
+    _fields_ = [("status", C.c_int32), ("slot", C.c_int32), ("mesh", MeshC), ("h_verts", C.c_void_p),
+                ("h_tris", C.c_void_p), ("t_submit", C.c_double), ("t_start", C.c_double), ("t_end", C.c_double),
+                ("est_bytes", C.c_uint64)]
+
+
 def launch_total() -> int:
     """Kernel launches issued by the library so far (all contexts)."""
     return int(load().odc_launch_count())
@@ -79,7 +91,8 @@ def launch_total() -> int:
 
 EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
            "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_compact_edges_noalloc", "odc_status_str",
-           "odc_last_error"]
+           "odc_last_error", "odc_server_create", "odc_server_destroy", "odc_submit", "odc_poll", "odc_result_release",
+           "odc_server_clock"]
 
 _lib = None
 
@@ -104,13 +117,21 @@ def load(path: str = LIB_PATH):
     lib.odc_compact_edges_noalloc.argtypes = [P, C.POINTER(C.c_int32), P, C.c_uint32, P,
                                               C.POINTER(C.c_uint32), P]
     lib.odc_compact_edges_noalloc.restype = C.c_int
+    lib.odc_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(P)]
+    lib.odc_server_destroy.argtypes = [P]
+    lib.odc_submit.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.POINTER(C.c_uint64)]
+    lib.odc_poll.argtypes = [P, C.c_uint64, C.c_int32, C.POINTER(ResultC)]
+    lib.odc_result_release.argtypes = [P, C.c_uint64]
+    lib.odc_server_clock.argtypes = [P]
+    lib.odc_server_clock.restype = C.c_double
     lib.odc_launch_count.restype = C.c_int64
     lib.odc_launch_count.argtypes = []
     lib.odc_status_str.restype = C.c_char_p
     lib.odc_status_str.argtypes = [C.c_int]
     lib.odc_last_error.restype = C.c_char_p
     for f in ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
-              "odc_debug_copy", "odc_eval_points", "odc_source_upload"]:
+              "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_server_create", "odc_server_destroy",
+              "odc_submit", "odc_poll", "odc_result_release"]:
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -134,7 +155,7 @@ def _ptr(a: np.ndarray) -> int:
 class _SourceHolder:
     """Keeps the numpy buffers behind a Source structure alive."""
 
-    def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0):
+    def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0, reupload=False):
         self.keep = []
         self.src = Source()
         if src is None:
@@ -176,6 +197,7 @@ class _SourceHolder:
             m.band = 0.03 if band is None else band
             m.no_split = 0 if split else 1
             m.split_zmargin = split_zmargin
+            m.flags = MLP_REUPLOAD if reupload else 0
             self.keep.append(m)
             self.src.kind = SRC_MLP
             self.src.mlp = C.addressof(m)
@@ -265,9 +287,10 @@ class Context:
         _check(_lib.odc_source_upload(self.h, C.byref(holder.src)))
 
     def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, split=True,
-                split_zmargin=0.0, **kw) -> Mesh:
-        """Run ODC; ``src=None`` reuses the resident source."""
-        holder = _SourceHolder(src, precision, band, split, split_zmargin)
+                split_zmargin=0.0, reupload=False, **kw) -> Mesh:
+        """Run ODC; ``src=None`` reuses the resident source.  ``reupload`` forces
+        the network weights to be prepared and copied even if the context holds them."""
+        holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
         m = MeshC()
@@ -305,3 +328,71 @@ class Context:
         _check(_lib.odc_eval_points(self.h, C.byref(holder.src), _ptr(pts), pts.shape[0], iso, precision,
                                     _ptr(lab), _ptr(z)))
         return lab.astype(bool), z
+
+
+class Server:
+    """The library's request loop (``odc_server``): requests of any grid size
+    are admitted as slots and memory free up and run concurrently on the GPU."""
+
+    def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0, host_copy: bool = True):
+        load()
+        cfg = ServerConfig()
+        cfg.device, cfg.slots, cfg.mem_budget, cfg.host_copy = device, slots, mem_budget, int(bool(host_copy))
+        h = C.c_void_p()
+        _check(_lib.odc_server_create(C.byref(cfg), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.odc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def clock(self) -> float:
+        return float(_lib.odc_server_clock(self.h))
+
+    def submit(self, src, grid: I.Grid, steps_1d=15, precision=None, band=None, split=True, split_zmargin=0.0,
+               **kw) -> int:
+        """Queue one request (inputs are copied by the library); returns its id."""
+        holder = _SourceHolder(src, precision, band, split, split_zmargin)
+        g = make_grid(grid)
+        p = make_params(steps_1d=steps_1d, **kw)
+        rid = C.c_uint64()
+        _check(_lib.odc_submit(self.h, C.byref(holder.src), C.byref(g), C.byref(p), C.byref(rid)))
+        return int(rid.value)
+
+    def poll(self, rid: int, timeout_ms: int = -1):
+        """None while the request runs (after timeout_ms); else a dict with the
+        request's status, host mesh copies (when the server keeps them), times
+        and slot."""
+        r = ResultC()
+        st = _lib.odc_poll(self.h, rid, timeout_ms, C.byref(r))
+        if st == 4:
+            return None
+        _check(st)
+        out = dict(status=int(r.status), slot=int(r.slot), t_submit=r.t_submit, t_start=r.t_start, t_end=r.t_end,
+                   est_bytes=int(r.est_bytes), n_verts=int(r.mesh.n_verts), n_tris=int(r.mesh.n_tris))
+        if r.status != ODC_OK:
+            out["error"] = _lib.odc_last_error().decode(errors="replace")
+        else:
+            s = r.mesh.stats
+            out["stats"] = {f: getattr(s, f) for f, _ in Stats._fields_ if f != "stage_ms"}
+            if r.h_verts or not out["n_verts"]:
+                nv, nt = out["n_verts"], out["n_tris"]
+                out["verts"] = np.ctypeslib.as_array((C.c_float * (3 * nv)).from_address(r.h_verts)).reshape(nv, 3).copy() if nv else np.zeros((0, 3), np.float32)
+                out["tris"] = np.ctypeslib.as_array((C.c_int32 * (3 * nt)).from_address(r.h_tris)).reshape(nt, 3).copy() if nt else np.zeros((0, 3), np.int32)
+        return out
+
+    def release(self, rid: int):
+        _check(_lib.odc_result_release(self.h, rid))

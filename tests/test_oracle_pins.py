@@ -358,3 +358,19 @@ def test_replay_of_own_decisions_is_exact_and_detects_planted_errors():
     r3 = odc.extract(src, g, steps_1d=10, replay=bad, replay_margin=1e-12)
     assert r3.stats["edge_violations"] == 1
     assert r3.stats["face_violations"] >= 1
+
+
+def test_serving_trace_is_poisson_with_the_resolution_mix():
+    """The serving workload generator: Poisson arrivals (exponential gaps of
+    mean 1/rate) and the 0.4/0.3/0.2/0.1 resolution mix."""
+    import numpy as np
+    from paper_2409_13418_gb300 import inputs as I
+    tr = I.serving_trace(0, 40.0, 300.0)
+    t = np.array([a for a, _, _ in tr])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(len(tr) / 300.0 - 40.0) < 1.5
+    assert abs(gaps.mean() - 1 / 40.0) < 1.5e-3 and abs(gaps.std() / gaps.mean() - 1.0) < 0.05
+    res = np.array([r for _, r, _ in tr])
+    for r, w in zip((64, 128, 256, 512), (0.4, 0.3, 0.2, 0.1)):
+        assert abs(np.mean(res == r) - w) < 0.02
+    assert I.serving_trace(0, 40.0, 300.0) == tr
