@@ -14,4 +14,6 @@ Modules:
                 2D search (Sec. 5.2, A.1.3-A.1.4), normals (Sec. 5.3),
                 QEF (Eq. 2), quads with IC splitting (Sec. 5.4, A.1.5)
   meshcheck  -- manifold / watertight / Euler / volume checks of a mesh
+  quality    -- Sec. 6.1 metrics: |phi - 0.5| on area-uniform mesh samples
+                (counter-based SplitMix64) and self-intersecting triangle pairs
 """
