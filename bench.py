@@ -328,6 +328,13 @@ def main():
     torch.cuda.synchronize()
     t_e2e = reduce_max((time.perf_counter() - t0) * 1e3, dist, "cuda")
     e2e = throughput(cells, world, args.steps, t_e2e)
+    # Sec. 6.1 quality measures of the last mesh (outside every timed region)
+    tq = time.perf_counter()
+    quality = m.quality(n_samples=2_000_000, seed=1)
+    quality = {"occ_dev_mean": quality["occ_dev_mean"], "occ_dev_max": quality["occ_dev_max"],
+               "samples": quality["n_samples"], "manifold": bool(quality["manifold"]), "euler": quality["euler"],
+               "si_pairs": quality["n_si_pairs"], "si_tris": quality["n_si_tris"], "tris": quality["n_tris"],
+               "seconds": round(time.perf_counter() - tq, 3)}
 
     if rank == 0:
         peaks, peak_src = _peaks()
@@ -374,6 +381,7 @@ def main():
                            "stage_ms": [round(x, 3) for x in stats["stage_ms"]]},
                 "e2e": {"value": e2e, "unit": "Mcells/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(vbytes + tbytes)},
+                "quality": quality,
                 "gpu_launches": int(launches),
                 "roofline": roof,
                 "clocks": clocks}

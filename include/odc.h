@@ -265,6 +265,40 @@ odc_status odc_debug_copy(odc_ctx* ctx, int what, void* dst, size_t max_bytes,
 odc_status odc_eval_points(odc_ctx* ctx, const odc_source* src, const float* points, int64_t n,
                            float iso, int precision, uint8_t* labels, float* logits);
 
+/* Mesh quality: the measures of the paper's evaluation (Sec. 6.1 "Evaluation
+ * Metrics") for a mesh in device memory (an odc_extract or odc_poll result).
+ *   ODC_Q_OCC: |phi - iso| at n_samples points drawn uniformly by area on the
+ *     mesh (counter-based SplitMix64 from ``seed``), phi = sigmoid of the FP32
+ *     logit of the context's resident MLP source (the source of its last
+ *     extract); NaN for a CSG source, whose occupancy is binary.
+ *   ODC_Q_MANIFOLD: every directed edge used once with its reverse used once,
+ *     every vertex fan a single cycle; Euler characteristic V - E + F.
+ *   ODC_Q_SI: triangle pairs that intersect: pairs sharing no vertex whose
+ *     closed sets meet, or sharing one vertex where the edge of either
+ *     opposite to it meets the other; pairs sharing an edge never count.
+ * Scratch is allocated on the context's stream and freed before return. */
+enum { ODC_Q_OCC = 1, ODC_Q_MANIFOLD = 2, ODC_Q_SI = 4 };
+
+typedef struct {
+    int64_t n_samples;
+    double occ_dev_mean;         /* mean |phi - iso| over the samples */
+    double occ_dev_max;
+    int64_t n_tris;
+    int64_t n_verts;             /* vertices used by a triangle */
+    int64_t n_edges;             /* undirected edges */
+    int64_t euler;               /* V - E + F */
+    int64_t n_degenerate;        /* triangles with a repeated vertex */
+    int64_t n_bad_edges;         /* directed edge uses not matched one-to-one by the reverse edge */
+    int64_t n_bad_verts;         /* vertices whose fan is not a single cycle */
+    int32_t manifold;            /* 1: closed, oriented 2-manifold */
+    int32_t si_checked;
+    int64_t n_si_pairs;          /* intersecting triangle pairs */
+    int64_t n_si_tris;           /* triangles in at least one such pair */
+} odc_quality;
+
+odc_status odc_mesh_quality(odc_ctx* ctx, const odc_mesh* mesh, float iso, int64_t n_samples, uint64_t seed,
+                            int32_t what, odc_quality* out);
+
 /* ---- Request loop ---------------------------------------------------------
  * A server meshes requests of any grid size as they arrive.  Up to ``slots``
  * requests are on the GPU at once, each on its own stream with its own

@@ -23,6 +23,11 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          f"-I{os.path.join(ROOT, 'include')}"]
 
 
+# quality.cu's FP64 predicates and sampling run in plain IEEE arithmetic (no
+# FMA contraction), like the oracle's numpy arithmetic.
+PER_FILE_FLAGS = {"quality.cu": ["-fmad=false"]}
+
+
 def _nvcc() -> str:
     for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -55,7 +60,8 @@ def build(verbose: bool = False, force: bool = False, ptxas_v: bool = False) -> 
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        per_file = PER_FILE_FLAGS.get(os.path.basename(src), [])
+        cmd = [nvcc, *ARCH, *FLAGS, *per_file, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -550,6 +550,19 @@ odc_status odc_debug_copy(odc_ctx* c, int what, void* dst, size_t max_bytes, int
     return ODC_OK;
 }
 
+odc_status odc_mesh_quality(odc_ctx* c, const odc_mesh* m, float iso, int64_t n_samples, uint64_t seed,
+                            int32_t what, odc_quality* out) {
+    if (!c || !m || !out || n_samples < 0) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    if ((m->n_verts && !m->d_verts) || (m->n_tris && !m->d_tris)) return fail(ODC_ERR_INVALID_ARG, "mesh without buffers");
+    if ((what & ODC_Q_OCC) && c->res_kind < 0) return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
+    ODC_CK(cudaSetDevice(c->device));
+    std::memset(out, 0, sizeof(*out));
+    MlpState* mlp = c->res_kind == ODC_SRC_MLP ? c->mlp : nullptr;
+    odc_status s = mesh_quality(mlp, (const float3*)m->d_verts, m->n_verts, (const int3*)m->d_tris, m->n_tris, iso,
+                                n_samples, seed, what, c->own, out, &g_err);
+    return s == ODC_OK ? s : fail(s, g_err);
+}
+
 odc_status odc_eval_points(odc_ctx* c, const odc_source* src, const float* points, int64_t n, float iso,
                            int precision, uint8_t* labels, float* logits) {
     if (!c || !points || !labels || n < 0) return fail(ODC_ERR_INVALID_ARG, "NULL argument");

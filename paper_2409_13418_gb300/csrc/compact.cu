@@ -248,6 +248,7 @@ void exclusive_scan(const T* in, T* out, size_t n, T* tmp, T* total, cudaStream_
 template void exclusive_scan<uint32_t>(const uint32_t*, uint32_t*, size_t, uint32_t*, uint32_t*, cudaStream_t);
 template void exclusive_scan<unsigned long long>(const unsigned long long*, unsigned long long*, size_t,
                                                  unsigned long long*, unsigned long long*, cudaStream_t);
+template void exclusive_scan<double>(const double*, double*, size_t, double*, double*, cudaStream_t);
 
 // --------------------------------------------------------------- launchers
 void launch_csg_grid(const GridDev& g, const PrimDev* prims, const float4* cull, int n_prims, uint32_t* bits,

@@ -4,6 +4,9 @@
 #include <stdint.h>
 
 #include "odc_internal.h"
+#include "../../include/odc.h"
+
+#include <string>
 
 namespace odc {
 
@@ -51,5 +54,11 @@ void launch_quad_case(const GridDev& g, const uint32_t* bits, const WordInfo* wi
 void launch_quad_emit(const GridDev& g, const uint32_t* edges, const uint32_t* T, uint32_t ne, int k,
                       const uint8_t* qcase, const int4* qv, const unsigned long long* off, const uint32_t* v3tot,
                       float3* vworld, int3* tris, cudaStream_t st);
+
+// quality.cu (Sec. 6.1 metrics; mlp may be null for a CSG source)
+struct MlpState;
+odc_status mesh_quality(MlpState* mlp, const float3* v, int64_t nv, const int3* t, int64_t nt, float iso,
+                        int64_t n_samples, uint64_t seed, int what, cudaStream_t s, odc_quality* out,
+                        std::string* err);
 
 }  // namespace odc

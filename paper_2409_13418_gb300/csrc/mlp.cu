@@ -472,6 +472,7 @@ static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int
 odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
                          std::string* err, const float* hint) {
     QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
+    st->stream = s;
     return eval(st, Q, n, z, precision, hint, s, err);
 }
 

@@ -73,6 +73,17 @@ class MeshC(C.Structure):
                 ("stats", Stats)]
 
 
+class QualityC(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("occ_dev_mean", C.c_double), ("occ_dev_max", C.c_double),
+                ("n_tris", C.c_int64), ("n_verts", C.c_int64), ("n_edges", C.c_int64), ("euler", C.c_int64),
+                ("n_degenerate", C.c_int64), ("n_bad_edges", C.c_int64), ("n_bad_verts", C.c_int64),
+                ("manifold", C.c_int32), ("si_checked", C.c_int32), ("n_si_pairs", C.c_int64),
+                ("n_si_tris", C.c_int64)]
+
+
+Q_OCC, Q_MANIFOLD, Q_SI = 1, 2, 4
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("mem_budget", C.c_size_t), ("host_copy", C.c_int32),
                 ("reserved", C.c_int32)]
@@ -92,7 +103,7 @@ def launch_total() -> int:
 EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
            "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_compact_edges_noalloc", "odc_status_str",
            "odc_last_error", "odc_server_create", "odc_server_destroy", "odc_submit", "odc_poll", "odc_result_release",
-           "odc_server_clock"]
+           "odc_server_clock", "odc_mesh_quality"]
 
 _lib = None
 
@@ -117,6 +128,9 @@ def load(path: str = LIB_PATH):
     lib.odc_compact_edges_noalloc.argtypes = [P, C.POINTER(C.c_int32), P, C.c_uint32, P,
                                               C.POINTER(C.c_uint32), P]
     lib.odc_compact_edges_noalloc.restype = C.c_int
+    lib.odc_mesh_quality.argtypes = [P, C.POINTER(MeshC), C.c_float, C.c_int64, C.c_uint64, C.c_int32,
+                                     C.POINTER(QualityC)]
+    lib.odc_mesh_quality.restype = C.c_int
     lib.odc_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(P)]
     lib.odc_server_destroy.argtypes = [P]
     lib.odc_submit.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.POINTER(C.c_uint64)]
@@ -251,6 +265,14 @@ class Mesh:
         _check(_lib.odc_mesh_copy(self.ctx.h, C.byref(self.c), _ptr(v), _ptr(t), 0))
         return v, t
 
+    def quality(self, iso: float = 0.5, n_samples: int = 2_000_000, seed: int = 1,
+                what: int = Q_OCC | Q_MANIFOLD | Q_SI) -> dict:
+        """Sec. 6.1 measures of this mesh (odc_mesh_quality): occupancy deviation on
+        area-uniform samples, manifoldness and Euler characteristic, self-intersections."""
+        q = QualityC()
+        _check(_lib.odc_mesh_quality(self.ctx.h, C.byref(self.c), iso, n_samples, seed, what, C.byref(q)))
+        return {f: getattr(q, f) for f, _ in QualityC._fields_}
+
     def copy_to(self, verts_ptr: int, tris_ptr: int, on_device: bool):
         _check(_lib.odc_mesh_copy(self.ctx.h, C.byref(self.c), verts_ptr, tris_ptr, int(on_device)))
 
@@ -319,6 +341,16 @@ class Context:
         out = np.empty(int(n.value) * k, dt)
         _check(_lib.odc_debug_copy(self.h, DBG[what], _ptr(out), out.nbytes, C.byref(n), C.byref(eb)))
         return out.reshape(-1, k) if k > 1 else out
+
+    def quality_of(self, d_verts: int, n_verts: int, d_tris: int, n_tris: int, iso: float = 0.5,
+                   n_samples: int = 2_000_000, seed: int = 1, what: int = Q_OCC | Q_MANIFOLD | Q_SI) -> dict:
+        """odc_mesh_quality on any mesh in device memory (float32 [n][3] vertices,
+        int32 [m][3] triangles); the occupancy is the context's resident source."""
+        m = MeshC()
+        m.n_verts, m.n_tris, m.d_verts, m.d_tris = n_verts, n_tris, d_verts, d_tris
+        q = QualityC()
+        _check(_lib.odc_mesh_quality(self.h, C.byref(m), iso, n_samples, seed, what, C.byref(q)))
+        return {f: getattr(q, f) for f, _ in QualityC._fields_}
 
     def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None, split=True):
         holder = _SourceHolder(src, None if precision < 0 else min(precision, PREC_BF16), band, split)
