@@ -92,6 +92,112 @@ def csg_eval(src: CSGSource, points: np.ndarray):
     return inside, margin
 
 
+# ---- ablation variants (Sec. 6.3, Tab. 3): MDC's implicit value and gradient
+# The MDC baselines of the ablation need a continuous implicit psi with a
+# gradient (Sec. 4, Eqs. 1 and 3).  For a CSG source psi is the min/max fold of
+# the primitives' g (union: min(psi, g), difference: max(psi, -g)); its zero
+# set is the CSG surface.  Eq. 1 places a 1D point by linear interpolation of
+# psi; the value is taken in FP32 with the operation order written below, so
+# that the interpolation parameter (an integer after quantisation) is the
+# same in any implementation that follows it.
+
+def _prim_g32(src: CSGSource, i: int, x: np.ndarray) -> np.ndarray:
+    """g of primitive i in FP32 arithmetic at FP32 points x (n, 3)."""
+    f = np.float32
+    t = int(src.types[i])
+    c = src.centers[i].astype(f)
+    M = src.rot[i].astype(f)
+    p = src.params[i].astype(f)
+    dx, dy, dz = x[:, 0] - c[0], x[:, 1] - c[1], x[:, 2] - c[2]
+    if t == PRIM_SPHERE:
+        return ((dx * dx + dy * dy) + dz * dz) - p[0] * p[0]
+    if t == PRIM_AABB:
+        return np.maximum(np.maximum(np.abs(dx) - p[0], np.abs(dy) - p[1]), np.abs(dz) - p[2])
+    if t == PRIM_OBOX:
+        ls = [((M[k, 0] * dx + M[k, 1] * dy) + M[k, 2] * dz) for k in range(3)]
+        return np.maximum(np.maximum(np.abs(ls[0]) - p[0], np.abs(ls[1]) - p[1]), np.abs(ls[2]) - p[2])
+    ax = M[2]
+    tt = (ax[0] * dx + ax[1] * dy) + ax[2] * dz
+    d2 = (dx * dx + dy * dy) + dz * dz
+    if t == PRIM_CYLINDER:
+        radial = (d2 - tt * tt) - p[0] * p[0]
+        return np.maximum(radial / (f(2.0) * p[0]), np.abs(tt) - p[1])
+    if t == PRIM_TORUS:
+        q = (d2 + p[0] * p[0]) - p[1] * p[1]
+        return q * q - ((f(4.0) * p[0]) * p[0]) * (d2 - tt * tt)
+    raise ValueError(f"unknown primitive type {t}")
+
+
+def csg_psi32(src: CSGSource, points: np.ndarray) -> np.ndarray:
+    """psi in FP32 at FP32 points (every primitive evaluated, no culling)."""
+    x = np.asarray(points, np.float32)
+    psi = _prim_g32(src, 0, x)
+    for i in range(1, src.n_prims):
+        g = _prim_g32(src, i, x)
+        psi = np.minimum(psi, g) if int(src.ops[i]) == OP_UNION else np.maximum(psi, -g)
+    return psi
+
+
+def _prim_grad(src: CSGSource, i: int, x: np.ndarray) -> np.ndarray:
+    """Gradient of g of primitive i in FP64 (the branch attaining a max; the
+    first one on ties; the sign of 0 taken as +)."""
+    t = int(src.types[i])
+    c = src.centers[i].astype(np.float64)
+    M = src.rot[i].astype(np.float64)
+    p = src.params[i].astype(np.float64)
+    d = x - c
+    n = x.shape[0]
+
+    def sgn(v):
+        return np.where(v < 0, -1.0, 1.0)
+    if t == PRIM_SPHERE:
+        return 2.0 * d
+    if t in (PRIM_AABB, PRIM_OBOX):
+        L = d if t == PRIM_AABB else d @ M.T
+        rows = np.eye(3) if t == PRIM_AABB else M
+        val = np.abs(L) - p[:3]
+        k = np.zeros(n, np.int64)
+        k = np.where(val[:, 1] > val[np.arange(n), k], 1, k)
+        k = np.where(val[:, 2] > val[np.arange(n), k], 2, k)
+        return sgn(L[np.arange(n), k])[:, None] * rows[k]
+    ax = M[2]
+    tt = d @ ax
+    radial_dir = d - tt[:, None] * ax
+    if t == PRIM_CYLINDER:
+        r, hh = p[0], p[1]
+        d2 = np.einsum("ij,ij->i", d, d)
+        g_r = ((d2 - tt * tt) - r * r) / (2.0 * r)
+        axial = np.abs(tt) - hh
+        return np.where((g_r >= axial)[:, None], radial_dir / r, sgn(tt)[:, None] * ax)
+    if t == PRIM_TORUS:
+        R, r = p[0], p[1]
+        d2 = np.einsum("ij,ij->i", d, d)
+        q = (d2 + R * R) - r * r
+        return 4.0 * q[:, None] * d - 8.0 * R * R * radial_dir
+    raise ValueError(f"unknown primitive type {t}")
+
+
+def csg_grad(src: CSGSource, points: np.ndarray) -> np.ndarray:
+    """Gradient of psi in FP64 at FP32-rounded points: the gradient of the
+    primitive the min/max fold selects (strict comparisons: the earlier
+    operand wins ties), negated for a selected difference operand."""
+    x = to_query(points)
+    psi, _ = prim_g(src, 0, x)
+    grad = _prim_grad(src, 0, x)
+    for i in range(1, src.n_prims):
+        g, _ = prim_g(src, i, x)
+        gr = _prim_grad(src, i, x)
+        if int(src.ops[i]) == OP_UNION:
+            take = g < psi
+            psi = np.where(take, g, psi)
+            grad = np.where(take[:, None], gr, grad)
+        else:
+            take = -g > psi
+            psi = np.where(take, -g, psi)
+            grad = np.where(take[:, None], -gr, grad)
+    return grad
+
+
 def fourier_features(src: MLPSource, x: np.ndarray) -> np.ndarray:
     """g(x) = [sin(2 pi B x), cos(2 pi B x)] in FP64."""
     B = src.B.astype(np.float64)

@@ -37,6 +37,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from . import occupancy
 from . import topology as topo
 from .occupancy import Occupancy
 
@@ -302,8 +303,15 @@ def topology_triangles(labels):
 
 def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12,
             range2=float(np.float32(math.sqrt(2.0) / 2.0)), iso=0.5, ic_split=True,
-            replay=None, replay_margin=0.0) -> Result:
+            replay=None, replay_margin=0.0, linear_1d=False, gradient_normals=False) -> Result:
     """Run ODC on ``src`` (a CSG/MLP source or a callable) over ``grid``.
+
+    Ablation variants (Sec. 6.3, Tab. 3; CSG sources only, which have an
+    implicit psi and its gradient): ``linear_1d`` places each 1D point by
+    Eq. 1 (linear interpolation of psi between the edge's ends, taken in FP32
+    and quantised to the 1D lattice of 2^-(k+1) edge) instead of the binary
+    search; ``gradient_normals`` uses grad psi at the 1D point as the plane
+    normal of Eq. 3 instead of the 2D points (the 2D search is skipped).
 
     ``replay`` (optional) supplies the search decisions of another
     implementation instead of taking them from phi: ``T`` (1D results) and
@@ -415,7 +423,7 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     edge_viol = np.zeros(E, bool)
     if replay is not None:
         lo_rep = (np.asarray(replay["T"], np.int64) - 1) // 2      # k-bit low end of the final interval
-    for step in range(k1):
+    for step in range(0 if linear_1d else k1):
         mid = lo + width / 2.0
         q = x_lo.copy()
         q[np.arange(E), ea] = x_lo[np.arange(E), ea] + span * mid
@@ -429,6 +437,24 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
         lo = np.where(same, mid, lo)
         width /= 2.0
     T = (2 * np.round(lo * (1 << k1)).astype(np.int64) + 1) if E else np.zeros(0, np.int64)
+    if linear_1d and E:
+        # Eq. 1 in FP32: t = psi(p0) / (psi(p0) - psi(p1)) along the edge from its
+        # lower end, clamped to [0, 1], rounded to the nearest multiple of
+        # 2^-(k+1) strictly inside the edge
+        f32 = np.float32
+        x_hi = x_lo.copy()
+        up = eijk + np.eye(3, dtype=np.int64)[ea]
+        for a in range(3):
+            m = ea == a
+            x_hi[m, a] = X[a][up[m, a]]
+        psi0 = occupancy.csg_psi32(src, x_lo.astype(f32))
+        psi1 = occupancy.csg_psi32(src, x_hi.astype(f32))
+        den = psi0 - psi1
+        with np.errstate(divide="ignore", invalid="ignore"):
+            tl = np.where(den != 0, psi0 / np.where(den != 0, den, f32(1)), f32(0.5)).astype(f32)
+        tl = np.minimum(np.maximum(tl, f32(0.0)), f32(1.0))
+        full = 1 << (k1 + 1)
+        T = np.clip(np.rint(tl * f32(full)).astype(np.int64), 1, full - 1)
     tau = T / float(1 << (k1 + 1))
 
     def edge_pos(eid):
@@ -550,7 +576,7 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     pf = np.zeros((F, 2))
     search = dict(Jq=np.zeros(0, np.int64), J1=np.zeros(0, np.int64), J2=np.zeros(0, np.int64),
                   lab_m=np.zeros(0, bool), found=np.zeros(0, np.int64))
-    if F:
+    if F and not gradient_normals:
         allf = np.ones(F, bool)
         m = (P1 + P2) / 2.0
         lab_m, mar_m = query(m, allf)
@@ -635,6 +661,11 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     v1 = pfs[0] - pe
     v2 = pfs[1] - pe
     nrm = np.cross(v1, v2)
+    if gradient_normals and K:
+        # Eq. 3: grad psi at the 1D point, as a normal in cell-local units
+        span_c = np.stack([X[0][ci + 1] - X[0][ci], X[1][cj + 1] - X[1][cj], X[2][ck + 1] - X[2][ck]], axis=1)[pc]
+        world0 = np.stack([X[0][ci], X[1][cj], X[2][ck]], axis=1)[pc]
+        nrm = occupancy.csg_grad(src, world0 + span_c * pe) * span_c
     nn = np.linalg.norm(nrm, axis=1)
     pflag |= (nn < 1e4 * NORMAL_EPS) | (nn < 1e-4 * np.linalg.norm(v1, axis=1) * np.linalg.norm(v2, axis=1))
     keep = nn >= NORMAL_EPS

@@ -74,6 +74,30 @@ def occupancy_deviation(mlp, verts, tris, n: int, seed: int, iso: float = 0.5) -
     return float(d.mean()), float(d.max())
 
 
+def implicit_psi(src, points: np.ndarray) -> np.ndarray:
+    """psi of a CSG source in FP64 (the min/max fold of the primitives' g) at
+    FP32-rounded points."""
+    x = occupancy.to_query(points)
+    psi, _ = occupancy.prim_g(src, 0, x)
+    for i in range(1, src.n_prims):
+        g, _ = occupancy.prim_g(src, i, x)
+        psi = np.minimum(psi, g) if int(src.ops[i]) == 0 else np.maximum(psi, -g)
+    return psi
+
+
+def surface_distance(src, verts, tris, n: int, seed: int) -> tuple[float, float]:
+    """(mean, max) of the first-order distance |psi| / |grad psi| of a CSG
+    source's surface at n area-uniform mesh samples (the binary occupancy of a
+    CSG source has no |phi - 0.5| to measure, so its fidelity is measured as
+    a distance)."""
+    p = surface_samples(verts, tris, n, seed)
+    psi = implicit_psi(src, p)
+    gn = np.linalg.norm(occupancy.csg_grad(src, p), axis=1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = np.where(gn > 0, np.abs(psi) / gn, np.abs(psi))
+    return float(d.mean()), float(d.max())
+
+
 # ---------------------------------------------------------------- SI
 def _orient(a, b, c, d):
     """det[b - a, c - a, d - a] (signed six-fold tetrahedron volume), rows of points."""

@@ -165,3 +165,81 @@ def test_self_intersection_count_matches_an_independent_test_on_odc_meshes():
             c, flag = Q.self_intersections(v, t)
             assert c > 0 and c == _brute_si(v, t)
             assert flag.sum() <= 2 * c
+
+
+def test_csg_gradient_matches_finite_differences_and_psi32_matches_fp64():
+    from oracle import occupancy as O
+    src = I.random_csg(2, n_prims=64)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-0.9, 0.9, (4000, 3)).astype(np.float32).astype(np.float64)
+    psi = Q.implicit_psi(src, x)
+    g = O.csg_grad(src, x)          # x is FP32-representable: no rounding inside
+
+    def psi64(y):                   # the fold in FP64 at unrounded points
+        v, _ = O.prim_g(src, 0, y)
+        for i in range(1, src.n_prims):
+            gi, _ = O.prim_g(src, i, y)
+            v = np.minimum(v, gi) if int(src.ops[i]) == 0 else np.maximum(v, -gi)
+        return v
+    h = 1e-6
+    fd = np.stack([(psi64(x + h * e) - psi64(x - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+    # away from kinks of the min/max fold and of the box and cylinder maxima
+    # the central difference sees one smooth branch
+    err = np.linalg.norm(fd - g, axis=1) / np.maximum(np.linalg.norm(g, axis=1), 1e-12)
+    assert np.mean(err < 1e-4) > 0.97
+    # the FP32 value follows the FP64 one to FP32 rounding
+    p32 = O.csg_psi32(src, x.astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(p32 - psi) <= 1e-5 * np.maximum(1.0, np.abs(psi)))
+
+
+def test_surface_distance_on_a_sphere_mesh():
+    # unit-radius sphere primitive g = |x|^2 - 1: |g| / |grad g| = |1 - |x|^2| / (2 |x|)
+    # lies within the chord sag of an inscribed icosphere: (1 - r_in) (1 + r_in) / (2 r_in)
+    src = I.single_prim(I.PRIM_SPHERE, (0.0, 0.0, 0.0), params=(1.0,))
+    v, t = _icosphere(1.0, 3)
+    vv = v.astype(np.float64)
+    n = np.cross(vv[t[:, 1]] - vv[t[:, 0]], vv[t[:, 2]] - vv[t[:, 0]])
+    r_in = float(np.min(np.abs(np.einsum("ij,ij->i", n / np.linalg.norm(n, axis=1)[:, None], vv[t[:, 0]]))))
+    mean, mx = Q.surface_distance(src, v, t, 20000, seed=2)
+    bound = (1 - r_in) * (1 + r_in) / (2 * r_in)
+    assert 0 < mean < mx <= bound * (1 + 1e-6) + 1e-6
+
+
+def test_linear_1d_is_exact_on_box_faces_and_gradient_normals_recover_box_corners():
+    """Eq. 1 on an axis-aligned box: psi = max_a(|x_a - c_a| - h_a) is linear
+    along an edge crossing a face wherever the edge's own axis attains the
+    max at both ends, so there the FP32 linear 1D point sits within 2^-(k+2)
+    of an edge (quantisation) plus FP32 rounding from the face.  With
+    bisected 1D points and gradient normals (exact face normals) the QEF of a
+    corner cell returns the corner; linearly placed points near a corner are
+    off (there psi switches branch along the edge), so MDC misses it."""
+    c, hs = (0.013, -0.021, 0.008), (0.43, 0.37, 0.41)
+    src = I.single_prim(I.PRIM_AABB, c, params=hs)
+    g = I.cube_grid(24)
+    k = 12
+    r = oracle.extract(src, g, steps_1d=k, linear_1d=True, gradient_normals=True)
+    h = 2.0 / 24
+    e = r.edges
+    a = e % 3
+    v = e // 3
+    nv = 25
+    ijk = np.stack([v % nv, (v // nv) % nv, v // (nv * nv)], axis=1)
+    X = -1.0 + ijk * h
+    pos = X[np.arange(len(e)), a] + h * r.T / 2.0 ** (k + 1)
+    faces = np.array(c)[a] + np.where(X[np.arange(len(e)), a] + 0.5 * h > np.array(c)[a], 1, -1) * np.array(hs)[a]
+    lin = np.ones(len(e), bool)
+    for end in (0.0, 1.0):
+        P = X + end * h * np.eye(3)[a]
+        terms = np.abs(P - np.array(c)) - np.array(hs)
+        lin &= np.argmax(terms, axis=1) == a
+    assert lin.sum() > len(e) // 3
+    assert np.max(np.abs(pos - faces)[lin]) <= h * 2.0 ** -(k + 2) + 1e-6
+    corners = np.array([[c[0] + sx * hs[0], c[1] + sy * hs[1], c[2] + sz * hs[2]]
+                        for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+    assert meshcheck.check_closed_manifold(r.triangles)["ok"]
+    d_lin = np.min(np.linalg.norm(r.vertices[:, None, :] - corners[None], axis=2), axis=0)
+    r1 = oracle.extract(src, g, steps_1d=k, gradient_normals=True)
+    d = np.min(np.linalg.norm(r1.vertices[:, None, :] - corners[None], axis=2), axis=0)
+    assert np.all(d <= h * 2.0 ** -(k + 1) * math.sqrt(3) + 1e-6)
+    assert np.max(d_lin) > 10 * np.max(d)
+    assert meshcheck.check_closed_manifold(r1.triangles)["ok"]
