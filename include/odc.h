@@ -163,8 +163,19 @@ typedef struct {
     int32_t s2d_lin2, s2d_bin2;
     float s2d_range2;
     int32_t ic_split;            /* 1: IC quad splitting (A.1.5); 0: first diagonal */
-    int32_t reserved;
+    int32_t flags;               /* ablation variants (ODC_ABL_*), 0 for ODC */
 } odc_params;
+
+/* Ablation variants (Sec. 6.3, Tab. 3), CSG sources only (they need the
+ * implicit psi, the min/max fold of the primitives' g, and its gradient; an
+ * MLP source returns ODC_ERR_UNSUPPORTED).  ODC_ABL_LINEAR_1D: 1D points by
+ * Eq. 1 (psi interpolated linearly along the edge in FP32, rounded to the
+ * 2^-(k+1)-edge lattice) instead of the binary search.
+ * ODC_ABL_GRADIENT_NORMALS: grad psi at the 1D point as the QEF plane normal
+ * (Eq. 3) instead of the 2D points; the 2D search is skipped.  With ic_split
+ * = 0 both give Manifold Dual Contouring, ODC_ABL_GRADIENT_NORMALS alone its
+ * "+1D search" row. */
+enum { ODC_ABL_LINEAR_1D = 1, ODC_ABL_GRADIENT_NORMALS = 2 };
 
 typedef struct {
     int64_t n_edges;             /* |E^S| crossing edges */
@@ -270,7 +281,9 @@ odc_status odc_eval_points(odc_ctx* ctx, const odc_source* src, const float* poi
  *   ODC_Q_OCC: |phi - iso| at n_samples points drawn uniformly by area on the
  *     mesh (counter-based SplitMix64 from ``seed``), phi = sigmoid of the FP32
  *     logit of the context's resident MLP source (the source of its last
- *     extract); NaN for a CSG source, whose occupancy is binary.
+ *     extract).  A CSG source's occupancy is binary; its fidelity is the
+ *     first-order distance |psi| / |grad psi| of the implicit psi (the min/max
+ *     fold of the primitives' g, FP64) at the same samples.
  *   ODC_Q_MANIFOLD: every directed edge used once with its reverse used once,
  *     every vertex fan a single cycle; Euler characteristic V - E + F.
  *   ODC_Q_SI: triangle pairs that intersect: pairs sharing no vertex whose
@@ -281,8 +294,10 @@ enum { ODC_Q_OCC = 1, ODC_Q_MANIFOLD = 2, ODC_Q_SI = 4 };
 
 typedef struct {
     int64_t n_samples;
-    double occ_dev_mean;         /* mean |phi - iso| over the samples */
+    double occ_dev_mean;         /* MLP source: mean |phi - iso| over the samples; CSG: NaN */
     double occ_dev_max;
+    double dist_mean;            /* CSG source: mean first-order distance |psi| / |grad psi|; MLP: NaN */
+    double dist_max;
     int64_t n_tris;
     int64_t n_verts;             /* vertices used by a triangle */
     int64_t n_edges;             /* undirected edges */

@@ -667,7 +667,9 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
         world0 = np.stack([X[0][ci], X[1][cj], X[2][ck]], axis=1)[pc]
         nrm = occupancy.csg_grad(src, world0 + span_c * pe) * span_c
     nn = np.linalg.norm(nrm, axis=1)
-    pflag |= (nn < 1e4 * NORMAL_EPS) | (nn < 1e-4 * np.linalg.norm(v1, axis=1) * np.linalg.norm(v2, axis=1))
+    pflag |= nn < 1e4 * NORMAL_EPS
+    if not gradient_normals:   # a cross product of nearly parallel rays
+        pflag |= nn < 1e-4 * np.linalg.norm(v1, axis=1) * np.linalg.norm(v2, axis=1)
     keep = nn >= NORMAL_EPS
     nh = np.zeros((K, 3))
     nh[keep] = nrm[keep] / nn[keep, None]

@@ -23,9 +23,10 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          f"-I{os.path.join(ROOT, 'include')}"]
 
 
-# quality.cu's FP64 predicates and sampling run in plain IEEE arithmetic (no
-# FMA contraction), like the oracle's numpy arithmetic.
-PER_FILE_FLAGS = {"quality.cu": ["-fmad=false"]}
+# quality.cu's FP64 predicates and sampling and ablation.cu's FP32 implicit
+# values run in plain IEEE arithmetic (no FMA contraction), like the oracle's
+# numpy arithmetic.
+PER_FILE_FLAGS = {"quality.cu": ["-fmad=false"], "ablation.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:

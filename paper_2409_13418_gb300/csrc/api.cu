@@ -264,6 +264,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         !(prm->s2d_range2 > 0))
         return fail(ODC_ERR_INVALID_ARG, "2D search parameters out of range");
     if (!(prm->iso > 0.0f && prm->iso < 1.0f)) return fail(ODC_ERR_INVALID_ARG, "iso must be in (0, 1)");
+    if (prm->flags & ~(ODC_ABL_LINEAR_1D | ODC_ABL_GRADIENT_NORMALS))
+        return fail(ODC_ERR_INVALID_ARG, "unknown ablation flags");
     ODC_CK(cudaSetDevice(c->device));
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
     std::memset(out, 0, sizeof(*out));
@@ -276,6 +278,10 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
     }
     const int kind = c->res_kind;
+    if (prm->flags && kind != ODC_SRC_CSG)
+        return fail(ODC_ERR_UNSUPPORTED, "ablation variants need an implicit with a gradient: CSG sources only");
+    const bool linear_1d = (prm->flags & ODC_ABL_LINEAR_1D) != 0;
+    const bool grad_normals = (prm->flags & ODC_ABL_GRADIENT_NORMALS) != 0;
     PrimDev* d_prims = c->res_prims;
     float4* d_cull = c->res_cull;
     const int n_prims = c->res_nprims;
@@ -347,7 +353,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     size_t stmpB = scan_tmp_elems(std::max<size_t>(std::max(E, C), 1));
     size_t needB = 2 * al(E * 4ull) + al(F * 4ull) + 3 * al(F) + al(F * 16ull) + al(F * sizeof(FaceDecisions)) + al(C * 4ull) + al(C) + al(C * 8ull) +
                    2 * al(C * 4ull) + al(4ull * C * 12) + al((4ull * C + E) * 12) + al(E) + al(E * 16ull) +
-                   2 * al(E * 8ull) + al(4ull * E * 12) + al(stmpB * 8) + 1024;
+                   2 * al(E * 8ull) + al(4ull * E * 12) + al(stmpB * 8) + al(E * 12ull) + 1024;
     s = arena_ensure(c, c->B, needB, st);
     if (s != ODC_OK) return s;
     uint32_t* edges = (uint32_t*)c->B.take(E * 4ull);
@@ -371,6 +377,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     unsigned long long* qoff = (unsigned long long*)c->B.take(E * 8ull);
     int3* tris = (int3*)c->B.take(4ull * E * 12);
     void* tmpB = c->B.take(stmpB * 8);
+    float3* gnorm = grad_normals ? (float3*)c->B.take(E * 12ull) : nullptr;
 
     launch_emit(g, bits, wi, ebase, fbase, cbase, edges, faces, slots, cells, configs, st);
     ODC_CK(cudaGetLastError());
@@ -397,7 +404,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
 
     // ---- a4: 1D search
     if (kind == ODC_SRC_CSG) {
-        launch_bisect_csg(g, bits, edges, E, prm->steps_1d, d_prims, d_cull, n_prims, T, st);
+        if (linear_1d) launch_linear_1d(g, edges, E, prm->steps_1d, d_prims, n_prims, T, st);
+        else launch_bisect_csg(g, bits, edges, E, prm->steps_1d, d_prims, d_cull, n_prims, T, st);
         nq += (int64_t)E * prm->steps_1d;
     } else {
         s = mlp_bisect(c->mlp, g, bits, edges, E, prm->steps_1d, prm->iso, T, st, &nq, &g_err);
@@ -407,7 +415,14 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     ODC_CK(cudaEventRecord(c->ev[4], st));
 
     // ---- a5: 2D search
-    if (kind == ODC_SRC_CSG) {
+    if (grad_normals) {   // Eq. 3 normals replace the 2D points: no 2D search
+        launch_edge_grad(g, edges, T, E, prm->steps_1d, d_prims, n_prims, gnorm, st);
+        if (F) {
+            ODC_CK(cudaMemsetAsync(pf, 0, F * 16ull, st));
+            ODC_CK(cudaMemsetAsync(fflags, 0, F, st));
+            ODC_CK(cudaMemsetAsync(dec, 0, F * sizeof(FaceDecisions), st));
+        }
+    } else if (kind == ODC_SRC_CSG) {
         launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, n_prims, pf, fflags,
                         dec, st);
     } else {
@@ -419,7 +434,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     ODC_CK(cudaEventRecord(c->ev[5], st));
 
     // ---- a6, a7: normals and QEF
-    launch_qef(g, flips, wi, ebase, fbase, T, pf, cells, configs, cycles, vbase, C, prm->steps_1d, vlocal, vworld, st);
+    launch_qef(g, flips, wi, ebase, fbase, T, pf, gnorm, cells, configs, cycles, vbase, C, prm->steps_1d, vlocal,
+               vworld, st);
     ODC_CK(cudaGetLastError());
     ODC_CK(cudaEventRecord(c->ev[6], st));
 
@@ -558,8 +574,9 @@ odc_status odc_mesh_quality(odc_ctx* c, const odc_mesh* m, float iso, int64_t n_
     ODC_CK(cudaSetDevice(c->device));
     std::memset(out, 0, sizeof(*out));
     MlpState* mlp = c->res_kind == ODC_SRC_MLP ? c->mlp : nullptr;
-    odc_status s = mesh_quality(mlp, (const float3*)m->d_verts, m->n_verts, (const int3*)m->d_tris, m->n_tris, iso,
-                                n_samples, seed, what, c->own, out, &g_err);
+    const PrimDev* prims = c->res_kind == ODC_SRC_CSG ? c->res_prims : nullptr;
+    odc_status s = mesh_quality(mlp, prims, c->res_nprims, (const float3*)m->d_verts, m->n_verts,
+                                (const int3*)m->d_tris, m->n_tris, iso, n_samples, seed, what, c->own, out, &g_err);
     return s == ODC_OK ? s : fail(s, g_err);
 }
 

@@ -40,11 +40,18 @@ void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* fli
 void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, const float3* pts, int64_t n,
                        uint8_t* labels, cudaStream_t st);
 
-// qef.cu
+// qef.cu (gnorm: per crossing edge, grad psi at its 1D point replacing the
+// 2D-point normals; null for ODC)
 void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, const uint32_t* ebase,
-                const uint32_t* fbase, const uint32_t* T, const float4* pf, const uint32_t* cells,
+                const uint32_t* fbase, const uint32_t* T, const float4* pf, const float3* gnorm, const uint32_t* cells,
                 const uint8_t* configs, const unsigned long long* cycles, const uint32_t* vbase, uint32_t nc, int k,
                 float3* vlocal, float3* vworld, cudaStream_t st);
+
+// ablation.cu (MDC variants of the ablation, CSG sources)
+void launch_linear_1d(const GridDev& g, const uint32_t* edges, uint32_t ne, int k, const PrimDev* prims, int n_prims,
+                      uint32_t* T, cudaStream_t st);
+void launch_edge_grad(const GridDev& g, const uint32_t* edges, const uint32_t* T, uint32_t ne, int k,
+                      const PrimDev* prims, int n_prims, float3* grad, cudaStream_t st);
 
 // quads.cu
 void launch_quad_case(const GridDev& g, const uint32_t* bits, const WordInfo* wi, const uint32_t* cbase,
@@ -57,8 +64,8 @@ void launch_quad_emit(const GridDev& g, const uint32_t* edges, const uint32_t* T
 
 // quality.cu (Sec. 6.1 metrics; mlp may be null for a CSG source)
 struct MlpState;
-odc_status mesh_quality(MlpState* mlp, const float3* v, int64_t nv, const int3* t, int64_t nt, float iso,
-                        int64_t n_samples, uint64_t seed, int what, cudaStream_t s, odc_quality* out,
-                        std::string* err);
+odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const float3* v, int64_t nv, const int3* t,
+                        int64_t nt, float iso, int64_t n_samples, uint64_t seed, int what, cudaStream_t s,
+                        odc_quality* out, std::string* err);
 
 }  // namespace odc

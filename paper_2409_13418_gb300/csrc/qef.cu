@@ -9,7 +9,8 @@
 // accumulated as A = sum n n^T, b = sum n (n . p_e) and solved about the mass point
 // c of the cycle's 1D points: p = c + A^+ (b - A c), with A^+ the
 // pseudo-inverse keeping eigenvalues >= 0.01 of the largest (cyclic Jacobi
-// eigen-decomposition, FP64, in registers).
+// eigen-decomposition, FP64, in registers).  For the ablation's MDC variants
+// the normal is grad psi at the 1D point instead (Eq. 3).
 #include "kernels.h"
 #include "odc_device.cuh"
 
@@ -54,7 +55,8 @@ __device__ __forceinline__ void jacobi3(double a[3][3], double V[3][3], double w
 
 __global__ void k_qef(GridDev g, const uint32_t* __restrict__ flips, const WordInfo* __restrict__ wi,
                       const uint32_t* __restrict__ ebase, const uint32_t* __restrict__ fbase,
-                      const uint32_t* __restrict__ T, const float4* __restrict__ pf, const uint32_t* __restrict__ cells,
+                      const uint32_t* __restrict__ T, const float4* __restrict__ pf, const float3* __restrict__ gnorm,
+                      const uint32_t* __restrict__ cells,
                       const uint8_t* __restrict__ configs, const unsigned long long* __restrict__ cycles,
                       const uint32_t* __restrict__ vbase, uint32_t nc, int k, float3* __restrict__ vlocal,
                       float3* __restrict__ vworld) {
@@ -77,11 +79,12 @@ __global__ void k_qef(GridDev g, const uint32_t* __restrict__ flips, const WordI
             int a = le >> 2;
             int d0 = edge_corner0(le);
             int o[3] = {d0 & 1, (d0 >> 1) & 1, (d0 >> 2) & 1};
-            uint32_t te = T[edge_rank(g, wi, ebase, cp[0] + o[0], cp[1] + o[1], cp[2] + o[2], a)];
+            const uint32_t er = edge_rank(g, wi, ebase, cp[0] + o[0], cp[1] + o[1], cp[2] + o[2], a);
+            uint32_t te = T[er];
             double pe[3] = {(double)o[0], (double)o[1], (double)o[2]};
             pe[a] = (double)te * (double)inv;
-            double pfs[2][3];
-            for (int s = 0; s < 2; ++s) {
+            double pfs[2][3] = {{0, 0, 0}, {0, 0, 0}};
+            for (int s = 0; s < 2 && !gnorm; ++s) {
                 int f = s == 0 ? edge_face0(le) : edge_face1(le);
                 int fa = f >> 1, fs = f & 1;
                 int q[3] = {cp[0], cp[1], cp[2]};
@@ -96,6 +99,11 @@ __global__ void k_qef(GridDev g, const uint32_t* __restrict__ flips, const WordI
             double v1[3] = {pfs[0][0] - pe[0], pfs[0][1] - pe[1], pfs[0][2] - pe[2]};
             double v2[3] = {pfs[1][0] - pe[0], pfs[1][1] - pe[1], pfs[1][2] - pe[2]};
             double n[3] = {v1[1] * v2[2] - v1[2] * v2[1], v1[2] * v2[0] - v1[0] * v2[2], v1[0] * v2[1] - v1[1] * v2[0]};
+            if (gnorm) {   // Eq. 3: grad psi, as a normal in cell-local units
+                const float3 gw = gnorm[er];
+                const double gv[3] = {(double)gw.x, (double)gw.y, (double)gw.z};
+                for (int j = 0; j < 3; ++j) n[j] = gv[j] * ((double)g.X[j][cp[j] + 1] - (double)g.X[j][cp[j]]);
+            }
             for (int j = 0; j < 3; ++j) cs[j] += pe[j];
             ++cnt;
             double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
@@ -134,11 +142,11 @@ __global__ void k_qef(GridDev g, const uint32_t* __restrict__ flips, const WordI
 }
 
 void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, const uint32_t* ebase,
-                const uint32_t* fbase, const uint32_t* T, const float4* pf, const uint32_t* cells,
+                const uint32_t* fbase, const uint32_t* T, const float4* pf, const float3* gnorm, const uint32_t* cells,
                 const uint8_t* configs, const unsigned long long* cycles, const uint32_t* vbase, uint32_t nc, int k,
                 float3* vlocal, float3* vworld, cudaStream_t st) {
-    if (nc) { k_qef<<<(nc + 127) / 128, 128, 0, st>>>(g, flips, wi, ebase, fbase, T, pf, cells, configs, cycles, vbase,
-                                                   nc, k, vlocal, vworld); note_launch(); }
+    if (nc) { k_qef<<<(nc + 127) / 128, 128, 0, st>>>(g, flips, wi, ebase, fbase, T, pf, gnorm, cells, configs, cycles,
+                                                   vbase, nc, k, vlocal, vworld); note_launch(); }
 }
 
 }  // namespace odc

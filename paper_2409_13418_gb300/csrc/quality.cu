@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/odc.h"
+#include "csg_psi.cuh"
 #include "kernels.h"
 #include "mlp.h"
 #include "odc_internal.h"
@@ -104,11 +105,8 @@ __device__ __forceinline__ void atomic_max_pos(double* a, double v) {
     }
 }
 
-__global__ void k_deviation(const float* __restrict__ z, int64_t n, double iso, double* __restrict__ acc) {
+__device__ __forceinline__ void block_sum_max(double d, double* acc) {
     __shared__ double ssum[8], smax[8];
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double d = 0.0;
-    if (i < n) d = fabs(1.0 / (1.0 + exp(-(double)z[i])) - iso);
     double s = d, m = d;
     for (int o = 16; o; o >>= 1) {
         s += __shfl_down_sync(0xffffffffu, s, o);
@@ -123,6 +121,28 @@ __global__ void k_deviation(const float* __restrict__ z, int64_t n, double iso, 
         atomicAdd(&acc[0], S);
         atomic_max_pos(&acc[1], M);
     }
+}
+
+__global__ void k_deviation(const float* __restrict__ z, int64_t n, double iso, double* __restrict__ acc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double d = 0.0;
+    if (i < n) d = fabs(1.0 / (1.0 + exp(-(double)z[i])) - iso);
+    block_sum_max(d, acc);
+}
+
+// First-order distance |psi| / |grad psi| of the CSG surface (FP64).
+__global__ void k_csg_distance(const float3* __restrict__ pts, int64_t n, const PrimDev* __restrict__ prims,
+                               int n_prims, double* __restrict__ acc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double d = 0.0;
+    if (i < n) {
+        float3 p = pts[i];
+        double gr[3];
+        double psi = csg_psi<double>(prims, n_prims, (double)p.x, (double)p.y, (double)p.z, gr);
+        double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+        d = gn > 0.0 ? fabs(psi) / gn : fabs(psi);
+    }
+    block_sum_max(d, acc);
 }
 
 __global__ void k_check_indices(const int3* __restrict__ t, int64_t nt, int64_t nv, unsigned long long* __restrict__ bad) {
@@ -426,12 +446,13 @@ __global__ void k_count_flags(const uint8_t* __restrict__ flag, int64_t n, unsig
 
 static inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-odc_status mesh_quality(MlpState* mlp, const float3* v, int64_t nv, const int3* t, int64_t nt, float iso,
-                        int64_t n_samples, uint64_t seed, int what, cudaStream_t s, odc_quality* out,
-                        std::string* err) {
+odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const float3* v, int64_t nv, const int3* t,
+                        int64_t nt, float iso, int64_t n_samples, uint64_t seed, int what, cudaStream_t s,
+                        odc_quality* out, std::string* err) {
     out->n_tris = nt;
     out->n_samples = 0;
     out->occ_dev_mean = out->occ_dev_max = NAN;
+    out->dist_mean = out->dist_max = NAN;
     unsigned long long* dcnt;
     Q_CK(cudaMallocAsync((void**)&dcnt, 16 * sizeof(unsigned long long), s));
     Q_CK(cudaMemsetAsync(dcnt, 0, 16 * sizeof(unsigned long long), s));
@@ -458,7 +479,7 @@ odc_status mesh_quality(MlpState* mlp, const float3* v, int64_t nv, const int3* 
     }
     do {
         // ---- occupancy deviation on area-uniform samples
-        if ((what & ODC_Q_OCC) && mlp && nt > 0 && n_samples > 0) {
+        if ((what & ODC_Q_OCC) && (mlp || prims) && nt > 0 && n_samples > 0) {
             double *area, *excl, *acc;
             float3* pts;
             float* z;
@@ -473,15 +494,19 @@ odc_status mesh_quality(MlpState* mlp, const float3* v, int64_t nv, const int3* 
             k_areas<<<nb(nt), 256, 0, s>>>(v, t, nt, area); note_launch();
             exclusive_scan<double>(area, excl, (size_t)nt, tmp, total, s);
             k_samples<<<nb(n_samples), 256, 0, s>>>(v, t, nt, excl, area, total, n_samples, seed, pts); note_launch();
-            if ((r = mlp_eval_list(mlp, pts, n_samples, z, ODC_PREC_FP32, s, err)) != ODC_OK) break;
             Q_CK(cudaMemsetAsync(acc, 0, 16, s));
-            k_deviation<<<nb(n_samples), 256, 0, s>>>(z, n_samples, (double)iso, acc); note_launch();
+            if (mlp) {
+                if ((r = mlp_eval_list(mlp, pts, n_samples, z, ODC_PREC_FP32, s, err)) != ODC_OK) break;
+                k_deviation<<<nb(n_samples), 256, 0, s>>>(z, n_samples, (double)iso, acc); note_launch();
+            } else {
+                k_csg_distance<<<nb(n_samples), 256, 0, s>>>(pts, n_samples, prims, n_prims, acc); note_launch();
+            }
             double h[2];
             Q_CK(cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, s));
             Q_CK(cudaStreamSynchronize(s));
             out->n_samples = n_samples;
-            out->occ_dev_mean = h[0] / (double)n_samples;
-            out->occ_dev_max = h[1];
+            (mlp ? out->occ_dev_mean : out->dist_mean) = h[0] / (double)n_samples;
+            (mlp ? out->occ_dev_max : out->dist_max) = h[1];
         }
         // ---- manifoldness and Euler characteristic
         if (what & ODC_Q_MANIFOLD) {

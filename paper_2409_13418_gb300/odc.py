@@ -54,7 +54,7 @@ class Grid(C.Structure):
 class Params(C.Structure):
     _fields_ = [("iso", C.c_float), ("steps_1d", C.c_int32), ("s2d_lin1", C.c_int32), ("s2d_bin1", C.c_int32),
                 ("s2d_range1", C.c_float), ("s2d_lin2", C.c_int32), ("s2d_bin2", C.c_int32),
-                ("s2d_range2", C.c_float), ("ic_split", C.c_int32), ("reserved", C.c_int32)]
+                ("s2d_range2", C.c_float), ("ic_split", C.c_int32), ("flags", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -75,6 +75,7 @@ class MeshC(C.Structure):
 
 class QualityC(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("occ_dev_mean", C.c_double), ("occ_dev_max", C.c_double),
+                ("dist_mean", C.c_double), ("dist_max", C.c_double),
                 ("n_tris", C.c_int64), ("n_verts", C.c_int64), ("n_edges", C.c_int64), ("euler", C.c_int64),
                 ("n_degenerate", C.c_int64), ("n_bad_edges", C.c_int64), ("n_bad_verts", C.c_int64),
                 ("manifold", C.c_int32), ("si_checked", C.c_int32), ("n_si_pairs", C.c_int64),
@@ -226,13 +227,18 @@ def make_grid(grid: I.Grid) -> Grid:
     return g
 
 
+ABL_LINEAR_1D, ABL_GRADIENT_NORMALS = 1, 2
+
+
 def make_params(steps_1d=15, iso=0.5, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12,
-                range2=float(np.float32(np.sqrt(2.0) / 2.0)), ic_split=True) -> Params:
+                range2=float(np.float32(np.sqrt(2.0) / 2.0)), ic_split=True, linear_1d=False,
+                gradient_normals=False) -> Params:
     p = Params()
     p.iso, p.steps_1d = iso, steps_1d
     p.s2d_lin1, p.s2d_bin1, p.s2d_range1 = lin1, bin1, range1
     p.s2d_lin2, p.s2d_bin2, p.s2d_range2 = lin2, bin2, range2
     p.ic_split = int(bool(ic_split))
+    p.flags = (ABL_LINEAR_1D if linear_1d else 0) | (ABL_GRADIENT_NORMALS if gradient_normals else 0)
     return p
 
 

@@ -44,8 +44,11 @@ def test_csg_mesh_quality_matches_oracle(ctx):
     src = I.random_csg(4, n_prims=12)
     mesh = ctx.extract(src, I.cube_grid(20), steps_1d=10)
     v, t = mesh.to_host()
-    q = mesh.quality(n_samples=1000)
-    assert math.isnan(q["occ_dev_mean"]) and q["n_samples"] == 0     # binary occupancy
+    q = mesh.quality(n_samples=100000, seed=4)
+    assert math.isnan(q["occ_dev_mean"]) and q["n_samples"] == 100000   # binary occupancy: distance instead
+    dm, dx = Q.surface_distance(src, v, t, 100000, seed=4)
+    print(q["dist_mean"], dm, q["dist_max"], dx)
+    assert abs(q["dist_mean"] - dm) <= 1e-6 * max(dm, 1e-3) + 1e-9 and abs(q["dist_max"] - dx) <= 1e-5 * dx
     c, flag = Q.self_intersections(v, t)
     assert q["n_si_pairs"] == c > 0 and q["n_si_tris"] == int(flag.sum())
     assert q["manifold"] == 1 and q["euler"] == meshcheck.euler_characteristic(t)
