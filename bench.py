@@ -159,6 +159,34 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def ablation_table(odc, I, res: int = 128, seed: int = 1):
+    """The shape of the paper's ablation (Sec. 6.3, Tab. 3) on a seeded
+    64-primitive CSG tree at res^3 (k = 12): Manifold Dual Contouring, + 1D
+    search, + 2D search, + IC split (= ODC).  Per variant: device ms of the
+    extraction (CUDA events inside the library), #V, #T, the mean first-order
+    surface distance at 2M area-uniform samples (in cells), self-intersecting
+    triangle pairs and manifoldness."""
+    src = I.random_csg(seed, n_prims=64)
+    g = I.cube_grid(res)
+    h = 2.0 / res
+    rows = {}
+    variants = (("MDC", dict(linear_1d=True, gradient_normals=True, ic_split=False)),
+                ("+1D search", dict(gradient_normals=True, ic_split=False)),
+                ("+2D search", dict(ic_split=False)),
+                ("+IC (ODC)", dict()))
+    with odc.Context(0) as ctx:
+        for name, kw in variants:
+            ms = []
+            for _ in range(4):
+                m = ctx.extract(src, g, steps_1d=12, **kw)
+                ms.append(m.stats["stage_ms"][7])
+            q = m.quality(n_samples=2_000_000, seed=1)
+            rows[name] = {"ms": round(min(ms[1:]), 3), "verts": m.n_verts, "tris": m.n_tris,
+                          "dist_mean_cells": q["dist_mean"] / h, "si_pairs": q["n_si_pairs"],
+                          "manifold": bool(q["manifold"])}
+    return {"workload": f"seeded 64-primitive CSG tree (seed {seed}), {res}^3 cells, k=12", "rows": rows}
+
+
 def serve_arm(odc, I, net, trace, slots, precision, budget):
     """Replays an arrival trace through the request loop: a submitter thread
     submits each request at its arrival time, the caller collects them.
@@ -241,6 +269,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the serving arrival trace (0: skip the serving comparison)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--no-ablation", action="store_true", help="skip the ablation table (Sec. 6.3 variants)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -385,6 +414,9 @@ def main():
                 "gpu_launches": int(launches),
                 "roofline": roof,
                 "clocks": clocks}
+        if world == 1 and not args.no_ablation:
+            from paper_2409_13418_gb300 import inputs as I
+            line["ablation"] = ablation_table(odc, I)
         if world == 1 and args.serve_seconds > 0:
             ctx.close()
             from paper_2409_13418_gb300 import inputs as I
