@@ -303,7 +303,7 @@ def topology_triangles(labels):
 
 def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12,
             range2=float(np.float32(math.sqrt(2.0) / 2.0)), iso=0.5, ic_split=True,
-            replay=None, replay_margin=0.0, linear_1d=False, gradient_normals=False) -> Result:
+            replay=None, replay_margin=0.0, linear_1d=False, gradient_normals=False, mc=False) -> Result:
     """Run ODC on ``src`` (a CSG/MLP source or a callable) over ``grid``.
 
     Ablation variants (Sec. 6.3, Tab. 3; CSG sources only, which have an
@@ -312,6 +312,12 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     and quantised to the 1D lattice of 2^-(k+1) edge) instead of the binary
     search; ``gradient_normals`` uses grad psi at the 1D point as the plane
     normal of Eq. 3 instead of the 2D points (the 2D search is skipped).
+
+    ``mc`` polygonizes as marching cubes with the same cycles (Tab. A8's "MC"
+    rows): the mesh vertices are the 1D points (edge order) and every cycle
+    of every crossing cell (cell order, cycle order) is fanned from its
+    smallest local edge along topology.mc_successors; no 2D search, QEF or
+    quads.
 
     ``replay`` (optional) supplies the search decisions of another
     implementation instead of taking them from phi: ``T`` (1D results) and
@@ -576,7 +582,7 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     pf = np.zeros((F, 2))
     search = dict(Jq=np.zeros(0, np.int64), J1=np.zeros(0, np.int64), J2=np.zeros(0, np.int64),
                   lab_m=np.zeros(0, bool), found=np.zeros(0, np.int64))
-    if F and not gradient_normals:
+    if F and not gradient_normals and not mc:
         allf = np.ones(F, bool)
         m = (P1 + P2) / 2.0
         lab_m, mar_m = query(m, allf)
@@ -622,6 +628,42 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
         flags[near_par & ~par] |= 4
 
     fkey = faces[:, 0] * 2 + faces[:, 1]
+
+    if mc:
+        # ---- marching-cubes polygons through the 1D points (Tab. A8) ---------------
+        pw = x_lo.copy()
+        pw[np.arange(E), ea] = x_lo[np.arange(E), ea] + span * tau
+        verts = pw.astype(np.float32).astype(np.float64)
+        tris = []
+        for c in range(C):
+            cyc = cell_cyc[c]
+            succ = topo.mc_successors(int(configs[c]), int(cell_flipm[c]))
+            cell = np.array([ci[c], cj[c], ck[c]])
+            gid = {}
+            for le in range(12):
+                if cyc[le] >= 0:
+                    a, o1, o2 = topo.edge_axis_offsets(le)
+                    q = cell.copy()
+                    q[(a + 1) % 3] += o1
+                    q[(a + 2) % 3] += o2
+                    gid[le] = int(np.searchsorted(edges, 3 * geo.vid(q[0], q[1], q[2]) + a))
+            for cy in range(int(cell_ncyc[c])):
+                le0 = min(le for le in range(12) if cyc[le] == cy)
+                ring = [le0]
+                while succ[ring[-1]] != le0:
+                    ring.append(succ[ring[-1]])
+                for t in range(1, len(ring) - 1):
+                    tris.append((gid[ring[0]], gid[ring[t]], gid[ring[t + 1]]))
+        z3 = np.zeros((0, 3))
+        return Result(res=N, steps=k1, labels=labels, label_margin=label_margin,
+                      edges=edges, T=T, edge_margin=edge_margin, faces=faces, face_pts=pf, face_flags=flags,
+                      face_margin=face_margin, flips=flips, cells=cells, configs=configs, cell_cyc=cell_cyc,
+                      cell_ncyc=cell_ncyc, vbase=vbase, verts_local=z3, vert_margin=np.zeros(0), vert_flag=np.zeros(0, bool),
+                      vertices=verts, triangles=np.array(tris, np.int64).reshape(-1, 3),
+                      quad_edges=np.zeros(0, np.int64), quad_case=np.zeros(0, np.int64), quad_flag=np.zeros(0, bool),
+                      quad_margin=np.zeros(0), queries=phi.queries, search=search,
+                      stats=dict(E=E, F=F, C=C, V3=0, case3=0, flips=len(flips), fix_rounds=rounds,
+                                 queries=phi.queries, edge_violations=int(edge_viol.sum()), face_violations=0))
 
     # ---- normals (Sec. 5.3) and QEF 3D points (Eq. 2) --------------------------------
     # every (crossing cell, crossing local edge) pair contributes one plane to

@@ -156,6 +156,34 @@ def cell_cycles(config: int, flips: int = 0):
     return tuple(cyc), n
 
 
+@lru_cache(maxsize=None)
+def mc_successors(config: int, flips: int = 0):
+    """Oriented order of every cycle of a cell, for marching-cubes polygons
+    (Tab. A8's MC variants): successor of each crossing local edge, -1 if not
+    crossing.
+
+    Each face boundary is walked counter-clockwise as seen from outside the
+    cell (face order for side 1, reversed for side 0: the face spans
+    u = (a+1)%3, v = (a+2)%3 with u x v along +a).  A segment runs from the
+    face's out->in crossing to its in->out crossing; the surface polygon then
+    turns counter-clockwise about its outward normal (inside corners on its
+    right when walked on the face from outside).  A crossing edge is an
+    out->in crossing on exactly one of its two faces (the faces walk their
+    shared edge in opposite directions), where its successor is the other end
+    of its segment."""
+    nxt = [-1] * 12
+    for f in range(6):
+        lab4 = _cell_face_labels(config, f)
+        fe = face_edges(f)
+        side = f % 2
+        for (i, j) in face_segments(lab4, bool((flips >> f) & 1)):
+            for (x, y) in ((i, j), (j, i)):
+                a, b = (x, (x + 1) % 4) if side else ((x + 1) % 4, x)   # walk from corner a to b
+                if not lab4[a] and lab4[b]:
+                    nxt[fe[x]] = fe[y]
+    return tuple(nxt)
+
+
 def cell_crossing_edges(config: int):
     out = []
     for le in range(12):

@@ -97,3 +97,67 @@ def test_random_voxel_grids_are_closed_manifold(density):
         tris, t = odc.topology_triangles(lab)
         chk = meshcheck.check_closed_manifold(tris)
         assert chk["ok"], chk
+
+
+# ---- marching-cubes polygons (Tab. A8's MC variants) ------------------------
+
+def _label_source(lab, lo=-1.0, h=0.5):
+    """Occupancy of a label grid: the label of the nearest grid vertex (ties
+    to the upper one), so every crossing edge's bisection ends at its middle."""
+    nz, ny, nx = lab.shape
+
+    def phi(x):
+        idx = np.floor((x - lo) / h + 0.5).astype(np.int64)
+        i = np.clip(idx[:, 0], 0, nx - 1)
+        j = np.clip(idx[:, 1], 0, ny - 1)
+        k = np.clip(idx[:, 2], 0, nz - 1)
+        return lab[k, j, i], np.full(x.shape[0], np.inf)
+    return phi
+
+
+def test_mc_polygons_close_and_face_outward_for_every_cell_configuration():
+    from oracle import meshcheck, odc
+    from paper_2409_13418_gb300 import inputs as I
+    g = I.Grid((-1.0, -1.0, -1.0), (0.5, 0.5, 0.5), (3, 3, 3))
+    for cfg in range(1, 256):
+        lab = np.zeros((4, 4, 4), bool)
+        for c in range(8):
+            lab[1 + (c >> 2), 1 + ((c >> 1) & 1), 1 + (c & 1)] = (cfg >> c) & 1
+        r = odc.extract(_label_source(lab), g, steps_1d=4, mc=True)
+        assert meshcheck.check_closed_manifold(r.triangles)["ok"], cfg
+        assert meshcheck.signed_volume(r.vertices, r.triangles) > 0, cfg
+
+
+def test_mc_polygons_on_random_label_grids():
+    from oracle import meshcheck, odc
+    from paper_2409_13418_gb300 import inputs as I
+    rng = np.random.default_rng(11)
+    g = I.Grid((-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), (4, 4, 4))
+    for _ in range(300):
+        lab = np.zeros((5, 5, 5), bool)
+        lab[1:4, 1:4, 1:4] = rng.random((3, 3, 3)) < 0.5
+        if not lab.any():
+            continue
+        r = odc.extract(_label_source(lab), g, steps_1d=4, mc=True)
+        assert meshcheck.check_closed_manifold(r.triangles)["ok"]
+        # the surface bounds the union of the inside vertices' half-cell
+        # neighbourhoods: positive volume
+        assert meshcheck.signed_volume(r.vertices, r.triangles) > 0
+
+
+def test_mc_around_a_single_inside_vertex_is_an_octahedron():
+    """A sphere of radius 0.3 h around one grid vertex: six crossing edges,
+    eight triangles, vertices within 2^-(k+1) h of distance 0.3 h, volume
+    (4/3) r^3 of the octahedron with those vertices."""
+    from oracle import meshcheck, odc
+    from paper_2409_13418_gb300 import inputs as I
+    h = 0.25
+    src = I.single_prim(I.PRIM_SPHERE, (0.0, 0.0, 0.0), params=(0.3 * h,))
+    k = 12
+    r = odc.extract(src, I.cube_grid(8), steps_1d=k, mc=True)
+    assert r.vertices.shape == (6, 3) and r.triangles.shape == (8, 3)
+    d = np.linalg.norm(r.vertices, axis=1)
+    assert np.all(np.abs(d - 0.3 * h) <= h * 2.0 ** -(k + 1) + 1e-7)
+    vol = meshcheck.signed_volume(r.vertices, r.triangles)
+    lo, hi = (4 / 3) * d.min() ** 3, (4 / 3) * d.max() ** 3
+    assert lo * (1 - 1e-6) <= vol <= hi * (1 + 1e-6)
