@@ -160,9 +160,10 @@ def run_reference(args, rank, world):
 
 
 def ablation_table(odc, I, res: int = 128, seed: int = 1):
-    """The shape of the paper's ablation (Sec. 6.3, Tab. 3) on a seeded
-    64-primitive CSG tree at res^3 (k = 12): Manifold Dual Contouring, + 1D
-    search, + 2D search, + IC split (= ODC).  Per variant: device ms of the
+    """The shape of the paper's ablations (Sec. 6.3, Tab. 3; Tab. A8) on a
+    seeded 64-primitive CSG tree at res^3 (k = 12): marching cubes through
+    linearly placed and through bisected 1D points, Manifold Dual Contouring,
+    + 1D search, + 2D search, + IC split (= ODC).  Per variant: device ms of the
     extraction (CUDA events inside the library), #V, #T, the mean first-order
     surface distance at 2M area-uniform samples (in cells), self-intersecting
     triangle pairs and manifoldness."""
@@ -170,7 +171,9 @@ def ablation_table(odc, I, res: int = 128, seed: int = 1):
     g = I.cube_grid(res)
     h = 2.0 / res
     rows = {}
-    variants = (("MDC", dict(linear_1d=True, gradient_normals=True, ic_split=False)),
+    variants = (("MC", dict(linear_1d=True, mc=True)),
+                ("MC + 1D search", dict(mc=True)),
+                ("MDC", dict(linear_1d=True, gradient_normals=True, ic_split=False)),
                 ("+1D search", dict(gradient_normals=True, ic_split=False)),
                 ("+2D search", dict(ic_split=False)),
                 ("+IC (ODC)", dict()))
@@ -360,10 +363,16 @@ def main():
     # Sec. 6.1 quality measures of the last mesh (outside every timed region)
     tq = time.perf_counter()
     quality = m.quality(n_samples=2_000_000, seed=1)
+    mc = ctx.extract(mlp, grid, steps_1d=STEPS_1D, stream=stream.cuda_stream, precision=prec, band=args.band,
+                     mc=True)
+    qmc = mc.quality(n_samples=2_000_000, seed=1)
+    mc_quality = {"occ_dev_mean": qmc["occ_dev_mean"], "manifold": bool(qmc["manifold"]), "si_pairs": qmc["n_si_pairs"],
+                  "verts": mc.n_verts, "tris": mc.n_tris, "device_ms": round(mc.stats["stage_ms"][7], 3)}
     quality = {"occ_dev_mean": quality["occ_dev_mean"], "occ_dev_max": quality["occ_dev_max"],
                "samples": quality["n_samples"], "manifold": bool(quality["manifold"]), "euler": quality["euler"],
                "si_pairs": quality["n_si_pairs"], "si_tris": quality["n_si_tris"], "tris": quality["n_tris"],
-               "seconds": round(time.perf_counter() - tq, 3)}
+               "seconds": round(time.perf_counter() - tq, 3),
+               "mc_1d_same_grid": mc_quality}
 
     if rank == 0:
         peaks, peak_src = _peaks()

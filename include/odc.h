@@ -177,6 +177,14 @@ typedef struct {
  * "+1D search" row. */
 enum { ODC_ABL_LINEAR_1D = 1, ODC_ABL_GRADIENT_NORMALS = 2 };
 
+/* Marching-cubes polygonization through the 1D points (Tab. A8's "MC" rows),
+ * any source: the mesh vertices are the 1D points of the crossing edges in
+ * edge order, and every cycle of every crossing cell (the same A.1.1 cycles
+ * and manifold fix) is a polygon fanned from its smallest local edge, cells
+ * in cell order, counter-clockwise seen from outside; no 2D search, QEF or
+ * quads.  With ODC_ABL_LINEAR_1D (CSG) it is plain marching cubes. */
+enum { ODC_POLY_MC = 4 };
+
 typedef struct {
     int64_t n_edges;             /* |E^S| crossing edges */
     int64_t n_face_segs;         /* 2D points (one per face segment) */

@@ -264,8 +264,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         !(prm->s2d_range2 > 0))
         return fail(ODC_ERR_INVALID_ARG, "2D search parameters out of range");
     if (!(prm->iso > 0.0f && prm->iso < 1.0f)) return fail(ODC_ERR_INVALID_ARG, "iso must be in (0, 1)");
-    if (prm->flags & ~(ODC_ABL_LINEAR_1D | ODC_ABL_GRADIENT_NORMALS))
-        return fail(ODC_ERR_INVALID_ARG, "unknown ablation flags");
+    if (prm->flags & ~(ODC_ABL_LINEAR_1D | ODC_ABL_GRADIENT_NORMALS | ODC_POLY_MC))
+        return fail(ODC_ERR_INVALID_ARG, "unknown flags");
     ODC_CK(cudaSetDevice(c->device));
     cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
     std::memset(out, 0, sizeof(*out));
@@ -278,10 +278,11 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
     }
     const int kind = c->res_kind;
-    if (prm->flags && kind != ODC_SRC_CSG)
+    if ((prm->flags & (ODC_ABL_LINEAR_1D | ODC_ABL_GRADIENT_NORMALS)) && kind != ODC_SRC_CSG)
         return fail(ODC_ERR_UNSUPPORTED, "ablation variants need an implicit with a gradient: CSG sources only");
     const bool linear_1d = (prm->flags & ODC_ABL_LINEAR_1D) != 0;
-    const bool grad_normals = (prm->flags & ODC_ABL_GRADIENT_NORMALS) != 0;
+    const bool mc = (prm->flags & ODC_POLY_MC) != 0;
+    const bool grad_normals = !mc && (prm->flags & ODC_ABL_GRADIENT_NORMALS) != 0;
     PrimDev* d_prims = c->res_prims;
     float4* d_cull = c->res_cull;
     const int n_prims = c->res_nprims;
@@ -353,7 +354,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     size_t stmpB = scan_tmp_elems(std::max<size_t>(std::max(E, C), 1));
     size_t needB = 2 * al(E * 4ull) + al(F * 4ull) + 3 * al(F) + al(F * 16ull) + al(F * sizeof(FaceDecisions)) + al(C * 4ull) + al(C) + al(C * 8ull) +
                    2 * al(C * 4ull) + al(4ull * C * 12) + al((4ull * C + E) * 12) + al(E) + al(E * 16ull) +
-                   2 * al(E * 8ull) + al(4ull * E * 12) + al(stmpB * 8) + al(E * 12ull) + 1024;
+                   2 * al(E * 8ull) + al(4ull * E * 12) + al(stmpB * 8) + al(E * 12ull) + 2 * al(C * 4ull) + 1024;
     s = arena_ensure(c, c->B, needB, st);
     if (s != ODC_OK) return s;
     uint32_t* edges = (uint32_t*)c->B.take(E * 4ull);
@@ -378,6 +379,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     int3* tris = (int3*)c->B.take(4ull * E * 12);
     void* tmpB = c->B.take(stmpB * 8);
     float3* gnorm = grad_normals ? (float3*)c->B.take(E * 12ull) : nullptr;
+    uint32_t* mc_cnt = (uint32_t*)c->B.take(C * 4ull);
+    uint32_t* mc_off = (uint32_t*)c->B.take(C * 4ull);
 
     launch_emit(g, bits, wi, ebase, fbase, cbase, edges, faces, slots, cells, configs, st);
     ODC_CK(cudaGetLastError());
@@ -414,42 +417,65 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     ODC_CK(cudaGetLastError());
     ODC_CK(cudaEventRecord(c->ev[4], st));
 
-    // ---- a5: 2D search
-    if (grad_normals) {   // Eq. 3 normals replace the 2D points: no 2D search
-        launch_edge_grad(g, edges, T, E, prm->steps_1d, d_prims, n_prims, gnorm, st);
+    uint32_t V3 = 0, NT = 0, N3 = 0, NV = 0;
+    if (mc) {
+        // ---- marching-cubes polygons through the 1D points: no 2D search, QEF or quads
         if (F) {
             ODC_CK(cudaMemsetAsync(pf, 0, F * 16ull, st));
             ODC_CK(cudaMemsetAsync(fflags, 0, F, st));
             ODC_CK(cudaMemsetAsync(dec, 0, F * sizeof(FaceDecisions), st));
         }
-    } else if (kind == ODC_SRC_CSG) {
-        launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, n_prims, pf, fflags,
-                        dec, st);
+        if (E) ODC_CK(cudaMemsetAsync(qcase, 0, E, st));
+        ODC_CK(cudaEventRecord(c->ev[5], st));
+        ODC_CK(cudaEventRecord(c->ev[6], st));
+        launch_mc(g, flips, wi, ebase, edges, T, E, prm->steps_1d, cells, configs, cycles, C, mc_cnt, mc_off,
+                  (uint32_t*)tmpB, dcnt + 24, vworld, tris, st);
+        ODC_CK(cudaGetLastError());
+        ODC_CK(cudaEventRecord(c->ev[7], st));
+        ODC_CK(cudaMemcpyAsync(c->h_cnt + 16, dcnt, 32 * 4, cudaMemcpyDeviceToHost, st));
+        ODC_CK(cudaStreamSynchronize(st));
+        NT = c->h_cnt[16 + 24];
+        NV = E;
     } else {
-        s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, dec, st, &nq,
-                      &g_err);
-        if (s != ODC_OK) return s;
+        // ---- a5: 2D search
+        if (grad_normals) {   // Eq. 3 normals replace the 2D points: no 2D search
+            launch_edge_grad(g, edges, T, E, prm->steps_1d, d_prims, n_prims, gnorm, st);
+            if (F) {
+                ODC_CK(cudaMemsetAsync(pf, 0, F * 16ull, st));
+                ODC_CK(cudaMemsetAsync(fflags, 0, F, st));
+                ODC_CK(cudaMemsetAsync(dec, 0, F * sizeof(FaceDecisions), st));
+            }
+        } else if (kind == ODC_SRC_CSG) {
+            launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, n_prims, pf, fflags,
+                            dec, st);
+        } else {
+            s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, dec, st, &nq,
+                          &g_err);
+            if (s != ODC_OK) return s;
+        }
+        ODC_CK(cudaGetLastError());
+        ODC_CK(cudaEventRecord(c->ev[5], st));
+
+        // ---- a6, a7: normals and QEF
+        launch_qef(g, flips, wi, ebase, fbase, T, pf, gnorm, cells, configs, cycles, vbase, C, prm->steps_1d, vlocal,
+                   vworld, st);
+        ODC_CK(cudaGetLastError());
+        ODC_CK(cudaEventRecord(c->ev[6], st));
+
+        // ---- a8: quads with IC split
+        launch_quad_case(g, bits, wi, cbase, edges, E, cycles, vbase, vlocal, prm->ic_split, qcase, qv, qcnt, st);
+        exclusive_scan<unsigned long long>(qcnt, qoff, E, (unsigned long long*)tmpB, (unsigned long long*)(dcnt + 16), st);
+        launch_quad_emit(g, edges, T, E, prm->steps_1d, qcase, qv, qoff, dcnt + 3, vworld, tris, st);
+        ODC_CK(cudaGetLastError());
+        ODC_CK(cudaEventRecord(c->ev[7], st));
+        ODC_CK(cudaMemcpyAsync(c->h_cnt + 16, dcnt, 24 * 4, cudaMemcpyDeviceToHost, st));
+        ODC_CK(cudaStreamSynchronize(st));
+        V3 = c->h_cnt[16 + 3];
+        unsigned long long qt = ((unsigned long long)c->h_cnt[16 + 17] << 32) | c->h_cnt[16 + 16];
+        NT = (uint32_t)(qt >> 32);
+        N3 = (uint32_t)(qt & 0xffffffffu);
+        NV = V3 + N3;
     }
-    ODC_CK(cudaGetLastError());
-    ODC_CK(cudaEventRecord(c->ev[5], st));
-
-    // ---- a6, a7: normals and QEF
-    launch_qef(g, flips, wi, ebase, fbase, T, pf, gnorm, cells, configs, cycles, vbase, C, prm->steps_1d, vlocal,
-               vworld, st);
-    ODC_CK(cudaGetLastError());
-    ODC_CK(cudaEventRecord(c->ev[6], st));
-
-    // ---- a8: quads with IC split
-    launch_quad_case(g, bits, wi, cbase, edges, E, cycles, vbase, vlocal, prm->ic_split, qcase, qv, qcnt, st);
-    exclusive_scan<unsigned long long>(qcnt, qoff, E, (unsigned long long*)tmpB, (unsigned long long*)(dcnt + 16), st);
-    launch_quad_emit(g, edges, T, E, prm->steps_1d, qcase, qv, qoff, dcnt + 3, vworld, tris, st);
-    ODC_CK(cudaGetLastError());
-    ODC_CK(cudaEventRecord(c->ev[7], st));
-    ODC_CK(cudaMemcpyAsync(c->h_cnt + 16, dcnt, 24 * 4, cudaMemcpyDeviceToHost, st));
-    ODC_CK(cudaStreamSynchronize(st));
-    uint32_t V3 = c->h_cnt[16 + 3];
-    unsigned long long qt = ((unsigned long long)c->h_cnt[16 + 17] << 32) | c->h_cnt[16 + 16];
-    uint32_t NT = (uint32_t)(qt >> 32), N3 = (uint32_t)(qt & 0xffffffffu);
 
     c->g = g;
     c->k = prm->steps_1d;
@@ -458,7 +484,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     c->slots = slots; c->fflags = fflags; c->configs = configs; c->qcase = qcase; c->pf = pf; c->dec = dec; c->cycles = cycles;
     c->vlocal = vlocal; c->vworld = vworld; c->tris = tris; c->nw = nw;
 
-    out->n_verts = (int64_t)V3 + N3;
+    out->n_verts = (int64_t)NV;
     out->n_tris = NT;
     out->d_verts = (const float*)vworld;
     out->d_tris = (const int32_t*)tris;

@@ -47,6 +47,12 @@ void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, con
                 const uint8_t* configs, const unsigned long long* cycles, const uint32_t* vbase, uint32_t nc, int k,
                 float3* vlocal, float3* vworld, cudaStream_t st);
 
+// mc.cu (marching-cubes polygons through the 1D points)
+void launch_mc(const GridDev& g, const uint32_t* flips, const WordInfo* wi, const uint32_t* ebase,
+               const uint32_t* edges, const uint32_t* T, uint32_t ne, int k, const uint32_t* cells,
+               const uint8_t* configs, const unsigned long long* cycles, uint32_t nc, uint32_t* cnt, uint32_t* off,
+               uint32_t* tmp, uint32_t* total, float3* vworld, int3* tris, cudaStream_t st);
+
 // ablation.cu (MDC variants of the ablation, CSG sources)
 void launch_linear_1d(const GridDev& g, const uint32_t* edges, uint32_t ne, int k, const PrimDev* prims, int n_prims,
                       uint32_t* T, cudaStream_t st);

@@ -228,6 +228,29 @@ __device__ __forceinline__ int face_slot_of(uint32_t cfg, uint32_t flipmask, int
     return 0;
 }
 
+// Marching-cubes polygon order (Tab. A8's MC variants): the successor of
+// crossing local edge le in its oriented cycle.  Each face boundary is walked
+// counter-clockwise as seen from outside the cell (face-corner order for side
+// 1, reversed for side 0); a segment runs from the face's out->in crossing to
+// its in->out crossing, and le is the out->in crossing on exactly one of its
+// two faces, where its successor is the other end of its segment.
+__device__ __forceinline__ int mc_next(uint32_t cfg, uint32_t flipmask, int le) {
+    for (int w = 0; w < 2; ++w) {
+        const int f = w == 0 ? edge_face0(le) : edge_face1(le);
+        const int lab4 = face_lab4(cfg, f);
+        int seg[2][2];
+        const int ns = face_segments(lab4, (flipmask >> f) & 1, seg);
+        for (int s = 0; s < ns; ++s)
+            for (int e = 0; e < 2; ++e) {
+                const int x = seg[s][e];
+                if (face_edge(f, x) != le) continue;
+                const int a = (f & 1) ? x : ((x + 1) & 3), b = (f & 1) ? ((x + 1) & 3) : x;
+                if (!((lab4 >> a) & 1) && ((lab4 >> b) & 1)) return face_edge(f, seg[s][1 - e]);
+            }
+    }
+    return -1;
+}
+
 // ------------------------------------------------------------- grid access
 __device__ __forceinline__ uint32_t label_at(const GridDev& g, const uint32_t* bits, int x, int y, int z) {
     return (bits[((size_t)z * g.nv[1] + y) * g.W + (x >> 5)] >> (x & 31)) & 1u;

@@ -227,18 +227,19 @@ def make_grid(grid: I.Grid) -> Grid:
     return g
 
 
-ABL_LINEAR_1D, ABL_GRADIENT_NORMALS = 1, 2
+ABL_LINEAR_1D, ABL_GRADIENT_NORMALS, POLY_MC = 1, 2, 4
 
 
 def make_params(steps_1d=15, iso=0.5, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12,
                 range2=float(np.float32(np.sqrt(2.0) / 2.0)), ic_split=True, linear_1d=False,
-                gradient_normals=False) -> Params:
+                gradient_normals=False, mc=False) -> Params:
     p = Params()
     p.iso, p.steps_1d = iso, steps_1d
     p.s2d_lin1, p.s2d_bin1, p.s2d_range1 = lin1, bin1, range1
     p.s2d_lin2, p.s2d_bin2, p.s2d_range2 = lin2, bin2, range2
     p.ic_split = int(bool(ic_split))
-    p.flags = (ABL_LINEAR_1D if linear_1d else 0) | (ABL_GRADIENT_NORMALS if gradient_normals else 0)
+    p.flags = (ABL_LINEAR_1D if linear_1d else 0) | (ABL_GRADIENT_NORMALS if gradient_normals else 0) | \
+        (POLY_MC if mc else 0)
     return p
 
 
