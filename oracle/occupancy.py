@@ -24,7 +24,7 @@ import math
 import numpy as np
 
 from paper_2409_13418_gb300.inputs import (CSGSource, MLPSource, OP_UNION, PRIM_AABB,
-                                           PRIM_CYLINDER, PRIM_OBOX, PRIM_SPHERE, PRIM_TORUS)
+                                           PRIM_CYLINDER, PRIM_OBOX, PRIM_SPHERE, PRIM_TORUS, VoxelSource)
 
 
 def to_query(points: np.ndarray) -> np.ndarray:
@@ -239,6 +239,40 @@ def mlp_eval(src: MLPSource, points: np.ndarray, iso: float = 0.5):
     return z > t, np.abs(occ - iso)
 
 
+def voxel_value(src: VoxelSource, points: np.ndarray) -> np.ndarray:
+    """Trilinear interpolation of the sample volume at FP32-rounded points
+    (FP64): per axis u = (x - lo) / (hi - lo) * (dims - 1) clamped to
+    [0, dims - 1], cell i = min(floor(u), dims - 2), fraction u - i; then
+    lerps along x, y, z."""
+    x = to_query(points)
+    v = src.values.astype(np.float64)
+    dims = src.dims
+    idx, frac = [], []
+    for a in range(3):
+        lo, hi = float(np.float32(src.lo[a])), float(np.float32(src.hi[a]))
+        u = (x[:, a] - lo) / (hi - lo) * (dims[a] - 1)
+        u = np.clip(u, 0.0, dims[a] - 1)
+        i = np.minimum(np.floor(u).astype(np.int64), dims[a] - 2)
+        idx.append(i)
+        frac.append(u - i)
+    i, j, k = idx
+    fx, fy, fz = frac
+
+    def lerp(a, b, f):
+        return a + (b - a) * f
+    c00 = lerp(v[k, j, i], v[k, j, i + 1], fx)
+    c10 = lerp(v[k, j + 1, i], v[k, j + 1, i + 1], fx)
+    c01 = lerp(v[k + 1, j, i], v[k + 1, j, i + 1], fx)
+    c11 = lerp(v[k + 1, j + 1, i], v[k + 1, j + 1, i + 1], fx)
+    return lerp(lerp(c00, c10, fy), lerp(c01, c11, fy), fz)
+
+
+def voxel_eval(src: VoxelSource, points: np.ndarray, iso: float = 0.5):
+    """Labels (value > iso) and margins |value - iso| of a voxel source."""
+    phi = voxel_value(src, points)
+    return phi > iso, np.abs(phi - iso)
+
+
 class Occupancy:
     """Callable phi with query accounting: ``labels, margins = phi(points)``."""
 
@@ -256,6 +290,8 @@ class Occupancy:
             return csg_eval(self.src, points)
         if isinstance(self.src, MLPSource):
             return mlp_eval(self.src, points, self.iso)
+        if isinstance(self.src, VoxelSource):
+            return voxel_eval(self.src, points, self.iso)
         if callable(self.src):
             return self.src(to_query(points))
         raise TypeError(type(self.src))

@@ -17,6 +17,11 @@ Instances:
   f a Kaiming-initialised 128 -> 4 x 256 ReLU -> 1 MLP over 64 random Fourier
   frequencies (sigma = 4).
 
+* ``voxel_random(seed, dims)`` / ``voxel_blobs(seed, dims)``: dense sample
+  volumes (vertex-centred samples over a box) whose trilinear interpolation
+  is the occupancy; random values stress the topology, smoothed blobs model
+  user-provided volumes.
+
 The occupancy function phi of the paper (Sec. 3) is any map R^3 -> {0, 1};
 CSG and MLP sources stand in for the paper's neural occupancies (Sec. 6,
 A.2.2), which need trained weights that are not available.
@@ -259,6 +264,48 @@ def envelope_mlp(seed: int = 0, n_freq: int = 64, sigma: float = 4.0, hidden: in
         latent = rng.standard_normal(latent_dim).astype(np.float32)
     return MLPSource(B=B, weights=weights, biases=biases, latent=latent,
                      name=f"mlp_seed{seed}")
+
+
+@dataclass
+class VoxelSource:
+    """Dense sample volume: values[k, j, i] (float32) sit at lo + (hi - lo) *
+    (i, j, k) / (dims - 1); the occupancy is their trilinear interpolation
+    (clamped to the box) against iso."""
+    values: np.ndarray          # (nz, ny, nx) float32
+    lo: tuple = (-1.0, -1.0, -1.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+    name: str = "voxels"
+
+    @property
+    def dims(self):
+        nz, ny, nx = self.values.shape
+        return (nx, ny, nz)
+
+
+def voxel_random(seed: int, dims=(17, 17, 17), lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0),
+                 shell_out: bool = True) -> VoxelSource:
+    """Independent U[0, 1) samples (a random-sign stress volume); with
+    ``shell_out`` the outer layer of samples is 0 so surfaces close inside."""
+    rng = np.random.default_rng(seed)
+    v = rng.random((dims[2], dims[1], dims[0])).astype(np.float32)
+    if shell_out:
+        v[0], v[-1], v[:, 0], v[:, -1], v[:, :, 0], v[:, :, -1] = 0, 0, 0, 0, 0, 0
+    return VoxelSource(values=v, lo=tuple(float(np.float32(x)) for x in lo),
+                       hi=tuple(float(np.float32(x)) for x in hi), name=f"voxel_random{seed}")
+
+
+def voxel_blobs(seed: int, dims=(65, 65, 65), n_blobs: int = 12) -> VoxelSource:
+    """Sum of Gaussian bumps sampled on the volume's vertices (a smooth
+    user-style volume); iso 0.5 cuts a few merged blobs."""
+    rng = np.random.default_rng(seed)
+    x = [np.linspace(-1.0, 1.0, d) for d in dims]
+    zz, yy, xx = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    v = np.zeros(zz.shape)
+    for _ in range(n_blobs):
+        c = rng.uniform(-0.55, 0.55, 3)
+        r = rng.uniform(0.15, 0.35)
+        v += np.exp(-((xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2) / (2 * r * r))
+    return VoxelSource(values=(0.8 * v / v.max()).astype(np.float32), name=f"voxel_blobs{seed}")
 
 
 def with_latent(src: MLPSource, seed: int) -> MLPSource:

@@ -374,3 +374,49 @@ def test_serving_trace_is_poisson_with_the_resolution_mix():
     for r, w in zip((64, 128, 256, 512), (0.4, 0.3, 0.2, 0.1)):
         assert abs(np.mean(res == r) - w) < 0.02
     assert I.serving_trace(0, 40.0, 300.0) == tr
+
+
+# ---- dense voxel-grid occupancy source ----------------------------------------
+
+def test_voxel_trilinear_reproduces_samples_and_multilinear_fields():
+    from oracle import occupancy as O
+    from paper_2409_13418_gb300 import inputs as I
+    dims = (7, 5, 9)
+    lo, hi = (-0.75, -1.0, -0.5), (0.75, 0.5, 1.0)
+    xs = [np.linspace(lo[a], hi[a], dims[a]) for a in range(3)]
+    zz, yy, xx = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    f = lambda x, y, z: 0.3 * x - 0.2 * y + 0.1 * z + 0.25 * x * y - 0.5 * x * y * z + 0.4   # multilinear
+    src = I.VoxelSource(values=f(xx, yy, zz).astype(np.float32), lo=lo, hi=hi)
+    vals = src.values.astype(np.float64)
+    # at the sample positions: the samples themselves
+    idx = np.array([[0, 0, 0], [6, 4, 8], [3, 2, 5], [1, 3, 7]])
+    pts = np.stack([xs[0][idx[:, 0]], xs[1][idx[:, 1]], xs[2][idx[:, 2]]], axis=1)
+    assert np.allclose(O.voxel_value(src, pts), vals[idx[:, 2], idx[:, 1], idx[:, 0]], rtol=0, atol=1e-6)
+    # inside every cell, trilinear interpolation reproduces a multilinear field
+    rng = np.random.default_rng(3)
+    p = np.stack([rng.uniform(lo[a], hi[a], 2000) for a in range(3)], axis=1).astype(np.float32).astype(np.float64)
+    ref = f(p[:, 0], p[:, 1], p[:, 2])
+    assert np.max(np.abs(O.voxel_value(src, p) - ref)) < 1e-6      # float32 samples
+    # outside the box the value of the nearest face point (clamped)
+    q = np.array([[5.0, 0.0, 0.0], [-5.0, -5.0, 5.0]])
+    qc = np.clip(q, lo, hi)
+    assert np.allclose(O.voxel_value(src, q), f(qc[:, 0], qc[:, 1], qc[:, 2]), atol=1e-6)
+
+
+def test_voxel_plane_gives_coplanar_points():
+    """A linear volume's iso-surface is a plane: every 1D point lies on it to
+    the bisection bound and every 3D point on it within the search error."""
+    from oracle import odc as oracle
+    from paper_2409_13418_gb300 import inputs as I
+    n = np.array([0.31, -0.62, 0.72])
+    n /= np.linalg.norm(n)
+    dims = (9, 9, 9)
+    xs = np.linspace(-1, 1, 9)
+    zz, yy, xx = np.meshgrid(xs, xs, xs, indexing="ij")
+    src = I.VoxelSource(values=(0.5 + 0.4 * (n[0] * xx + n[1] * yy + n[2] * zz - 0.05)).astype(np.float32))
+    k = 14
+    g = I.cube_grid(16)
+    r = oracle.extract(src, g, steps_1d=k)
+    h = 2.0 / 16
+    d = r.vertices @ n - 0.05
+    assert np.max(np.abs(d)) < 2e-3 * h
