@@ -69,7 +69,7 @@ typedef struct odc_ctx odc_ctx;
 
 /* Occupancy source kinds.  ODC_SRC_RESIDENT reuses the source last uploaded
  * to the context (by odc_source_upload or a previous odc_extract). */
-enum { ODC_SRC_CSG = 0, ODC_SRC_MLP = 1, ODC_SRC_RESIDENT = 2 };
+enum { ODC_SRC_CSG = 0, ODC_SRC_MLP = 1, ODC_SRC_RESIDENT = 2, ODC_SRC_VOXEL = 3 };
 
 /* CSG primitive types and operations (Sec. 3: any phi; CSG is a synthetic
  * stand-in for the paper's neural occupancies). */
@@ -139,11 +139,25 @@ typedef struct {
 
 enum { ODC_MLP_REUPLOAD = 1 };
 
+/* Dense voxel-grid occupancy: values[k][j][i] (host float32, i fastest) are
+ * samples at lo + (hi - lo) (i, j, k) / (dims - 1); phi(x) is their trilinear
+ * interpolation with x clamped to the box, inside iff phi > iso.  The
+ * decision is taken in float-float (~48 bits), so it equals the exact one
+ * except within ~1e-13 of iso.  dims in [2, 2048] per axis, at most 2^31
+ * samples, lo < hi. */
 typedef struct {
-    int32_t kind;                /* ODC_SRC_CSG or ODC_SRC_MLP */
+    int32_t dims[3];
+    float lo[3];
+    float hi[3];
+    const float* values;
+} odc_voxels;
+
+typedef struct {
+    int32_t kind;                /* ODC_SRC_CSG, ODC_SRC_MLP, ODC_SRC_VOXEL or ODC_SRC_RESIDENT */
     int32_t n_prims;
     const odc_csg_prim* prims;   /* host, n_prims records (CSG) */
     const odc_mlp* mlp;          /* host (MLP) */
+    const odc_voxels* voxels;    /* host (VOXEL) */
 } odc_source;
 
 typedef struct {

@@ -278,7 +278,7 @@ class Occupancy:
 
     def __init__(self, src, iso: float = 0.5):
         self.src = src
-        self.iso = iso
+        self.iso = float(np.float32(iso))   # iso is an FP32 parameter of the instance, like every other
         self.queries = 0
 
     def __call__(self, points: np.ndarray):

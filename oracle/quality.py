@@ -74,6 +74,14 @@ def occupancy_deviation(mlp, verts, tris, n: int, seed: int, iso: float = 0.5) -
     return float(d.mean()), float(d.max())
 
 
+def voxel_deviation(src, verts, tris, n: int, seed: int, iso: float = 0.5) -> tuple[float, float]:
+    """(mean, max) of |phi(p) - iso| for a voxel source (trilinear, FP64) at n
+    area-uniform mesh samples."""
+    p = surface_samples(verts, tris, n, seed)
+    d = np.abs(occupancy.voxel_value(src, p) - iso)
+    return float(d.mean()), float(d.max())
+
+
 def implicit_psi(src, points: np.ndarray) -> np.ndarray:
     """psi of a CSG source in FP64 (the min/max fold of the primitives' g) at
     FP32-rounded points."""

@@ -67,6 +67,7 @@ struct odc_ctx {
     int res_nprims = 0;
     PrimDev* res_prims = nullptr;
     float4* res_cull = nullptr;
+    VoxDev res_vox{};
     // last extract
     GridDev g{};
     int k = 0;
@@ -181,6 +182,18 @@ static odc_status check_source(const odc_source* src) {
         return ODC_OK;
     }
     if (src->kind == ODC_SRC_MLP) return mlp_check(src->mlp, &g_err);
+    if (src->kind == ODC_SRC_VOXEL) {
+        const odc_voxels* v = src->voxels;
+        if (!v || !v->values) return fail(ODC_ERR_INVALID_ARG, "voxel source without values");
+        double n = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            if (v->dims[a] < 2 || v->dims[a] > 2048) return fail(ODC_ERR_INVALID_ARG, "voxel dims out of [2, 2048]");
+            if (!(v->lo[a] < v->hi[a])) return fail(ODC_ERR_INVALID_ARG, "voxel box: lo must be < hi");
+            n *= v->dims[a];
+        }
+        if (n > 2147483648.0) return fail(ODC_ERR_INVALID_ARG, "voxel volume above 2^31 samples");
+        return ODC_OK;
+    }
     return fail(ODC_ERR_INVALID_ARG, "unknown source kind");
 }
 
@@ -227,10 +240,35 @@ static odc_status upload_csg(odc_ctx* c, const odc_source* src, cudaStream_t st,
     return ODC_OK;
 }
 
+// Upload a voxel volume (values into the source arena).
+static odc_status upload_voxels(odc_ctx* c, const odc_voxels* v, cudaStream_t st) {
+    const size_t n = (size_t)v->dims[0] * v->dims[1] * v->dims[2];
+    odc_status s = arena_ensure(c, c->S, al(n * 4), st);
+    if (s != ODC_OK) return s;
+    float* d = (float*)c->S.take(n * 4);
+    ODC_CK(cudaMemcpyAsync(d, v->values, n * 4, cudaMemcpyHostToDevice, st));
+    VoxDev& x = c->res_vox;
+    x.v = d;
+    for (int a = 0; a < 3; ++a) {
+        x.dims[a] = v->dims[a];
+        x.lo[a] = v->lo[a];
+        // hi - lo as float-float: the rounded difference and its exact remainder
+        const float hi = v->hi[a], lo = v->lo[a], r = hi - lo;
+        const float bb = r - hi;
+        x.rng_hi[a] = r;
+        x.rng_lo[a] = (hi - (r - bb)) + (-lo - bb);
+    }
+    x.iso = 0.5f;
+    return ODC_OK;
+}
+
 static odc_status upload_source(odc_ctx* c, const odc_source* src, cudaStream_t st) {
     odc_status s;
     c->res_kind = -1;
-    if (src->kind == ODC_SRC_CSG) {
+    if (src->kind == ODC_SRC_VOXEL) {
+        s = upload_voxels(c, src->voxels, st);
+        if (s != ODC_OK) return s;
+    } else if (src->kind == ODC_SRC_CSG) {
         s = upload_csg(c, src, st, &c->res_prims, &c->res_cull);
         if (s != ODC_OK) return s;
         c->res_nprims = src->n_prims;
@@ -331,8 +369,12 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     mlp_timing_begin(c->mlp, st);
     ODC_CK(cudaEventRecord(c->ev[0], st));
     // ---- a1: grid occupancy
+    VoxDev vox = c->res_vox;
+    vox.iso = prm->iso;
     if (kind == ODC_SRC_CSG) {
         launch_csg_grid(g, d_prims, d_cull, n_prims, bits, st);
+    } else if (kind == ODC_SRC_VOXEL) {
+        launch_vox_grid(g, vox, bits, st);
     } else {
         s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &g_err);
         if (s != ODC_OK) return s;
@@ -410,6 +452,9 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         if (linear_1d) launch_linear_1d(g, edges, E, prm->steps_1d, d_prims, n_prims, T, st);
         else launch_bisect_csg(g, bits, edges, E, prm->steps_1d, d_prims, d_cull, n_prims, T, st);
         nq += (int64_t)E * prm->steps_1d;
+    } else if (kind == ODC_SRC_VOXEL) {
+        launch_bisect_vox(g, bits, edges, E, prm->steps_1d, vox, T, st);
+        nq += (int64_t)E * prm->steps_1d;
     } else {
         s = mlp_bisect(c->mlp, g, bits, edges, E, prm->steps_1d, prm->iso, T, st, &nq, &g_err);
         if (s != ODC_OK) return s;
@@ -448,6 +493,8 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         } else if (kind == ODC_SRC_CSG) {
             launch_face_csg(g, bits, flips, wi, ebase, T, faces, slots, F, sp, d_prims, d_cull, n_prims, pf, fflags,
                             dec, st);
+        } else if (kind == ODC_SRC_VOXEL) {
+            launch_face_vox(g, bits, flips, wi, ebase, T, faces, slots, F, sp, vox, pf, fflags, dec, st);
         } else {
             s = mlp_faces(c->mlp, g, bits, flips, wi, ebase, T, faces, slots, F, sp, prm->iso, pf, fflags, dec, st, &nq,
                           &g_err);
@@ -601,7 +648,8 @@ odc_status odc_mesh_quality(odc_ctx* c, const odc_mesh* m, float iso, int64_t n_
     std::memset(out, 0, sizeof(*out));
     MlpState* mlp = c->res_kind == ODC_SRC_MLP ? c->mlp : nullptr;
     const PrimDev* prims = c->res_kind == ODC_SRC_CSG ? c->res_prims : nullptr;
-    odc_status s = mesh_quality(mlp, prims, c->res_nprims, (const float3*)m->d_verts, m->n_verts,
+    const VoxDev* vox = c->res_kind == ODC_SRC_VOXEL ? &c->res_vox : nullptr;
+    odc_status s = mesh_quality(mlp, prims, c->res_nprims, vox, (const float3*)m->d_verts, m->n_verts,
                                 (const int3*)m->d_tris, m->n_tris, iso, n_samples, seed, what, c->own, out, &g_err);
     return s == ODC_OK ? s : fail(s, g_err);
 }
@@ -632,6 +680,10 @@ odc_status odc_eval_points(odc_ctx* c, const odc_source* src, const float* point
     ODC_CK(cudaMemcpyAsync(dp, points, n * 12, cudaMemcpyHostToDevice, st));
     if (c->res_kind == ODC_SRC_CSG) {
         launch_csg_points(d_prims, d_cull, c->res_nprims, dp, n, dl, st);
+    } else if (c->res_kind == ODC_SRC_VOXEL) {
+        VoxDev vox = c->res_vox;
+        vox.iso = iso;
+        launch_vox_points(vox, dp, n, dl, st);
     } else {
         s = mlp_points(c->mlp, dp, n, iso, precision, dl, dz, st, &g_err);
         if (s != ODC_OK) return s;

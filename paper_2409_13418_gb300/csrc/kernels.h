@@ -40,6 +40,16 @@ void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* fli
 void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, const float3* pts, int64_t n,
                        uint8_t* labels, cudaStream_t st);
 
+// search_csg.cu, voxel volumes
+void launch_vox_grid(const GridDev& g, const VoxDev& vox, uint32_t* bits, cudaStream_t st);
+void launch_vox_points(const VoxDev& vox, const float3* pts, int64_t n, uint8_t* labels, cudaStream_t st);
+void launch_bisect_vox(const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
+                       const VoxDev& vox, uint32_t* T, cudaStream_t st);
+void launch_face_vox(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
+                     const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
+                     uint32_t nf, const SearchParams& sp, const VoxDev& vox, float4* pf, uint8_t* flags,
+                     FaceDecisions* dec, cudaStream_t st);
+
 // qef.cu (gnorm: per crossing edge, grad psi at its 1D point replacing the
 // 2D-point normals; null for ODC)
 void launch_qef(const GridDev& g, const uint32_t* flips, const WordInfo* wi, const uint32_t* ebase,
@@ -70,7 +80,8 @@ void launch_quad_emit(const GridDev& g, const uint32_t* edges, const uint32_t* T
 
 // quality.cu (Sec. 6.1 metrics; mlp may be null for a CSG source)
 struct MlpState;
-odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const float3* v, int64_t nv, const int3* t,
+odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const VoxDev* vox, const float3* v,
+                        int64_t nv, const int3* t,
                         int64_t nt, float iso, int64_t n_samples, uint64_t seed, int what, cudaStream_t s,
                         odc_quality* out, std::string* err);
 

@@ -45,6 +45,15 @@ struct PrimDev {
 };
 static_assert(sizeof(PrimDev) == 80, "PrimDev must match odc_csg_prim");
 
+// Dense voxel volume on the device (trilinear occupancy against iso).
+struct VoxDev {
+    const float* v;       // values [nz][ny][nx]
+    int dims[3];
+    float lo[3];
+    float rng_hi[3], rng_lo[3];   // hi - lo per axis as float-float (exact)
+    float iso;
+};
+
 // Search parameters (device copy of odc_params).
 // Kernel launches issued by the library (all streams, all contexts).
 void note_launch();

@@ -130,6 +130,33 @@ __global__ void k_deviation(const float* __restrict__ z, int64_t n, double iso, 
     block_sum_max(d, acc);
 }
 
+// |phi - iso| of a voxel volume: trilinear interpolation in FP64 (clamped).
+__global__ void k_vox_deviation(const float3* __restrict__ pts, int64_t n, VoxDev d, double iso,
+                                double* __restrict__ acc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dev = 0.0;
+    if (i < n) {
+        const float3 p = pts[i];
+        const double pc[3] = {(double)p.x, (double)p.y, (double)p.z};
+        int c[3];
+        double f[3];
+        for (int a = 0; a < 3; ++a) {
+            const double lo = (double)d.lo[a], rng = (double)d.rng_hi[a] + (double)d.rng_lo[a];
+            double u = (pc[a] - lo) / rng * (double)(d.dims[a] - 1);
+            u = fmin(fmax(u, 0.0), (double)(d.dims[a] - 1));
+            c[a] = min((int)floor(u), d.dims[a] - 2);
+            f[a] = u - (double)c[a];
+        }
+        const size_t sy = (size_t)d.dims[0], sz = (size_t)d.dims[0] * d.dims[1];
+        const float* b = d.v + (size_t)c[2] * sz + (size_t)c[1] * sy + (size_t)c[0];
+        auto L = [](double x, double y, double t) { return x + (y - x) * t; };
+        const double c00 = L(b[0], b[1], f[0]), c10 = L(b[sy], b[sy + 1], f[0]);
+        const double c01 = L(b[sz], b[sz + 1], f[0]), c11 = L(b[sz + sy], b[sz + sy + 1], f[0]);
+        dev = fabs(L(L(c00, c10, f[1]), L(c01, c11, f[1]), f[2]) - iso);
+    }
+    block_sum_max(dev, acc);
+}
+
 // First-order distance |psi| / |grad psi| of the CSG surface (FP64).
 __global__ void k_csg_distance(const float3* __restrict__ pts, int64_t n, const PrimDev* __restrict__ prims,
                                int n_prims, double* __restrict__ acc) {
@@ -446,7 +473,8 @@ __global__ void k_count_flags(const uint8_t* __restrict__ flag, int64_t n, unsig
 
 static inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const float3* v, int64_t nv, const int3* t,
+odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const VoxDev* vox, const float3* v,
+                        int64_t nv, const int3* t,
                         int64_t nt, float iso, int64_t n_samples, uint64_t seed, int what, cudaStream_t s,
                         odc_quality* out, std::string* err) {
     out->n_tris = nt;
@@ -479,7 +507,7 @@ odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const 
     }
     do {
         // ---- occupancy deviation on area-uniform samples
-        if ((what & ODC_Q_OCC) && (mlp || prims) && nt > 0 && n_samples > 0) {
+        if ((what & ODC_Q_OCC) && (mlp || prims || vox) && nt > 0 && n_samples > 0) {
             double *area, *excl, *acc;
             float3* pts;
             float* z;
@@ -498,6 +526,8 @@ odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const 
             if (mlp) {
                 if ((r = mlp_eval_list(mlp, pts, n_samples, z, ODC_PREC_FP32, s, err)) != ODC_OK) break;
                 k_deviation<<<nb(n_samples), 256, 0, s>>>(z, n_samples, (double)iso, acc); note_launch();
+            } else if (vox) {
+                k_vox_deviation<<<nb(n_samples), 256, 0, s>>>(pts, n_samples, *vox, (double)iso, acc); note_launch();
             } else {
                 k_csg_distance<<<nb(n_samples), 256, 0, s>>>(pts, n_samples, prims, n_prims, acc); note_launch();
             }
@@ -505,8 +535,8 @@ odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const 
             Q_CK(cudaMemcpyAsync(h, acc, 16, cudaMemcpyDeviceToHost, s));
             Q_CK(cudaStreamSynchronize(s));
             out->n_samples = n_samples;
-            (mlp ? out->occ_dev_mean : out->dist_mean) = h[0] / (double)n_samples;
-            (mlp ? out->occ_dev_max : out->dist_max) = h[1];
+            (prims ? out->dist_mean : out->occ_dev_mean) = h[0] / (double)n_samples;
+            (prims ? out->dist_max : out->occ_dev_max) = h[1];
         }
         // ---- manifoldness and Euler characteristic
         if (what & ODC_Q_MANIFOLD) {

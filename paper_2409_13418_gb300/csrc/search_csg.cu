@@ -1,6 +1,7 @@
-// search_csg.cu -- 1D and 2D point searches against a CSG occupancy, one
-// thread per crossing edge / face segment running its whole search in
-// registers (CSG queries cost tens of FMAs, so no batching is needed).
+// search_csg.cu -- grid labels and 1D and 2D point searches against the
+// directly evaluated occupancies (CSG trees and voxel volumes), one thread per
+// crossing edge / face segment running its whole search in registers (these
+// queries cost tens to hundreds of flops, so no batching is needed).
 //
 // 1D (Sec. 5.1): k bisections of the edge keeping ends of opposite labels;
 // the result is the midpoint of the final interval, stored as the odd integer
@@ -11,6 +12,7 @@
 // (p_e1, q1) and (p_e2, q2).
 #include "kernels.h"
 #include "search.cuh"
+#include "voxel.cuh"
 
 namespace odc {
 
@@ -21,8 +23,9 @@ struct CsgOcc {
     __device__ __forceinline__ uint32_t operator()(float3 p) const { return csg_label(prims, cull, n, p.x, p.y, p.z); }
 };
 
-__global__ void k_bisect_csg(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ edges,
-                             uint32_t ne, int k, CsgOcc occ, uint32_t* __restrict__ T) {
+template <class Occ>
+__global__ void k_bisect(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ edges,
+                         uint32_t ne, int k, Occ occ, uint32_t* __restrict__ T) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     uint32_t e = edges[i];
@@ -66,11 +69,12 @@ __device__ __forceinline__ uint32_t lbs(const GridDev& g, const FaceSeg& F, cons
     return Ja;
 }
 
-__global__ void k_face_csg(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ flips,
-                           const WordInfo* __restrict__ wi, const uint32_t* __restrict__ ebase,
-                           const uint32_t* __restrict__ T, const uint32_t* __restrict__ faces,
-                           const uint8_t* __restrict__ slots, uint32_t nf, SearchParams sp, CsgOcc occ,
-                           float4* __restrict__ pf, uint8_t* __restrict__ flags, FaceDecisions* __restrict__ dec) {
+template <class Occ>
+__global__ void k_face(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ flips,
+                       const WordInfo* __restrict__ wi, const uint32_t* __restrict__ ebase,
+                       const uint32_t* __restrict__ T, const uint32_t* __restrict__ faces,
+                       const uint8_t* __restrict__ slots, uint32_t nf, SearchParams sp, Occ occ,
+                       float4* __restrict__ pf, uint8_t* __restrict__ flags, FaceDecisions* __restrict__ dec) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     FaceSeg F;
@@ -106,24 +110,39 @@ __global__ void k_face_csg(GridDev g, const uint32_t* __restrict__ bits, const u
     dec[i] = D;
 }
 
-__global__ void k_csg_points(CsgOcc occ, const float3* __restrict__ pts, int64_t n, uint8_t* __restrict__ labels) {
+template <class Occ>
+__global__ void k_points(Occ occ, const float3* __restrict__ pts, int64_t n, uint8_t* __restrict__ labels) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     labels[i] = (uint8_t)occ(pts[i]);
+}
+
+// Grid labels of a voxel volume: one warp per label word (ballot).
+__global__ void k_vox_grid(GridDev g, VoxOcc occ, uint32_t* __restrict__ bits) {
+    size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int l = threadIdx.x & 31;
+    size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
+    if (w >= nw) return;
+    int x = (int)(w % g.W) * 32 + l;
+    size_t row = w / g.W;
+    int y = (int)(row % g.nv[1]), z = (int)(row / g.nv[1]);
+    bool in = x < g.nv[0] && occ(make_float3(g.X[0][x], g.X[1][y], g.X[2][z]));
+    uint32_t word = __ballot_sync(0xffffffffu, in);
+    if (l == 0) bits[w] = word;
 }
 
 void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, const float3* pts, int64_t n,
                        uint8_t* labels, cudaStream_t st) {
     if (n <= 0) return;
     CsgOcc occ{prims, cull, n_prims};
-    k_csg_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(occ, pts, n, labels); note_launch();
+    k_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(occ, pts, n, labels); note_launch();
 }
 
 void launch_bisect_csg(const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
                        const PrimDev* prims, const float4* cull, int n_prims, uint32_t* T, cudaStream_t st) {
     if (!ne) return;
     CsgOcc occ{prims, cull, n_prims};
-    k_bisect_csg<<<(ne + 127) / 128, 128, 0, st>>>(g, bits, edges, ne, k, occ, T); note_launch();
+    k_bisect<<<(ne + 127) / 128, 128, 0, st>>>(g, bits, edges, ne, k, occ, T); note_launch();
 }
 
 void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
@@ -132,8 +151,33 @@ void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* fli
                      float4* pf, uint8_t* flags, FaceDecisions* dec, cudaStream_t st) {
     if (!nf) return;
     CsgOcc occ{prims, cull, n_prims};
-    k_face_csg<<<(nf + 127) / 128, 128, 0, st>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp, occ, pf,
-                                                  flags, dec); note_launch();
+    k_face<<<(nf + 127) / 128, 128, 0, st>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp, occ, pf,
+                                              flags, dec); note_launch();
+}
+
+void launch_vox_grid(const GridDev& g, const VoxDev& vox, uint32_t* bits, cudaStream_t st) {
+    size_t threads = (size_t)g.W * g.nv[1] * g.nv[2] * 32;
+    k_vox_grid<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, VoxOcc{vox}, bits); note_launch();
+}
+
+void launch_vox_points(const VoxDev& vox, const float3* pts, int64_t n, uint8_t* labels, cudaStream_t st) {
+    if (n <= 0) return;
+    k_points<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(VoxOcc{vox}, pts, n, labels); note_launch();
+}
+
+void launch_bisect_vox(const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
+                       const VoxDev& vox, uint32_t* T, cudaStream_t st) {
+    if (!ne) return;
+    k_bisect<<<(ne + 127) / 128, 128, 0, st>>>(g, bits, edges, ne, k, VoxOcc{vox}, T); note_launch();
+}
+
+void launch_face_vox(const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
+                     const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
+                     uint32_t nf, const SearchParams& sp, const VoxDev& vox, float4* pf, uint8_t* flags,
+                     FaceDecisions* dec, cudaStream_t st) {
+    if (!nf) return;
+    k_face<<<(nf + 127) / 128, 128, 0, st>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp, VoxOcc{vox}, pf,
+                                              flags, dec); note_launch();
 }
 
 }  // namespace odc

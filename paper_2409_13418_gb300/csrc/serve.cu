@@ -37,6 +37,8 @@ struct Request {
     uint64_t id = 0;
     odc_source src{};
     std::vector<odc_csg_prim> prims;
+    odc_voxels vox{};
+    std::vector<float> vox_values;
     odc_mlp mlp{};
     std::vector<float> B, latent, W[8], b[8];
     odc_grid grid{};
@@ -62,13 +64,15 @@ struct Request {
 // lists: 17 B per vertex), and the crossing-sized buffers (about 8 N^2
 // crossing edges for a closed surface spanning the grid; ~700 B per edge
 // over the lists, search states and mesh), plus 64 MiB of weights and fixed
-// buffers.
+// buffers (plus the samples of a voxel source).
 uint64_t estimate_bytes(const odc_source& src, const odc_grid& g) {
     const uint64_t nv0 = (uint64_t)g.res[0] + 1, nv1 = (uint64_t)g.res[1] + 1, nv2 = (uint64_t)g.res[2] + 1;
     const uint64_t W = (nv0 + 31) / 32, nw = W * nv1 * nv2, V = nw * 32;
     const uint64_t r = (uint64_t)std::max(g.res[0], std::max(g.res[1], g.res[2]));
     uint64_t b = nw * 90 + 8 * r * r * 700 + (64ull << 20);
     if (src.kind == ODC_SRC_MLP) b += V * 17;
+    if (src.kind == ODC_SRC_VOXEL && src.voxels)
+        b += 4ull * (uint64_t)src.voxels->dims[0] * src.voxels->dims[1] * src.voxels->dims[2];
     return b;
 }
 
@@ -81,7 +85,21 @@ odc_status copy_source(const odc_source* s, Request& q, std::string* err) {
         q.src.mlp = nullptr;
         return ODC_OK;
     }
-    if (s->kind != ODC_SRC_MLP) { *err = "odc_submit takes CSG or MLP sources (not resident ones)"; return ODC_ERR_INVALID_ARG; }
+    if (s->kind == ODC_SRC_VOXEL) {
+        const odc_voxels* v = s->voxels;
+        if (!v || !v->values) { *err = "voxel source without values"; return ODC_ERR_INVALID_ARG; }
+        double n = 1.0;
+        for (int a = 0; a < 3; ++a) n *= v->dims[a] >= 2 ? v->dims[a] : 0;
+        if (n <= 0 || n > 2147483648.0) { *err = "voxel dims out of range"; return ODC_ERR_INVALID_ARG; }
+        q.vox = *v;
+        q.vox_values.assign(v->values, v->values + (size_t)n);
+        q.vox.values = q.vox_values.data();
+        q.src.voxels = &q.vox;
+        q.src.prims = nullptr;
+        q.src.mlp = nullptr;
+        return ODC_OK;
+    }
+    if (s->kind != ODC_SRC_MLP) { *err = "odc_submit takes CSG, MLP or voxel sources (not resident ones)"; return ODC_ERR_INVALID_ARG; }
     const odc_mlp* m = s->mlp;
     if (!m || !m->B) { *err = "MLP source without descriptor or Fourier matrix"; return ODC_ERR_INVALID_ARG; }
     if (m->n_hidden < 1 || m->n_hidden > 7 || m->hidden < 1 || m->n_freq < 1 || m->latent_dim < 0)

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libodc.so")
 ODC_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
           5: "unsupported", 6: "internal error"}
-SRC_CSG, SRC_MLP, SRC_RESIDENT = 0, 1, 2
+SRC_CSG, SRC_MLP, SRC_RESIDENT, SRC_VOXEL = 0, 1, 2, 3
 PREC_FP32, PREC_BF16, PREC_SPLIT = 0, 1, 2
 MLP_REUPLOAD = 1
 DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
@@ -43,8 +43,13 @@ class Mlp(C.Structure):
                 ("split_zmargin", C.c_float), ("flags", C.c_int32)]
 
 
+class Voxels(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("lo", C.c_float * 3), ("hi", C.c_float * 3), ("values", C.c_void_p)]
+
+
 class Source(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("n_prims", C.c_int32), ("prims", C.c_void_p), ("mlp", C.c_void_p)]
+    _fields_ = [("kind", C.c_int32), ("n_prims", C.c_int32), ("prims", C.c_void_p), ("mlp", C.c_void_p),
+                ("voxels", C.c_void_p)]
 
 
 class Grid(C.Structure):
@@ -216,6 +221,16 @@ class _SourceHolder:
             self.keep.append(m)
             self.src.kind = SRC_MLP
             self.src.mlp = C.addressof(m)
+        elif isinstance(src, I.VoxelSource):
+            vals = np.ascontiguousarray(src.values, np.float32)
+            vx = Voxels()
+            for a in range(3):
+                vx.dims[a] = int(src.dims[a])
+                vx.lo[a], vx.hi[a] = float(src.lo[a]), float(src.hi[a])
+            vx.values = _ptr(vals)
+            self.keep += [vals, vx]
+            self.src.kind = SRC_VOXEL
+            self.src.voxels = C.addressof(vx)
         else:
             raise TypeError(type(src))
 
