@@ -10,7 +10,8 @@
 // round to BF16 and write the next layer's A operand (K-major, SWIZZLE_128B)
 // into shared memory in place; after the last hidden layer they fold the
 // 256 -> 1 output layer and the envelope into the logit z.  The Fourier
-// features (float-float phase, sincospi) are computed by the same warps.
+// features are computed by the same warps (FP32 phase and SFU sin/cos for the
+// BF16 pass; float-float phase and sincospi for the split-FP16 tier).
 //
 // Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
 // CTA raises an error flag, stops issuing work, waits (bounded) for its TMA
@@ -129,19 +130,37 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
+// Split TMEM read: the load is issued now, its registers are valid after
+// tmem_wait (whose "+r" operands keep every use of them behind the wait).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) :: "memory");
+}
+
+// Visit the 256 accumulator columns of a TMEM row in 32-column chunks,
+// fn(chunk, values), loading chunk c + 1 while chunk c is processed (two
+// register buffers; the loop over chunk pairs is not unrolled, to keep the
+// register count where nothing spills: a spill of a buffer between its load
+// and its wait would read the registers before the load lands).
+template <class Fn>
+__device__ __forceinline__ void tmem_row_chunks(uint32_t trow, Fn&& fn) {
+    uint32_t ra[32], rb[32];
+    tmem_ld32_async(trow, ra);
+    tmem_wait(ra);
+#pragma unroll 1
+    for (int cb = 0; cb < kH / 32; cb += 2) {
+        tmem_ld32_async(trow + (cb + 1) * 32, rb);
+        fn(cb, ra);
+        tmem_wait(rb);
+        if (cb + 2 < kH / 32) tmem_ld32_async(trow + (cb + 2) * 32, ra);
+        fn(cb + 1, rb);
+        if (cb + 2 < kH / 32) tmem_wait(ra);
+    }
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -300,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float s[8], cs[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    float2 v = fourier_sincos(Bf[3 * (j + i)], Bf[3 * (j + i) + 1], Bf[3 * (j + i) + 2], x);
+                    float2 v = fourier_sincos_fast(Bf[3 * (j + i)], Bf[3 * (j + i) + 1], Bf[3 * (j + i) + 2], x);
                     s[i] = v.x;
                     cs[i] = v.y;
                 }
@@ -322,9 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const float* bias = sp + l * kH;
                 if (l < kNL - 1) {
-                    for (int cb = 0; cb < kH / 32; ++cb) {
-                        float v[32];
-                        tmem_ld32(trow + cb * 32, v);
+                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             float h[8];
@@ -332,12 +349,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float4 b1 = *reinterpret_cast<const float4*>(bias + cb * 32 + u * 8 + 4);
                             const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) h[i] = fmaxf(v[u * 8 + i] + bb[i], 0.f);
+                            for (int i = 0; i < 8; ++i) h[i] = fmaxf(__uint_as_float(v[u * 8 + i]) + bb[i], 0.f);
                             uint4 p = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
                                                  pack_bf16(h[6], h[7]));
                             *reinterpret_cast<uint4*>(As + a_offset(r, cb * 32 + u * 8)) = p;
                         }
-                    }
+                    });
                     fence_async_smem();
                     tc_fence_before();
                     __syncwarp();
@@ -345,19 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
                     const float* w4 = sp + 4 * kH;
                     float f = 0.0f;
-                    for (int cb = 0; cb < kH / 32; ++cb) {
-                        float v[32];
-                        tmem_ld32(trow + cb * 32, v);
+                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int i = 0; i < 32; i += 4) {
                             const float4 b = *reinterpret_cast<const float4*>(bias + cb * 32 + i);
                             const float4 w = *reinterpret_cast<const float4*>(w4 + cb * 32 + i);
-                            f = fmaf(fmaxf(v[i] + b.x, 0.f), w.x, f);
-                            f = fmaf(fmaxf(v[i + 1] + b.y, 0.f), w.y, f);
-                            f = fmaf(fmaxf(v[i + 2] + b.z, 0.f), w.z, f);
-                            f = fmaf(fmaxf(v[i + 3] + b.w, 0.f), w.w, f);
+                            f = fmaf(fmaxf(__uint_as_float(v[i]) + b.x, 0.f), w.x, f);
+                            f = fmaf(fmaxf(__uint_as_float(v[i + 1]) + b.y, 0.f), w.y, f);
+                            f = fmaf(fmaxf(__uint_as_float(v[i + 2]) + b.z, 0.f), w.z, f);
+                            f = fmaf(fmaxf(__uint_as_float(v[i + 3]) + b.w, 0.f), w.w, f);
                         }
-                    }
+                    });
                     tc_fence_before();
                     f += sp[5 * kH];
                     if (valid) P.z[query_index(P.Q, q)] = envelope_logit(x, f, P.scale, P.radius, P.amp);
@@ -553,21 +568,20 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 const float* bias = P.wblob + kOffb_(l);
                 const float unscale = P.wscale_inv[l];
                 if (l < kNL - 1) {
-                    for (int cb = 0; cb < kH / 32; ++cb) {
-                        float v[32];
-                        tmem_ld32(trow + cb * 32, v);
+                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             float h[8];
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
-                                h[i] = fmaxf(fmaf(v[u * 8 + i], unscale, __ldg(bias + cb * 32 + u * 8 + i)), 0.f);
+                                h[i] = fmaxf(fmaf(__uint_as_float(v[u * 8 + i]), unscale,
+                                                  __ldg(bias + cb * 32 + u * 8 + i)), 0.f);
                                 range_ok &= h[i] < kF16Safe;
                                 h[i] = fminf(h[i], kF16Safe);
                             }
                             store_split8(Ahi, Alo, a_offset(r, cb * 32 + u * 8), h);
                         }
-                    }
+                    });
                     fence_async_smem();
                     tc_fence_before();
                     __syncwarp();
@@ -575,14 +589,12 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 } else {
                     const float* w4 = P.wblob + kOffW_(kNL);
                     float f = 0.0f;
-                    for (int cb = 0; cb < kH / 32; ++cb) {
-                        float v[32];
-                        tmem_ld32(trow + cb * 32, v);
+                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i)
-                            f = fmaf(fmaxf(fmaf(v[i], unscale, __ldg(bias + cb * 32 + i)), 0.f), __ldg(w4 + cb * 32 + i),
-                                     f);
-                    }
+                            f = fmaf(fmaxf(fmaf(__uint_as_float(v[i]), unscale, __ldg(bias + cb * 32 + i)), 0.f),
+                                     __ldg(w4 + cb * 32 + i), f);
+                    });
                     tc_fence_before();
                     f += __ldg(P.wblob + kOffb_(kNL));
                     // an activation out of FP16 range sends the query to the FP32 tier (|z| = 0)
