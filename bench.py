@@ -159,6 +159,62 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def voxel_bench(odc, I, res: int = 512, vox: int = 513):
+    """Dense voxel-grid source: a smooth blob volume of vox^3 float32 samples
+    (larger than L2) meshed on a res^3 grid (k = 15).  Reports the extraction
+    rate and the grid-label kernel's volume bytes per second (every sample is
+    read at least once when the grid is as fine as the volume)."""
+    src = I.voxel_blobs(7, dims=(vox, vox, vox))
+    g = I.cube_grid(res)
+    with odc.Context(0) as ctx:
+        ctx.upload(src)
+        ms, grid_ms = [], []
+        for _ in range(4):
+            m = ctx.extract(None, g, steps_1d=15)
+            ms.append(m.stats["stage_ms"][7])
+            grid_ms.append(m.stats["stage_ms"][0])
+        st = m.stats
+    t, tg = min(ms[1:]), min(grid_ms[1:])
+    vbytes = 4.0 * vox ** 3
+    return {"workload": f"smooth blob volume {vox}^3 float32 ({vbytes / 1e6:.0f} MB), {res}^3 cells, k=15",
+            "mcells_per_s": res ** 3 / (t * 1e-3) / 1e6, "device_ms": round(t, 3),
+            "grid_label_ms": round(tg, 3), "grid_label_volume_gbs": vbytes / (tg * 1e-3) / 1e9,
+            "edges": st["n_edges"], "face_segs": st["n_face_segs"], "tris": m.n_tris}
+
+
+def batch_bench(odc, I, n_shapes: int = 64, slots: int = 8, seed: int = 9):
+    """The batched workload: n_shapes shapes with resolutions log-uniform in
+    64^3..256^3, even ones seeded 64-primitive CSG trees (k = 12), odd ones
+    latent-conditioned envelope MLPs (128-d latent, BF16, k = 15), all
+    submitted at once to the request loop with ``slots`` slots; the rate is
+    the total cells over the wall time from the first submission to the last
+    completion (after one warm-up round of the same shapes)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    res = np.round(np.exp(rng.uniform(np.log(64), np.log(256), n_shapes))).astype(int)
+    net = I.envelope_mlp(12, latent_dim=128)
+    jobs = []
+    for i, r in enumerate(res):
+        if i % 2 == 0:
+            jobs.append((I.random_csg(1000 + i, n_prims=64), I.cube_grid(int(r)), dict(steps_1d=12)))
+        else:
+            jobs.append((I.with_latent(net, 2000 + i), I.cube_grid(int(r)), dict(steps_1d=15, precision=odc.PREC_BF16)))
+    cells = float(np.sum(res.astype(np.float64) ** 3))
+    with odc.Server(0, slots=slots, host_copy=False) as srv:
+        for _ in range(2):
+            t0 = srv.clock()
+            ids = [srv.submit(src, g, **kw) for src, g, kw in jobs]
+            out = [srv.poll(i) for i in ids]
+            for i in ids:
+                srv.release(i)
+            span = max(o["t_end"] for o in out) - t0
+    assert all(o["status"] == 0 for o in out)
+    return {"workload": f"{n_shapes} shapes, res log-uniform 64^3..256^3 (total {cells / 1e6:.0f} M cells), half "
+                        "64-primitive CSG trees (k=12), half latent-conditioned envelope MLPs (BF16, k=15)",
+            "slots": slots, "seconds": round(span, 3), "mcells_per_s": cells / span / 1e6,
+            "shapes_per_s": n_shapes / span}
+
+
 def ablation_table(odc, I, res: int = 128, seed: int = 1):
     """The shape of the paper's ablations (Sec. 6.3, Tab. 3; Tab. A8) on a
     seeded 64-primitive CSG tree at res^3 (k = 12): marching cubes through
@@ -426,6 +482,8 @@ def main():
         if world == 1 and not args.no_ablation:
             from paper_2409_13418_gb300 import inputs as I
             line["ablation"] = ablation_table(odc, I)
+            line["voxel"] = voxel_bench(odc, I)
+            line["batched"] = batch_bench(odc, I)
         if world == 1 and args.serve_seconds > 0:
             ctx.close()
             from paper_2409_13418_gb300 import inputs as I

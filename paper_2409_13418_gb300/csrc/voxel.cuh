@@ -1,11 +1,15 @@
 // voxel.cuh -- dense voxel-grid occupancy: trilinear interpolation of a
-// sample volume against iso, decided in float-float.
+// sample volume against iso.
 //
-// Per axis u = (x - lo) / (hi - lo) * (dims - 1) (x - lo and hi - lo exact in
-// float-float, the quotient to ~48 bits), clamped to [0, dims - 1]; cell
-// i = min(floor(u), dims - 2), fraction u - i; lerps a + (b - a) f along x,
-// then y, then z.  The decision phi > iso then equals the exact one except
-// within ~1e-13 of iso.
+// Per axis u = (x - lo) / (hi - lo) * (dims - 1), clamped to [0, dims - 1];
+// cell i = min(floor(u), dims - 2), fraction u - i; lerps a + (b - a) f along
+// x, then y, then z.  A float32 evaluation decides first: its error is at
+// most the fraction error (|du| <= 4 2^-24 (dims - 1), times the Lipschitz
+// constant 2 vmax of each axis, vmax the largest corner magnitude) plus the
+// rounding of seven lerps (< 30 2^-24 vmax); twice that bound, vmax (3e-6
+// (dims - 1) + 4e-6), separates a sure decision from a near one.  Near ones
+// are re-decided in float-float (x - lo and hi - lo exact, the quotient to
+// ~48 bits), which equals the exact decision except within ~1e-13 of iso.
 #pragma once
 #include "odc_device.cuh"
 
@@ -17,6 +21,33 @@ struct VoxOcc {
     VoxDev d;
     __device__ __forceinline__ uint32_t operator()(float3 p) const {
         const float pc[3] = {p.x, p.y, p.z};
+        {   // float32 fast path
+            int i[3];
+            float f[3];
+            int dmax = 2;
+            for (int a = 0; a < 3; ++a) {
+                const float top = (float)(d.dims[a] - 1);
+                float u = (pc[a] - d.lo[a]) / d.rng_hi[a] * top;
+                u = fminf(fmaxf(u, 0.0f), top);
+                const int c = min((int)u, d.dims[a] - 2);
+                i[a] = c;
+                f[a] = u - (float)c;
+                dmax = max(dmax, d.dims[a]);
+            }
+            const size_t sy = (size_t)d.dims[0], sz = (size_t)d.dims[0] * d.dims[1];
+            const float* b = d.v + (size_t)i[2] * sz + (size_t)i[1] * sy + (size_t)i[0];
+            const float v0 = __ldg(b), v1 = __ldg(b + 1), v2 = __ldg(b + sy), v3 = __ldg(b + sy + 1);
+            const float v4 = __ldg(b + sz), v5 = __ldg(b + sz + 1), v6 = __ldg(b + sz + sy), v7 = __ldg(b + sz + sy + 1);
+            const float c00 = fmaf(v1 - v0, f[0], v0), c10 = fmaf(v3 - v2, f[0], v2);
+            const float c01 = fmaf(v5 - v4, f[0], v4), c11 = fmaf(v7 - v6, f[0], v6);
+            const float c0 = fmaf(c10 - c00, f[1], c00), c1 = fmaf(c11 - c01, f[1], c01);
+            const float phi = fmaf(c1 - c0, f[2], c0);
+            const float vmax = fmaxf(fmaxf(fmaxf(fabsf(v0), fabsf(v1)), fmaxf(fabsf(v2), fabsf(v3))),
+                                     fmaxf(fmaxf(fabsf(v4), fabsf(v5)), fmaxf(fabsf(v6), fabsf(v7))));
+            const float bound = vmax * (3e-6f * (float)(dmax - 1) + 4e-6f);
+            if (phi - d.iso > bound) return 1u;
+            if (d.iso - phi > bound) return 0u;
+        }
         int i[3];
         ff f[3];
         for (int a = 0; a < 3; ++a) {
