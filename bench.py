@@ -182,6 +182,24 @@ def voxel_bench(odc, I, res: int = 512, vox: int = 513):
             "edges": st["n_edges"], "face_segs": st["n_face_segs"], "tris": m.n_tris}
 
 
+def resolution_scaling(odc, I, resolutions=(128, 256, 512, 1024)):
+    """Extraction rate of the envelope MLP (BF16 tiered, k = 15) against grid
+    resolution, one GPU, whole grid in one piece (the shape of Tab. A3's
+    128/256/512^3 rows; 1024^3 holds ~31 GB of device memory)."""
+    mlp = I.envelope_mlp(0)
+    rows = {}
+    with odc.Context(0) as ctx:
+        ctx.upload(mlp, precision=odc.PREC_BF16)
+        for r in resolutions:
+            g = I.cube_grid(r)
+            ctx.extract(None, g, steps_1d=15)          # arenas sized for r
+            m = ctx.extract(None, g, steps_1d=15)
+            t = m.stats["stage_ms"][7]
+            rows[f"{r}^3"] = {"device_ms": round(t, 1), "mcells_per_s": r ** 3 / (t * 1e-3) / 1e6,
+                              "edges": m.stats["n_edges"], "tris": m.n_tris}
+    return rows
+
+
 def batch_bench(odc, I, n_shapes: int = 64, slots: int = 8, seed: int = 9):
     """The batched workload: n_shapes shapes with resolutions log-uniform in
     64^3..256^3, even ones seeded 64-primitive CSG trees (k = 12), odd ones
@@ -484,6 +502,7 @@ def main():
             line["ablation"] = ablation_table(odc, I)
             line["voxel"] = voxel_bench(odc, I)
             line["batched"] = batch_bench(odc, I)
+            line["resolution_scaling"] = resolution_scaling(odc, I)
         if world == 1 and args.serve_seconds > 0:
             ctx.close()
             from paper_2409_13418_gb300 import inputs as I
