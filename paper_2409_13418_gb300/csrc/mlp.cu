@@ -218,12 +218,24 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
 }
 
 // ----------------------------------------------------------- FP32 network
+// Register tiles: each thread holds kTR rows x 4 kTG columns of a layer's
+// output; a warp covers kTR rows x 128 kTG columns, kCPW warps one row block.
 #ifndef ODC_FP32_WARPS
 #define ODC_FP32_WARPS 12
 #endif
-constexpr int kWarps = ODC_FP32_WARPS;   // one warp per 8 queries of the tile
-constexpr int kTM = 8 * kWarps;          // queries per CTA
+#ifndef ODC_FP32_TR
+#define ODC_FP32_TR 8
+#endif
+#ifndef ODC_FP32_TG
+#define ODC_FP32_TG 2
+#endif
+constexpr int kWarps = ODC_FP32_WARPS;
+constexpr int kTR = ODC_FP32_TR;         // rows (queries) per thread
+constexpr int kTG = ODC_FP32_TG;         // groups of 4 columns per thread
+constexpr int kCPW = 2 / kTG;            // warps per row block
+constexpr int kTM = kWarps / kCPW * kTR; // queries per CTA
 constexpr int kThreads = 32 * kWarps;
+static_assert(kWarps % kCPW == 0 && 4 * kTM <= kThreads, "FP32 tile shape");
 #ifndef ODC_FP32_KC
 #define ODC_FP32_KC 32
 #endif
@@ -239,17 +251,20 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // act[m][n] = relu(sum_k act[m][k] Wt[k][n] + b[n]) for the CTA's kTM queries,
-// in place.  Thread (tr, tc): rows tr*8..tr*8+7, columns tc*4..tc*4+3 and
-// 128+tc*4..+3.  The sums live in registers until every k has been read; the
-// last chunk ends with a barrier before the epilogue overwrites the tile.
+// in place.  Thread lane tc of warp w: rows (w / kCPW) kTR .. + kTR - 1,
+// columns (g kCPW + w % kCPW) 128 + tc*4 .. + 3 for g < kTG.  Every output
+// sums its products in order k = 0..K-1 with one rounding per FMA.  The sums
+// live in registers until every k has been read; the last chunk ends with a
+// barrier before the epilogue overwrites the tile.
 __device__ __forceinline__ void dense_relu(float* act, int K, const float* __restrict__ Wt,
                                            const float* __restrict__ bias, float* __restrict__ wbuf) {
-    const int tid = threadIdx.x, tr = tid >> 5, tc = tid & 31;
-    float acc[8][8];
+    const int tid = threadIdx.x, warp = tid >> 5, tc = tid & 31;
+    const int row0 = (warp / kCPW) * kTR, cb = warp % kCPW;
+    float acc[kTR][4 * kTG];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < kTR; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < 4 * kTG; ++j) acc[i][j] = 0.0f;
     const int nchunk = K / kKC;
     auto stage = [&](int c, int buf) {
         const float* src = Wt + (size_t)c * kKC * kH;
@@ -270,38 +285,40 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
         const float* w = wbuf + (c & 1) * kKC * kH;
 #pragma unroll
         for (int kk = 0; kk < kKC; kk += 4) {
-            float4 a4[8];
+            float4 a4[kTR];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                a4[i] = *reinterpret_cast<const float4*>(act + (tr * 8 + i) * kActStride + c * kKC + kk);
+            for (int i = 0; i < kTR; ++i)
+                a4[i] = *reinterpret_cast<const float4*>(act + (row0 + i) * kActStride + c * kKC + kk);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float* wr = w + (kk + q) * kH;
-                float4 w0 = *reinterpret_cast<const float4*>(wr + tc * 4);
-                float4 w1 = *reinterpret_cast<const float4*>(wr + 128 + tc * 4);
-                float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                float wv[4 * kTG];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int g = 0; g < kTG; ++g) {
+                    const float4 t = *reinterpret_cast<const float4*>(wr + (g * kCPW + cb) * 128 + tc * 4);
+                    wv[4 * g] = t.x; wv[4 * g + 1] = t.y; wv[4 * g + 2] = t.z; wv[4 * g + 3] = t.w;
+                }
+#pragma unroll
+                for (int i = 0; i < kTR; ++i) {
                     float av = q == 0 ? a4[i].x : (q == 1 ? a4[i].y : (q == 2 ? a4[i].z : a4[i].w));
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av, wv[j], acc[i][j]);
+                    for (int j = 0; j < 4 * kTG; ++j) acc[i][j] = fmaf(av, wv[j], acc[i][j]);
                 }
             }
         }
         __syncthreads();
     }
-    float4 b0 = *reinterpret_cast<const float4*>(bias + tc * 4);
-    float4 b1 = *reinterpret_cast<const float4*>(bias + 128 + tc * 4);
-    float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float* o = act + (tr * 8 + i) * kActStride;
-        float4 v0 = make_float4(fmaxf(acc[i][0] + bv[0], 0.f), fmaxf(acc[i][1] + bv[1], 0.f),
-                                fmaxf(acc[i][2] + bv[2], 0.f), fmaxf(acc[i][3] + bv[3], 0.f));
-        float4 v1 = make_float4(fmaxf(acc[i][4] + bv[4], 0.f), fmaxf(acc[i][5] + bv[5], 0.f),
-                                fmaxf(acc[i][6] + bv[6], 0.f), fmaxf(acc[i][7] + bv[7], 0.f));
-        *reinterpret_cast<float4*>(o + tc * 4) = v0;
-        *reinterpret_cast<float4*>(o + 128 + tc * 4) = v1;
+    for (int g = 0; g < kTG; ++g) {
+        const int col = (g * kCPW + cb) * 128 + tc * 4;
+        const float4 b = *reinterpret_cast<const float4*>(bias + col);
+#pragma unroll
+        for (int i = 0; i < kTR; ++i) {
+            float* o = act + (row0 + i) * kActStride + col;
+            *reinterpret_cast<float4*>(o) =
+                make_float4(fmaxf(acc[i][4 * g] + b.x, 0.f), fmaxf(acc[i][4 * g + 1] + b.y, 0.f),
+                            fmaxf(acc[i][4 * g + 2] + b.z, 0.f), fmaxf(acc[i][4 * g + 3] + b.w, 0.f));
+        }
     }
     __syncthreads();
 }
@@ -333,8 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncthreads();
         for (int l = 0; l < kNL; ++l) dense_relu(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
-        {
-            int m = tid >> 2, p = tid & 3;
+        for (int t = tid; t < 4 * kTM; t += kThreads) {
+            const int m = t >> 2, p = t & 3;
             const float* w5 = wb + kOffW[kNL];
             float s = 0.0f;
             for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[m * kActStride + k], w5[k], s);
