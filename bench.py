@@ -331,6 +331,31 @@ def serve_bench(odc, I, seconds: float, slots: int):
     return out
 
 
+def csg_run(args):
+    """The CSG pipeline alone (a seeded 64-primitive tree, k = 12) at
+    --csg-res^3: warm-up and timed extractions with the stage times, for
+    profiling the non-network kernels (every stage but the MLP network)."""
+    import torch
+    from paper_2409_13418_gb300 import build, inputs as I, odc
+    build.build()
+    src, g = I.random_csg(1, n_prims=64), I.cube_grid(args.csg_res)
+    with odc.Context(0) as ctx:
+        ctx.upload(src)
+        for _ in range(args.warmup):
+            ctx.extract(None, g, steps_1d=12)
+        ms, stages = [], None
+        for _ in range(args.steps):
+            m = ctx.extract(None, g, steps_1d=12)
+            ms.append(m.stats["stage_ms"][7])
+            stages = m.stats["stage_ms"]
+        torch.cuda.synchronize()
+    t = min(ms)
+    print(json.dumps({"workload": f"seeded 64-primitive CSG tree, {args.csg_res}^3 cells, k=12",
+                      "device_ms": t, "mcells_per_s": args.csg_res ** 3 / (t * 1e-3) / 1e6,
+                      "stage_ms": [round(x, 4) for x in stages], "edges": m.stats["n_edges"],
+                      "face_segs": m.stats["n_face_segs"], "cells": m.stats["n_cells"], "tris": m.n_tris}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,6 +372,8 @@ def main():
                     help="length of the serving arrival trace (0: skip the serving comparison)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-ablation", action="store_true", help="skip the ablation table (Sec. 6.3 variants)")
+    ap.add_argument("--csg-res", type=int, default=0,
+                    help="profile run: only the CSG pipeline at this resolution (prints its own JSON line)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -357,6 +384,9 @@ def main():
         run_reference(args, rank, world)
         return
     args.cpu_cells = args.cpu_cells or 40
+    if args.csg_res:
+        csg_run(args)
+        return
 
     import numpy as np
     import torch
