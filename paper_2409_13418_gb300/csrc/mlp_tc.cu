@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -41,7 +42,8 @@ constexpr int kKC = 32;                     // K per weight slice
 constexpr int kStages = 5;
 constexpr int kSliceBytes = kH * kKC * 2;   // 16 KB
 constexpr int kABytes = kTileM * kH * 2;    // 64 KB per sub-tile
-constexpr int kEpiWarps = 8;
+constexpr int kHalves = 2;                  // epilogue warps per (sub-tile, TMEM lane quarter): column halves
+constexpr int kEpiWarps = 4 * kSub * kHalves;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr uint32_t kTmemCols = 512;
 constexpr int kParamFloats = 4 * kH + kH + 4 + 3 * kNF;      // biases, w4, b4 (padded), Fourier B
@@ -142,24 +144,39 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) :: "memory");
 }
 
-// Visit the 256 accumulator columns of a TMEM row in 32-column chunks,
+// Visit NCH 32-column chunks of a TMEM row from column address trow,
 // fn(chunk, values), loading chunk c + 1 while chunk c is processed (two
 // register buffers; the loop over chunk pairs is not unrolled, to keep the
 // register count where nothing spills: a spill of a buffer between its load
 // and its wait would read the registers before the load lands).
-template <class Fn>
+template <int NCH, class Fn>
 __device__ __forceinline__ void tmem_row_chunks(uint32_t trow, Fn&& fn) {
+    static_assert(NCH % 2 == 0, "chunk pairs");
     uint32_t ra[32], rb[32];
     tmem_ld32_async(trow, ra);
     tmem_wait(ra);
 #pragma unroll 1
-    for (int cb = 0; cb < kH / 32; cb += 2) {
+    for (int cb = 0; cb < NCH; cb += 2) {
         tmem_ld32_async(trow + (cb + 1) * 32, rb);
         fn(cb, ra);
         tmem_wait(rb);
-        if (cb + 2 < kH / 32) tmem_ld32_async(trow + (cb + 2) * 32, ra);
+        if (cb + 2 < NCH) tmem_ld32_async(trow + (cb + 2) * 32, ra);
         fn(cb + 1, rb);
-        if (cb + 2 < kH / 32) tmem_wait(ra);
+        if (cb + 2 < NCH) tmem_wait(ra);
+    }
+}
+
+// The same visit with one register buffer (load, wait, process): for
+// kernels whose warp count leaves too few registers for two buffers; the
+// other epilogue warps of the SM sub-partition cover the load latency.
+template <int NCH, class Fn>
+__device__ __forceinline__ void tmem_row_chunks_serial(uint32_t trow, Fn&& fn) {
+#pragma unroll 1
+    for (int cb = 0; cb < NCH; ++cb) {
+        uint32_t ra[32];
+        tmem_ld32_async(trow + cb * 32, ra);
+        tmem_wait(ra);
+        fn(cb, ra);
     }
 }
 
@@ -301,10 +318,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------ epilogue warps
-        const int e = warp - 2;                 // 0..7
-        const int sub = e >> 2;                 // sub-tile
+        // warp w may read TMEM lanes 32 (w % 4) ..; the four warps of each
+        // lane quarter split into (sub-tile, column half)
+        const int e = warp - 2;                 // 0..15
         const int quad = warp & 3;              // TMEM lane quarter this warp may access
+        const int sub = (e >> 2) / kHalves;     // sub-tile
+        const int half = (e >> 2) % kHalves;    // columns half * 128 .. + 127
         const int r = quad * 32 + lane;         // row within the sub-tile
+        const int c0 = half * (kH / kHalves);
         uint8_t* As = A + sub * kABytes;
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sub * kH);
         const float* Bf = sp + 5 * kH + 4;
@@ -314,8 +335,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t q = t * kRows + sub * kTileM + r;
             const bool valid = q < n;
             float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
-            // Fourier features -> A[:, 0:128]
-            for (int j = 0; j < kNF; j += 8) {
+            // Fourier features of this half's frequencies -> A[:, f], A[:, 64 + f]
+            for (int j = half * (kNF / kHalves); j < (half + 1) * (kNF / kHalves); j += 8) {
                 float s[8], cs[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -341,28 +362,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const float* bias = sp + l * kH;
                 if (l < kNL - 1) {
-                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
+                    tmem_row_chunks_serial<kH / 32 / kHalves>(trow + c0, [&](int cb, const uint32_t (&v)[32]) {
+                        const int col = c0 + cb * 32;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             float h[8];
-                            const float4 b0 = *reinterpret_cast<const float4*>(bias + cb * 32 + u * 8);
-                            const float4 b1 = *reinterpret_cast<const float4*>(bias + cb * 32 + u * 8 + 4);
+                            const float4 b0 = *reinterpret_cast<const float4*>(bias + col + u * 8);
+                            const float4 b1 = *reinterpret_cast<const float4*>(bias + col + u * 8 + 4);
                             const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
                             for (int i = 0; i < 8; ++i) h[i] = fmaxf(__uint_as_float(v[u * 8 + i]) + bb[i], 0.f);
                             uint4 p = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
                                                  pack_bf16(h[6], h[7]));
-                            *reinterpret_cast<uint4*>(As + a_offset(r, cb * 32 + u * 8)) = p;
+                            *reinterpret_cast<uint4*>(As + a_offset(r, col + u * 8)) = p;
                         }
                     });
                     fence_async_smem();
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(act_ready);
-                } else {
+                } else if (half == 0) {
+                    // the 256 -> 1 output layer over all columns (one warp per row group)
                     const float* w4 = sp + 4 * kH;
                     float f = 0.0f;
-                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
+                    tmem_row_chunks_serial<kH / 32>(trow, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int i = 0; i < 32; i += 4) {
                             const float4 b = *reinterpret_cast<const float4*>(bias + cb * 32 + i);
@@ -376,6 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_before();
                     f += sp[5 * kH];
                     if (valid) P.z[query_index(P.Q, q)] = envelope_logit(x, f, P.scale, P.radius, P.amp);
+                } else {
+                    tc_fence_before();
                 }
             }
         }
@@ -398,9 +423,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 // scale exactly.  An activation beyond the FP16 range marks its query (logit
 // 0) so that the FP32 tier re-evaluates it.  One 128-query tile per CTA:
 // A_hi and A_lo (64 KB each), a 3-stage ring of (W_hi, W_lo) K = 32 slices
-// (32 KB), 256 TMEM columns, four epilogue warps.
+// (32 KB), 256 TMEM columns, eight epilogue warps (two per TMEM lane
+// quarter, one per column half).
 constexpr int kStages3 = 3;
-constexpr int kEpiWarps3 = 4;
+constexpr int kEpiWarps3 = 4 * kHalves;    // per TMEM lane quarter, one warp per column half
 constexpr int kThreads3 = 32 * (2 + kEpiWarps3);
 constexpr uint32_t kTmemCols3 = 256;
 constexpr size_t kSmemBytes3 = 1024 + 2 * kABytes + kStages3 * 2 * kSliceBytes + 256;
@@ -534,8 +560,12 @@ __global__ void __launch_bounds__(kThreads3, 1)
             }
         }
     } else {
+        // warp w may read TMEM lanes 32 (w % 4) ..; two warps per lane quarter
+        // take the column halves (and half the Fourier frequencies)
         const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int r = quad * 32 + lane;
+        const int c0 = half * (kH / kHalves);
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
         const float* Bf = P.wblob + kOffB;
         uint32_t acc_phase = 0;
@@ -545,7 +575,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
             const bool valid = q < n;
             bool range_ok = true;
             float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
-            for (int j = 0; j < kNF; j += 8) {
+            for (int j = half * (kNF / kHalves); j < (half + 1) * (kNF / kHalves); j += 8) {
                 float sv[8], cv[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -568,37 +598,47 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 const float* bias = P.wblob + kOffb_(l);
                 const float unscale = P.wscale_inv[l];
                 if (l < kNL - 1) {
-                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
+                    tmem_row_chunks<kH / 32 / kHalves>(trow + c0, [&](int cb, const uint32_t (&v)[32]) {
+                        const int col = c0 + cb * 32;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             float h[8];
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 h[i] = fmaxf(fmaf(__uint_as_float(v[u * 8 + i]), unscale,
-                                                  __ldg(bias + cb * 32 + u * 8 + i)), 0.f);
+                                                  __ldg(bias + col + u * 8 + i)), 0.f);
                                 range_ok &= h[i] < kF16Safe;
                                 h[i] = fminf(h[i], kF16Safe);
                             }
-                            store_split8(Ahi, Alo, a_offset(r, cb * 32 + u * 8), h);
+                            store_split8(Ahi, Alo, a_offset(r, col + u * 8), h);
                         }
                     });
+                    // a row that left the FP16 range is poisoned with an infinite
+                    // input to the last layer: every accumulator of that row turns
+                    // non-finite, which the warp of the other column half sees
+                    if (l == kNL - 2 && !range_ok)
+                        *reinterpret_cast<uint16_t*>(Ahi + a_offset(r, c0)) = (uint16_t)0x7C00u;
                     fence_async_smem();
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(act_ready);
-                } else {
+                } else if (half == 0) {
                     const float* w4 = P.wblob + kOffW_(kNL);
                     float f = 0.0f;
-                    tmem_row_chunks(trow, [&](int cb, const uint32_t (&v)[32]) {
+                    tmem_row_chunks<kH / 32>(trow, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            f = fmaf(fmaxf(fmaf(__uint_as_float(v[i]), unscale, __ldg(bias + cb * 32 + i)), 0.f),
-                                     __ldg(w4 + cb * 32 + i), f);
+                        for (int i = 0; i < 32; ++i) {
+                            const float a = fmaf(__uint_as_float(v[i]), unscale, __ldg(bias + cb * 32 + i));
+                            range_ok &= fabsf(a) <= FLT_MAX;   // false for the poison (inf or NaN)
+                            f = fmaf(fmaxf(a, 0.f), __ldg(w4 + cb * 32 + i), f);
+                        }
                     });
                     tc_fence_before();
                     f += __ldg(P.wblob + kOffb_(kNL));
-                    // an activation out of FP16 range sends the query to the FP32 tier (|z| = 0)
+                    // an activation out of FP16 range sends the query to the FP32 tier (|z - zt| = 0)
                     if (valid) P.z[query_index(P.Q, q)] = range_ok ? envelope_logit(x, f, P.scale, P.radius, P.amp) : P.zt;
+                } else {
+                    tc_fence_before();
                 }
             }
         }
