@@ -111,9 +111,10 @@ enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2 };
  * occupancy lies within ``band`` of iso is re-evaluated so that its sign
  * equals the FP32 plain path's: first by a split-precision tensor-core pass
  * (operands split into FP16 hi + lo, three products per layer, FP32
- * accumulation), then, for the logits still within ``split_zmargin`` of the
- * threshold (0: the default 1e-4, three times the measured split-tier logit
- * error of 3.2e-5), by the FP32 network; ``no_split`` nonzero sends every
+ * accumulation of hi hi and of the lo corrections in separate accumulators),
+ * then, for the logits still within ``split_zmargin`` of the threshold (0:
+ * the default 4e-5, three times the measured split-tier logit error of
+ * 1.34e-5), by the FP32 network; ``no_split`` nonzero sends every
  * band decision to the FP32 network directly.  A band of 0.03 (|z| < 0.12)
  * covers the measured BF16 logit error (0.063) twice over. */
 typedef struct {

@@ -155,7 +155,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->precision = m->precision;
     st->band = m->band;
     st->split = m->no_split ? 0 : 1;
-    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 1e-4f;
+    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 4e-5f;
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
     st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
     st->scale = m->env_scale;

@@ -66,7 +66,7 @@ struct MlpState {
     double flops[3] = {0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
     int64_t launches[3] = {0, 0, 0};
     int split = 1;              // use the split-FP16 tier for band re-evaluation
-    float zsplit = 1e-4f;       // |z - zt| below which a split-tier decision is re-taken in FP32
+    float zsplit = 4e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     int sms = 0;                // SM count of the device

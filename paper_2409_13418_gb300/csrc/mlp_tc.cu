@@ -180,6 +180,24 @@ __device__ __forceinline__ void tmem_row_chunks_serial(uint32_t trow, Fn&& fn) {
     }
 }
 
+// Visit NCH 32-column chunks of the sum main + corr 2^-11 of two TMEM
+// accumulators (columns ta.. and tb..), one chunk at a time.
+template <int NCH, class Fn>
+__device__ __forceinline__ void tmem_row_chunks_sum(uint32_t ta, uint32_t tb, float sb, Fn&& fn) {
+#pragma unroll 1
+    for (int cb = 0; cb < NCH; ++cb) {
+        uint32_t ra[32], rb[32];
+        tmem_ld32_async(ta + cb * 32, ra);
+        tmem_ld32_async(tb + cb * 32, rb);
+        tmem_wait(ra);
+        tmem_wait(rb);
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            ra[i] = __float_as_uint(fmaf(__uint_as_float(rb[i]), sb, __uint_as_float(ra[i])));
+        fn(cb, ra);
+    }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -417,18 +435,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ------------------------------------------------------------------------
 // Split-FP16 variant (FP32-class accuracy on the tensor pipe).  Every FP32
 // activation a and scaled weight w 2^s is split into hi = fp16(v) and lo =
-// fp16(v - hi) (22 significant bits); each layer accumulates A_hi W_hi +
-// A_lo W_hi + A_hi W_lo in FP32, where every product is exact and the dropped
-// A_lo W_lo term is ~2^-22 relative, and the epilogue undoes the 2^s weight
-// scale exactly.  An activation beyond the FP16 range marks its query (logit
-// 0) so that the FP32 tier re-evaluates it.  One 128-query tile per CTA:
-// A_hi and A_lo (64 KB each), a 3-stage ring of (W_hi, W_lo) K = 32 slices
-// (32 KB), 256 TMEM columns, eight epilogue warps (two per TMEM lane
-// quarter, one per column half).
+// fp16((v - hi) 2^11) (22 significant bits; the 2^11 keeps lo out of the
+// FP16 subnormals).  Each layer accumulates A_hi W_hi in one TMEM accumulator
+// and the corrections A_lo W_hi + A_hi W_lo in a second one, so that the
+// accumulator rounding of the large main term does not also absorb the
+// corrections (the scheme of Ootomo and Yokota, 2022, for FP32 GEMM on FP16
+// tensor cores); the epilogue forms main + corr 2^-11 in FP32 and undoes the
+// 2^s weight scale exactly.  The dropped A_lo W_lo term is ~2^-22 relative.
+// An activation beyond the FP16 range marks its query (logit zt) so that the
+// FP32 tier re-evaluates it.  One 128-query tile per CTA: A_hi and A_lo
+// (64 KB each), a 3-stage ring of (W_hi, W_lo) K = 32 slices (32 KB), 512
+// TMEM columns, eight epilogue warps (two per TMEM lane quarter, one per
+// column half).
 constexpr int kStages3 = 3;
 constexpr int kEpiWarps3 = 4 * kHalves;    // per TMEM lane quarter, one warp per column half
 constexpr int kThreads3 = 32 * (2 + kEpiWarps3);
-constexpr uint32_t kTmemCols3 = 256;
+constexpr uint32_t kTmemCols3 = 512;       // main accumulator, then the correction accumulator
+constexpr float kLoScale = 2048.0f;        // lo parts carried as fp16((v - hi) 2^11), kept normal
+constexpr float kLoUnscale = 1.0f / 2048.0f;
 constexpr size_t kSmemBytes3 = 1024 + 2 * kABytes + kStages3 * 2 * kSliceBytes + 256;
 
 constexpr float kF16Safe = 30000.0f;      // activations kept well inside the FP16 range
@@ -447,7 +471,7 @@ __device__ __forceinline__ void store_split8(uint8_t* Ahi, uint8_t* Alo, uint32_
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         h[i] = __float2half_rn(v[i]);
-        l[i] = __float2half_rn(v[i] - __half2float(h[i]));
+        l[i] = __float2half_rn((v[i] - __half2float(h[i])) * kLoScale);
     }
     *reinterpret_cast<uint4*>(Ahi + off) = *reinterpret_cast<const uint4*>(h);
     *reinterpret_cast<uint4*>(Alo + off) = *reinterpret_cast<const uint4*>(l);
@@ -549,8 +573,8 @@ __global__ void __launch_bounds__(kThreads3, 1)
                             uint64_t dbh = sdesc(bh, 512, kLayoutSW64);
                             uint64_t dbl = sdesc(bh + kSliceBytes, 512, kLayoutSW64);
                             umma_f16(tmem, dah, dbh, (c | kk) != 0);
-                            umma_f16(tmem, dal, dbh, 1);
-                            umma_f16(tmem, dah, dbl, 1);
+                            umma_f16(tmem + kH, dal, dbh, (c | kk) != 0);
+                            umma_f16(tmem + kH, dah, dbl, 1);
                         }
                         umma_commit(&empty[stage]);
                         if (++stage == kStages3) { stage = 0; phase ^= 1; }
@@ -598,7 +622,8 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 const float* bias = P.wblob + kOffb_(l);
                 const float unscale = P.wscale_inv[l];
                 if (l < kNL - 1) {
-                    tmem_row_chunks<kH / 32 / kHalves>(trow + c0, [&](int cb, const uint32_t (&v)[32]) {
+                    tmem_row_chunks_sum<kH / 32 / kHalves>(trow + c0, trow + kH + c0, kLoUnscale,
+                                                           [&](int cb, const uint32_t (&v)[32]) {
                         const int col = c0 + cb * 32;
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
@@ -625,7 +650,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 } else if (half == 0) {
                     const float* w4 = P.wblob + kOffW_(kNL);
                     float f = 0.0f;
-                    tmem_row_chunks<kH / 32>(trow, [&](int cb, const uint32_t (&v)[32]) {
+                    tmem_row_chunks_sum<kH / 32>(trow, trow + kH, kLoUnscale, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
                             const float a = fmaf(__uint_as_float(v[i]), unscale, __ldg(bias + cb * 32 + i));
@@ -710,7 +735,7 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
                 float ws = std::ldexp(w, sexp);
                 __half hi = __float2half_rn(ws);
                 h16[off + (size_t)n * K[l] + k] = hi;
-                h16[total + off + (size_t)n * K[l] + k] = __float2half_rn(ws - __half2float(hi));
+                h16[total + off + (size_t)n * K[l] + k] = __float2half_rn((ws - __half2float(hi)) * tc::kLoScale);
             }
         off += (size_t)kH * K[l];
     }

@@ -62,7 +62,7 @@ odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, c
 __device__ __forceinline__ float bracket_hint(float za, float zc, float t, float zb, float zs) {
     float da = fabsf(za - t), dc = fabsf(zc - t);
     float dm = fmaxf(da, dc);
-    float e = dm >= zb ? 0.07f : (dm >= zs ? 4e-5f : 0.0f);
+    float e = dm >= zb ? 0.07f : (dm >= zs ? 0.4f * zs : 0.0f);
     return fabsf(0.5f * (za + zc) - t) + 0.25f * fabsf(zc - za) + e;
 }
 

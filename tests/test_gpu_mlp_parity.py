@@ -116,9 +116,9 @@ def test_bf16_logits_within_band_of_fp32(ctx, mlp):
 
 
 def test_split_bf16_logits_within_margin_of_fp32(ctx, mlp):
-    """The split tier (FP16 hi + lo operands, three products per layer)
-    stays within half the default re-decision margin (1e-4) of the FP32
-    network."""
+    """The split tier (FP16 hi + lo operands, three products per layer,
+    corrections in their own accumulator) stays within 0.4 of the default
+    re-decision margin (4e-5) of the FP32 network."""
     rng = np.random.default_rng(4)
     pts = rng.uniform(-1, 1, (1000000, 3)).astype(np.float32)
     _, z32 = ctx.eval_points(mlp, pts, precision=0)
@@ -126,7 +126,7 @@ def test_split_bf16_logits_within_margin_of_fp32(ctx, mlp):
     d = np.abs(zs.astype(np.float64) - z32)
     print("split |dz| max", d.max(), "median", np.median(d))
     assert np.isfinite(zs).all()
-    assert d.max() < 0.5 * 1e-4
+    assert d.max() < 0.4 * 4e-5
 
 
 @pytest.mark.parametrize("n,split", [(48, True), (97, True), (64, False), (131, True), (131, False)])
