@@ -218,29 +218,29 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
 }
 
 // ----------------------------------------------------------- FP32 network
-// Register tiles: each thread holds kTR rows x 4 kTG columns of a layer's
-// output; a warp covers kTR rows x 128 kTG columns, kCPW warps one row block.
+// Register tiles of 8 rows (queries) x 8 columns per thread; a warp's lanes
+// form 4 x 8 threads (32 rows x 64 columns), the CTA's warps 4 column blocks
+// x kWarps / 4 row blocks.  Activations sit transposed in shared memory
+// (act[k][m], k-major), so that a thread's 8 rows at one k are two vector
+// loads, shared by the 8 lanes of its row group.
 #ifndef ODC_FP32_WARPS
-#define ODC_FP32_WARPS 12
-#endif
-#ifndef ODC_FP32_TR
-#define ODC_FP32_TR 8
-#endif
-#ifndef ODC_FP32_TG
-#define ODC_FP32_TG 2
+#define ODC_FP32_WARPS 16
 #endif
 constexpr int kWarps = ODC_FP32_WARPS;
-constexpr int kTR = ODC_FP32_TR;         // rows (queries) per thread
-constexpr int kTG = ODC_FP32_TG;         // groups of 4 columns per thread
-constexpr int kCPW = 2 / kTG;            // warps per row block
-constexpr int kTM = kWarps / kCPW * kTR; // queries per CTA
+constexpr int kTM = kWarps / 4 * 32;     // queries per CTA
 constexpr int kThreads = 32 * kWarps;
-static_assert(kWarps % kCPW == 0 && 4 * kTM <= kThreads, "FP32 tile shape");
+static_assert(kWarps % 4 == 0 && 4 * kTM <= kThreads, "FP32 tile shape");
 #ifndef ODC_FP32_KC
 #define ODC_FP32_KC 32
 #endif
 constexpr int kKC = ODC_FP32_KC;         // weight rows per staged chunk
-constexpr int kActStride = kH + 4;
+#ifndef ODC_FP32_STAGES
+#define ODC_FP32_STAGES 2
+#endif
+constexpr int kWStages = ODC_FP32_STAGES; // weight chunks in flight (ring)
+constexpr int kActStride = kTM + 4;      // floats between consecutive k of act[k][m]
+static_assert(kWStages >= 2 && sizeof(float) * (kH * kActStride + kWStages * kKC * kH) <= 220 * 1024,
+              "FP32 tile and weight ring exceed shared memory");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -250,75 +250,68 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// act[m][n] = relu(sum_k act[m][k] Wt[k][n] + b[n]) for the CTA's kTM queries,
-// in place.  Thread lane tc of warp w: rows (w / kCPW) kTR .. + kTR - 1,
-// columns (g kCPW + w % kCPW) 128 + tc*4 .. + 3 for g < kTG.  Every output
-// sums its products in order k = 0..K-1 with one rounding per FMA.  The sums
-// live in registers until every k has been read; the last chunk ends with a
-// barrier before the epilogue overwrites the tile.
+// act[n][m] = relu(sum_k act[k][m] Wt[k][n] + b[n]) for the CTA's kTM queries,
+// in place.  Lane (ty, tx) = (lane / 8, lane % 8) of warp w: rows
+// (w / 4) 32 + ty 8 .. + 7, columns (w % 4) 64 + tx 4 .. + 3 and 32 more.
+// Every output sums its products in order k = 0..K-1 with one rounding per
+// FMA.  The sums live in registers until every k has been read; the last
+// chunk ends with a barrier before the epilogue overwrites the tile.
 __device__ __forceinline__ void dense_relu(float* act, int K, const float* __restrict__ Wt,
                                            const float* __restrict__ bias, float* __restrict__ wbuf) {
-    const int tid = threadIdx.x, warp = tid >> 5, tc = tid & 31;
-    const int row0 = (warp / kCPW) * kTR, cb = warp % kCPW;
-    float acc[kTR][4 * kTG];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row0 = (warp >> 2) * 32 + (lane >> 3) * 8;
+    const int col0 = (warp & 3) * 64 + (lane & 7) * 4;
+    float acc[8][8];
 #pragma unroll
-    for (int i = 0; i < kTR; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4 * kTG; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
     const int nchunk = K / kKC;
-    auto stage = [&](int c, int buf) {
-        const float* src = Wt + (size_t)c * kKC * kH;
-        float* dst = wbuf + buf * kKC * kH;
+    // ring of kWStages chunk buffers: chunk c + kWStages - 1 is issued at the
+    // top of chunk c into the buffer chunk c - 1 used, which every thread
+    // has left once it passed chunk c's barrier (one barrier per chunk)
+    auto stage = [&](int c) {
+        if (c < nchunk) {
+            const float* src = Wt + (size_t)c * kKC * kH;
+            float* dst = wbuf + (c % kWStages) * kKC * kH;
 #pragma unroll
-        for (int v = tid; v < kKC * kH / 4; v += kThreads) cp_async16(dst + 4 * v, src + 4 * v);
-        cp_async_commit();
+            for (int v = tid; v < kKC * kH / 4; v += kThreads) cp_async16(dst + 4 * v, src + 4 * v);
+        }
+        cp_async_commit();   // possibly empty: keeps the group count uniform
     };
-    stage(0, 0);
+#pragma unroll
+    for (int c = 0; c < kWStages - 1; ++c) stage(c);
     for (int c = 0; c < nchunk; ++c) {
-        if (c + 1 < nchunk) {
-            stage(c + 1, (c + 1) & 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        cp_async_wait<kWStages - 2>();   // chunk c has landed (this thread's copies)
+        __syncthreads();                 // ... and every thread's; chunk c - 1 is released
+        stage(c + kWStages - 1);
+        const float* w = wbuf + (c % kWStages) * kKC * kH + col0;
+        const float* a = act + (size_t)(c * kKC) * kActStride + row0;
+#pragma unroll 4
+        for (int kk = 0; kk < kKC; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(a + kk * kActStride);
+            const float4 a1 = *reinterpret_cast<const float4*>(a + kk * kActStride + 4);
+            const float4 w0 = *reinterpret_cast<const float4*>(w + kk * kH);
+            const float4 w1 = *reinterpret_cast<const float4*>(w + kk * kH + 32);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], wv[j], acc[i][j]);
         }
-        __syncthreads();
-        const float* w = wbuf + (c & 1) * kKC * kH;
-#pragma unroll
-        for (int kk = 0; kk < kKC; kk += 4) {
-            float4 a4[kTR];
-#pragma unroll
-            for (int i = 0; i < kTR; ++i)
-                a4[i] = *reinterpret_cast<const float4*>(act + (row0 + i) * kActStride + c * kKC + kk);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float* wr = w + (kk + q) * kH;
-                float wv[4 * kTG];
-#pragma unroll
-                for (int g = 0; g < kTG; ++g) {
-                    const float4 t = *reinterpret_cast<const float4*>(wr + (g * kCPW + cb) * 128 + tc * 4);
-                    wv[4 * g] = t.x; wv[4 * g + 1] = t.y; wv[4 * g + 2] = t.z; wv[4 * g + 3] = t.w;
-                }
-#pragma unroll
-                for (int i = 0; i < kTR; ++i) {
-                    float av = q == 0 ? a4[i].x : (q == 1 ? a4[i].y : (q == 2 ? a4[i].z : a4[i].w));
-#pragma unroll
-                    for (int j = 0; j < 4 * kTG; ++j) acc[i][j] = fmaf(av, wv[j], acc[i][j]);
-                }
-            }
-        }
-        __syncthreads();
     }
+    cp_async_wait<0>();
+    __syncthreads();   // every thread has read the last chunk and the whole input tile
 #pragma unroll
-    for (int g = 0; g < kTG; ++g) {
-        const int col = (g * kCPW + cb) * 128 + tc * 4;
-        const float4 b = *reinterpret_cast<const float4*>(bias + col);
-#pragma unroll
-        for (int i = 0; i < kTR; ++i) {
-            float* o = act + (row0 + i) * kActStride + col;
-            *reinterpret_cast<float4*>(o) =
-                make_float4(fmaxf(acc[i][4 * g] + b.x, 0.f), fmaxf(acc[i][4 * g + 1] + b.y, 0.f),
-                            fmaxf(acc[i][4 * g + 2] + b.z, 0.f), fmaxf(acc[i][4 * g + 3] + b.w, 0.f));
-        }
+    for (int j = 0; j < 8; ++j) {
+        const int col = col0 + (j < 4 ? j : 28 + j);
+        const float b = bias[col];
+        float* o = act + (size_t)col * kActStride + row0;
+        *reinterpret_cast<float4*>(o) = make_float4(fmaxf(acc[0][j] + b, 0.f), fmaxf(acc[1][j] + b, 0.f),
+                                                    fmaxf(acc[2][j] + b, 0.f), fmaxf(acc[3][j] + b, 0.f));
+        *reinterpret_cast<float4*>(o + 4) = make_float4(fmaxf(acc[4][j] + b, 0.f), fmaxf(acc[5][j] + b, 0.f),
+                                                        fmaxf(acc[6][j] + b, 0.f), fmaxf(acc[7][j] + b, 0.f));
     }
     __syncthreads();
 }
@@ -329,8 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n_max, float scale, float radius, float amp,
                float* __restrict__ zout) {
     extern __shared__ __align__(16) float sm[];
-    float* act = sm;                         // [kTM][kActStride], layers run in place
-    float* wbuf = sm + kTM * kActStride;     // two staged weight chunks
+    float* act = sm;                         // [kH][kActStride], layers run in place
+    float* wbuf = sm + kH * kActStride;      // kWStages staged weight chunks
     __shared__ float3 xs[kTM];
     __shared__ float part[kTM][4];
     const int tid = threadIdx.x;
@@ -345,16 +338,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = tid; i < kNF * kTM; i += kThreads) {
             int j = i / kTM, m = i % kTM;
             float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
-            act[m * kActStride + j] = sc.x;
-            act[m * kActStride + kNF + j] = sc.y;
+            act[j * kActStride + m] = sc.x;
+            act[(kNF + j) * kActStride + m] = sc.y;
         }
         __syncthreads();
         for (int l = 0; l < kNL; ++l) dense_relu(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
         for (int t = tid; t < 4 * kTM; t += kThreads) {
-            const int m = t >> 2, p = t & 3;
+            const int m = t % kTM, p = t / kTM;
             const float* w5 = wb + kOffW[kNL];
             float s = 0.0f;
-            for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[m * kActStride + k], w5[k], s);
+            for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[k * kActStride + m], w5[k], s);
             part[m][p] = s;
         }
         __syncthreads();
@@ -365,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-static size_t fp32_smem() { return sizeof(float) * (kTM * kActStride + 2 * kKC * kH); }
+static size_t fp32_smem() { return sizeof(float) * (kH * kActStride + kWStages * kKC * kH); }
 
 static odc_status fp32_kernel_setup(std::string* err) {
     MLP_CK(cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp32_smem()));
