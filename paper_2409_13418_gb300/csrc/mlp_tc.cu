@@ -102,6 +102,64 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Load of this CTA's part of a pair operand whose completion is counted on
+// the mbarrier at shared::cluster address bar (in this CTA or its peer).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// shared::cluster address of the same shared-memory object in CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_cluster(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (as mbar_wait) with cluster-scope acquire, for phases that
+// the peer CTA's threads complete
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* b, uint32_t parity, volatile int* abort) {
+    if (mbar_try_cluster(b, parity)) return true;
+    unsigned long long t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_cluster(b, parity)) return true;
+        if ((i & 255) == 0) {
+            if (*abort) return false;
+            if (gtimer() - t0 > kWaitNs) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+// every thread of every CTA of the cluster (both CTAs are co-scheduled)
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // shared-memory matrix descriptor: K-major, swizzled (LBO unused), SBO =
 // byte distance between 8-row groups, descriptor version 1 (bits 46-47)
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo, uint32_t layout) {
@@ -180,21 +238,35 @@ __device__ __forceinline__ void tmem_row_chunks_serial(uint32_t trow, Fn&& fn) {
     }
 }
 
-// Visit NCH 32-column chunks of the sum main + corr 2^-11 of two TMEM
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :: "memory");
+}
+
+// Visit NCH 16-column chunks of the sum main + corr sb of two TMEM
 // accumulators (columns ta.. and tb..), one chunk at a time.
 template <int NCH, class Fn>
-__device__ __forceinline__ void tmem_row_chunks_sum(uint32_t ta, uint32_t tb, float sb, Fn&& fn) {
+__device__ __forceinline__ void tmem_row_chunks_sum16(uint32_t ta, uint32_t tb, float sb, Fn&& fn) {
 #pragma unroll 1
     for (int cb = 0; cb < NCH; ++cb) {
-        uint32_t ra[32], rb[32];
-        tmem_ld32_async(ta + cb * 32, ra);
-        tmem_ld32_async(tb + cb * 32, rb);
-        tmem_wait(ra);
-        tmem_wait(rb);
+        uint32_t ra[16], rb[16];
+        tmem_ld16_async(ta + cb * 16, ra);
+        tmem_ld16_async(tb + cb * 16, rb);
+        tmem_wait16(ra);
+        tmem_wait16(rb);
+        float v[16];
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-            ra[i] = __float_as_uint(fmaf(__uint_as_float(rb[i]), sb, __uint_as_float(ra[i])));
-        fn(cb, ra);
+        for (int i = 0; i < 16; ++i) v[i] = fmaf(__uint_as_float(rb[i]), sb, __uint_as_float(ra[i]));
+        fn(cb, v);
     }
 }
 
@@ -436,34 +508,61 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Split-FP16 variant (FP32-class accuracy on the tensor pipe).  Every FP32
 // activation a and scaled weight w 2^s is split into hi = fp16(v) and lo =
 // fp16((v - hi) 2^11) (22 significant bits; the 2^11 keeps lo out of the
-// FP16 subnormals).  Each layer accumulates A_hi W_hi in one TMEM accumulator
-// and the corrections A_lo W_hi + A_hi W_lo in a second one, so that the
-// accumulator rounding of the large main term does not also absorb the
-// corrections (the scheme of Ootomo and Yokota, 2022, for FP32 GEMM on FP16
-// tensor cores); the epilogue forms main + corr 2^-11 in FP32 and undoes the
-// 2^s weight scale exactly.  The dropped A_lo W_lo term is ~2^-22 relative.
-// An activation beyond the FP16 range marks its query (logit zt) so that the
-// FP32 tier re-evaluates it.  One 128-query tile per CTA: A_hi and A_lo
-// (64 KB each), a 3-stage ring of (W_hi, W_lo) K = 32 slices (32 KB), 512
-// TMEM columns, eight epilogue warps (two per TMEM lane quarter, one per
-// column half).
-constexpr int kStages3 = 3;
-constexpr int kEpiWarps3 = 4 * kHalves;    // per TMEM lane quarter, one warp per column half
+// FP16 subnormals).  Each layer accumulates A_hi W_hi in one TMEM
+// accumulator and the corrections A_lo W_hi + A_hi W_lo in a second one, so
+// that the accumulator rounding of the large main term does not also absorb
+// the corrections (the scheme of Ootomo and Yokota, 2022, for FP32 GEMM on
+// FP16 tensor cores); the epilogue forms main + corr 2^-11 in FP32 and undoes
+// the 2^s weight scale exactly.  The dropped A_lo W_lo term is ~2^-22
+// relative.  An activation beyond the FP16 range marks its query (logit zt)
+// so that the FP32 tier re-evaluates it.
+//
+// CTA pairs (clusters of two) run the 2-SM form of the MMA (cta_group::2,
+// M = 256): each CTA holds its own 128 query rows (A_hi, A_lo: 64 KB each)
+// and the 128 weight rows N = 128 rank .. + 127 of every K = 32 slice
+// (W_hi, W_lo: 8 KB each), so each SM takes in half the weight bytes per
+// query that a one-SM tile would (weight streaming, not the tensor pipe,
+// bounds a one-SM tile: measured ~56 GB/s per SM).  The leader CTA (rank 0)
+// issues the MMAs; its mbarriers count both CTAs' weight bytes and epilogue
+// warps, and the MMAs' completion is signalled to both CTAs.  Sixteen
+// epilogue warps per CTA (four per TMEM lane quarter, one per 64-column
+// group) read their CTA's 128 rows of the 512 TMEM columns (main,
+// corrections); the 256 -> 1 output layer sums the four groups' partial dot
+// products through shared memory.  A CTA whose rows lie past the end runs
+// them as invalid rows and stores nothing.
+constexpr int kStages3 = 5;
+constexpr int kPairRows = 2 * kTileM;      // queries per pair step
+constexpr int kBRows = kH / 2;             // weight rows (N) per CTA
+constexpr int kHalfSlice = kBRows * kKC * 2;   // 8 KB
+constexpr uint16_t kPairMask = 3;
+constexpr int kGroups3 = 4;                // epilogue warps per TMEM lane quarter: 64-column groups
+constexpr int kGCols = kH / kGroups3;
+constexpr int kEpiWarps3 = 4 * kGroups3;
 constexpr int kThreads3 = 32 * (2 + kEpiWarps3);
-constexpr uint32_t kTmemCols3 = 512;       // main accumulator, then the correction accumulator
+constexpr uint32_t kTmemCols3 = 2 * kH;    // main accumulator, then the correction accumulator
 constexpr float kLoScale = 2048.0f;        // lo parts carried as fp16((v - hi) 2^11), kept normal
 constexpr float kLoUnscale = 1.0f / 2048.0f;
-constexpr size_t kSmemBytes3 = 1024 + 2 * kABytes + kStages3 * 2 * kSliceBytes + 256;
+constexpr size_t kSmemBytes3 =
+    1024 + 2 * kABytes + kStages3 * 2 * kHalfSlice + 256 + kGroups3 * kTileM * 4 + (5 * kH + 4) * 4;
 
 constexpr float kF16Safe = 30000.0f;      // activations kept well inside the FP16 range
-// instruction descriptor: D F32, A/B F16, both K-major, N = 256, M = 128
-constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+// instruction descriptor: D F32, A/B F16, both K-major, N = 256, M = 256 (pair)
+constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kPairRows >> 4) << 24);
 
-__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma_f16_pair(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(a), "l"(b), "r"(kIdescF16), "r"(acc));
+}
+// arrive on the mbarrier at this offset in both CTAs of the pair when the
+// pair MMAs issued so far have completed
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            su32(bar)),
+        "h"(kPairMask)
+        : "memory");
 }
 
 __device__ __forceinline__ void store_split8(uint8_t* Ahi, uint8_t* Alo, uint32_t off, const float* v) {
@@ -486,19 +585,28 @@ __global__ void __launch_bounds__(kThreads3, 1)
     uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* Ahi = sm;
     uint8_t* Alo = sm + kABytes;
-    uint8_t* Bring = sm + 2 * kABytes;                 // stage s: hi slice, then lo slice
-    uint64_t* bars = (uint64_t*)(Bring + kStages3 * 2 * kSliceBytes);
-    uint64_t* full = bars;
-    uint64_t* empty = bars + kStages3;
-    uint64_t* acc_full = bars + 2 * kStages3;
-    uint64_t* act_ready = bars + 2 * kStages3 + 1;
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages3 + 2);
+    uint8_t* Bring = sm + 2 * kABytes;                 // stage s: W_hi rows, then W_lo rows (8 KB each)
+    uint64_t* bars = (uint64_t*)(Bring + kStages3 * 2 * kHalfSlice);
+    uint64_t* full = bars;                             // leader: both CTAs' slice halves landed
+    uint64_t* empty = bars + kStages3;                 // both CTAs: the pair MMAs released stage s
+    uint64_t* acc_full = bars + 2 * kStages3;          // both CTAs: layer accumulators complete
+    uint64_t* act_ready = bars + 2 * kStages3 + 1;     // leader: both CTAs' activations written
+    uint64_t* mma_done = bars + 2 * kStages3 + 2;      // leader: every MMA it issued has completed
+    uint64_t* part_ready = bars + 2 * kStages3 + 3;    // groups 1..3 wrote their output-layer partials
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages3 + 4);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
+    float* part = (float*)((uint8_t*)bars + 256);      // [kGroups3][kTileM] partial output sums
+    float* sp = part + kGroups3 * kTileM;              // biases [4][256], w4 [256], b4
+    for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sp[i] = P.wblob[kOffb_(i / kH) + (i % kH)];
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) sp[4 * kH + i] = P.wblob[kOffW_(kNL) + i];
+    if (threadIdx.x == 0) sp[5 * kH] = P.wblob[kOffb_(kNL)];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = query_count(P.Q, P.n);
-    const int64_t ntiles = (n + kTileM - 1) / kTileM;
-    if ((int64_t)blockIdx.x >= ntiles) return;   // uniform per CTA, before any barrier or TMEM use
+    const int64_t nsteps = (n + kPairRows - 1) / kPairRows;
+    const int64_t step0 = blockIdx.x / 2, sstride = gridDim.x / 2;
+    const uint32_t rank = cluster_rank();
+    if (step0 >= nsteps) return;   // uniform per pair, before any barrier or TMEM use
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages3; ++s) {
@@ -506,100 +614,105 @@ __global__ void __launch_bounds__(kThreads3, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(act_ready, kEpiWarps3);
+        mbar_init(act_ready, 2 * kEpiWarps3);   // every epilogue warp of both CTAs
+        mbar_init(mma_done, 1);
+        mbar_init(part_ready, 4 * (kGroups3 - 1));
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+    if (warp == 1) {   // one warp of each CTA allocates the pair's columns
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"(kTmemCols3));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
     }
-    __syncthreads();
+    cluster_sync();   // both CTAs' barriers initialised (and TMEM allocated) before any cross-CTA signal
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
+        // ------------------------------------------------ TMA producer (both CTAs):
+        // this CTA's rows of (W_hi, W_lo) for every chunk, counted on the
+        // leader's stage barrier
         if (lane == 0) {
             int stage = 0;
-            uint32_t phase = 0, issued = 0;
+            uint32_t phase = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int64_t g = step0; g < nsteps && ok; g += sstride) {
                 for (int l = 0; l < kNL && ok; ++l) {
                     const CUtensorMap* mh = l == 0 ? &h0 : l == 1 ? &h1 : l == 2 ? &h2 : &h3;
                     const CUtensorMap* ml = l == 0 ? &l0 : l == 1 ? &l1 : l == 2 ? &l2 : &l3;
-                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    const int nck = l == 0 ? kChunks0 : kChunksH;
                     for (int c = 0; c < nck; ++c) {
                         if (!mbar_wait(&empty[stage], phase ^ 1, abort)) { ok = false; break; }
-                        mbar_expect_tx(&full[stage], 2 * kSliceBytes);
-                        uint8_t* dst = Bring + stage * 2 * kSliceBytes;
-                        tma_load_2d(dst, mh, c * kKC, 0, &full[stage]);
-                        tma_load_2d(dst + kSliceBytes, ml, c * kKC, 0, &full[stage]);
-                        ++issued;
+                        const uint32_t fb = cluster_addr(&full[stage], 0);
+                        if (rank == 0) mbar_expect_tx_cluster(fb, 4 * kHalfSlice);
+                        uint8_t* dst = Bring + stage * 2 * kHalfSlice;
+                        tma_load_2d_pair(dst, mh, c * kKC, (int)rank * kBRows, fb);
+                        tma_load_2d_pair(dst + kHalfSlice, ml, c * kKC, (int)rank * kBRows, fb);
                         if (++stage == kStages3) { stage = 0; phase ^= 1; }
                     }
                 }
             }
-            for (int s = 0; s < kStages3; ++s) {
-                uint32_t uses = issued / kStages3 + (issued % kStages3 > (uint32_t)s ? 1 : 0);
-                if (uses) {
-                    unsigned long long t0 = gtimer();
-                    while (!mbar_try(&full[s], (uses - 1) & 1) && gtimer() - t0 < kWaitNs) {}
-                }
-            }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        // ------------------------------------------------ MMA issuer (leader CTA)
+        if (lane == 0 && rank == 0) {
             int stage = 0;
             uint32_t phase = 0, act_phase = 0;
             bool ok = true;
             const uint32_t ahi = su32(Ahi), alo = su32(Alo), b_base = su32(Bring);
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int64_t g = step0; g < nsteps && ok; g += sstride) {
                 for (int l = 0; l < kNL && ok; ++l) {
-                    if (!mbar_wait(act_ready, act_phase, abort)) { ok = false; break; }
+                    if (!mbar_wait_cluster(act_ready, act_phase, abort)) { ok = false; break; }
                     act_phase ^= 1;
                     tc_fence_after();
-                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    const int nck = l == 0 ? kChunks0 : kChunksH;
                     for (int c = 0; c < nck; ++c) {
                         if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
                         tc_fence_after();
 #pragma unroll
                         for (int kk = 0; kk < kKC / 16; ++kk) {
-                            int kg = c * kKC + kk * 16;
-                            uint32_t aoff = (kg >> 6) * (kTileM * 128) + (kg & 63) * 2;
-                            uint32_t bh = b_base + stage * 2 * kSliceBytes + kk * 32;
-                            uint64_t dah = sdesc(ahi + aoff, 1024, kLayoutSW128);
-                            uint64_t dal = sdesc(alo + aoff, 1024, kLayoutSW128);
-                            uint64_t dbh = sdesc(bh, 512, kLayoutSW64);
-                            uint64_t dbl = sdesc(bh + kSliceBytes, 512, kLayoutSW64);
-                            umma_f16(tmem, dah, dbh, (c | kk) != 0);
-                            umma_f16(tmem + kH, dal, dbh, (c | kk) != 0);
-                            umma_f16(tmem + kH, dah, dbl, 1);
+                            const int kg = c * kKC + kk * 16;
+                            const uint32_t aoff = (kg >> 6) * (kTileM * 128) + (kg & 63) * 2;
+                            const uint32_t bh = b_base + stage * 2 * kHalfSlice + kk * 32;
+                            const uint64_t dah = sdesc(ahi + aoff, 1024, kLayoutSW128);
+                            const uint64_t dbh = sdesc(bh, 512, kLayoutSW64);
+                            umma_f16_pair(tmem, dah, dbh, (c | kk) != 0);
+                            umma_f16_pair(tmem + kH, sdesc(alo + aoff, 1024, kLayoutSW128), dbh, (c | kk) != 0);
+                            umma_f16_pair(tmem + kH, dah, sdesc(bh + kHalfSlice, 512, kLayoutSW64), 1);
                         }
-                        umma_commit(&empty[stage]);
+                        umma_commit_pair(&empty[stage]);   // released in both CTAs
                         if (++stage == kStages3) { stage = 0; phase ^= 1; }
                     }
-                    if (ok) umma_commit(acc_full);
+                    if (ok) umma_commit_pair(acc_full);
                 }
             }
+            // nothing of the pair's columns may be freed while an MMA still runs
+            umma_commit_pair(mma_done);
+            unsigned long long t0 = gtimer();
+            while (!mbar_try(mma_done, 0) && gtimer() - t0 < kWaitNs) {}
         }
     } else {
-        // warp w may read TMEM lanes 32 (w % 4) ..; two warps per lane quarter
-        // take the column halves (and half the Fourier frequencies)
+        // ------------------------------------------------ epilogue warps (both CTAs)
+        // warp w may read TMEM lanes 32 (w % 4) ..; the four warps of a lane
+        // quarter take 64-column groups (and 16 of the Fourier frequencies)
         const int quad = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int grp = (warp - 2) >> 2;
         const int r = quad * 32 + lane;
-        const int c0 = half * (kH / kHalves);
+        const int c0 = grp * kGCols;
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
         const float* Bf = P.wblob + kOffB;
-        uint32_t acc_phase = 0;
+        const uint32_t ready = cluster_addr(act_ready, 0);   // the leader's barrier
+        uint32_t acc_phase = 0, part_phase = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int64_t q = t * kTileM + r;
+        int64_t qn = step0 * kPairRows + (int64_t)rank * kTileM + r;
+        float3 xn = qn < n ? query_point(P.Q, qn) : make_float3(0.f, 0.f, 0.f);
+        for (int64_t g = step0; g < nsteps && ok; g += sstride) {
+            const int64_t q = qn;
             const bool valid = q < n;
             bool range_ok = true;
-            float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
-            for (int j = half * (kNF / kHalves); j < (half + 1) * (kNF / kHalves); j += 8) {
+            const float3 x = xn;
+            for (int j = grp * (kNF / kGroups3); j < (grp + 1) * (kNF / kGroups3); j += 8) {
                 float sv[8], cv[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -613,25 +726,25 @@ __global__ void __launch_bounds__(kThreads3, 1)
             }
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(act_ready);
+            if (lane == 0) mbar_arrive_cluster(ready);
+            __syncwarp();
             for (int l = 0; l < kNL; ++l) {
                 bool got = mbar_wait(acc_full, acc_phase, abort);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 acc_phase ^= 1;
                 tc_fence_after();
-                const float* bias = P.wblob + kOffb_(l);
+                const float* bias = sp + l * kH;
                 const float unscale = P.wscale_inv[l];
                 if (l < kNL - 1) {
-                    tmem_row_chunks_sum<kH / 32 / kHalves>(trow + c0, trow + kH + c0, kLoUnscale,
-                                                           [&](int cb, const uint32_t (&v)[32]) {
-                        const int col = c0 + cb * 32;
+                    tmem_row_chunks_sum16<kGCols / 16>(trow + c0, trow + kH + c0, kLoUnscale,
+                                                       [&](int cb, const float (&v)[16]) {
+                        const int col = c0 + cb * 16;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < 2; ++u) {
                             float h[8];
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
-                                h[i] = fmaxf(fmaf(__uint_as_float(v[u * 8 + i]), unscale,
-                                                  __ldg(bias + col + u * 8 + i)), 0.f);
+                                h[i] = fmaxf(fmaf(v[u * 8 + i], unscale, bias[col + u * 8 + i]), 0.f);
                                 range_ok &= h[i] < kF16Safe;
                                 h[i] = fminf(h[i], kF16Safe);
                             }
@@ -640,38 +753,60 @@ __global__ void __launch_bounds__(kThreads3, 1)
                     });
                     // a row that left the FP16 range is poisoned with an infinite
                     // input to the last layer: every accumulator of that row turns
-                    // non-finite, which the warp of the other column half sees
+                    // non-finite, which every column group sees
                     if (l == kNL - 2 && !range_ok)
                         *reinterpret_cast<uint16_t*>(Ahi + a_offset(r, c0)) = (uint16_t)0x7C00u;
                     fence_async_smem();
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(act_ready);
-                } else if (half == 0) {
-                    const float* w4 = P.wblob + kOffW_(kNL);
+                    if (lane == 0) mbar_arrive_cluster(ready);
+                    __syncwarp();
+                    if (l == kNL - 2) {   // the next tile's query point, under the last layer's MMAs
+                        qn = (g + sstride) * kPairRows + (int64_t)rank * kTileM + r;
+                        if (g + sstride < nsteps && qn < n) xn = query_point(P.Q, qn);
+                    }
+                } else {
+                    // this group's share of the 256 -> 1 output layer; a non-finite
+                    // accumulator (the poison) makes the partial NaN
+                    const float* w4 = sp + 4 * kH;
                     float f = 0.0f;
-                    tmem_row_chunks_sum<kH / 32>(trow, trow + kH, kLoUnscale, [&](int cb, const uint32_t (&v)[32]) {
+                    tmem_row_chunks_sum16<kGCols / 16>(trow + c0, trow + kH + c0, kLoUnscale,
+                                                       [&](int cb, const float (&v)[16]) {
+                        const int col = c0 + cb * 16;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const float a = fmaf(__uint_as_float(v[i]), unscale, __ldg(bias + cb * 32 + i));
-                            range_ok &= fabsf(a) <= FLT_MAX;   // false for the poison (inf or NaN)
-                            f = fmaf(fmaxf(a, 0.f), __ldg(w4 + cb * 32 + i), f);
+                        for (int i = 0; i < 16; ++i) {
+                            const float a = fmaf(v[i], unscale, bias[col + i]);
+                            range_ok &= fabsf(a) <= FLT_MAX;
+                            f = fmaf(fmaxf(a, 0.f), w4[col + i], f);
                         }
                     });
                     tc_fence_before();
-                    f += __ldg(P.wblob + kOffb_(kNL));
-                    // an activation out of FP16 range sends the query to the FP32 tier (|z - zt| = 0)
-                    if (valid) P.z[query_index(P.Q, q)] = range_ok ? envelope_logit(x, f, P.scale, P.radius, P.amp) : P.zt;
-                } else {
-                    tc_fence_before();
+                    if (!range_ok) f = __int_as_float(0x7fc00000);
+                    if (grp > 0) {
+                        part[grp * kTileM + r] = f;
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(part_ready);
+                    } else {
+                        bool have = mbar_wait(part_ready, part_phase, abort);
+                        if (!__all_sync(0xffffffffu, have)) { ok = false; break; }
+                        part_phase ^= 1;
+                        f = ((f + part[kTileM + r]) + (part[2 * kTileM + r] + part[3 * kTileM + r])) + sp[5 * kH];
+                        // an activation out of FP16 range sends the query to the FP32 tier (|z - zt| = 0)
+                        if (valid)
+                            P.z[query_index(P.Q, q)] =
+                                isfinite(f) ? envelope_logit(x, f, P.scale, P.radius, P.amp) : P.zt;
+                    }
                 }
             }
         }
     }
     __syncthreads();
+    // no CTA leaves (or frees its columns) while its peer may still signal its
+    // barriers or the pair MMAs still run
+    cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols3));
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols3));
     }
     if (threadIdx.x == 0 && *abort) atomicExch(P.err, 1);
 }
@@ -684,9 +819,12 @@ struct MlpTc {
     CUtensorMap maps[4];            // BF16 weights
     CUtensorMap maps_hi[4];         // split path hi parts
     CUtensorMap maps_lo[4];         // split path lo parts
+    CUtensorMap maps_hi_mc[4];      // split path, 128 weight rows per box (each CTA of a pair)
+    CUtensorMap maps_lo_mc[4];
     float wscale_inv[4];
     int* err = nullptr;
     int sms = 0;
+    int clusters3 = 0;              // co-resident CTA pairs of the split kernel
     bool ready = false;
 };
 
@@ -772,6 +910,15 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
             r = fn(&T->maps_lo[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + total + offs[l]), gdim,
                    gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        cuuint32_t box_mc[2] = {(cuuint32_t)tc::kKC, (cuuint32_t)tc::kBRows};
+        if (r == CUDA_SUCCESS)
+            r = fn(&T->maps_hi_mc[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + offs[l]), gdim, gstride,
+                   box_mc, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = fn(&T->maps_lo_mc[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + total + offs[l]), gdim,
+                   gstride, box_mc, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             *err = "cuTensorMapEncodeTiled failed for layer " + std::to_string(l);
             return ODC_ERR_CUDA;
@@ -787,6 +934,26 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
         cudaGetLastError();
         *err = "cannot reserve shared memory for the tensor-core kernel";
         return ODC_ERR_CUDA;
+    }
+    {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * std::max(1, T->sms / 2));
+        cfg.blockDim = dim3(tc::kThreads3);
+        cfg.dynamicSmemBytes = tc::kSmemBytes3;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, (const void*)tc::k_mlp_tc3, &cfg) != cudaSuccess || nc < 1) {
+            cudaGetLastError();
+            *err = "the split-precision kernel's cluster does not fit on this device";
+            return ODC_ERR_UNSUPPORTED;
+        }
+        T->clusters3 = nc;
     }
     T->ready = true;
     return ODC_OK;
@@ -828,18 +995,31 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
         *err = "tensor-core path not prepared";
         return ODC_ERR_INTERNAL;
     }
-    int64_t tiles = (n + tc::kTileM - 1) / tc::kTileM;
-    int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
+    // CTA pairs, each pair 256 queries per step
+    int64_t steps = (n + tc::kPairRows - 1) / tc::kPairRows;
+    int grid = 2 * (int)std::min<int64_t>(steps, (int64_t)T->clusters3);
     tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {}, st->zt};
     for (int l = 0; l < 4; ++l) P.wscale_inv[l] = T->wscale_inv[l];
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tc::kThreads3);
+    cfg.dynamicSmemBytes = tc::kSmemBytes3;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     cudaEvent_t* ev = mlp_ev_pair(st, 2);
     if (ev) cudaEventRecord(ev[0], s);
-    tc::k_mlp_tc3<<<grid, tc::kThreads3, tc::kSmemBytes3, s>>>(T->maps_hi[0], T->maps_hi[1], T->maps_hi[2], T->maps_hi[3],
-                                                             T->maps_lo[0], T->maps_lo[1], T->maps_lo[2],
-                                                             T->maps_lo[3], P);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, tc::k_mlp_tc3, T->maps_hi_mc[0], T->maps_hi_mc[1], T->maps_hi_mc[2],
+                                       T->maps_hi_mc[3], T->maps_lo_mc[0], T->maps_lo_mc[1], T->maps_lo_mc[2],
+                                       T->maps_lo_mc[3], P);
     note_launch();
     if (ev) cudaEventRecord(ev[1], s);
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         *err = std::string("k_mlp_tc3 launch: ") + cudaGetErrorString(e);
         return ODC_ERR_CUDA;
