@@ -229,6 +229,10 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
 constexpr int kWarps = ODC_FP32_WARPS;
 constexpr int kTM = kWarps / 4 * 32;     // queries per CTA
 constexpr int kThreads = 32 * kWarps;
+#ifndef ODC_FP32_CTAS
+#define ODC_FP32_CTAS 1
+#endif
+constexpr int kCtasPerSm = ODC_FP32_CTAS;   // resident CTAs per SM (persistent grid)
 static_assert(kWarps % 4 == 0 && 4 * kTM <= kThreads, "FP32 tile shape");
 #ifndef ODC_FP32_KC
 #define ODC_FP32_KC 32
@@ -240,7 +244,7 @@ constexpr int kKC = ODC_FP32_KC;         // weight rows per staged chunk
 constexpr int kWStages = ODC_FP32_STAGES; // weight chunks in flight (ring)
 constexpr int kActStride = kTM + 4;      // floats between consecutive k of act[k][m]
 constexpr int kFUnroll = 16;              // k steps unrolled in the inner loop
-static_assert(kWStages >= 2 && sizeof(float) * (kH * kActStride + kWStages * kKC * kH) <= 220 * 1024,
+static_assert(kWStages >= 2 && sizeof(float) * (kH * kActStride + kWStages * kKC * kH) <= 220 * 1024 / kCtasPerSm,
               "FP32 tile and weight ring exceed shared memory");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -320,7 +324,7 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
 
 // Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // of min(n, *Q.cnt) queries (the tile loop is uniform within a CTA).
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
     k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n_max, float scale, float radius, float amp,
                float* __restrict__ zout) {
     extern __shared__ __align__(16) float sm[];
@@ -372,7 +376,7 @@ static odc_status fp32_kernel_setup(std::string* err) {
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
     if (n <= 0) return ODC_OK;
     int64_t tiles = (n + kTM - 1) / kTM;
-    unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)std::max(st->sms, 1));
+    unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)kCtasPerSm * std::max(st->sms, 1));
     cudaEvent_t* ev = mlp_ev_pair(st, 0);
     if (ev) MLP_CK(cudaEventRecord(ev[0], s));
     k_mlp_fp32<<<grid, kThreads, fp32_smem(), s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z); note_launch();
