@@ -248,6 +248,64 @@ odc_status odc_ctx_destroy(odc_ctx* ctx);
 odc_status odc_extract(odc_ctx* ctx, const odc_source* src, const odc_grid* grid,
                        const odc_params* params, void* cuda_stream, odc_mesh* out);
 
+/* ---- z-slab extraction (a grid cut into slabs of cell layers along z)
+ *
+ * A slab owns the cells of layers [z0, z1), their 3D points, the crossing
+ * edges whose lower end lies in those layers and the quads (with IC case-3
+ * edge points) of those edges (Sec. 4 "Polygonization", A.1.5).  It is
+ * extracted on its layers plus ``halo`` layers each side (clamped to the
+ * grid), with the whole grid's vertex coordinates, so that every value it
+ * owns equals the whole-grid extraction's; halo >= 2 covers the manifold
+ * fix and the face searches of its boundary cells.  The whole grid's mesh
+ * numbers 3D points in cell order, then edge points in edge order, and
+ * triangles in edge order, so a slab's owned part is three contiguous
+ * ranges and the merged mesh equals the whole-grid mesh byte for byte. */
+typedef struct {
+    int32_t z0, z1;              /* owned cell layers [z0, z1), 0 <= z0 < z1 <= res[2] */
+    int32_t halo;                /* extra cell layers each side, >= 1 */
+} odc_slab;
+
+typedef struct {
+    int64_t verts3_local;        /* 3D points of the slab extraction (its edge points follow them) */
+    int64_t verts3_before;       /* its 3D points below layer z0 */
+    int64_t verts3_owned;        /* 3D points of the owned cells */
+    int64_t case3_before;        /* edge points of halo edges before the owned edges */
+    int64_t case3_owned;         /* edge points of the owned edges */
+    int64_t tris_before;         /* triangles of halo edges before the owned edges */
+    int64_t tris_owned;          /* triangles of the owned edges */
+} odc_slab_info;
+
+/* Extract one slab of ``grid`` (same source, parameters and stream rules
+ * as odc_extract; ODC_POLY_MC is not supported).  ``out`` is the slab
+ * extraction's own mesh (context memory, valid until the next extract on
+ * this context); ``info`` locates its owned part.  Grid limits: res[0],
+ * res[1] <= 2048, res[2] <= 8192, and the slab with its halo must keep
+ * 3 (res[0]+1)(res[1]+1)(layers+1) below 2^32.  ODC_ERR_INVALID_ARG
+ * otherwise. */
+odc_status odc_extract_slab(odc_ctx* ctx, const odc_source* src, const odc_grid* grid, const odc_params* params,
+                            const odc_slab* slab, void* cuda_stream, odc_mesh* out, odc_slab_info* info);
+
+/* Place the owned part of a slab extraction (``mesh``, ``info`` from
+ * odc_extract_slab on this context, before any other extract) into the
+ * whole grid's mesh in device memory: 3D points at vertex index
+ * ``verts3_base`` (the owned 3D points of all slabs below), edge points at
+ * vertex index ``case3_base`` (all slabs' 3D points plus the owned edge
+ * points of the slabs below), triangles at ``tris_base``.  d_verts
+ * float[3 * total vertices], d_tris int32[3 * total triangles], device
+ * pointers owned by the caller.  Asynchronous on ``cuda_stream``. */
+odc_status odc_slab_place(odc_ctx* ctx, const odc_mesh* mesh, const odc_slab_info* info, int64_t verts3_base,
+                          int64_t case3_base, int64_t tris_base, float* d_verts, int32_t* d_tris,
+                          void* cuda_stream);
+
+/* The whole grid in ``n_slabs`` slabs of near-equal depth, one after the
+ * other on this context (peak device memory: one slab's), merged into one
+ * mesh in context memory (valid until the next extract).  The result equals
+ * odc_extract's mesh on the same grid byte for byte; stats are summed over
+ * the slabs (element counts include halo layers).  Grid limits as for
+ * odc_extract_slab. */
+odc_status odc_extract_slabbed(odc_ctx* ctx, const odc_source* src, const odc_grid* grid, const odc_params* params,
+                               int32_t n_slabs, int32_t halo, void* cuda_stream, odc_mesh* out);
+
 /* Upload an occupancy source (host descriptors) to the context's device
  * memory without extracting, so that later odc_extract calls with kind
  * ODC_SRC_RESIDENT start from device-resident inputs.  Returns

@@ -79,7 +79,15 @@ struct odc_ctx {
     unsigned long long* cycles = nullptr;
     float3 *vlocal = nullptr, *vworld = nullptr;
     int3* tris = nullptr;
+    uint32_t* vbase = nullptr;           // exclusive scan of cycles per crossing cell
+    unsigned long long* qoff = nullptr;  // exclusive scan of (triangles << 32 | edge points) per edge
     size_t nw = 0;
+    // merged mesh of odc_extract_slabbed
+    float3* sv = nullptr;       // vertices
+    int3* stri = nullptr;       // triangles
+    float3* sc3 = nullptr;      // edge points, staged until the 3D point count is known
+    unsigned long long* sinfo = nullptr;   // slab range counters (device, 8)
+    size_t sv_cap = 0, st_cap = 0, sc3_cap = 0;
 };
 
 // Grow an arena (stream-ordered: the old block is freed and the new one
@@ -90,7 +98,7 @@ static odc_status arena_ensure(odc_ctx* c, Arena& a, size_t need, cudaStream_t s
         a.reset();
         return ODC_OK;
     }
-    size_t others = c->A.cap + c->B.cap + c->S.cap - a.cap;
+    size_t others = c->A.cap + c->B.cap + c->S.cap - a.cap + c->sv_cap * 12 + c->st_cap * 12 + c->sc3_cap * 12;
     size_t want = std::max(need, a.cap + a.cap / 4);
     if (c->budget && others + want > c->budget) {
         want = need;
@@ -110,6 +118,32 @@ static odc_status arena_ensure(odc_ctx* c, Arena& a, size_t need, cudaStream_t s
     }
     a.cap = want;
     a.reset();
+    return ODC_OK;
+}
+
+// Grow a device array (stream-ordered; the old contents are kept).
+template <typename T>
+static odc_status grow(odc_ctx* c, T** p, size_t* cap, size_t need, cudaStream_t st) {
+    if (need <= *cap) return ODC_OK;
+    size_t want = std::max(need, *cap + *cap / 2);
+    size_t others = c->A.cap + c->B.cap + c->S.cap + (c->sv_cap + c->st_cap + c->sc3_cap - *cap) * 12;
+    if (c->budget && others + want * sizeof(T) > c->budget) {
+        want = need;
+        if (others + want * sizeof(T) > c->budget)
+            return fail(ODC_ERR_OOM, "merged slab mesh would exceed the context memory budget");
+    }
+    T* q = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&q, want * sizeof(T), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ODC_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    if (*p) {
+        if (*cap) ODC_CK(cudaMemcpyAsync(q, *p, *cap * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        ODC_CK(cudaFreeAsync(*p, st));
+    }
+    *p = q;
+    *cap = want;
     return ODC_OK;
 }
 
@@ -160,6 +194,8 @@ odc_status odc_ctx_destroy(odc_ctx* c) {
     mlp_destroy(c->mlp);
     for (Arena* a : {&c->A, &c->B, &c->S})
         if (a->base) cudaFree(a->base);
+    for (void* p : {(void*)c->sv, (void*)c->stri, (void*)c->sc3, (void*)c->sinfo})
+        if (p) cudaFree(p);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
@@ -287,15 +323,7 @@ static void grid_coords(const odc_grid* grid, int a, std::vector<float>& X) {
         X[i] = (float)((double)grid->lo[a] + ((double)grid->hi[a] - (double)grid->lo[a]) * (double)i / (double)n);
 }
 
-odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, const odc_params* prm,
-                       void* cuda_stream, odc_mesh* out) {
-    if (!c || !grid || !prm || !out) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
-    odc_status s = check_source(src);
-    if (s != ODC_OK) return s;
-    for (int a = 0; a < 3; ++a) {
-        if (grid->res[a] < 1 || grid->res[a] > kMaxRes) return fail(ODC_ERR_INVALID_ARG, "res out of [1, 1024]");
-        if (!(grid->lo[a] < grid->hi[a])) return fail(ODC_ERR_INVALID_ARG, "lo must be < hi");
-    }
+static odc_status check_params(const odc_params* prm) {
     if (prm->steps_1d < 1 || prm->steps_1d > 20) return fail(ODC_ERR_INVALID_ARG, "steps_1d out of [1, 20]");
     if (prm->s2d_lin1 < 1 || prm->s2d_lin2 < 1 || prm->s2d_bin1 < 0 || prm->s2d_bin2 < 0 || prm->s2d_lin1 > 64 ||
         prm->s2d_lin2 > 64 || prm->s2d_bin1 > 20 || prm->s2d_bin2 > 20 || !(prm->s2d_range1 > 0) ||
@@ -304,8 +332,14 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     if (!(prm->iso > 0.0f && prm->iso < 1.0f)) return fail(ODC_ERR_INVALID_ARG, "iso must be in (0, 1)");
     if (prm->flags & ~(ODC_ABL_LINEAR_1D | ODC_ABL_GRADIENT_NORMALS | ODC_POLY_MC))
         return fail(ODC_ERR_INVALID_ARG, "unknown flags");
-    ODC_CK(cudaSetDevice(c->device));
-    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    return ODC_OK;
+}
+
+// The whole path on the grid whose vertex coordinates per axis are Xh[a]
+// (Xh[a].size() - 1 cells); arguments already checked.
+static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vector<float> (&Xh)[3],
+                               const odc_params* prm, cudaStream_t st, odc_mesh* out) {
+    odc_status s = ODC_OK;
     std::memset(out, 0, sizeof(*out));
 
     // ---- source upload (skipped for a resident source)
@@ -328,13 +362,11 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     // ---- grid-sized buffers
     GridDev g{};
     for (int a = 0; a < 3; ++a) {
-        g.n[a] = grid->res[a];
-        g.nv[a] = grid->res[a] + 1;
+        g.n[a] = (int)Xh[a].size() - 1;
+        g.nv[a] = (int)Xh[a].size();
     }
     g.W = (g.nv[0] + 31) / 32;
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
-    std::vector<float> Xh[3];
-    for (int a = 0; a < 3; ++a) grid_coords(grid, a, Xh[a]);
     size_t nX = Xh[0].size() + Xh[1].size() + Xh[2].size();
     size_t stmp = scan_tmp_elems(nw);
     size_t needA = al(nX * 4) + al(nw * 4) + al(nw * sizeof(WordInfo)) + 6 * al(nw * 4) + al(3 * nw * 4) +
@@ -530,6 +562,7 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
     c->bits = bits; c->flips = flips; c->edges = edges; c->T = T; c->faces = faces; c->cells = cells;
     c->slots = slots; c->fflags = fflags; c->configs = configs; c->qcase = qcase; c->pf = pf; c->dec = dec; c->cycles = cycles;
     c->vlocal = vlocal; c->vworld = vworld; c->tris = tris; c->nw = nw;
+    c->vbase = vbase; c->qoff = mc ? nullptr : qoff;
 
     out->n_verts = (int64_t)NV;
     out->n_tris = NT;
@@ -549,6 +582,173 @@ odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, 
         mlp_timing_collect(c->mlp, 2, &S.split_ms, &S.split_flops, &S.split_launches);
         S.n_split = mlp_split_count(c->mlp);
     }
+    return ODC_OK;
+}
+
+odc_status odc_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, const odc_params* prm,
+                       void* cuda_stream, odc_mesh* out) {
+    if (!c || !grid || !prm || !out) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    odc_status s = check_source(src);
+    if (s != ODC_OK) return s;
+    for (int a = 0; a < 3; ++a) {
+        if (grid->res[a] < 1 || grid->res[a] > kMaxRes) return fail(ODC_ERR_INVALID_ARG, "res out of [1, 1024]");
+        if (!(grid->lo[a] < grid->hi[a])) return fail(ODC_ERR_INVALID_ARG, "lo must be < hi");
+    }
+    s = check_params(prm);
+    if (s != ODC_OK) return s;
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    std::vector<float> Xh[3];
+    for (int a = 0; a < 3; ++a) grid_coords(grid, a, Xh[a]);
+    return extract_impl(c, src, Xh, prm, st, out);
+}
+
+// ---- z-slab extraction
+static odc_status check_slab_grid(const odc_grid* grid) {
+    for (int a = 0; a < 3; ++a) {
+        const int lim = a < 2 ? 2048 : 8192;
+        if (grid->res[a] < 1 || grid->res[a] > lim)
+            return fail(ODC_ERR_INVALID_ARG, "slab grid res out of [1, 2048] x [1, 2048] x [1, 8192]");
+        if (!(grid->lo[a] < grid->hi[a])) return fail(ODC_ERR_INVALID_ARG, "lo must be < hi");
+    }
+    return ODC_OK;
+}
+
+static odc_status slab_extract(odc_ctx* c, const odc_source* src, const odc_grid* grid, const odc_params* prm,
+                               const odc_slab* sl, cudaStream_t st, odc_mesh* out, odc_slab_info* info) {
+    if (prm->flags & ODC_POLY_MC) return fail(ODC_ERR_UNSUPPORTED, "slab extraction of marching-cubes polygons");
+    const int nz = grid->res[2];
+    if (sl->z0 < 0 || sl->z1 <= sl->z0 || sl->z1 > nz || sl->halo < 1)
+        return fail(ODC_ERR_INVALID_ARG, "slab needs 0 <= z0 < z1 <= res[2] and halo >= 1");
+    const int za = std::max(0, sl->z0 - sl->halo), zb = std::min(nz, sl->z1 + sl->halo);
+    const unsigned long long nv01 = (unsigned long long)(grid->res[0] + 1) * (grid->res[1] + 1);
+    if (3ull * nv01 * (unsigned long long)(zb - za + 1) >= (1ull << 32))
+        return fail(ODC_ERR_INVALID_ARG, "slab too deep for 32-bit element ids: use more slabs");
+    std::vector<float> Xh[3], Xz;
+    for (int a = 0; a < 3; ++a) grid_coords(grid, a, Xh[a]);
+    Xh[2] = std::vector<float>(Xh[2].begin() + za, Xh[2].begin() + zb + 1);   // the whole grid's z coordinates
+    odc_status s = extract_impl(c, src, Xh, prm, st, out);
+    if (s != ODC_OK) return s;
+    if (!c->sinfo) ODC_CK(cudaMalloc((void**)&c->sinfo, 8 * sizeof(unsigned long long)));
+    const uint32_t n01 = (uint32_t)grid->res[0] * (uint32_t)grid->res[1];
+    const uint32_t zl0 = (uint32_t)(sl->z0 - za), zl1 = (uint32_t)(sl->z1 - za);
+    launch_slab_ranges(c->cells, c->C, c->vbase, c->V3, c->edges, c->E, c->qoff, c->N3, c->NT, n01 * zl0, n01 * zl1,
+                       (uint32_t)(3ull * nv01 * zl0), (uint32_t)(3ull * nv01 * zl1), c->sinfo, st);
+    unsigned long long h[6];
+    ODC_CK(cudaMemcpyAsync(h, c->sinfo, sizeof(h), cudaMemcpyDeviceToHost, st));
+    ODC_CK(cudaStreamSynchronize(st));
+    ODC_CK(cudaGetLastError());
+    info->verts3_local = c->V3;
+    info->verts3_before = (int64_t)h[0];
+    info->verts3_owned = (int64_t)(h[1] - h[0]);
+    info->case3_before = (int64_t)h[2];
+    info->case3_owned = (int64_t)(h[3] - h[2]);
+    info->tris_before = (int64_t)h[4];
+    info->tris_owned = (int64_t)(h[5] - h[4]);
+    return ODC_OK;
+}
+
+static odc_status slab_place(odc_ctx* c, const odc_mesh* m, const odc_slab_info* in, int64_t verts3_base,
+                             int64_t case3_base, int64_t tris_base, float3* dv, float3* dc3, int3* dt,
+                             cudaStream_t st) {
+    const float3* v = (const float3*)m->d_verts;
+    if (in->verts3_owned)
+        ODC_CK(cudaMemcpyAsync(dv + verts3_base, v + in->verts3_before, in->verts3_owned * 12,
+                               cudaMemcpyDeviceToDevice, st));
+    if (in->case3_owned)
+        ODC_CK(cudaMemcpyAsync(dc3, v + in->verts3_local + in->case3_before, in->case3_owned * 12,
+                               cudaMemcpyDeviceToDevice, st));
+    // 3D points: local id i -> verts3_base + (i - verts3_before); edge points -> case3_base + ...
+    launch_slab_tris((const int3*)m->d_tris + in->tris_before, in->tris_owned, in->verts3_local,
+                     verts3_base - in->verts3_before, in->case3_before, case3_base, dt + tris_base, st);
+    ODC_CK(cudaGetLastError());
+    return ODC_OK;
+}
+
+odc_status odc_extract_slab(odc_ctx* c, const odc_source* src, const odc_grid* grid, const odc_params* prm,
+                            const odc_slab* slab, void* cuda_stream, odc_mesh* out, odc_slab_info* info) {
+    if (!c || !grid || !prm || !slab || !out || !info) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    odc_status s = check_source(src);
+    if (s == ODC_OK) s = check_slab_grid(grid);
+    if (s == ODC_OK) s = check_params(prm);
+    if (s != ODC_OK) return s;
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    return slab_extract(c, src, grid, prm, slab, st, out, info);
+}
+
+odc_status odc_slab_place(odc_ctx* c, const odc_mesh* m, const odc_slab_info* info, int64_t verts3_base,
+                          int64_t case3_base, int64_t tris_base, float* d_verts, int32_t* d_tris, void* cuda_stream) {
+    if (!c || !m || !info || !d_verts || !d_tris) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    if (verts3_base < 0 || case3_base < 0 || tris_base < 0) return fail(ODC_ERR_INVALID_ARG, "negative base");
+    if (m->d_tris != (const int32_t*)c->tris || info->verts3_local != (int64_t)c->V3)
+        return fail(ODC_ERR_INVALID_ARG, "mesh is not this context's latest slab extraction");
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    float3* dv = (float3*)d_verts;
+    return slab_place(c, m, info, verts3_base, case3_base, tris_base, dv, dv + case3_base, (int3*)d_tris, st);
+}
+
+odc_status odc_extract_slabbed(odc_ctx* c, const odc_source* src, const odc_grid* grid, const odc_params* prm,
+                               int32_t n_slabs, int32_t halo, void* cuda_stream, odc_mesh* out) {
+    if (!c || !grid || !prm || !out) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    odc_status s = check_source(src);
+    if (s == ODC_OK) s = check_slab_grid(grid);
+    if (s == ODC_OK) s = check_params(prm);
+    if (s != ODC_OK) return s;
+    if (n_slabs < 1 || n_slabs > grid->res[2]) return fail(ODC_ERR_INVALID_ARG, "n_slabs out of [1, res[2]]");
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    std::memset(out, 0, sizeof(*out));
+    // edge points are numbered after every slab's 3D points: staged, and the
+    // triangles' edge-point ids held at kMark + index until the count is known
+    constexpr int64_t kMark = 1ll << 30;
+    odc_source resident{};
+    resident.kind = ODC_SRC_RESIDENT;
+    int64_t V = 0, N = 0, T = 0;
+    odc_stats sum{};
+    for (int i = 0; i < n_slabs; ++i) {
+        odc_slab sl{(int32_t)((int64_t)grid->res[2] * i / n_slabs), (int32_t)((int64_t)grid->res[2] * (i + 1) / n_slabs),
+                    halo};
+        odc_mesh m;
+        odc_slab_info in;
+        s = slab_extract(c, i == 0 ? src : &resident, grid, prm, &sl, st, &m, &in);
+        if (s != ODC_OK) return s;
+        if (V + in.verts3_owned >= kMark || N + in.case3_owned >= kMark)
+            return fail(ODC_ERR_INVALID_ARG, "merged mesh exceeds 2^30 vertices");
+        if ((s = grow(c, &c->sv, &c->sv_cap, (size_t)(V + in.verts3_owned), st)) != ODC_OK ||
+            (s = grow(c, &c->sc3, &c->sc3_cap, (size_t)(N + in.case3_owned), st)) != ODC_OK ||
+            (s = grow(c, &c->stri, &c->st_cap, (size_t)(T + in.tris_owned), st)) != ODC_OK)
+            return s;
+        s = slab_place(c, &m, &in, V, kMark + N, T, c->sv, c->sc3 + N, c->stri, st);
+        if (s != ODC_OK) return s;
+        V += in.verts3_owned;
+        N += in.case3_owned;
+        T += in.tris_owned;
+        const odc_stats& a = m.stats;
+        sum.n_edges += a.n_edges; sum.n_face_segs += a.n_face_segs; sum.n_cells += a.n_cells;
+        sum.n_verts3 += a.n_verts3; sum.n_case3 += a.n_case3; sum.n_flips += a.n_flips;
+        sum.fix_rounds = std::max(sum.fix_rounds, a.fix_rounds);
+        sum.n_queries += a.n_queries; sum.n_requeries += a.n_requeries;
+        for (int k = 0; k < 8; ++k) sum.stage_ms[k] += a.stage_ms[k];
+        sum.mlp_flops += a.mlp_flops; sum.mlp_ms += a.mlp_ms; sum.n_launches += a.n_launches;
+        sum.mlp_launches += a.mlp_launches; sum.tc_flops += a.tc_flops; sum.tc_ms += a.tc_ms;
+        sum.tc_launches += a.tc_launches; sum.split_flops += a.split_flops; sum.split_ms += a.split_ms;
+        sum.split_launches += a.split_launches; sum.n_split += a.n_split;
+        // the next slab's extraction reuses the arenas: the placement must be done
+        ODC_CK(cudaStreamSynchronize(st));
+    }
+    if ((s = grow(c, &c->sv, &c->sv_cap, (size_t)(V + N), st)) != ODC_OK) return s;
+    if (N) ODC_CK(cudaMemcpyAsync(c->sv + V, c->sc3, N * 12, cudaMemcpyDeviceToDevice, st));
+    launch_slab_fix(c->stri, T, (int)kMark, (int)V, st);
+    ODC_CK(cudaStreamSynchronize(st));
+    ODC_CK(cudaGetLastError());
+    out->n_verts = V + N;
+    out->n_tris = T;
+    out->d_verts = (const float*)c->sv;
+    out->d_tris = (const int32_t*)c->stri;
+    out->stats = sum;
+    out->stats.n_launches += 1;
     return ODC_OK;
 }
 

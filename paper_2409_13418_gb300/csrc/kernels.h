@@ -78,6 +78,15 @@ void launch_quad_emit(const GridDev& g, const uint32_t* edges, const uint32_t* T
                       const uint8_t* qcase, const int4* qv, const unsigned long long* off, const uint32_t* v3tot,
                       float3* vworld, int3* tris, cudaStream_t st);
 
+// z-slab extraction (slab.cu)
+void launch_slab_ranges(const uint32_t* cells, uint32_t C, const uint32_t* vbase, uint32_t V3, const uint32_t* edges,
+                        uint32_t E, const unsigned long long* qoff, uint32_t N3, uint32_t NT, uint32_t cell_lo,
+                        uint32_t cell_hi, uint32_t edge_lo, uint32_t edge_hi, unsigned long long* out,
+                        cudaStream_t st);
+void launch_slab_tris(const int3* src, int64_t n, int64_t v3, int64_t vshift, int64_t c3skip, int64_t c3dst,
+                      int3* dst, cudaStream_t st);
+void launch_slab_fix(int3* t, int64_t n, int mark, int v3, cudaStream_t st);
+
 // quality.cu (Sec. 6.1 metrics; mlp may be null for a CSG source)
 struct MlpState;
 odc_status mesh_quality(MlpState* mlp, const PrimDev* prims, int n_prims, const VoxDev* vox, const float3* v,

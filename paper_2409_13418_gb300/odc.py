@@ -73,6 +73,36 @@ class Stats(C.Structure):
                 ("split_launches", C.c_int64), ("n_split", C.c_int64)]
 
 
+class SlabC(C.Structure):
+    _fields_ = [("z0", C.c_int32), ("z1", C.c_int32), ("halo", C.c_int32)]
+
+
+class SlabInfoC(C.Structure):
+    _fields_ = [("verts3_local", C.c_int64), ("verts3_before", C.c_int64), ("verts3_owned", C.c_int64),
+                ("case3_before", C.c_int64), ("case3_owned", C.c_int64), ("tris_before", C.c_int64),
+                ("tris_owned", C.c_int64)]
+
+
+def slab_bounds(res_z: int, n_slabs: int) -> list:
+    """Cell-layer ranges [z0, z1) of n_slabs slabs of near-equal depth (the
+    split odc_extract_slabbed uses)."""
+    return [(res_z * i // n_slabs, res_z * (i + 1) // n_slabs) for i in range(n_slabs)]
+
+
+def slab_bases(counts: list, rank: int) -> dict:
+    """Placement of slab ``rank`` in the merged mesh from every slab's owned
+    counts (verts3_owned, case3_owned, tris_owned), slabs in z order: its 3D
+    points follow the lower slabs' 3D points, its edge points follow all 3D
+    points and the lower slabs' edge points, its triangles the lower slabs'
+    triangles.  Also the merged totals."""
+    v3 = [int(c[0]) for c in counts]
+    c3 = [int(c[1]) for c in counts]
+    tr = [int(c[2]) for c in counts]
+    V = sum(v3)
+    return dict(verts3_base=sum(v3[:rank]), case3_base=V + sum(c3[:rank]), tris_base=sum(tr[:rank]),
+                n_verts=V + sum(c3), n_tris=sum(tr))
+
+
 class MeshC(C.Structure):
     _fields_ = [("n_verts", C.c_int64), ("n_tris", C.c_int64), ("d_verts", C.c_void_p), ("d_tris", C.c_void_p),
                 ("stats", Stats)]
@@ -109,7 +139,7 @@ def launch_total() -> int:
 EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
            "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_compact_edges_noalloc", "odc_status_str",
            "odc_last_error", "odc_server_create", "odc_server_destroy", "odc_submit", "odc_poll", "odc_result_release",
-           "odc_server_clock", "odc_mesh_quality"]
+           "odc_server_clock", "odc_mesh_quality", "odc_extract_slab", "odc_slab_place", "odc_extract_slabbed"]
 
 _lib = None
 
@@ -127,6 +157,12 @@ def load(path: str = LIB_PATH):
     lib.odc_ctx_destroy.argtypes = [P]
     lib.odc_extract.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), P, C.POINTER(MeshC)]
     lib.odc_mesh_copy.argtypes = [P, C.POINTER(MeshC), P, P, C.c_int]
+    lib.odc_extract_slab.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.POINTER(SlabC), P,
+                                     C.POINTER(MeshC), C.POINTER(SlabInfoC)]
+    lib.odc_slab_place.argtypes = [P, C.POINTER(MeshC), C.POINTER(SlabInfoC), C.c_int64, C.c_int64, C.c_int64, P, P,
+                                   P]
+    lib.odc_extract_slabbed.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.c_int32,
+                                        C.c_int32, P, C.POINTER(MeshC)]
     lib.odc_mesh_release.argtypes = [P, C.POINTER(MeshC)]
     lib.odc_debug_copy.argtypes = [P, C.c_int, P, C.c_size_t, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
     lib.odc_eval_points.argtypes = [P, C.POINTER(Source), P, C.c_int64, C.c_float, C.c_int, P, P]
@@ -340,6 +376,37 @@ class Context:
         m = MeshC()
         _check(_lib.odc_extract(self.h, C.byref(holder.src), C.byref(g), C.byref(p),
                                 stream if stream else None, C.byref(m)))
+        return Mesh(self, m)
+
+    def extract_slab(self, src, grid: I.Grid, z0: int, z1: int, halo: int = 2, steps_1d=15, stream=None,
+                     precision=None, band=None, split=True, split_zmargin=0.0, **kw):
+        """odc_extract_slab: the slab extraction's mesh and its owned ranges."""
+        holder = _SourceHolder(src, precision, band, split, split_zmargin)
+        g = make_grid(grid)
+        p = make_params(steps_1d=steps_1d, **kw)
+        sl = SlabC(z0, z1, halo)
+        m = MeshC()
+        info = SlabInfoC()
+        _check(_lib.odc_extract_slab(self.h, C.byref(holder.src), C.byref(g), C.byref(p), C.byref(sl),
+                                     stream if stream else None, C.byref(m), C.byref(info)))
+        return Mesh(self, m), info
+
+    def slab_place(self, mesh, info, verts3_base: int, case3_base: int, tris_base: int, d_verts: int, d_tris: int,
+                   stream=None):
+        """odc_slab_place: the owned part of the latest slab extraction into a
+        whole-grid mesh in device memory (caller-owned pointers)."""
+        _check(_lib.odc_slab_place(self.h, C.byref(mesh.c), C.byref(info), verts3_base, case3_base, tris_base,
+                                   d_verts, d_tris, stream if stream else None))
+
+    def extract_slabbed(self, src, grid: I.Grid, n_slabs: int, halo: int = 2, steps_1d=15, stream=None,
+                        precision=None, band=None, split=True, split_zmargin=0.0, **kw) -> Mesh:
+        """odc_extract_slabbed: the grid in n_slabs z-slabs on this context, merged."""
+        holder = _SourceHolder(src, precision, band, split, split_zmargin)
+        g = make_grid(grid)
+        p = make_params(steps_1d=steps_1d, **kw)
+        m = MeshC()
+        _check(_lib.odc_extract_slabbed(self.h, C.byref(holder.src), C.byref(g), C.byref(p), n_slabs, halo,
+                                        stream if stream else None, C.byref(m)))
         return Mesh(self, m)
 
     def face_points(self) -> np.ndarray:
