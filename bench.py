@@ -196,8 +196,33 @@ def resolution_scaling(odc, I, resolutions=(128, 256, 512, 1024)):
             m = ctx.extract(None, g, steps_1d=15)
             t = m.stats["stage_ms"][7]
             rows[f"{r}^3"] = {"device_ms": round(t, 1), "mcells_per_s": r ** 3 / (t * 1e-3) / 1e6,
-                              "edges": m.stats["n_edges"], "tris": m.n_tris}
+                              "edges": m.stats["n_edges"], "tris": m.n_tris,
+                              "device_gb_held": round(ctx.device_bytes() / 1e9, 2)}
     return rows
+
+
+def slab_scaling(odc, I, r: int = 1024, n_slabs: int = 8):
+    """The same 1024^3 envelope-MLP extraction in z-slabs, one after the
+    other on one context (odc_extract_slabbed): the merged mesh equals the
+    whole-grid one byte for byte, and the device memory held is one slab's
+    arenas plus the merged mesh.  Wall time around the call (slab
+    orchestration and placement included)."""
+    import time
+    import torch
+    mlp = I.envelope_mlp(0)
+    g = I.cube_grid(r)
+    with odc.Context(0) as ctx:
+        ctx.upload(mlp, precision=odc.PREC_BF16)
+        ctx.extract_slabbed(None, g, n_slabs, halo=2, steps_1d=15)   # arenas sized for one slab
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = ctx.extract_slabbed(None, g, n_slabs, halo=2, steps_1d=15)
+        wall = time.perf_counter() - t0
+        held = ctx.device_bytes()
+    return {f"{r}^3 in {n_slabs} slabs (halo 2)": {"wall_ms": round(wall * 1e3, 1),
+                                                  "mcells_per_s": r ** 3 / wall / 1e6,
+                                                  "device_ms_summed": round(m.stats["stage_ms"][7], 1),
+                                                  "tris": m.n_tris, "device_gb_held": round(held / 1e9, 2)}}
 
 
 def batch_bench(odc, I, n_shapes: int = 64, slots: int = 8, seed: int = 9):
@@ -374,6 +399,9 @@ def main():
     ap.add_argument("--no-ablation", action="store_true", help="skip the ablation table (Sec. 6.3 variants)")
     ap.add_argument("--csg-res", type=int, default=0,
                     help="profile run: only the CSG pipeline at this resolution (prints its own JSON line)")
+    ap.add_argument("--slab-res", type=int, default=0,
+                    help="only the envelope MLP at this resolution in --slab-count z-slabs (prints its own JSON line)")
+    ap.add_argument("--slab-count", type=int, default=8)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -386,6 +414,14 @@ def main():
     args.cpu_cells = args.cpu_cells or 40
     if args.csg_res:
         csg_run(args)
+        return
+    if args.slab_res:
+        from paper_2409_13418_gb300 import build, inputs as I, odc
+        build.build()
+        odc.load()
+        print(json.dumps({"workload": f"envelope MLP occupancy, {args.slab_res}^3 cells, k=15, bf16 band 0.03, "
+                                      f"z-slabs on one GPU",
+                          "rows": slab_scaling(odc, I, args.slab_res, args.slab_count)}), flush=True)
         return
 
     import numpy as np
@@ -533,6 +569,7 @@ def main():
             line["voxel"] = voxel_bench(odc, I)
             line["batched"] = batch_bench(odc, I)
             line["resolution_scaling"] = resolution_scaling(odc, I)
+            line["resolution_scaling"].update(slab_scaling(odc, I))
         if world == 1 and args.serve_seconds > 0:
             ctx.close()
             from paper_2409_13418_gb300 import inputs as I

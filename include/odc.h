@@ -238,6 +238,10 @@ typedef struct {
  * ``mem_budget`` bytes (0 = no limit).  *out is NULL on failure. */
 odc_status odc_ctx_create(int device, size_t mem_budget, odc_ctx** out);
 
+/* Device bytes the context holds now (arenas, merged slab mesh, network
+ * weights and scratch), for memory accounting. */
+odc_status odc_ctx_memory(odc_ctx* ctx, size_t* bytes);
+
 /* Destroy a context and free its device memory.  NULL is accepted. */
 odc_status odc_ctx_destroy(odc_ctx* ctx);
 
@@ -259,10 +263,21 @@ odc_status odc_extract(odc_ctx* ctx, const odc_source* src, const odc_grid* grid
  * fix and the face searches of its boundary cells.  The whole grid's mesh
  * numbers 3D points in cell order, then edge points in edge order, and
  * triangles in edge order, so a slab's owned part is three contiguous
- * ranges and the merged mesh equals the whole-grid mesh byte for byte. */
+ * ranges and the merged mesh equals the whole-grid mesh byte for byte.  The
+ * manifold fix (A.1.1) is the one non-local step: its flips chain from cell
+ * to cell, round by round, across any slab plane.  So the slabs take the
+ * whole grid's flips, computed once from the whole grid's label words:
+ * odc_grid_labels fills the label words of a range of vertex layers (each
+ * slab, or each rank, its own), odc_manifold_flips runs the fix over the
+ * complete words.  Label words: W = (res[0] + 32) / 32 words per row,
+ * word (w, y, z) at (z (res[1] + 1) + y) W + w, bit x % 32 of word x / 32
+ * set where the vertex is inside; flip words: three such planes sets
+ * (one per face axis), 3 W (res[1] + 1) (res[2] + 1) words. */
 typedef struct {
     int32_t z0, z1;              /* owned cell layers [z0, z1), 0 <= z0 < z1 <= res[2] */
     int32_t halo;                /* extra cell layers each side, >= 1 */
+    const uint32_t* flips;       /* device: the whole grid's flip words (odc_manifold_flips), or NULL: the
+                                    slab runs the manifold fix on its own window (see fix_near_plane) */
 } odc_slab;
 
 typedef struct {
@@ -273,6 +288,9 @@ typedef struct {
     int64_t case3_owned;         /* edge points of the owned edges */
     int64_t tris_before;         /* triangles of halo edges before the owned edges */
     int64_t tris_owned;          /* triangles of the owned edges */
+    int64_t fix_near_plane;      /* without whole-grid flips: manifold-fix marks within two layers of an
+                                    inner slab plane (the owned part may then differ from the whole
+                                    grid's); 0 with whole-grid flips */
 } odc_slab_info;
 
 /* Extract one slab of ``grid`` (same source, parameters and stream rules
@@ -284,6 +302,21 @@ typedef struct {
  * otherwise. */
 odc_status odc_extract_slab(odc_ctx* ctx, const odc_source* src, const odc_grid* grid, const odc_params* params,
                             const odc_slab* slab, void* cuda_stream, odc_mesh* out, odc_slab_info* info);
+
+/* Label words of the vertex layers [z0, z1] of ``grid`` (the grid stage of
+ * the path on that window) into d_bits, the whole grid's label words
+ * (device, caller-owned, layout above); layers outside are not touched.
+ * Synchronous. */
+odc_status odc_grid_labels(odc_ctx* ctx, const odc_source* src, const odc_grid* grid, const odc_params* params,
+                           int32_t z0, int32_t z1, uint32_t* d_bits, void* cuda_stream);
+
+/* The manifold fix (A.1.1) of the whole grid from its complete label words:
+ * the ambiguous faces are gathered in ``n_chunks`` windows of layers, then
+ * rounds of mark-all / flip-all run over all of them; d_flips (device,
+ * caller-owned) receives the flip words.  *n_flips = faces flipped.
+ * Synchronous. */
+odc_status odc_manifold_flips(odc_ctx* ctx, const odc_grid* grid, const uint32_t* d_bits, uint32_t* d_flips,
+                              int32_t n_chunks, void* cuda_stream, int64_t* n_flips);
 
 /* Place the owned part of a slab extraction (``mesh``, ``info`` from
  * odc_extract_slab on this context, before any other extract) into the
@@ -298,8 +331,10 @@ odc_status odc_slab_place(odc_ctx* ctx, const odc_mesh* mesh, const odc_slab_inf
                           void* cuda_stream);
 
 /* The whole grid in ``n_slabs`` slabs of near-equal depth, one after the
- * other on this context (peak device memory: one slab's), merged into one
- * mesh in context memory (valid until the next extract).  The result equals
+ * other on this context (peak device memory: one slab's arenas plus the
+ * whole grid's label and flip words), the manifold fix taken from the
+ * whole grid, merged into one mesh in context memory (valid until the next
+ * extract).  The result equals
  * odc_extract's mesh on the same grid byte for byte; stats are summed over
  * the slabs (element counts include halo layers).  Grid limits as for
  * odc_extract_slab. */

@@ -88,6 +88,14 @@ struct odc_ctx {
     float3* sc3 = nullptr;      // edge points, staged until the 3D point count is known
     unsigned long long* sinfo = nullptr;   // slab range counters (device, 8)
     size_t sv_cap = 0, st_cap = 0, sc3_cap = 0;
+    // whole-grid topology of a slabbed extraction: label words, flip words,
+    // ambiguous faces
+    uint32_t* gbits = nullptr;
+    uint32_t* gflips = nullptr;
+    uint32_t* gfaces = nullptr;
+    size_t gb_cap = 0, gfl_cap = 0, gf_cap = 0;
+    size_t nga = 0;
+    size_t extra_bytes() const { return (sv_cap + st_cap + sc3_cap) * 12 + (gb_cap + gfl_cap + gf_cap) * 4; }
 };
 
 // Grow an arena (stream-ordered: the old block is freed and the new one
@@ -98,7 +106,7 @@ static odc_status arena_ensure(odc_ctx* c, Arena& a, size_t need, cudaStream_t s
         a.reset();
         return ODC_OK;
     }
-    size_t others = c->A.cap + c->B.cap + c->S.cap - a.cap + c->sv_cap * 12 + c->st_cap * 12 + c->sc3_cap * 12;
+    size_t others = c->A.cap + c->B.cap + c->S.cap - a.cap + c->extra_bytes();
     size_t want = std::max(need, a.cap + a.cap / 4);
     if (c->budget && others + want > c->budget) {
         want = need;
@@ -126,7 +134,7 @@ template <typename T>
 static odc_status grow(odc_ctx* c, T** p, size_t* cap, size_t need, cudaStream_t st) {
     if (need <= *cap) return ODC_OK;
     size_t want = std::max(need, *cap + *cap / 2);
-    size_t others = c->A.cap + c->B.cap + c->S.cap + (c->sv_cap + c->st_cap + c->sc3_cap - *cap) * 12;
+    size_t others = c->A.cap + c->B.cap + c->S.cap + c->extra_bytes() - *cap * sizeof(T);
     if (c->budget && others + want * sizeof(T) > c->budget) {
         want = need;
         if (others + want * sizeof(T) > c->budget)
@@ -194,7 +202,8 @@ odc_status odc_ctx_destroy(odc_ctx* c) {
     mlp_destroy(c->mlp);
     for (Arena* a : {&c->A, &c->B, &c->S})
         if (a->base) cudaFree(a->base);
-    for (void* p : {(void*)c->sv, (void*)c->stri, (void*)c->sc3, (void*)c->sinfo})
+    for (void* p : {(void*)c->sv, (void*)c->stri, (void*)c->sc3, (void*)c->sinfo, (void*)c->gbits, (void*)c->gflips,
+                    (void*)c->gfaces})
         if (p) cudaFree(p);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -338,7 +347,9 @@ static odc_status check_params(const odc_params* prm) {
 // The whole path on the grid whose vertex coordinates per axis are Xh[a]
 // (Xh[a].size() - 1 cells); arguments already checked.
 static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vector<float> (&Xh)[3],
-                               const odc_params* prm, cudaStream_t st, odc_mesh* out) {
+                               const odc_params* prm, cudaStream_t st, odc_mesh* out,
+                               const int* watch = nullptr, unsigned long long* watch_cnt = nullptr,
+                               const uint32_t* ext_flips = nullptr, int ext_z0 = 0, int ext_nz = 0) {
     odc_status s = ODC_OK;
     std::memset(out, 0, sizeof(*out));
 
@@ -460,16 +471,25 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
     ODC_CK(cudaGetLastError());
     ODC_CK(cudaEventRecord(c->ev[2], st));
 
-    // ---- a3: manifold fix rounds, cycles, 3D point ids
+    // ---- a3: manifold fix rounds (or the whole grid's flips, for a window
+    // of its vertex layers), cycles, 3D point ids
     int rounds = 0;
     uint32_t nflip = 0;
-    for (;;) {
+    if (ext_flips) {
+        const size_t plane = (size_t)g.nv[1] * g.W;
+        for (int a = 0; a < 3; ++a)
+            ODC_CK(cudaMemcpyAsync(flips + (size_t)a * g.nv[2] * plane,
+                                   ext_flips + ((size_t)a * (ext_nz + 1) + ext_z0) * plane, g.nv[2] * plane * 4,
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+    for (; !ext_flips;) {
         ODC_CK(cudaMemsetAsync(dcnt + 8, 0, 4, st));
         launch_manifold_mark(g, bits, flips, faces, slots, F, mark, dcnt + 8, st);
         ODC_CK(cudaMemcpyAsync(c->h_cnt + 8, dcnt + 8, 4, cudaMemcpyDeviceToHost, st));
         ODC_CK(cudaStreamSynchronize(st));
         uint32_t marked = c->h_cnt[8];
         if (!marked) break;
+        if (watch) launch_slab_watch(g, faces, mark, F, watch, watch_cnt, st);
         launch_manifold_apply(g, flips, faces, mark, F, st);
         nflip += marked;   // faces flipped (each flip round toggles distinct faces)
         if (++rounds > 64) return fail(ODC_ERR_INTERNAL, "manifold fix did not converge");
@@ -627,14 +647,21 @@ static odc_status slab_extract(odc_ctx* c, const odc_source* src, const odc_grid
     std::vector<float> Xh[3], Xz;
     for (int a = 0; a < 3; ++a) grid_coords(grid, a, Xh[a]);
     Xh[2] = std::vector<float>(Xh[2].begin() + za, Xh[2].begin() + zb + 1);   // the whole grid's z coordinates
-    odc_status s = extract_impl(c, src, Xh, prm, st, out);
-    if (s != ODC_OK) return s;
     if (!c->sinfo) ODC_CK(cudaMalloc((void**)&c->sinfo, 8 * sizeof(unsigned long long)));
+    ODC_CK(cudaMemsetAsync(c->sinfo + 6, 0, sizeof(unsigned long long), st));
+    // with the whole grid's flips the window takes them; otherwise it runs the
+    // fix itself and counts marks within two layers of an inner slab plane
+    int watch[4] = {0, 0, 0, 0};
+    if (sl->z0 > 0) { watch[0] = std::max(0, sl->z0 - 2 - za); watch[1] = sl->z0 + 2 - za; }
+    if (sl->z1 < nz) { watch[2] = sl->z1 - 2 - za; watch[3] = sl->z1 + 2 - za; }
+    odc_status s = sl->flips ? extract_impl(c, src, Xh, prm, st, out, nullptr, nullptr, sl->flips, za, nz)
+                             : extract_impl(c, src, Xh, prm, st, out, watch, c->sinfo + 6);
+    if (s != ODC_OK) return s;
     const uint32_t n01 = (uint32_t)grid->res[0] * (uint32_t)grid->res[1];
     const uint32_t zl0 = (uint32_t)(sl->z0 - za), zl1 = (uint32_t)(sl->z1 - za);
     launch_slab_ranges(c->cells, c->C, c->vbase, c->V3, c->edges, c->E, c->qoff, c->N3, c->NT, n01 * zl0, n01 * zl1,
                        (uint32_t)(3ull * nv01 * zl0), (uint32_t)(3ull * nv01 * zl1), c->sinfo, st);
-    unsigned long long h[6];
+    unsigned long long h[7];
     ODC_CK(cudaMemcpyAsync(h, c->sinfo, sizeof(h), cudaMemcpyDeviceToHost, st));
     ODC_CK(cudaStreamSynchronize(st));
     ODC_CK(cudaGetLastError());
@@ -645,6 +672,7 @@ static odc_status slab_extract(odc_ctx* c, const odc_source* src, const odc_grid
     info->case3_owned = (int64_t)(h[3] - h[2]);
     info->tris_before = (int64_t)h[4];
     info->tris_owned = (int64_t)(h[5] - h[4]);
+    info->fix_near_plane = (int64_t)h[6];
     return ODC_OK;
 }
 
@@ -662,6 +690,138 @@ static odc_status slab_place(odc_ctx* c, const odc_mesh* m, const odc_slab_info*
     launch_slab_tris((const int3*)m->d_tris + in->tris_before, in->tris_owned, in->verts3_local,
                      verts3_base - in->verts3_before, in->case3_before, case3_base, dt + tris_base, st);
     ODC_CK(cudaGetLastError());
+    return ODC_OK;
+}
+
+// Label words of the whole grid's vertex layers [z0, z1] (grid-order word
+// layout, W words per row) into bits_g: the grid stage alone on that window.
+static odc_status labels_into(odc_ctx* c, const odc_grid* grid, const odc_params* prm, int z0, int z1,
+                              uint32_t* bits_g, cudaStream_t st) {
+    std::vector<float> Xh[3];
+    for (int a = 0; a < 3; ++a) grid_coords(grid, a, Xh[a]);
+    Xh[2] = std::vector<float>(Xh[2].begin() + z0, Xh[2].begin() + z1 + 1);
+    GridDev g{};
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = (int)Xh[a].size() - 1;
+        g.nv[a] = (int)Xh[a].size();
+    }
+    g.W = (g.nv[0] + 31) / 32;
+    const size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
+    const size_t nX = Xh[0].size() + Xh[1].size() + Xh[2].size();
+    odc_status s = arena_ensure(c, c->A, al(nX * 4), st);
+    if (s != ODC_OK) return s;
+    float* dX = (float*)c->A.take(nX * 4);
+    g.X[0] = dX;
+    g.X[1] = dX + Xh[0].size();
+    g.X[2] = dX + Xh[0].size() + Xh[1].size();
+    for (int a = 0; a < 3; ++a)
+        ODC_CK(cudaMemcpyAsync((void*)g.X[a], Xh[a].data(), Xh[a].size() * 4, cudaMemcpyHostToDevice, st));
+    uint32_t* bits = bits_g + (size_t)z0 * g.nv[1] * g.W;   // rows of layers z0.. are contiguous
+    const int kind = c->res_kind;
+    if (kind == ODC_SRC_CSG) {
+        launch_csg_grid(g, c->res_prims, c->res_cull, c->res_nprims, bits, st);
+    } else if (kind == ODC_SRC_VOXEL) {
+        VoxDev vox = c->res_vox;
+        vox.iso = prm->iso;
+        launch_vox_grid(g, vox, bits, st);
+    } else {
+        int64_t nq = 0;
+        s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &g_err);
+        if (s != ODC_OK) return s;
+    }
+    (void)nw;
+    ODC_CK(cudaGetLastError());
+    return ODC_OK;
+}
+
+// Ambiguous faces (second-segment entries, the only ones the manifold fix
+// marks) of vertex layers [z0, z1) -- and of layer z1 when it is the grid's
+// last -- as whole-grid face ids appended to c->gfaces.
+static odc_status amb_faces_into(odc_ctx* c, const odc_grid* grid, const uint32_t* bits_g, int z0, int z1,
+                                 cudaStream_t st) {
+    GridDev g{};
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = a < 2 ? grid->res[a] : z1 - z0;
+        g.nv[a] = g.n[a] + 1;
+    }
+    g.W = (g.nv[0] + 31) / 32;
+    const size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
+    const uint32_t* bits = bits_g + (size_t)z0 * g.nv[1] * g.W;
+    size_t stmp = scan_tmp_elems(nw);
+    odc_status s = arena_ensure(c, c->A, al(nw * sizeof(WordInfo)) + 6 * al(nw * 4) + al(stmp * 8) + al(64 * 8), st);
+    if (s != ODC_OK) return s;
+    WordInfo* wi = (WordInfo*)c->A.take(nw * sizeof(WordInfo));
+    uint32_t* ce = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* cf = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* cc = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* ebase = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* fbase = (uint32_t*)c->A.take(nw * 4);
+    uint32_t* cbase = (uint32_t*)c->A.take(nw * 4);
+    void* tmp = c->A.take(stmp * 8);
+    uint32_t* dcnt = (uint32_t*)c->A.take(64 * 8);
+    ODC_CK(cudaMemsetAsync(dcnt, 0, 64 * 8, st));
+    launch_classify(g, bits, wi, ce, cf, cc, st);
+    exclusive_scan<uint32_t>(ce, ebase, nw, (uint32_t*)tmp, dcnt + 0, st);
+    exclusive_scan<uint32_t>(cf, fbase, nw, (uint32_t*)tmp, dcnt + 1, st);
+    exclusive_scan<uint32_t>(cc, cbase, nw, (uint32_t*)tmp, dcnt + 2, st);
+    ODC_CK(cudaMemcpyAsync(c->h_cnt, dcnt, 3 * 4, cudaMemcpyDeviceToHost, st));
+    ODC_CK(cudaStreamSynchronize(st));
+    const uint32_t E = c->h_cnt[0], F = c->h_cnt[1], C = c->h_cnt[2];
+    s = arena_ensure(c, c->B, al(E * 4ull) + al(F * 4ull) + al(F) + al(C * 4ull) + al(C) + 1024, st);
+    if (s != ODC_OK) return s;
+    uint32_t* edges = (uint32_t*)c->B.take(E * 4ull);
+    uint32_t* faces = (uint32_t*)c->B.take(F * 4ull);
+    uint8_t* slots = (uint8_t*)c->B.take(F);
+    uint32_t* cells = (uint32_t*)c->B.take(C * 4ull);
+    uint8_t* configs = (uint8_t*)c->B.take(C);
+    launch_emit(g, bits, wi, ebase, fbase, cbase, edges, faces, slots, cells, configs, st);
+    // keep layers < z1 - z0 (the next window owns layer z1) unless this is the last window
+    const bool last = z1 == grid->res[2];
+    const uint32_t limit = last ? 0xffffffffu : (uint32_t)(3ull * g.nv[0] * g.nv[1] * (uint32_t)(z1 - z0));
+    const uint32_t offset = (uint32_t)(3ull * g.nv[0] * g.nv[1] * (uint32_t)z0);
+    s = grow(c, &c->gfaces, &c->gf_cap, (size_t)c->nga + F, st);
+    if (s != ODC_OK) return s;
+    launch_amb_select(faces, slots, F, limit, offset, c->gfaces, c->nga, (uint32_t*)(dcnt + 32), st);
+    ODC_CK(cudaMemcpyAsync(c->h_cnt + 32, dcnt + 32, 4, cudaMemcpyDeviceToHost, st));
+    ODC_CK(cudaStreamSynchronize(st));
+    ODC_CK(cudaGetLastError());
+    c->nga += c->h_cnt[32];
+    return ODC_OK;
+}
+
+// The manifold fix of the whole grid from its label words: rounds of mark
+// all, flip all over the ambiguous faces (as in the extraction), into flips_g.
+static odc_status global_fix(odc_ctx* c, const odc_grid* grid, const uint32_t* bits_g, uint32_t* flips_g,
+                             cudaStream_t st, int64_t* n_flips) {
+    GridDev g{};
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = grid->res[a];
+        g.nv[a] = g.n[a] + 1;
+    }
+    g.W = (g.nv[0] + 31) / 32;
+    const size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
+    ODC_CK(cudaMemsetAsync(flips_g, 0, 3 * nw * 4, st));
+    const uint32_t NA = (uint32_t)c->nga;
+    odc_status s = arena_ensure(c, c->B, 2 * al(NA) + 1024, st);
+    if (s != ODC_OK) return s;
+    uint8_t* slots = (uint8_t*)c->B.take(NA);
+    uint8_t* mark = (uint8_t*)c->B.take(NA);
+    uint32_t* cnt = (uint32_t*)c->B.take(64);
+    if (NA) ODC_CK(cudaMemsetAsync(slots, 1, NA, st));
+    int64_t total = 0;
+    for (int rounds = 0; NA; ++rounds) {
+        ODC_CK(cudaMemsetAsync(cnt, 0, 4, st));
+        launch_manifold_mark(g, bits_g, flips_g, c->gfaces, slots, NA, mark, cnt, st);
+        ODC_CK(cudaMemcpyAsync(c->h_cnt + 8, cnt, 4, cudaMemcpyDeviceToHost, st));
+        ODC_CK(cudaStreamSynchronize(st));
+        const uint32_t marked = c->h_cnt[8];
+        if (!marked) break;
+        launch_manifold_apply(g, flips_g, c->gfaces, mark, NA, st);
+        total += marked;
+        if (rounds > 64) return fail(ODC_ERR_INTERNAL, "manifold fix did not converge");
+    }
+    ODC_CK(cudaGetLastError());
+    if (n_flips) *n_flips = total;
     return ODC_OK;
 }
 
@@ -705,14 +865,35 @@ odc_status odc_extract_slabbed(odc_ctx* c, const odc_source* src, const odc_grid
     constexpr int64_t kMark = 1ll << 30;
     odc_source resident{};
     resident.kind = ODC_SRC_RESIDENT;
+    if (src->kind != ODC_SRC_RESIDENT) {
+        s = upload_source(c, src, st);
+        if (s != ODC_OK) return s;
+    } else if (c->res_kind < 0) {
+        return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
+    }
+    auto zcut = [&](int i) { return (int32_t)((int64_t)grid->res[2] * i / n_slabs); };
+    // ---- whole-grid topology: label words slab by slab, the ambiguous
+    // faces, and one manifold fix over them (its flips chain across slabs)
+    const size_t W = (size_t)(grid->res[0] + 32) / 32;
+    const size_t nwg = W * (grid->res[1] + 1) * (size_t)(grid->res[2] + 1);
+    if ((s = grow(c, &c->gbits, &c->gb_cap, nwg, st)) != ODC_OK ||
+        (s = grow(c, &c->gflips, &c->gfl_cap, 3 * nwg, st)) != ODC_OK)
+        return s;
+    if (!c->sinfo) ODC_CK(cudaMalloc((void**)&c->sinfo, 8 * sizeof(unsigned long long)));
+    for (int i = 0; i < n_slabs; ++i)
+        if ((s = labels_into(c, grid, prm, zcut(i), zcut(i + 1), c->gbits, st)) != ODC_OK) return s;
+    c->nga = 0;
+    for (int i = 0; i < n_slabs; ++i)
+        if ((s = amb_faces_into(c, grid, c->gbits, zcut(i), zcut(i + 1), st)) != ODC_OK) return s;
+    int64_t gflip = 0;
+    if ((s = global_fix(c, grid, c->gbits, c->gflips, st, &gflip)) != ODC_OK) return s;
     int64_t V = 0, N = 0, T = 0;
     odc_stats sum{};
     for (int i = 0; i < n_slabs; ++i) {
-        odc_slab sl{(int32_t)((int64_t)grid->res[2] * i / n_slabs), (int32_t)((int64_t)grid->res[2] * (i + 1) / n_slabs),
-                    halo};
+        odc_slab sl{zcut(i), zcut(i + 1), halo, c->gflips};
         odc_mesh m;
         odc_slab_info in;
-        s = slab_extract(c, i == 0 ? src : &resident, grid, prm, &sl, st, &m, &in);
+        s = slab_extract(c, &resident, grid, prm, &sl, st, &m, &in);
         if (s != ODC_OK) return s;
         if (V + in.verts3_owned >= kMark || N + in.case3_owned >= kMark)
             return fail(ODC_ERR_INVALID_ARG, "merged mesh exceeds 2^30 vertices");
@@ -748,7 +929,58 @@ odc_status odc_extract_slabbed(odc_ctx* c, const odc_source* src, const odc_grid
     out->d_verts = (const float*)c->sv;
     out->d_tris = (const int32_t*)c->stri;
     out->stats = sum;
+    out->stats.n_flips = gflip;
     out->stats.n_launches += 1;
+    return ODC_OK;
+}
+
+odc_status odc_grid_labels(odc_ctx* c, const odc_source* src, const odc_grid* grid, const odc_params* prm, int32_t z0,
+                           int32_t z1, uint32_t* d_bits, void* cuda_stream) {
+    if (!c || !grid || !prm || !d_bits) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    odc_status s = check_source(src);
+    if (s == ODC_OK) s = check_slab_grid(grid);
+    if (s == ODC_OK) s = check_params(prm);
+    if (s != ODC_OK) return s;
+    if (z0 < 0 || z1 < z0 || z1 > grid->res[2]) return fail(ODC_ERR_INVALID_ARG, "need 0 <= z0 <= z1 <= res[2]");
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    if (src->kind != ODC_SRC_RESIDENT) {
+        s = upload_source(c, src, st);
+        if (s != ODC_OK) return s;
+    } else if (c->res_kind < 0) {
+        return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
+    }
+    s = labels_into(c, grid, prm, z0, z1, d_bits, st);
+    if (s != ODC_OK) return s;
+    ODC_CK(cudaStreamSynchronize(st));
+    return ODC_OK;
+}
+
+odc_status odc_manifold_flips(odc_ctx* c, const odc_grid* grid, const uint32_t* d_bits, uint32_t* d_flips,
+                              int32_t n_chunks, void* cuda_stream, int64_t* n_flips) {
+    if (!c || !grid || !d_bits || !d_flips) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    odc_status s = check_slab_grid(grid);
+    if (s != ODC_OK) return s;
+    if (n_chunks < 1 || n_chunks > grid->res[2]) return fail(ODC_ERR_INVALID_ARG, "n_chunks out of [1, res[2]]");
+    ODC_CK(cudaSetDevice(c->device));
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->own;
+    c->nga = 0;
+    for (int i = 0; i < n_chunks; ++i) {
+        s = amb_faces_into(c, grid, d_bits, (int32_t)((int64_t)grid->res[2] * i / n_chunks),
+                           (int32_t)((int64_t)grid->res[2] * (i + 1) / n_chunks), st);
+        if (s != ODC_OK) return s;
+    }
+    int64_t nf = 0;
+    s = global_fix(c, grid, d_bits, d_flips, st, &nf);
+    if (s != ODC_OK) return s;
+    ODC_CK(cudaStreamSynchronize(st));
+    if (n_flips) *n_flips = nf;
+    return ODC_OK;
+}
+
+odc_status odc_ctx_memory(odc_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    *bytes = c->A.cap + c->B.cap + c->S.cap + c->extra_bytes() + mlp_device_bytes(c->mlp);
     return ODC_OK;
 }
 

@@ -86,6 +86,10 @@ void launch_slab_ranges(const uint32_t* cells, uint32_t C, const uint32_t* vbase
 void launch_slab_tris(const int3* src, int64_t n, int64_t v3, int64_t vshift, int64_t c3skip, int64_t c3dst,
                       int3* dst, cudaStream_t st);
 void launch_slab_fix(int3* t, int64_t n, int mark, int v3, cudaStream_t st);
+void launch_amb_select(const uint32_t* faces, const uint8_t* slots, uint32_t nf, uint32_t limit, uint32_t offset,
+                       uint32_t* out, size_t base, uint32_t* count, cudaStream_t st);
+void launch_slab_watch(const GridDev& g, const uint32_t* faces, const uint8_t* mark, uint32_t nf, const int* bands,
+                       unsigned long long* count, cudaStream_t st);
 
 // quality.cu (Sec. 6.1 metrics; mlp may be null for a CSG source)
 struct MlpState;

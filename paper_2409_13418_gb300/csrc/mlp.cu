@@ -132,6 +132,13 @@ void mlp_destroy(MlpState* st) {
     delete st;
 }
 
+size_t mlp_device_bytes(const MlpState* st) {
+    if (!st) return 0;
+    size_t b = st->wblob ? sizeof(float) * kBlobFloats : 0;
+    for (int i = 0; i < kScratchSlots; ++i) b += st->scr_cap[i];
+    return b + mlp_tc_device_bytes(st);
+}
+
 static odc_status fp32_kernel_setup(std::string* err);
 
 // Upload weights: FP32 transposed copies for the SIMT path (W^T [in][out]),

@@ -20,6 +20,8 @@ struct MlpState;
 odc_status mlp_check(const odc_mlp* m, std::string* err);
 odc_status mlp_prepare(MlpState** st, const odc_mlp* m, cudaStream_t s, std::string* err);
 void mlp_destroy(MlpState* st);
+// Device bytes held by the network state (weights, operand tiles, scratch).
+size_t mlp_device_bytes(const MlpState* st);
 
 // Device scratch owned by the MLP state (grows on demand, never shrinks).
 odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::string* err);

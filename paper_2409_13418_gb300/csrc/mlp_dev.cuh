@@ -87,6 +87,7 @@ odc_status mlp_tc_prepare(MlpState* st, const float* host_blob, cudaStream_t s, 
 struct QuerySrc;
 odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 void mlp_tc_destroy(MlpState* st);
+size_t mlp_tc_device_bytes(const MlpState* st);
 // ODC_ERR_TIMEOUT if a tensor-core launch since the last check hit a bounded wait.
 odc_status mlp_tc_check(MlpState* st, cudaStream_t s, std::string* err);
 // Split-BF16 network (three BF16 products per layer, FP32 accumulation).

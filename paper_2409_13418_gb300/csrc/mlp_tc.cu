@@ -1045,6 +1045,13 @@ odc_status mlp_tc_check(MlpState* st, cudaStream_t s, std::string* err) {
     return ODC_OK;
 }
 
+size_t mlp_tc_device_bytes(const MlpState* st) {
+    const MlpTc* T = st ? st->tc : nullptr;
+    if (!T || !T->w) return 0;
+    const size_t total = (size_t)kH * (2 * kNF + 3 * kH);
+    return total * sizeof(__nv_bfloat16) + 2 * total * sizeof(__half) + sizeof(int);
+}
+
 void mlp_tc_destroy(MlpState* st) {
     if (!st || !st->tc) return;
     if (st->tc->w) cudaFree(st->tc->w);

@@ -13,8 +13,13 @@
 // extraction, and the whole grid's mesh numbers them the same way: 3D
 // points in cell order, then edge points in edge order, triangles in edge
 // order.  Placing each slab's ranges at offsets from a prefix sum of the
-// slabs' counts therefore gives the whole grid's mesh byte for byte.
+// slabs' counts therefore gives the whole grid's mesh byte for byte -- as
+// long as the manifold fix (A.1.1), whose flips can chain from cell to cell
+// round by round, marks no face within two layers of a slab plane: then no
+// chain crosses a plane and each slab's fix is the whole grid's.  The
+// extraction counts such marks so that the caller can refuse the merge.
 #include "kernels.h"
+#include "odc_device.cuh"
 
 namespace odc {
 
@@ -75,7 +80,44 @@ __global__ void k_slab_fix(int3* __restrict__ t, int64_t n, int mark, int v3) {
     t[i] = v;
 }
 
+// marked faces whose vertex layer lies in [b0, b1) or [b2, b3) (local z)
+__global__ void k_slab_watch(GridDev g, const uint32_t* __restrict__ faces, const uint8_t* __restrict__ mark,
+                             uint32_t nf, int b0, int b1, int b2, int b3, unsigned long long* __restrict__ count) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf || !mark[i]) return;
+    int x, y, z;
+    vid_xyz(g, faces[i] / 3u, &x, &y, &z);
+    if ((z >= b0 && z < b1) || (z >= b2 && z < b3)) atomicAdd(count, 1ull);
+}
+
+// ambiguous faces (slot 1) with local id < limit, appended (any order) to
+// out[base ..] as id + offset
+__global__ void k_amb_select(const uint32_t* __restrict__ faces, const uint8_t* __restrict__ slots, uint32_t nf,
+                             uint32_t limit, uint32_t offset, uint32_t* __restrict__ out, uint32_t* __restrict__ count) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf || slots[i] != 1 || faces[i] >= limit) return;
+    out[atomicAdd(count, 1u)] = faces[i] + offset;
+}
+
 }  // namespace
+
+void launch_amb_select(const uint32_t* faces, const uint8_t* slots, uint32_t nf, uint32_t limit, uint32_t offset,
+                       uint32_t* out, size_t base, uint32_t* count, cudaStream_t st) {
+    cudaMemsetAsync(count, 0, 4, st);
+    if (nf) {
+        k_amb_select<<<(nf + 255) / 256, 256, 0, st>>>(faces, slots, nf, limit, offset, out + base, count);
+        note_launch();
+    }
+}
+
+void launch_slab_watch(const GridDev& g, const uint32_t* faces, const uint8_t* mark, uint32_t nf, const int* bands,
+                       unsigned long long* count, cudaStream_t st) {
+    if (nf) {
+        k_slab_watch<<<(nf + 255) / 256, 256, 0, st>>>(g, faces, mark, nf, bands[0], bands[1], bands[2], bands[3],
+                                                       count);
+        note_launch();
+    }
+}
 
 void launch_slab_ranges(const uint32_t* cells, uint32_t C, const uint32_t* vbase, uint32_t V3, const uint32_t* edges,
                         uint32_t E, const unsigned long long* qoff, uint32_t N3, uint32_t NT, uint32_t cell_lo,

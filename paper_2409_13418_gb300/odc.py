@@ -74,19 +74,24 @@ class Stats(C.Structure):
 
 
 class SlabC(C.Structure):
-    _fields_ = [("z0", C.c_int32), ("z1", C.c_int32), ("halo", C.c_int32)]
+    _fields_ = [("z0", C.c_int32), ("z1", C.c_int32), ("halo", C.c_int32), ("flips", C.c_void_p)]
 
 
 class SlabInfoC(C.Structure):
     _fields_ = [("verts3_local", C.c_int64), ("verts3_before", C.c_int64), ("verts3_owned", C.c_int64),
                 ("case3_before", C.c_int64), ("case3_owned", C.c_int64), ("tris_before", C.c_int64),
-                ("tris_owned", C.c_int64)]
+                ("tris_owned", C.c_int64), ("fix_near_plane", C.c_int64)]
 
 
 def slab_bounds(res_z: int, n_slabs: int) -> list:
     """Cell-layer ranges [z0, z1) of n_slabs slabs of near-equal depth (the
     split odc_extract_slabbed uses)."""
     return [(res_z * i // n_slabs, res_z * (i + 1) // n_slabs) for i in range(n_slabs)]
+
+
+def label_words(grid) -> int:
+    """Words of a grid's label bit set (odc_grid_labels); flip words are 3x."""
+    return ((grid.res[0] + 32) // 32) * (grid.res[1] + 1) * (grid.res[2] + 1)
 
 
 def slab_bases(counts: list, rank: int) -> dict:
@@ -139,7 +144,8 @@ def launch_total() -> int:
 EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", "odc_mesh_release",
            "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_compact_edges_noalloc", "odc_status_str",
            "odc_last_error", "odc_server_create", "odc_server_destroy", "odc_submit", "odc_poll", "odc_result_release",
-           "odc_server_clock", "odc_mesh_quality", "odc_extract_slab", "odc_slab_place", "odc_extract_slabbed"]
+           "odc_server_clock", "odc_mesh_quality", "odc_extract_slab", "odc_slab_place", "odc_extract_slabbed",
+           "odc_ctx_memory", "odc_grid_labels", "odc_manifold_flips"]
 
 _lib = None
 
@@ -157,6 +163,10 @@ def load(path: str = LIB_PATH):
     lib.odc_ctx_destroy.argtypes = [P]
     lib.odc_extract.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), P, C.POINTER(MeshC)]
     lib.odc_mesh_copy.argtypes = [P, C.POINTER(MeshC), P, P, C.c_int]
+    lib.odc_ctx_memory.argtypes = [P, C.POINTER(C.c_size_t)]
+    lib.odc_grid_labels.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.c_int32, C.c_int32, P,
+                                    P]
+    lib.odc_manifold_flips.argtypes = [P, C.POINTER(Grid), P, P, C.c_int32, P, C.POINTER(C.c_int64)]
     lib.odc_extract_slab.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.POINTER(SlabC), P,
                                      C.POINTER(MeshC), C.POINTER(SlabInfoC)]
     lib.odc_slab_place.argtypes = [P, C.POINTER(MeshC), C.POINTER(SlabInfoC), C.c_int64, C.c_int64, C.c_int64, P, P,
@@ -378,13 +388,37 @@ class Context:
                                 stream if stream else None, C.byref(m)))
         return Mesh(self, m)
 
+    def device_bytes(self) -> int:
+        """odc_ctx_memory: device bytes the context holds."""
+        b = C.c_size_t()
+        _check(_lib.odc_ctx_memory(self.h, C.byref(b)))
+        return int(b.value)
+
+    def grid_labels(self, src, grid: I.Grid, z0: int, z1: int, d_bits: int, stream=None, precision=None, band=None,
+                    split=True, split_zmargin=0.0, iso: float = 0.5):
+        """odc_grid_labels: label words of vertex layers [z0, z1] into d_bits."""
+        holder = _SourceHolder(src, precision, band, split, split_zmargin)
+        g = make_grid(grid)
+        p = make_params(iso=iso)
+        _check(_lib.odc_grid_labels(self.h, C.byref(holder.src), C.byref(g), C.byref(p), z0, z1, d_bits,
+                                    stream if stream else None))
+
+    def manifold_flips(self, grid: I.Grid, d_bits: int, d_flips: int, n_chunks: int = 8, stream=None) -> int:
+        """odc_manifold_flips: the whole grid's manifold fix; returns faces flipped."""
+        g = make_grid(grid)
+        n = C.c_int64()
+        _check(_lib.odc_manifold_flips(self.h, C.byref(g), d_bits, d_flips, n_chunks, stream if stream else None,
+                                       C.byref(n)))
+        return int(n.value)
+
     def extract_slab(self, src, grid: I.Grid, z0: int, z1: int, halo: int = 2, steps_1d=15, stream=None,
-                     precision=None, band=None, split=True, split_zmargin=0.0, **kw):
-        """odc_extract_slab: the slab extraction's mesh and its owned ranges."""
+                     precision=None, band=None, split=True, split_zmargin=0.0, flips: int = 0, **kw):
+        """odc_extract_slab: the slab extraction's mesh and its owned ranges
+        (``flips``: device pointer to the whole grid's flip words, or 0)."""
         holder = _SourceHolder(src, precision, band, split, split_zmargin)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
-        sl = SlabC(z0, z1, halo)
+        sl = SlabC(z0, z1, halo, flips if flips else None)
         m = MeshC()
         info = SlabInfoC()
         _check(_lib.odc_extract_slab(self.h, C.byref(holder.src), C.byref(g), C.byref(p), C.byref(sl),

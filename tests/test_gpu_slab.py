@@ -54,27 +54,42 @@ def test_slabbed_equals_whole_grid(ctx, case, n_slabs):
     assert nt > 100
 
 
-def test_rank_recipe_places_slabs_into_one_mesh(ctx):
-    """Each slab extracted and placed through odc_extract_slab /
-    odc_slab_place with bases from odc.slab_bases over all slabs' counts."""
+@pytest.mark.parametrize("case", ["csg", "voxel-random"])
+def test_rank_recipe_places_slabs_into_one_mesh(ctx, case):
+    """The multi-rank recipe driven slab by slab through the C ABI: label
+    words of each slab's layers (odc_grid_labels), the whole grid's manifold
+    fix (odc_manifold_flips), each slab extracted with those flips and placed
+    (odc_slab_place) at bases from odc.slab_bases over all slabs' counts."""
     import torch
     from paper_2409_13418_gb300 import odc
-    src, g = I.random_csg(7, 20), I.Grid((-1, -1, -1), (1, 1, 1), (40, 44, 50))
+    if case == "csg":
+        src, g = I.random_csg(7, 20), I.Grid((-1, -1, -1), (1, 1, 1), (40, 44, 50))
+    else:   # random signs: the manifold fix flips faces, across slab planes too
+        src, g = I.voxel_random(2, (17, 13, 15)), I.cube_grid(40)
     whole = ctx.extract(src, g, steps_1d=12)
+    nflip = whole.stats["n_flips"]
     vw, tw = whole.to_host()
     bounds = odc.slab_bounds(g.res[2], 4)
+    words = odc.label_words(g)
+    bits = torch.zeros(words, dtype=torch.int32, device="cuda")
+    flips = torch.zeros(3 * words, dtype=torch.int32, device="cuda")
+    for z0, z1 in bounds:   # each rank: its own vertex layers (then one all-gather of the words)
+        ctx.grid_labels(src, g, z0, z1, bits.data_ptr())
+    assert ctx.manifold_flips(g, bits.data_ptr(), flips.data_ptr(), n_chunks=3) == nflip
     counts = []
     for z0, z1 in bounds:   # pass 1: counts (what a rank all-gathers)
-        _, info = ctx.extract_slab(src, g, z0, z1, halo=2, steps_1d=12)
+        _, info = ctx.extract_slab(src, g, z0, z1, halo=2, steps_1d=12, flips=flips.data_ptr())
+        assert info.fix_near_plane == 0
         counts.append((info.verts3_owned, info.case3_owned, info.tris_owned))
     tot = odc.slab_bases(counts, 0)
     dv = torch.full((tot["n_verts"], 3), float("nan"), dtype=torch.float32, device="cuda")
     dt = torch.full((tot["n_tris"], 3), -1, dtype=torch.int32, device="cuda")
     for r, (z0, z1) in enumerate(bounds):   # pass 2: each slab places itself
-        mesh, info = ctx.extract_slab(src, g, z0, z1, halo=2, steps_1d=12)
+        mesh, info = ctx.extract_slab(src, g, z0, z1, halo=2, steps_1d=12, flips=flips.data_ptr())
         b = odc.slab_bases(counts, r)
         ctx.slab_place(mesh, info, b["verts3_base"], b["case3_base"], b["tris_base"], dv.data_ptr(), dt.data_ptr())
         torch.cuda.synchronize()
+    print(case, "flips", nflip, "verts", tot["n_verts"], "tris", tot["n_tris"])
     assert dv.cpu().numpy().tobytes() == vw.tobytes()
     assert np.array_equal(dt.cpu().numpy(), tw)
 
@@ -92,3 +107,27 @@ def test_slab_arguments_are_checked(ctx):
         ctx.extract_slabbed(src, g, 2, halo=2, mc=True)
     with pytest.raises(odc.OdcError):
         ctx.extract_slabbed(src, g, 17, halo=2)
+
+
+def test_manifold_fix_across_slab_planes(ctx):
+    """Random-sign volumes make the manifold fix flip faces, also next to
+    slab planes: with the whole grid's flips every split is exact, while a
+    slab running the fix on its own window reports the marks near its
+    planes (fix_near_plane)."""
+    src, g = I.voxel_random(2, (17, 13, 15)), I.cube_grid(40)
+    whole = ctx.extract(src, g, steps_1d=12)
+    vw, tw = whole.to_host()
+    print("flips whole grid", whole.stats["n_flips"])
+    assert whole.stats["n_flips"] > 0
+    near = 0
+    for n in (2, 3, 5, 8, 13):
+        m = ctx.extract_slabbed(src, g, n, halo=2, steps_1d=12)
+        assert m.stats["n_flips"] == whole.stats["n_flips"]
+        vs, ts = m.to_host()
+        assert vs.tobytes() == vw.tobytes() and np.array_equal(ts, tw), n
+        from paper_2409_13418_gb300 import odc
+        for z0, z1 in odc.slab_bounds(g.res[2], n):
+            _, info = ctx.extract_slab(src, g, z0, z1, halo=2, steps_1d=12)
+            near += info.fix_near_plane
+    print("own-window fix marks near slab planes", near)
+    assert near > 0
