@@ -381,7 +381,7 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
     size_t nX = Xh[0].size() + Xh[1].size() + Xh[2].size();
     size_t stmp = scan_tmp_elems(nw);
     size_t needA = al(nX * 4) + al(nw * 4) + al(nw * sizeof(WordInfo)) + 6 * al(nw * 4) + al(3 * nw * 4) +
-                   al(stmp * 8) + al(64 * 8);
+                   al(stmp * 8) + al(64 * 8) + 2 * al(nX * 4);
     s = arena_ensure(c, c->A, needA, st);
     if (s != ODC_OK) return s;
     float* dX = (float*)c->A.take(nX * 4);
@@ -396,6 +396,8 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
     uint32_t* flips = (uint32_t*)c->A.take(3 * nw * 4);
     void* tmp = c->A.take(stmp * 8);
     uint32_t* dcnt = (uint32_t*)c->A.take(64 * 8);
+    int* axis_c = (int*)c->A.take(nX * 4);
+    float* axis_f = (float*)c->A.take(nX * 4);
     g.X[0] = dX;
     g.X[1] = dX + Xh[0].size();
     g.X[2] = dX + Xh[0].size() + Xh[1].size();
@@ -417,7 +419,7 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
     if (kind == ODC_SRC_CSG) {
         launch_csg_grid(g, d_prims, d_cull, n_prims, bits, st);
     } else if (kind == ODC_SRC_VOXEL) {
-        launch_vox_grid(g, vox, bits, st);
+        launch_vox_grid(g, vox, axis_c, axis_f, bits, st);
     } else {
         s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &g_err);
         if (s != ODC_OK) return s;
@@ -708,9 +710,11 @@ static odc_status labels_into(odc_ctx* c, const odc_grid* grid, const odc_params
     g.W = (g.nv[0] + 31) / 32;
     const size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
     const size_t nX = Xh[0].size() + Xh[1].size() + Xh[2].size();
-    odc_status s = arena_ensure(c, c->A, al(nX * 4), st);
+    odc_status s = arena_ensure(c, c->A, 3 * al(nX * 4), st);
     if (s != ODC_OK) return s;
     float* dX = (float*)c->A.take(nX * 4);
+    int* axis_c = (int*)c->A.take(nX * 4);
+    float* axis_f = (float*)c->A.take(nX * 4);
     g.X[0] = dX;
     g.X[1] = dX + Xh[0].size();
     g.X[2] = dX + Xh[0].size() + Xh[1].size();
@@ -723,7 +727,7 @@ static odc_status labels_into(odc_ctx* c, const odc_grid* grid, const odc_params
     } else if (kind == ODC_SRC_VOXEL) {
         VoxDev vox = c->res_vox;
         vox.iso = prm->iso;
-        launch_vox_grid(g, vox, bits, st);
+        launch_vox_grid(g, vox, axis_c, axis_f, bits, st);
     } else {
         int64_t nq = 0;
         s = mlp_grid(c->mlp, g, prm->iso, bits, st, &nq, &g_err);

@@ -41,7 +41,9 @@ void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, co
                        uint8_t* labels, cudaStream_t st);
 
 // search_csg.cu, voxel volumes
-void launch_vox_grid(const GridDev& g, const VoxDev& vox, uint32_t* bits, cudaStream_t st);
+// axis_c / axis_f: scratch of nv[0] + nv[1] + nv[2] ints / floats
+void launch_vox_grid(const GridDev& g, const VoxDev& vox, int* axis_c, float* axis_f, uint32_t* bits,
+                     cudaStream_t st);
 void launch_vox_points(const VoxDev& vox, const float3* pts, int64_t n, uint8_t* labels, cudaStream_t st);
 void launch_bisect_vox(const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
                        const VoxDev& vox, uint32_t* T, cudaStream_t st);

@@ -117,8 +117,23 @@ __global__ void k_points(Occ occ, const float3* __restrict__ pts, int64_t n, uin
     labels[i] = (uint8_t)occ(pts[i]);
 }
 
-// Grid labels of a voxel volume: one warp per label word (ballot).
-__global__ void k_vox_grid(GridDev g, VoxOcc occ, uint32_t* __restrict__ bits) {
+// Per-axis sample coordinates of the grid's vertex coordinates (cell index
+// and fraction, the fast path's float32 rounding): the label kernel then
+// needs no division per vertex.
+__global__ void k_vox_axes(GridDev g, VoxDev d, int* __restrict__ ci, float* __restrict__ fi) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n0 = g.nv[0], n1 = g.nv[1], n2 = g.nv[2];
+    if (t >= n0 + n1 + n2) return;
+    const int a = t < n0 ? 0 : (t < n0 + n1 ? 1 : 2);
+    const int i = t - (a == 0 ? 0 : (a == 1 ? n0 : n0 + n1));
+    vox_axis32(d, a, g.X[a][i], &ci[t], &fi[t]);
+}
+
+// Grid labels of a voxel volume: one warp per label word (ballot); the
+// float32 decision from the axis tables, the full evaluation (float-float
+// when near iso) for what it leaves undecided.
+__global__ void k_vox_grid(GridDev g, VoxOcc occ, const int* __restrict__ ci, const float* __restrict__ fi,
+                           uint32_t* __restrict__ bits) {
     size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int l = threadIdx.x & 31;
     size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
@@ -126,7 +141,13 @@ __global__ void k_vox_grid(GridDev g, VoxOcc occ, uint32_t* __restrict__ bits) {
     int x = (int)(w % g.W) * 32 + l;
     size_t row = w / g.W;
     int y = (int)(row % g.nv[1]), z = (int)(row / g.nv[1]);
-    bool in = x < g.nv[0] && occ(make_float3(g.X[0][x], g.X[1][y], g.X[2][z]));
+    bool in = false;
+    if (x < g.nv[0]) {
+        const int i[3] = {__ldg(ci + x), __ldg(ci + g.nv[0] + y), __ldg(ci + g.nv[0] + g.nv[1] + z)};
+        const float f[3] = {__ldg(fi + x), __ldg(fi + g.nv[0] + y), __ldg(fi + g.nv[0] + g.nv[1] + z)};
+        const int r = vox_fast32(occ.d, i, f);
+        in = r >= 0 ? r != 0 : occ(make_float3(g.X[0][x], g.X[1][y], g.X[2][z])) != 0;
+    }
     uint32_t word = __ballot_sync(0xffffffffu, in);
     if (l == 0) bits[w] = word;
 }
@@ -155,9 +176,12 @@ void launch_face_csg(const GridDev& g, const uint32_t* bits, const uint32_t* fli
                                               flags, dec); note_launch();
 }
 
-void launch_vox_grid(const GridDev& g, const VoxDev& vox, uint32_t* bits, cudaStream_t st) {
+void launch_vox_grid(const GridDev& g, const VoxDev& vox, int* axis_c, float* axis_f, uint32_t* bits,
+                     cudaStream_t st) {
+    const int na = g.nv[0] + g.nv[1] + g.nv[2];
+    k_vox_axes<<<(na + 255) / 256, 256, 0, st>>>(g, vox, axis_c, axis_f); note_launch();
     size_t threads = (size_t)g.W * g.nv[1] * g.nv[2] * 32;
-    k_vox_grid<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, VoxOcc{vox}, bits); note_launch();
+    k_vox_grid<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, VoxOcc{vox}, axis_c, axis_f, bits); note_launch();
 }
 
 void launch_vox_points(const VoxDev& vox, const float3* pts, int64_t n, uint8_t* labels, cudaStream_t st) {

@@ -17,6 +17,37 @@ namespace odc {
 
 __device__ __forceinline__ ff vox_lerp(ff a, ff b, ff f) { return ff_add(a, ff_mul(ff_sub(b, a), f)); }
 
+// Float32 sample coordinate along axis a: cell index c and fraction f of
+// world coordinate x (the fast path's own rounding; the float-float path
+// below decides whatever this path leaves undecided).
+__device__ __forceinline__ void vox_axis32(const VoxDev& d, int a, float x, int* c, float* f) {
+    const float top = (float)(d.dims[a] - 1);
+    float u = (x - d.lo[a]) / d.rng_hi[a] * top;
+    u = fminf(fmaxf(u, 0.0f), top);
+    *c = min((int)u, d.dims[a] - 2);
+    *f = u - (float)*c;
+}
+
+// The float32 trilinear value at cell (i) fractions (f), decided against iso
+// when it lies beyond its rounding bound: 1 inside, 0 outside, -1 undecided.
+__device__ __forceinline__ int vox_fast32(const VoxDev& d, const int (&i)[3], const float (&f)[3]) {
+    const int dmax = max(max(2, d.dims[0]), max(d.dims[1], d.dims[2]));
+    const size_t sy = (size_t)d.dims[0], sz = (size_t)d.dims[0] * d.dims[1];
+    const float* b = d.v + (size_t)i[2] * sz + (size_t)i[1] * sy + (size_t)i[0];
+    const float v0 = __ldg(b), v1 = __ldg(b + 1), v2 = __ldg(b + sy), v3 = __ldg(b + sy + 1);
+    const float v4 = __ldg(b + sz), v5 = __ldg(b + sz + 1), v6 = __ldg(b + sz + sy), v7 = __ldg(b + sz + sy + 1);
+    const float c00 = fmaf(v1 - v0, f[0], v0), c10 = fmaf(v3 - v2, f[0], v2);
+    const float c01 = fmaf(v5 - v4, f[0], v4), c11 = fmaf(v7 - v6, f[0], v6);
+    const float c0 = fmaf(c10 - c00, f[1], c00), c1 = fmaf(c11 - c01, f[1], c01);
+    const float phi = fmaf(c1 - c0, f[2], c0);
+    const float vmax = fmaxf(fmaxf(fmaxf(fabsf(v0), fabsf(v1)), fmaxf(fabsf(v2), fabsf(v3))),
+                             fmaxf(fmaxf(fabsf(v4), fabsf(v5)), fmaxf(fabsf(v6), fabsf(v7))));
+    const float bound = vmax * (3e-6f * (float)(dmax - 1) + 4e-6f);
+    if (phi - d.iso > bound) return 1;
+    if (d.iso - phi > bound) return 0;
+    return -1;
+}
+
 struct VoxOcc {
     VoxDev d;
     __device__ __forceinline__ uint32_t operator()(float3 p) const {
@@ -24,29 +55,9 @@ struct VoxOcc {
         {   // float32 fast path
             int i[3];
             float f[3];
-            int dmax = 2;
-            for (int a = 0; a < 3; ++a) {
-                const float top = (float)(d.dims[a] - 1);
-                float u = (pc[a] - d.lo[a]) / d.rng_hi[a] * top;
-                u = fminf(fmaxf(u, 0.0f), top);
-                const int c = min((int)u, d.dims[a] - 2);
-                i[a] = c;
-                f[a] = u - (float)c;
-                dmax = max(dmax, d.dims[a]);
-            }
-            const size_t sy = (size_t)d.dims[0], sz = (size_t)d.dims[0] * d.dims[1];
-            const float* b = d.v + (size_t)i[2] * sz + (size_t)i[1] * sy + (size_t)i[0];
-            const float v0 = __ldg(b), v1 = __ldg(b + 1), v2 = __ldg(b + sy), v3 = __ldg(b + sy + 1);
-            const float v4 = __ldg(b + sz), v5 = __ldg(b + sz + 1), v6 = __ldg(b + sz + sy), v7 = __ldg(b + sz + sy + 1);
-            const float c00 = fmaf(v1 - v0, f[0], v0), c10 = fmaf(v3 - v2, f[0], v2);
-            const float c01 = fmaf(v5 - v4, f[0], v4), c11 = fmaf(v7 - v6, f[0], v6);
-            const float c0 = fmaf(c10 - c00, f[1], c00), c1 = fmaf(c11 - c01, f[1], c01);
-            const float phi = fmaf(c1 - c0, f[2], c0);
-            const float vmax = fmaxf(fmaxf(fmaxf(fabsf(v0), fabsf(v1)), fmaxf(fabsf(v2), fabsf(v3))),
-                                     fmaxf(fmaxf(fabsf(v4), fabsf(v5)), fmaxf(fabsf(v6), fabsf(v7))));
-            const float bound = vmax * (3e-6f * (float)(dmax - 1) + 4e-6f);
-            if (phi - d.iso > bound) return 1u;
-            if (d.iso - phi > bound) return 0u;
+            for (int a = 0; a < 3; ++a) vox_axis32(d, a, pc[a], &i[a], &f[a]);
+            const int r = vox_fast32(d, i, f);
+            if (r >= 0) return (uint32_t)r;
         }
         int i[3];
         ff f[3];
