@@ -129,27 +129,67 @@ __global__ void k_vox_axes(GridDev g, VoxDev d, int* __restrict__ ci, float* __r
     vox_axis32(d, a, g.X[a][i], &ci[t], &fi[t]);
 }
 
-// Grid labels of a voxel volume: one warp per label word (ballot); the
-// float32 decision from the axis tables, the full evaluation (float-float
-// when near iso) for what it leaves undecided.
+// Grid labels of a voxel volume: one warp per (label word, row y), marching
+// over kVoxZRun consecutive vertex layers z.  The float32 decision comes
+// from the axis tables, with the samples of the upper volume layer kept in
+// registers when the next vertex layer falls in the next volume cell (or
+// the same one), so that a layer's samples are read once instead of twice;
+// the full evaluation (float-float when near iso) decides what it leaves
+// undecided.
+constexpr int kVoxZRun = 8;
 __global__ void k_vox_grid(GridDev g, VoxOcc occ, const int* __restrict__ ci, const float* __restrict__ fi,
                            uint32_t* __restrict__ bits) {
-    size_t w = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int l = threadIdx.x & 31;
-    size_t nw = (size_t)g.W * g.nv[1] * g.nv[2];
-    if (w >= nw) return;
-    int x = (int)(w % g.W) * 32 + l;
-    size_t row = w / g.W;
-    int y = (int)(row % g.nv[1]), z = (int)(row / g.nv[1]);
-    bool in = false;
-    if (x < g.nv[0]) {
-        const int i[3] = {__ldg(ci + x), __ldg(ci + g.nv[0] + y), __ldg(ci + g.nv[0] + g.nv[1] + z)};
-        const float f[3] = {__ldg(fi + x), __ldg(fi + g.nv[0] + y), __ldg(fi + g.nv[0] + g.nv[1] + z)};
-        const int r = vox_fast32(occ.d, i, f);
-        in = r >= 0 ? r != 0 : occ(make_float3(g.X[0][x], g.X[1][y], g.X[2][z])) != 0;
+    const size_t wr = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // (word, row y, z run)
+    const int l = threadIdx.x & 31;
+    const int nzr = (g.nv[2] + kVoxZRun - 1) / kVoxZRun;
+    if (wr >= (size_t)g.W * g.nv[1] * nzr) return;
+    const int xw = (int)(wr % g.W);
+    const size_t t = wr / g.W;
+    const int y = (int)(t % g.nv[1]);
+    const int z0 = (int)(t / g.nv[1]) * kVoxZRun, z1 = min(z0 + kVoxZRun, g.nv[2]);
+    const int x = xw * 32 + l;
+    const bool live = x < g.nv[0];
+    const VoxDev& d = occ.d;
+    const int cx = live ? __ldg(ci + x) : 0, cy = __ldg(ci + g.nv[0] + y);
+    const float fx = live ? __ldg(fi + x) : 0.0f, fy = __ldg(fi + g.nv[0] + y);
+    const int* cz = ci + g.nv[0] + g.nv[1];
+    const float* fz = fi + g.nv[0] + g.nv[1];
+    const int dmax = max(max(2, d.dims[0]), max(d.dims[1], d.dims[2]));
+    const size_t sy = (size_t)d.dims[0], sz = (size_t)d.dims[0] * d.dims[1];
+    const float* col = d.v + (size_t)cy * sy + (size_t)cx;   // (cx, cy) column of the volume
+    int held = -2;                                            // volume layer whose 4 samples are in lo[]
+    float lo[4] = {0.f, 0.f, 0.f, 0.f}, hi[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int z = z0; z < z1; ++z) {
+        const int c = __ldg(cz + z);
+        const float f = __ldg(fz + z);
+        bool in = false;
+        if (live) {
+            if (c == held + 1) {          // the previous upper layer is this lower one
+                for (int k = 0; k < 4; ++k) lo[k] = hi[k];
+            } else if (c != held) {
+                const float* b = col + (size_t)c * sz;
+                lo[0] = __ldg(b); lo[1] = __ldg(b + 1); lo[2] = __ldg(b + sy); lo[3] = __ldg(b + sy + 1);
+            }
+            if (c != held) {
+                const float* b = col + (size_t)(c + 1) * sz;
+                hi[0] = __ldg(b); hi[1] = __ldg(b + 1); hi[2] = __ldg(b + sy); hi[3] = __ldg(b + sy + 1);
+                held = c;
+            }
+            // the same float32 trilinear value and bound as the direct evaluation
+            const float c00 = fmaf(lo[1] - lo[0], fx, lo[0]), c10 = fmaf(lo[3] - lo[2], fx, lo[2]);
+            const float c01 = fmaf(hi[1] - hi[0], fx, hi[0]), c11 = fmaf(hi[3] - hi[2], fx, hi[2]);
+            const float c0 = fmaf(c10 - c00, fy, c00), c1 = fmaf(c11 - c01, fy, c01);
+            const float phi = fmaf(c1 - c0, f, c0);
+            const float vmax = fmaxf(fmaxf(fmaxf(fabsf(lo[0]), fabsf(lo[1])), fmaxf(fabsf(lo[2]), fabsf(lo[3]))),
+                                     fmaxf(fmaxf(fabsf(hi[0]), fabsf(hi[1])), fmaxf(fabsf(hi[2]), fabsf(hi[3]))));
+            const float bound = vmax * (3e-6f * (float)(dmax - 1) + 4e-6f);
+            if (phi - d.iso > bound) in = true;
+            else if (d.iso - phi > bound) in = false;
+            else in = occ(make_float3(g.X[0][x], g.X[1][y], g.X[2][z])) != 0;
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, in);
+        if (l == 0) bits[((size_t)z * g.nv[1] + y) * g.W + xw] = word;
     }
-    uint32_t word = __ballot_sync(0xffffffffu, in);
-    if (l == 0) bits[w] = word;
 }
 
 void launch_csg_points(const PrimDev* prims, const float4* cull, int n_prims, const float3* pts, int64_t n,
@@ -180,7 +220,8 @@ void launch_vox_grid(const GridDev& g, const VoxDev& vox, int* axis_c, float* ax
                      cudaStream_t st) {
     const int na = g.nv[0] + g.nv[1] + g.nv[2];
     k_vox_axes<<<(na + 255) / 256, 256, 0, st>>>(g, vox, axis_c, axis_f); note_launch();
-    size_t threads = (size_t)g.W * g.nv[1] * g.nv[2] * 32;
+    const size_t runs = (size_t)(g.nv[2] + kVoxZRun - 1) / kVoxZRun;
+    const size_t threads = (size_t)g.W * g.nv[1] * runs * 32;
     k_vox_grid<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, VoxOcc{vox}, axis_c, axis_f, bits); note_launch();
 }
 
