@@ -399,6 +399,8 @@ def main():
     ap.add_argument("--no-ablation", action="store_true", help="skip the ablation table (Sec. 6.3 variants)")
     ap.add_argument("--csg-res", type=int, default=0,
                     help="profile run: only the CSG pipeline at this resolution (prints its own JSON line)")
+    ap.add_argument("--fp32-points", type=int, default=0,
+                    help="profile run: only the FP32 network over this many seeded points (list mode, 3 launches)")
     ap.add_argument("--slab-res", type=int, default=0,
                     help="only the envelope MLP at this resolution in --slab-count z-slabs (prints its own JSON line)")
     ap.add_argument("--slab-count", type=int, default=8)
@@ -414,6 +416,19 @@ def main():
     args.cpu_cells = args.cpu_cells or 40
     if args.csg_res:
         csg_run(args)
+        return
+    if args.fp32_points:
+        import numpy as np
+        from paper_2409_13418_gb300 import build, inputs as I, odc
+        build.build()
+        odc.load()
+        pts = np.random.default_rng(1).uniform(-1, 1, (args.fp32_points, 3)).astype(np.float32)
+        with odc.Context(0) as ctx:
+            mlp = I.envelope_mlp(0)
+            for _ in range(3):
+                ctx.eval_points(mlp, pts, precision=odc.PREC_FP32)
+        print(json.dumps({"workload": f"FP32 network over {args.fp32_points} seeded points (list mode)",
+                          "launches": 3}), flush=True)
         return
     if args.slab_res:
         from paper_2409_13418_gb300 import build, inputs as I, odc
@@ -521,9 +536,16 @@ def main():
         rows = []
         if mlp_launches:
             a = mlp_flops / (mlp_ms * 1e-3) / 1e12
+            # DRAM bytes of one launch: ncu on launches of 256 K and 1 M points
+            # (dram__bytes_read + write): 0.95 MB (the weights) + 12.0 B per query
+            q_per_launch = mlp_flops / mlp_launches / 459264.0
             rows.append({"bound": "alu", "kernel": "k_mlp_fp32 (FP32 SIMT network; the plain path and the band "
                                                    "re-evaluation)", "achieved": a, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": a / fp32_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": a / fp32_peak,
+                         "traffic": 0.95e6 + 12.0 * q_per_launch,
+                         "traffic_source": "bytes per launch at this run's mean queries per launch, from ncu "
+                                           "dram__bytes_read.sum + dram__bytes_write.sum of launches of 256K and "
+                                           "1M points: 0.95 MB + 12.0 B per query",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock (unit counts)",
                          "ms_per_step": mlp_ms / args.steps, "flops_per_launch": mlp_flops / mlp_launches})
         if tc_launches:
