@@ -578,6 +578,7 @@ def main():
                            "bf16_pass_queries": int(round(stats["tc_flops"] / 459264.0)),
                            "requeries_split_fp16": stats["n_split"],
                            "requeries_fp32": stats["n_requeries"],
+                           "fp32_tile_autotuned": stats["fp32_tile"],
                            "stage_ms": [round(x, 3) for x in stats["stage_ms"]]},
                 "e2e": {"value": e2e, "unit": "Mcells/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(vbytes + tbytes)},

@@ -135,10 +135,17 @@ typedef struct {
     float split_zmargin;
     int32_t flags;               /* ODC_MLP_REUPLOAD: prepare and upload the weights even when the
                                     context already holds the same ones (by default a context that
-                                    holds the same B, W and b only refreshes the latent's folded bias) */
+                                    holds the same B, W and b only refreshes the latent's folded bias);
+                                    ODC_MLP_FP32_TILE(v): run the FP32 network with tile shape v
+                                    (0..3) instead of the autotuner's pick -- every shape gives the
+                                    same bits */
 } odc_mlp;
 
+/* The FP32 network has four tile shapes (warps x K chunk x chunks in flight:
+ * 16x32x2, 16x16x3, 12x32x3, 8x32x3); the first upload on a device times
+ * each on a calibration list and keeps the fastest (odc_stats.fp32_tile). */
 enum { ODC_MLP_REUPLOAD = 1 };
+#define ODC_MLP_FP32_TILE(v) (((v) + 1) << 8)
 
 /* Dense voxel-grid occupancy: values[k][j][i] (host float32, i fastest) are
  * samples at lo + (hi - lo) (i, j, k) / (dims - 1); phi(x) is their trilinear
@@ -224,6 +231,7 @@ typedef struct {
     int32_t pad2_;
     int64_t split_launches;
     int64_t n_split;             /* band decisions re-evaluated by the split-FP16 tier */
+    int64_t fp32_tile;           /* FP32 network tile shape used (MLP sources; -1 otherwise) */
 } odc_stats;
 
 typedef struct {

@@ -603,6 +603,9 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
         mlp_timing_collect(c->mlp, 1, &S.tc_ms, &S.tc_flops, &S.tc_launches);
         mlp_timing_collect(c->mlp, 2, &S.split_ms, &S.split_flops, &S.split_launches);
         S.n_split = mlp_split_count(c->mlp);
+        S.fp32_tile = mlp_fp32_variant(c->mlp);
+    } else {
+        S.fp32_tile = -1;
     }
     return ODC_OK;
 }

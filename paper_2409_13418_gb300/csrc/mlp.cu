@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "mlp.h"
@@ -140,6 +141,8 @@ size_t mlp_device_bytes(const MlpState* st) {
 }
 
 static odc_status fp32_kernel_setup(std::string* err);
+static odc_status fp32_autotune(MlpState* st, cudaStream_t s, std::string* err);
+constexpr int kFp32VariantCount = 4;
 
 // Upload weights: FP32 transposed copies for the SIMT path (W^T [in][out]),
 // and the BF16 operand tiles of the tensor-core path.
@@ -158,6 +161,14 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
         MLP_CK(cudaMalloc((void**)&st->dq, 8 * sizeof(unsigned long long)));
         odc_status r0 = fp32_kernel_setup(err);
         if (r0 != ODC_OK) return r0;
+    }
+    {
+        const int f = (m->flags >> 8) & 0xf;
+        if ((m->flags & ~(ODC_MLP_REUPLOAD | 0xf00)) || f > kFp32VariantCount) {
+            *err = "unknown MLP flags";
+            return ODC_ERR_INVALID_ARG;
+        }
+        st->fp32_forced = f - 1;
     }
     st->precision = m->precision;
     st->band = m->band;
@@ -221,38 +232,32 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     r = mlp_tc_prepare(st, h.data(), s, err);
     if (r != ODC_OK) return r;
     st->wkey.swap(key);
+    if (st->fp32_variant < 0) return fp32_autotune(st, s, err);
     return ODC_OK;
 }
 
 // ----------------------------------------------------------- FP32 network
 // Register tiles of 8 rows (queries) x 8 columns per thread; a warp's lanes
 // form 4 x 8 threads (32 rows x 64 columns), the CTA's warps 4 column blocks
-// x kWarps / 4 row blocks.  Activations sit transposed in shared memory
+// x WARPS / 4 row blocks.  Activations sit transposed in shared memory
 // (act[k][m], k-major), so that a thread's 8 rows at one k are two vector
-// loads, shared by the 8 lanes of its row group.
-#ifndef ODC_FP32_WARPS
-#define ODC_FP32_WARPS 16
-#endif
-constexpr int kWarps = ODC_FP32_WARPS;
-constexpr int kTM = kWarps / 4 * 32;     // queries per CTA
-constexpr int kThreads = 32 * kWarps;
-#ifndef ODC_FP32_CTAS
-#define ODC_FP32_CTAS 1
-#endif
-constexpr int kCtasPerSm = ODC_FP32_CTAS;   // resident CTAs per SM (persistent grid)
-static_assert(kWarps % 4 == 0 && 4 * kTM <= kThreads, "FP32 tile shape");
-#ifndef ODC_FP32_KC
-#define ODC_FP32_KC 32
-#endif
-constexpr int kKC = ODC_FP32_KC;         // weight rows per staged chunk
-#ifndef ODC_FP32_STAGES
-#define ODC_FP32_STAGES 2
-#endif
-constexpr int kWStages = ODC_FP32_STAGES; // weight chunks in flight (ring)
-constexpr int kActStride = kTM + 4;      // floats between consecutive k of act[k][m]
+// loads, shared by the 8 lanes of its row group.  The tile shape (warps,
+// weight rows per staged chunk, chunks in flight) is a template parameter:
+// every shape computes the same bits (each output sums its products in
+// order k = 0..K-1 with one rounding per FMA), and the autotuner below picks
+// the fastest on the device at hand.
+template <int WARPS, int KC, int STAGES>
+struct Fp32Tile {
+    static constexpr int kWarps = WARPS;
+    static constexpr int kTM = WARPS / 4 * 32;         // queries per CTA
+    static constexpr int kThreads = 32 * WARPS;
+    static constexpr int kKC = KC;                     // weight rows per staged chunk
+    static constexpr int kWStages = STAGES;            // weight chunks in flight (ring)
+    static constexpr int kActStride = kTM + 4;         // floats between consecutive k of act[k][m]
+    static constexpr size_t kSmem = sizeof(float) * (kH * kActStride + STAGES * KC * kH);
+    static_assert(WARPS % 4 == 0 && kTM <= kThreads && STAGES >= 2 && kSmem <= 220 * 1024, "FP32 tile shape");
+};
 constexpr int kFUnroll = 16;              // k steps unrolled in the inner loop
-static_assert(kWStages >= 2 && sizeof(float) * (kH * kActStride + kWStages * kKC * kH) <= 220 * 1024 / kCtasPerSm,
-              "FP32 tile and weight ring exceed shared memory");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -265,9 +270,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // act[n][m] = relu(sum_k act[k][m] Wt[k][n] + b[n]) for the CTA's kTM queries,
 // in place.  Lane (ty, tx) = (lane / 8, lane % 8) of warp w: rows
 // (w / 4) 32 + ty 8 .. + 7, columns (w % 4) 64 + tx 4 .. + 3 and 32 more.
-// Every output sums its products in order k = 0..K-1 with one rounding per
-// FMA.  The sums live in registers until every k has been read; the last
-// chunk ends with a barrier before the epilogue overwrites the tile.
+// The sums live in registers until every k has been read; the last chunk
+// ends with a barrier before the epilogue overwrites the tile.
+template <class T>
 __device__ __forceinline__ void dense_relu(float* act, int K, const float* __restrict__ Wt,
                                            const float* __restrict__ bias, float* __restrict__ wbuf) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -278,31 +283,31 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    const int nchunk = K / kKC;
+    const int nchunk = K / T::kKC;
     // ring of kWStages chunk buffers: chunk c + kWStages - 1 is issued at the
     // top of chunk c into the buffer chunk c - 1 used, which every thread
     // has left once it passed chunk c's barrier (one barrier per chunk)
     auto stage = [&](int c) {
         if (c < nchunk) {
-            const float* src = Wt + (size_t)c * kKC * kH;
-            float* dst = wbuf + (c % kWStages) * kKC * kH;
+            const float* src = Wt + (size_t)c * T::kKC * kH;
+            float* dst = wbuf + (c % T::kWStages) * T::kKC * kH;
 #pragma unroll
-            for (int v = tid; v < kKC * kH / 4; v += kThreads) cp_async16(dst + 4 * v, src + 4 * v);
+            for (int v = tid; v < T::kKC * kH / 4; v += T::kThreads) cp_async16(dst + 4 * v, src + 4 * v);
         }
         cp_async_commit();   // possibly empty: keeps the group count uniform
     };
 #pragma unroll
-    for (int c = 0; c < kWStages - 1; ++c) stage(c);
+    for (int c = 0; c < T::kWStages - 1; ++c) stage(c);
     for (int c = 0; c < nchunk; ++c) {
-        cp_async_wait<kWStages - 2>();   // chunk c has landed (this thread's copies)
-        __syncthreads();                 // ... and every thread's; chunk c - 1 is released
-        stage(c + kWStages - 1);
-        const float* w = wbuf + (c % kWStages) * kKC * kH + col0;
-        const float* a = act + (size_t)(c * kKC) * kActStride + row0;
+        cp_async_wait<T::kWStages - 2>();   // chunk c has landed (this thread's copies)
+        __syncthreads();                    // ... and every thread's; chunk c - 1 is released
+        stage(c + T::kWStages - 1);
+        const float* w = wbuf + (c % T::kWStages) * T::kKC * kH + col0;
+        const float* a = act + (size_t)(c * T::kKC) * T::kActStride + row0;
 #pragma unroll kFUnroll
-        for (int kk = 0; kk < kKC; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(a + kk * kActStride);
-            const float4 a1 = *reinterpret_cast<const float4*>(a + kk * kActStride + 4);
+        for (int kk = 0; kk < T::kKC; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(a + kk * T::kActStride);
+            const float4 a1 = *reinterpret_cast<const float4*>(a + kk * T::kActStride + 4);
             const float4 w0 = *reinterpret_cast<const float4*>(w + kk * kH);
             const float4 w1 = *reinterpret_cast<const float4*>(w + kk * kH + 32);
             const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
@@ -320,7 +325,7 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
     for (int j = 0; j < 8; ++j) {
         const int col = col0 + (j < 4 ? j : 28 + j);
         const float b = bias[col];
-        float* o = act + (size_t)col * kActStride + row0;
+        float* o = act + (size_t)col * T::kActStride + row0;
         *reinterpret_cast<float4*>(o) = make_float4(fmaxf(acc[0][j] + b, 0.f), fmaxf(acc[1][j] + b, 0.f),
                                                     fmaxf(acc[2][j] + b, 0.f), fmaxf(acc[3][j] + b, 0.f));
         *reinterpret_cast<float4*>(o + 4) = make_float4(fmaxf(acc[4][j] + b, 0.f), fmaxf(acc[5][j] + b, 0.f),
@@ -331,62 +336,174 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
 
 // Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // of min(n, *Q.cnt) queries (the tile loop is uniform within a CTA).
-__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+template <class T>
+__global__ void __launch_bounds__(T::kThreads, 1)
     k_mlp_fp32(const float* __restrict__ wb, QuerySrc Q, int64_t n_max, float scale, float radius, float amp,
                float* __restrict__ zout) {
     extern __shared__ __align__(16) float sm[];
-    float* act = sm;                         // [kH][kActStride], layers run in place
-    float* wbuf = sm + kH * kActStride;      // kWStages staged weight chunks
-    __shared__ float3 xs[kTM];
-    __shared__ float part[kTM][4];
+    float* act = sm;                            // [kH][kActStride], layers run in place
+    float* wbuf = sm + kH * T::kActStride;      // kWStages staged weight chunks
+    __shared__ float3 xs[T::kTM];
+    __shared__ float part[T::kTM][4];
     const int tid = threadIdx.x;
     const int64_t n = query_count(Q, n_max);
     const float* B = wb + kOffB;
-    for (int64_t base = (int64_t)blockIdx.x * kTM; base < n; base += (int64_t)gridDim.x * kTM) {
-        if (tid < kTM) {
+    for (int64_t base = (int64_t)blockIdx.x * T::kTM; base < n; base += (int64_t)gridDim.x * T::kTM) {
+        if (tid < T::kTM) {
             int64_t q = base + tid;
             xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
         }
         __syncthreads();
-        for (int i = tid; i < kNF * kTM; i += kThreads) {
-            int j = i / kTM, m = i % kTM;
+        for (int i = tid; i < kNF * T::kTM; i += T::kThreads) {
+            int j = i / T::kTM, m = i % T::kTM;
             float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
-            act[j * kActStride + m] = sc.x;
-            act[(kNF + j) * kActStride + m] = sc.y;
+            act[j * T::kActStride + m] = sc.x;
+            act[(kNF + j) * T::kActStride + m] = sc.y;
         }
         __syncthreads();
-        for (int l = 0; l < kNL; ++l) dense_relu(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
-        for (int t = tid; t < 4 * kTM; t += kThreads) {
-            const int m = t % kTM, p = t / kTM;
+        for (int l = 0; l < kNL; ++l)
+            dense_relu<T>(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
+        for (int t = tid; t < 4 * T::kTM; t += T::kThreads) {
+            const int m = t % T::kTM, p = t / T::kTM;
             const float* w5 = wb + kOffW[kNL];
             float s = 0.0f;
-            for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[k * kActStride + m], w5[k], s);
+            for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[k * T::kActStride + m], w5[k], s);
             part[m][p] = s;
         }
         __syncthreads();
-        if (tid < kTM && base + tid < n) {
+        if (tid < T::kTM && base + tid < n) {
             float f = ((part[tid][0] + part[tid][1]) + (part[tid][2] + part[tid][3])) + wb[kOffb[kNL]];
             zout[query_index(Q, base + tid)] = envelope_logit(xs[tid], f, scale, radius, amp);
         }
     }
 }
 
-static size_t fp32_smem() { return sizeof(float) * (kH * kActStride + kWStages * kKC * kH); }
+// The tile shapes the autotuner chooses from (warps, K chunk, chunks in
+// flight); index 0 is the shape measured best on GB300 and the fallback.
+using Fp32T0 = Fp32Tile<16, 32, 2>;
+using Fp32T1 = Fp32Tile<16, 16, 3>;
+using Fp32T2 = Fp32Tile<12, 32, 3>;
+using Fp32T3 = Fp32Tile<8, 32, 3>;
+constexpr int kFp32Variants = kFp32VariantCount;
+
+template <class T>
+static void launch_fp32_tile(const MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s) {
+    const int64_t tiles = (n + T::kTM - 1) / T::kTM;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)std::max(st->sms, 1));
+    k_mlp_fp32<T><<<grid, T::kThreads, T::kSmem, s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z);
+    note_launch();
+}
+
+static void launch_fp32_variant(int v, const MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s) {
+    switch (v) {
+        case 1: launch_fp32_tile<Fp32T1>(st, Q, n, z, s); break;
+        case 2: launch_fp32_tile<Fp32T2>(st, Q, n, z, s); break;
+        case 3: launch_fp32_tile<Fp32T3>(st, Q, n, z, s); break;
+        default: launch_fp32_tile<Fp32T0>(st, Q, n, z, s); break;
+    }
+}
 
 static odc_status fp32_kernel_setup(std::string* err) {
-    MLP_CK(cudaFuncSetAttribute(k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp32_smem()));
+    MLP_CK(cudaFuncSetAttribute(k_mlp_fp32<Fp32T0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fp32T0::kSmem));
+    MLP_CK(cudaFuncSetAttribute(k_mlp_fp32<Fp32T1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fp32T1::kSmem));
+    MLP_CK(cudaFuncSetAttribute(k_mlp_fp32<Fp32T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fp32T2::kSmem));
+    MLP_CK(cudaFuncSetAttribute(k_mlp_fp32<Fp32T3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Fp32T3::kSmem));
     return ODC_OK;
+}
+
+// Deterministic calibration points in [-1, 1]^3 (a hash of the index).
+__global__ void k_calib_points(float3* p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    float c[3];
+    for (int a = 0; a < 3; ++a) {
+        h ^= h >> 29;
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 32;
+        c[a] = (float)(h >> 40) * (2.0f / 16777216.0f) - 1.0f;
+    }
+    p[i] = make_float3(c[0], c[1], c[2]);
+}
+
+// Autotuner: time every tile shape on a calibration list of 4 tiles per SM
+// (three runs each, CUDA events on the stream, best of three) and keep the
+// fastest.  Runs once per process and device; the choice never changes a
+// result, only the time.
+static int g_fp32_pick[64];
+static float g_fp32_ms[64][kFp32Variants];
+static bool g_fp32_init = false;
+
+static std::mutex g_fp32_mu;   // request-loop slots prepare their networks on their own threads
+
+static odc_status fp32_autotune(MlpState* st, cudaStream_t s, std::string* err) {
+    int dev = 0;
+    MLP_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_fp32_mu);
+    if (!g_fp32_init) {
+        for (int& v : g_fp32_pick) v = -1;
+        g_fp32_init = true;
+    }
+    if (dev < 0 || dev >= 64) return ODC_OK;
+    if (g_fp32_pick[dev] >= 0) {
+        st->fp32_variant = g_fp32_pick[dev];
+        return ODC_OK;
+    }
+    const int64_t n = (int64_t)4 * std::max(st->sms, 1) * 128;
+    float3* pts = nullptr;
+    float* z = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MLP_CK(cudaMallocAsync((void**)&pts, n * sizeof(float3), s));
+    MLP_CK(cudaMallocAsync((void**)&z, n * sizeof(float), s));
+    MLP_CK(cudaEventCreate(&e0));
+    MLP_CK(cudaEventCreate(&e1));
+    k_calib_points<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n);
+    note_launch();
+    QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int v = 0; v < kFp32Variants; ++v) {
+        float vbest = 0.0f;
+        for (int rep = 0; rep < 4; ++rep) {   // the first run warms up
+            MLP_CK(cudaEventRecord(e0, s));
+            launch_fp32_variant(v, st, Q, n, z, s);
+            MLP_CK(cudaEventRecord(e1, s));
+            MLP_CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            MLP_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0 && (rep == 1 || ms < vbest)) vbest = ms;
+        }
+        g_fp32_ms[dev][v] = vbest;
+        if (v == 0 || vbest < best_ms) { best = v; best_ms = vbest; }
+    }
+    MLP_CK(cudaGetLastError());
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    MLP_CK(cudaFreeAsync(pts, s));
+    MLP_CK(cudaFreeAsync(z, s));
+    g_fp32_pick[dev] = best;
+    st->fp32_variant = best;
+    return ODC_OK;
+}
+
+int mlp_fp32_variant(const MlpState* st) {
+    return !st ? -1 : (st->fp32_forced >= 0 ? st->fp32_forced : st->fp32_variant);
+}
+
+float mlp_fp32_variant_ms(int v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return (g_fp32_init && dev >= 0 && dev < 64 && v >= 0 && v < kFp32Variants) ? g_fp32_ms[dev][v] : 0.0f;
 }
 
 // n is the query count, or with Q.cnt its upper bound (the count is then
 // accumulated on the device for the FLOP accounting).
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
     if (n <= 0) return ODC_OK;
-    int64_t tiles = (n + kTM - 1) / kTM;
-    unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)kCtasPerSm * std::max(st->sms, 1));
+    const int v = st->fp32_forced >= 0 ? st->fp32_forced : std::max(st->fp32_variant, 0);
     cudaEvent_t* ev = mlp_ev_pair(st, 0);
     if (ev) MLP_CK(cudaEventRecord(ev[0], s));
-    k_mlp_fp32<<<grid, kThreads, fp32_smem(), s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z); note_launch();
+    launch_fp32_variant(v, st, Q, n, z, s);
     if (ev) MLP_CK(cudaEventRecord(ev[1], s));
     MLP_CK(cudaGetLastError());
     if (!Q.cnt) {

@@ -22,6 +22,11 @@ odc_status mlp_prepare(MlpState** st, const odc_mlp* m, cudaStream_t s, std::str
 void mlp_destroy(MlpState* st);
 // Device bytes held by the network state (weights, operand tiles, scratch).
 size_t mlp_device_bytes(const MlpState* st);
+// FP32 network tile shape in use (forced, else autotuned; -1 before the
+// first upload) and
+// the autotuner's time for shape v on this device (ms, 0 if not measured).
+int mlp_fp32_variant(const MlpState* st);
+float mlp_fp32_variant_ms(int v);
 
 // Device scratch owned by the MLP state (grows on demand, never shrinks).
 odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::string* err);

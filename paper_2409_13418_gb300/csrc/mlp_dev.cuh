@@ -66,6 +66,8 @@ struct MlpState {
     double flops[3] = {0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
     int64_t launches[3] = {0, 0, 0};
     int split = 1;              // use the split-FP16 tier for band re-evaluation
+    int fp32_variant = -1;      // FP32 network tile shape picked by the autotuner (-1: not yet)
+    int fp32_forced = -1;       // tile shape forced by the source's flags (-1: the autotuner's)
     float zsplit = 4e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)

@@ -70,7 +70,7 @@ class Stats(C.Structure):
                 ("n_launches", C.c_int32), ("mlp_launches", C.c_int64), ("tc_flops", C.c_double),
                 ("tc_ms", C.c_float), ("pad_", C.c_int32), ("tc_launches", C.c_int64),
                 ("split_flops", C.c_double), ("split_ms", C.c_float), ("pad2_", C.c_int32),
-                ("split_launches", C.c_int64), ("n_split", C.c_int64)]
+                ("split_launches", C.c_int64), ("n_split", C.c_int64), ("fp32_tile", C.c_int64)]
 
 
 class SlabC(C.Structure):
@@ -221,7 +221,8 @@ def _ptr(a: np.ndarray) -> int:
 class _SourceHolder:
     """Keeps the numpy buffers behind a Source structure alive."""
 
-    def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0, reupload=False):
+    def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0, reupload=False,
+                 fp32_tile=None):
         self.keep = []
         self.src = Source()
         if src is None:
@@ -263,7 +264,7 @@ class _SourceHolder:
             m.band = 0.03 if band is None else band
             m.no_split = 0 if split else 1
             m.split_zmargin = split_zmargin
-            m.flags = MLP_REUPLOAD if reupload else 0
+            m.flags = (MLP_REUPLOAD if reupload else 0) | (((fp32_tile + 1) << 8) if fp32_tile is not None else 0)
             self.keep.append(m)
             self.src.kind = SRC_MLP
             self.src.mlp = C.addressof(m)
@@ -475,8 +476,10 @@ class Context:
         _check(_lib.odc_mesh_quality(self.h, C.byref(m), iso, n_samples, seed, what, C.byref(q)))
         return {f: getattr(q, f) for f, _ in QualityC._fields_}
 
-    def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None, split=True):
-        holder = _SourceHolder(src, None if precision < 0 else min(precision, PREC_BF16), band, split)
+    def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None, split=True,
+                    fp32_tile=None):
+        holder = _SourceHolder(src, None if precision < 0 else min(precision, PREC_BF16), band, split,
+                               fp32_tile=fp32_tile)
         pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
         lab = np.empty(pts.shape[0], np.uint8)
         z = np.empty(pts.shape[0], np.float32)

@@ -171,3 +171,22 @@ def test_bf16_extract_equals_fp32_plain_path_off_half_iso(ctx, mlp, iso):
 def test_bf16_extract_replay_parity(ctx, mlp):
     mesh, ref, rep, verts, tris = replay_parity(ctx, mlp, I.cube_grid(32), 15, precision=1, band=BF16_BAND)
     assert rep["vert_max_err"] < 1e-4
+
+
+def test_fp32_tile_shapes_give_identical_bits(ctx, mlp):
+    """The autotuner may pick any of the FP32 network's tile shapes: all give
+    the same logits bit for bit (same FMA order per output), and the pick is
+    one of them."""
+    rng = np.random.default_rng(7)
+    pts = rng.uniform(-1, 1, (50000, 3)).astype(np.float32)
+    ref = None
+    for v in range(4):
+        _, z = ctx.eval_points(mlp, pts, precision=0, fp32_tile=v)
+        if ref is None:
+            ref = z
+        assert z.tobytes() == ref.tobytes(), v
+    _, z = ctx.eval_points(mlp, pts, precision=0)
+    assert z.tobytes() == ref.tobytes()
+    m = ctx.extract(mlp, I.cube_grid(24), steps_1d=10, precision=0)
+    assert m.stats["fp32_tile"] in (0, 1, 2, 3)
+    print("autotuned FP32 tile shape", m.stats["fp32_tile"])
