@@ -291,7 +291,7 @@ struct TcParams {
     float scale, radius, amp;
     float* z;
     int* err;
-    float wscale_inv[4];    // split path: 2^-s_l undoing the weight scale of layer l
+    const float* wsc;       // split path (device [4]): 2^-s_l undoing the weight scale of layer l
     float zt;               // split path: logit written for an out-of-range query (forces re-evaluation)
 };
 
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 acc_phase ^= 1;
                 tc_fence_after();
                 const float* bias = sp + l * kH;
-                const float unscale = P.wscale_inv[l];
+                const float unscale = __ldg(P.wsc + l);
                 if (l < kNL - 1) {
                     tmem_row_chunks_sum16<kGCols / 16>(trow + c0, trow + kH + c0, kLoUnscale,
                                                        [&](int cb, const float (&v)[16]) {
@@ -817,11 +817,9 @@ struct MlpTc {
     __nv_bfloat16* w = nullptr;     // W_l as BF16 [256][K_l], l = 0..3
     __half* w16 = nullptr;          // split path: fp16 hi parts of W_l 2^s_l, then the lo parts
     CUtensorMap maps[4];            // BF16 weights
-    CUtensorMap maps_hi[4];         // split path hi parts
-    CUtensorMap maps_lo[4];         // split path lo parts
     CUtensorMap maps_hi_mc[4];      // split path, 128 weight rows per box (each CTA of a pair)
     CUtensorMap maps_lo_mc[4];
-    float wscale_inv[4];
+    float* wsc = nullptr;           // device [4]: split path weight unscale per layer
     int* err = nullptr;
     int sms = 0;
     int clusters3 = 0;              // co-resident CTA pairs of the split kernel
@@ -847,51 +845,87 @@ static EncodeTiledFn encode_fn(std::string* err) {
     return fn;
 }
 
+// Operand tiles of the tensor-core networks, built on the device from the
+// FP32 blob: BF16 W^T tiles [n][k] per layer (K-major), and for the split
+// path a power-of-two scale per layer (the largest 2^s keeping |w| 2^s below
+// 2^14) with the FP16 hi and 2^11-scaled lo parts of w 2^s.
+namespace {
+__global__ void k_wprep_scale(const float* __restrict__ blob, float* __restrict__ wsc, int* __restrict__ sexp_out) {
+    const int l = blockIdx.x;
+    const size_t K = l == 0 ? 2 * kNF : kH;
+    const float* Wt = blob + kOffW_(l);
+    float m = 0.0f;
+    for (size_t i = threadIdx.x; i < K * kH; i += blockDim.x) m = fmaxf(m, fabsf(Wt[i]));
+    __shared__ float red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float wmax = red[0];
+        int sexp = 0;
+        while (sexp < 24 && wmax * __int_as_float((127 + sexp + 1) << 23) < 16384.0f) ++sexp;
+        wsc[l] = __int_as_float((127 - sexp) << 23);
+        sexp_out[l] = sexp;
+    }
+}
+
+__global__ void k_wprep_conv(const float* __restrict__ blob, const int* __restrict__ sexp_in, size_t total,
+                             __nv_bfloat16* __restrict__ wb, __half* __restrict__ w16) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // tile element, layers in order
+    if (i >= total) return;
+    size_t off = 0;
+    int l = 0;
+    for (; l < 3; ++l) {
+        const size_t sz = (size_t)kH * (l == 0 ? 2 * kNF : kH);
+        if (i < off + sz) break;
+        off += sz;
+    }
+    const size_t K = l == 0 ? 2 * kNF : kH;
+    const size_t j = i - off, n = j / K, k = j % K;
+    const float w = blob[kOffW_(l) + k * kH + n];
+    wb[i] = __float2bfloat16_rn(w);
+    const float ws = w * __int_as_float((127 + sexp_in[l]) << 23);
+    const __half hi = __float2half_rn(ws);
+    w16[i] = hi;
+    w16[total + i] = __float2half_rn((ws - __half2float(hi)) * tc::kLoScale);
+}
+}  // namespace
+
 odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::string* err) {
+    (void)hb;   // the tiles are built from the device copy of the blob
     if (!st->tc) st->tc = new MlpTc();
     MlpTc* T = st->tc;
     const size_t K[4] = {2 * kNF, kH, kH, kH};
     size_t total = 0;
-    for (int l = 0; l < 4; ++l) total += (size_t)kH * K[l];
-    std::vector<__nv_bfloat16> h(total);
-    std::vector<__half> h16(2 * total);
-    size_t off = 0;
     size_t offs[4];
     for (int l = 0; l < 4; ++l) {
-        offs[l] = off;
-        const float* Wt = hb + kOffW[l];   // [K][256]
-        float wmax = 0.0f;
-        for (size_t i = 0; i < K[l] * kH; ++i) wmax = std::max(wmax, std::fabs(Wt[i]));
-        // largest power of two keeping |w| 2^s below 2^14 (FP16 max 65504)
-        int sexp = 0;
-        while (sexp < 24 && wmax * std::ldexp(1.0f, sexp + 1) < 16384.0f) ++sexp;
-        T->wscale_inv[l] = std::ldexp(1.0f, -sexp);
-        for (int n = 0; n < kH; ++n)
-            for (size_t k = 0; k < K[l]; ++k) {
-                float w = Wt[k * kH + n];
-                h[off + (size_t)n * K[l] + k] = __float2bfloat16_rn(w);
-                float ws = std::ldexp(w, sexp);
-                __half hi = __float2half_rn(ws);
-                h16[off + (size_t)n * K[l] + k] = hi;
-                h16[total + off + (size_t)n * K[l] + k] = __float2half_rn((ws - __half2float(hi)) * tc::kLoScale);
-            }
-        off += (size_t)kH * K[l];
+        offs[l] = total;
+        total += (size_t)kH * K[l];
     }
-    if (!T->w) {
+    const bool fresh = !T->w;
+    if (fresh) {
         if (cudaMalloc((void**)&T->w, total * sizeof(__nv_bfloat16)) != cudaSuccess ||
             cudaMalloc((void**)&T->w16, 2 * total * sizeof(__half)) != cudaSuccess ||
+            cudaMalloc((void**)&T->wsc, 4 * sizeof(float) + 4 * sizeof(int)) != cudaSuccess ||
             cudaMalloc((void**)&T->err, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             *err = "tensor-core weight allocation failed";
             return ODC_ERR_OOM;
         }
     }
-    if (cudaMemcpyAsync(T->w, h.data(), total * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(T->w16, h16.data(), 2 * total * sizeof(__half), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
-        *err = "tensor-core weight upload failed";
+    int* sexp = (int*)(T->wsc + 4);
+    k_wprep_scale<<<4, 256, 0, s>>>(st->wblob, T->wsc, sexp);
+    note_launch();
+    k_wprep_conv<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(st->wblob, sexp, total, T->w, T->w16);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess || cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess) {
+        *err = "tensor-core weight preparation failed";
         return ODC_ERR_CUDA;
     }
+    if (!fresh && T->ready) return ODC_OK;   // tensor maps, attributes and occupancy are set up already
     EncodeTiledFn fn = encode_fn(err);
     if (!fn) return ODC_ERR_UNSUPPORTED;
     for (int l = 0; l < 4; ++l) {
@@ -902,14 +936,6 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
         CUresult r = fn(&T->maps[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)(T->w + offs[l]), gdim, gstride, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r == CUDA_SUCCESS)
-            r = fn(&T->maps_hi[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + offs[l]), gdim, gstride, box,
-                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r == CUDA_SUCCESS)
-            r = fn(&T->maps_lo[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + total + offs[l]), gdim,
-                   gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         cuuint32_t box_mc[2] = {(cuuint32_t)tc::kKC, (cuuint32_t)tc::kBRows};
         if (r == CUDA_SUCCESS)
             r = fn(&T->maps_hi_mc[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + offs[l]), gdim, gstride,
@@ -968,7 +994,7 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
     }
     int64_t tiles = (n + tc::kRows - 1) / tc::kRows;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {1.f, 1.f, 1.f, 1.f}, st->zt};
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, nullptr, st->zt};
     cudaEvent_t* ev = mlp_ev_pair(st, 1);
     if (ev) cudaEventRecord(ev[0], s);
     tc::k_mlp_tc<<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2], T->maps[3], P);
@@ -998,8 +1024,8 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
     // CTA pairs, each pair 256 queries per step
     int64_t steps = (n + tc::kPairRows - 1) / tc::kPairRows;
     int grid = 2 * (int)std::min<int64_t>(steps, (int64_t)T->clusters3);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, {}, st->zt};
-    for (int l = 0; l < 4; ++l) P.wscale_inv[l] = T->wscale_inv[l];
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, nullptr, st->zt};
+    P.wsc = T->wsc;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1049,7 +1075,7 @@ size_t mlp_tc_device_bytes(const MlpState* st) {
     const MlpTc* T = st ? st->tc : nullptr;
     if (!T || !T->w) return 0;
     const size_t total = (size_t)kH * (2 * kNF + 3 * kH);
-    return total * sizeof(__nv_bfloat16) + 2 * total * sizeof(__half) + sizeof(int);
+    return total * sizeof(__nv_bfloat16) + 2 * total * sizeof(__half) + sizeof(int) + 4 * (sizeof(float) + sizeof(int));
 }
 
 void mlp_tc_destroy(MlpState* st) {
@@ -1057,6 +1083,7 @@ void mlp_tc_destroy(MlpState* st) {
     if (st->tc->w) cudaFree(st->tc->w);
     if (st->tc->w16) cudaFree(st->tc->w16);
     if (st->tc->err) cudaFree(st->tc->err);
+    if (st->tc->wsc) cudaFree(st->tc->wsc);
     delete st->tc;
     st->tc = nullptr;
 }
