@@ -116,6 +116,7 @@ class Result:
     queries: int = 0
     stats: dict = field(default_factory=dict)
     search: dict = field(default_factory=dict)   # 2D decisions: Jq, J1, J2, lab_m, found
+    violations: dict = field(default_factory=dict)   # per-element replay violations: edges (E,), faces (F,)
 
 
 def grid_coords(grid):
@@ -324,7 +325,8 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     the 2D decisions ``Jq, J1, J2, lab_m, found``.  Every replayed decision is
     still checked against phi here: a replayed label that disagrees with phi
     where phi's margin is at least ``replay_margin`` is a violation, counted
-    per element in ``stats['edge_violations']`` / ``stats['face_violations']``.
+    per element in ``stats['edge_violations']`` / ``stats['face_violations']``
+    (totals) and ``violations['edges']`` / ``violations['faces']`` (masks).
     All geometry downstream is then computed from the replayed decisions.
     """
     phi = Occupancy(src, iso)
@@ -662,6 +664,7 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
                       vertices=verts, triangles=np.array(tris, np.int64).reshape(-1, 3),
                       quad_edges=np.zeros(0, np.int64), quad_case=np.zeros(0, np.int64), quad_flag=np.zeros(0, bool),
                       quad_margin=np.zeros(0), queries=phi.queries, search=search,
+                      violations=dict(edges=edge_viol, faces=np.zeros(F, bool)),
                       stats=dict(E=E, F=F, C=C, V3=0, case3=0, flips=len(flips), fix_rounds=rounds,
                                  queries=phi.queries, edge_violations=int(edge_viol.sum()), face_violations=0))
 
@@ -816,6 +819,7 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
                   quad_edges=quad_edges.astype(np.int64), quad_case=quad_case.astype(np.int64),
                   quad_flag=quad_flag.astype(bool), quad_margin=qmar,
                   queries=phi.queries, search=search,
+                  violations=dict(edges=edge_viol, faces=face_viol),
                   stats=dict(E=E, F=F, C=C, V3=V3, case3=int(is3.sum()), flips=len(flips),
                              fix_rounds=rounds, queries=phi.queries,
                              edge_violations=int(edge_viol.sum()), face_violations=int(face_viol.sum())))
