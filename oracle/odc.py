@@ -10,7 +10,7 @@ Follows the paper step by step:
   Sec. 4, 5.4, A.1.5 one quad per interior crossing edge, split into 2 or 4
                     triangles by the convex/concave analysis (Eqs. A1, A2)
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent:
   * 1D output: the midpoint of the final interval, T/2^(k+1) with T odd.
   * 2D ray r: towards the side of l whose segment corners carry the label
     opposite to m's; "q coincides with m" means the line-binary search never

@@ -1,6 +1,6 @@
 """Helpers comparing the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (the benchmark spec): masks, configurations, cycles, flips, quads and
+Tolerances: masks, configurations, cycles, flips, quads and
 triangles bit-exact; 1D results T bit-exact (both sides query the same float32
 points and decide the exact predicate); 2D points and 3D points within 1e-4
 cell.  Elements whose oracle decision margin is below ``margin_eps`` or whose

@@ -51,7 +51,7 @@ def test_config2_random_csg_128(ctx, seed):
     src = I.random_csg(seed)
     ref, mesh, rep, verts, tris = _run(ctx, src, I.cube_grid(128), 12)
     print(seed, rep, ref.stats)
-    # spec: grid margins >= 1e-6 on reported seeds
+    # required: grid margins >= 1e-6 on reported seeds
     assert ref.label_margin.min() > 0
     assert meshcheck.check_closed_manifold(tris)["ok"]
 
