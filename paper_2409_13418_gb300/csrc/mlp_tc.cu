@@ -566,11 +566,13 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
 }
 
 __device__ __forceinline__ void store_split8(uint8_t* Ahi, uint8_t* Alo, uint32_t off, const float* v) {
-    __align__(16) __half h[8], l[8];
+    __align__(16) __half2 h[4], l[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        h[i] = __float2half_rn(v[i]);
-        l[i] = __float2half_rn((v[i] - __half2float(h[i])) * kLoScale);
+    for (int i = 0; i < 4; ++i) {
+        // two round-to-nearest conversions per instruction; v - hi is exact
+        h[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+        const float2 hf = __half22float2(h[i]);
+        l[i] = __floats2half2_rn((v[2 * i] - hf.x) * kLoScale, (v[2 * i + 1] - hf.y) * kLoScale);
     }
     *reinterpret_cast<uint4*>(Ahi + off) = *reinterpret_cast<const uint4*>(h);
     *reinterpret_cast<uint4*>(Alo + off) = *reinterpret_cast<const uint4*>(l);
@@ -736,6 +738,9 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 const float* bias = sp + l * kH;
                 const float unscale = __ldg(P.wsc + l);
                 if (l < kNL - 1) {
+                    // an activation at or above kF16Safe marks the row (poisoned
+                    // below); its stored values no longer matter
+                    float mx = 0.0f;
                     tmem_row_chunks_sum16<kGCols / 16>(trow + c0, trow + kH + c0, kLoUnscale,
                                                        [&](int cb, const float (&v)[16]) {
                         const int col = c0 + cb * 16;
@@ -745,12 +750,12 @@ __global__ void __launch_bounds__(kThreads3, 1)
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 h[i] = fmaxf(fmaf(v[u * 8 + i], unscale, bias[col + u * 8 + i]), 0.f);
-                                range_ok &= h[i] < kF16Safe;
-                                h[i] = fminf(h[i], kF16Safe);
+                                mx = fmaxf(mx, h[i]);
                             }
                             store_split8(Ahi, Alo, a_offset(r, col + u * 8), h);
                         }
                     });
+                    range_ok &= mx < kF16Safe;
                     // a row that left the FP16 range is poisoned with an infinite
                     // input to the last layer: every accumulator of that row turns
                     // non-finite, which every column group sees
