@@ -527,14 +527,18 @@ __global__ void k_route(const float* __restrict__ hint, int64_t n, float zs, flo
     r[i] = h < zs ? 2 : (h < zb ? (split ? 1 : 2) : 0);
 }
 // Queries of tier `from` whose logit lies within thr of t move to tier `to`;
-// the queries now in tier `to` are appended to list (one atomic per warp:
+// the queries now in tier `to` are appended to list (one atomic per block:
 // the list order varies between runs, the logits written back through it do
-// not) and counted in *cnt and *total.
-__global__ void k_tier_list(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr,
-                            uint8_t* __restrict__ r, int* __restrict__ list, unsigned long long* __restrict__ cnt,
-                            unsigned long long* __restrict__ total) {
+// not) and counted in *cnt and *total.  Launched with kTierBlock threads.
+constexpr int kTierBlock = 256;
+__global__ void __launch_bounds__(kTierBlock)
+    k_tier_list(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr,
+                uint8_t* __restrict__ r, int* __restrict__ list, unsigned long long* __restrict__ cnt,
+                unsigned long long* __restrict__ total) {
+    __shared__ unsigned wbase[kTierBlock / 32];
+    __shared__ unsigned long long bbase;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool f = false;
     if (i < n) {
         int ri = r[i];
@@ -545,15 +549,21 @@ __global__ void k_tier_list(const float* __restrict__ z, int64_t n, float t, int
         f = ri == to;
     }
     const uint32_t b = __ballot_sync(0xffffffffu, f);
-    if (!b) return;
-    const int leader = __ffs(b) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) {
-        base = atomicAdd(cnt, (unsigned long long)__popc(b));
-        atomicAdd(total, (unsigned long long)__popc(b));
+    if (lane == 0) wbase[warp] = (unsigned)__popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+#pragma unroll
+        for (int w = 0; w < kTierBlock / 32; ++w) {
+            const unsigned c = wbase[w];
+            wbase[w] = tot;
+            tot += c;
+        }
+        bbase = tot ? atomicAdd(cnt, (unsigned long long)tot) : 0ull;
+        if (tot) atomicAdd(total, (unsigned long long)tot);
     }
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (f) list[base + __popc(b & ((1u << lane) - 1u))] = (int)i;
+    __syncthreads();
+    if (f) list[bbase + wbase[warp] + __popc(b & ((1u << lane) - 1u))] = (int)i;
 }
 
 // Tiered evaluation (A.2.2 binary decision at iso): the sign of every logit
@@ -576,25 +586,25 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     if (Q.idx) { *err = "nested query index"; return ODC_ERR_INTERNAL; }
     uint8_t* route = (uint8_t*)pr;
     unsigned long long* cnt = st->dq + 4;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const unsigned blocks = (unsigned)((n + kTierBlock - 1) / kTierBlock);
     MLP_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
-    k_route<<<blocks, 256, 0, s>>>(hint, n, st->zsplit, st->zband, st->split, route); note_launch();
+    k_route<<<blocks, kTierBlock, 0, s>>>(hint, n, st->zsplit, st->zband, st->split, route); note_launch();
     if (!hint) {
         if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
     } else {
         if ((r = mlp_scratch(st, 27, (size_t)n * 4 + 64, &pl0, err)) != ODC_OK) return r;
-        k_tier_list<<<blocks, 256, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, route, (int*)pl0, cnt + 0, st->dq + 0); note_launch();
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, route, (int*)pl0, cnt + 0, st->dq + 0); note_launch();
         QuerySrc L0{Q.pts, (const int*)pl0, Q.g, cnt + 0};
         if ((r = mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK) return r;
     }
     if (st->split) {
-        k_tier_list<<<blocks, 256, 0, s>>>(z, n, st->zt, 0, 1, st->zband, route, (int*)pl1, cnt + 1, st->dq + 1); note_launch();
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, 0, 1, st->zband, route, (int*)pl1, cnt + 1, st->dq + 1); note_launch();
         QuerySrc L1{Q.pts, (const int*)pl1, Q.g, cnt + 1};
         if ((r = mlp_tc3_eval(st, L1, n, z, s, err)) != ODC_OK) return r;
     }
     const int from = st->split ? 1 : 0;
     const float thr = st->split ? st->zsplit : st->zband;
-    k_tier_list<<<blocks, 256, 0, s>>>(z, n, st->zt, from, 2, thr, route, (int*)pl2, cnt + 2, st->dq + 2); note_launch();
+    k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, 2, thr, route, (int*)pl2, cnt + 2, st->dq + 2); note_launch();
     QuerySrc L2{Q.pts, (const int*)pl2, Q.g, cnt + 2};
     if ((r = launch_fp32(st, L2, n, z, s, err)) != ODC_OK) return r;
     MLP_CK(cudaGetLastError());
