@@ -116,6 +116,20 @@ def workload(seed: int = 0):
     return I.envelope_mlp(seed), I.cube_grid(RES)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_sample(mlp, n_cells: int = 40):
     """Oracle on an n^3-cell block of the same 256^3 grid crossing the surface shell."""
     import numpy as np
@@ -154,7 +168,7 @@ def run_reference(args, rank, world):
             "impl": "reference",
             "config": {"workload": f"envelope MLP 256^3 (k={STEPS_1D}), sampled as a {args.cpu_cells}^3-cell block "
                                    f"of the same grid crossing the surface shell"},
-            "cpu_baseline": {"value": v, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "Mcells/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                              "sample": f"{args.cpu_cells}^3-cell block of the 256^3 grid per step"},
             "e2e": {"value": v, "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -608,9 +622,10 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             c, dt, st = cpu_sample(mlp, args.cpu_cells)
             line["cpu_baseline"] = {"value": c / dt / 1e6, "unit": "Mcells/s", "cores": os.cpu_count(),
-                                    "kind": "oracle",
+                                    "cpu": cpu_model(), "kind": "oracle",
                                     "sample": f"{args.cpu_cells}^3-cell block of the same 256^3 grid crossing the "
-                                              f"surface shell, FP64 numpy oracle"}
+                                              f"surface shell, FP64 numpy oracle (network products on numpy's "
+                                              f"threaded BLAS, the rest single-threaded Python)"}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
