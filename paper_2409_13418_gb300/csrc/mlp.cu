@@ -519,20 +519,28 @@ static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float*
 // Tier of every query: 0 = BF16 tensor-core pass first, 1 = split-FP16 pass
 // first, 2 = FP32 directly.  hint[i] estimates |z_i - zt| (from the logits
 // around the query in its search); no hint routes to the BF16 pass.
-__global__ void k_route(const float* __restrict__ hint, int64_t n, float zs, float zb, int split,
-                        uint8_t* __restrict__ r) {
+struct RouteArgs {
+    const float* hint;
+    float zs, zb;
+    int split;
+};
+__device__ __forceinline__ int route_of(const RouteArgs& ra, int64_t i) {
+    const float h = ra.hint ? ra.hint[i] : INFINITY;
+    return h < ra.zs ? 2 : (h < ra.zb ? (ra.split ? 1 : 2) : 0);
+}
+__global__ void k_route(RouteArgs ra, int64_t n, uint8_t* __restrict__ r) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float h = hint ? hint[i] : INFINITY;
-    r[i] = h < zs ? 2 : (h < zb ? (split ? 1 : 2) : 0);
+    r[i] = (uint8_t)route_of(ra, i);
 }
-// Queries of tier `from` whose logit lies within thr of t move to tier `to`;
-// the queries now in tier `to` are appended to list (one atomic per block:
-// the list order varies between runs, the logits written back through it do
-// not) and counted in *cnt and *total.  Launched with kTierBlock threads.
+// Queries of tier `from` whose logit lies within thr of t move to tier `to`
+// (from < 0: every query takes its tier from the hints first); the queries
+// now in tier `to` are appended to list (one atomic per block: the list order
+// varies between runs, the logits written back through it do not) and
+// counted in *cnt and *total.  Launched with kTierBlock threads.
 constexpr int kTierBlock = 256;
 __global__ void __launch_bounds__(kTierBlock)
-    k_tier_list(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr,
+    k_tier_list(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr, RouteArgs ra,
                 uint8_t* __restrict__ r, int* __restrict__ list, unsigned long long* __restrict__ cnt,
                 unsigned long long* __restrict__ total) {
     __shared__ unsigned wbase[kTierBlock / 32];
@@ -541,10 +549,16 @@ __global__ void __launch_bounds__(kTierBlock)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool f = false;
     if (i < n) {
-        int ri = r[i];
-        if (ri == from && fabsf(z[i] - t) < thr) {
-            ri = to;
-            r[i] = (uint8_t)to;
+        int ri;
+        if (from < 0) {
+            ri = route_of(ra, i);
+            r[i] = (uint8_t)ri;
+        } else {
+            ri = r[i];
+            if (ri == from && fabsf(z[i] - t) < thr) {
+                ri = to;
+                r[i] = (uint8_t)to;
+            }
         }
         f = ri == to;
     }
@@ -588,23 +602,25 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     unsigned long long* cnt = st->dq + 4;
     const unsigned blocks = (unsigned)((n + kTierBlock - 1) / kTierBlock);
     MLP_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
-    k_route<<<blocks, kTierBlock, 0, s>>>(hint, n, st->zsplit, st->zband, st->split, route); note_launch();
+    const RouteArgs ra{hint, st->zsplit, st->zband, st->split};
     if (!hint) {
+        k_route<<<blocks, kTierBlock, 0, s>>>(ra, n, route); note_launch();
         if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
     } else {
+        // routing and the BF16 pass's list in one pass
         if ((r = mlp_scratch(st, 27, (size_t)n * 4 + 64, &pl0, err)) != ODC_OK) return r;
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, route, (int*)pl0, cnt + 0, st->dq + 0); note_launch();
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, ra, route, (int*)pl0, cnt + 0, st->dq + 0); note_launch();
         QuerySrc L0{Q.pts, (const int*)pl0, Q.g, cnt + 0};
         if ((r = mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK) return r;
     }
     if (st->split) {
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, 0, 1, st->zband, route, (int*)pl1, cnt + 1, st->dq + 1); note_launch();
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, 0, 1, st->zband, ra, route, (int*)pl1, cnt + 1, st->dq + 1); note_launch();
         QuerySrc L1{Q.pts, (const int*)pl1, Q.g, cnt + 1};
         if ((r = mlp_tc3_eval(st, L1, n, z, s, err)) != ODC_OK) return r;
     }
     const int from = st->split ? 1 : 0;
     const float thr = st->split ? st->zsplit : st->zband;
-    k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, 2, thr, route, (int*)pl2, cnt + 2, st->dq + 2); note_launch();
+    k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, 2, thr, ra, route, (int*)pl2, cnt + 2, st->dq + 2); note_launch();
     QuerySrc L2{Q.pts, (const int*)pl2, Q.g, cnt + 2};
     if ((r = launch_fp32(st, L2, n, z, s, err)) != ODC_OK) return r;
     MLP_CK(cudaGetLastError());
