@@ -97,9 +97,10 @@ typedef struct {
     float pad[2];
 } odc_csg_prim;
 
-/* MLP precisions.  ODC_PREC_SPLIT (odc_eval_points only) evaluates every
- * point with the split-FP16 tensor-core network, without band handling. */
-enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2 };
+/* MLP precisions.  ODC_PREC_SPLIT and ODC_PREC_F16 (odc_eval_points only)
+ * evaluate every point with the split-FP16 tensor-core network or with the
+ * single-product FP16 network, without band handling. */
+enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2, ODC_PREC_F16 = 3 };
 
 /* Envelope MLP occupancy: occ(x) = sigmoid(env_scale (env_radius - |x| +
  * env_amp f(x))), f(x) = W_L relu(... relu(W_0 [latent, g(x)] + b_0) ...) + b_L,
@@ -109,7 +110,10 @@ enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2 };
  * b_l [rows of W_l].  Supported: n_freq = 64, hidden = 256, n_hidden = 4,
  * latent_dim in {0, 128}.  With ODC_PREC_BF16 every decision whose BF16
  * occupancy lies within ``band`` of iso is re-evaluated so that its sign
- * equals the FP32 plain path's: first by a split-precision tensor-core pass
+ * equals the FP32 plain path's: first by a single-product FP16 tensor-core
+ * pass (FP16 activations and weights w 2^s, FP32 accumulation), whose logits
+ * within 0.025 of the threshold (2.7 times its measured logit error of
+ * 0.0091) go on to a split-precision tensor-core pass
  * (operands split into FP16 hi + lo, three products per layer, FP32
  * accumulation of hi hi and of the lo corrections in separate accumulators),
  * then, for the logits still within ``split_zmargin`` of the threshold (0:
@@ -136,6 +140,8 @@ typedef struct {
     int32_t flags;               /* ODC_MLP_REUPLOAD: prepare and upload the weights even when the
                                     context already holds the same ones (by default a context that
                                     holds the same B, W and b only refreshes the latent's folded bias);
+                                    ODC_MLP_NO_F16_TIER: band decisions skip the FP16 tier and go
+                                    to the split tier directly (same decisions, other cost);
                                     ODC_MLP_FP32_TILE(v): run the FP32 network with tile shape v
                                     (0..3) instead of the autotuner's pick -- every shape gives the
                                     same bits */
@@ -144,7 +150,7 @@ typedef struct {
 /* The FP32 network has four tile shapes (warps x K chunk x chunks in flight:
  * 16x32x2, 16x16x3, 12x32x3, 8x32x3); the first upload on a device times
  * each on a calibration list and keeps the fastest (odc_stats.fp32_tile). */
-enum { ODC_MLP_REUPLOAD = 1 };
+enum { ODC_MLP_REUPLOAD = 1, ODC_MLP_NO_F16_TIER = 2 };
 #define ODC_MLP_FP32_TILE(v) (((v) + 1) << 8)
 
 /* Dense voxel-grid occupancy: values[k][j][i] (host float32, i fastest) are
@@ -232,6 +238,11 @@ typedef struct {
     int64_t split_launches;
     int64_t n_split;             /* band decisions re-evaluated by the split-FP16 tier */
     int64_t fp32_tile;           /* FP32 network tile shape used (MLP sources; -1 otherwise) */
+    double h16_flops;            /* algorithmic FLOPs of the FP16-tier launches */
+    float h16_ms;                /* CUDA-event time of the FP16-tier launches */
+    int32_t pad3_;
+    int64_t h16_launches;
+    int64_t n_h16;               /* band decisions re-evaluated by the FP16 tier */
 } odc_stats;
 
 typedef struct {

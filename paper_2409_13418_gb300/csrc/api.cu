@@ -602,7 +602,9 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
         mlp_timing_collect(c->mlp, 0, &S.mlp_ms, &S.mlp_flops, &S.mlp_launches);
         mlp_timing_collect(c->mlp, 1, &S.tc_ms, &S.tc_flops, &S.tc_launches);
         mlp_timing_collect(c->mlp, 2, &S.split_ms, &S.split_flops, &S.split_launches);
+        mlp_timing_collect(c->mlp, 3, &S.h16_ms, &S.h16_flops, &S.h16_launches);
         S.n_split = mlp_split_count(c->mlp);
+        S.n_h16 = mlp_h16_count(c->mlp);
         S.fp32_tile = mlp_fp32_variant(c->mlp);
     } else {
         S.fp32_tile = -1;
@@ -923,6 +925,8 @@ odc_status odc_extract_slabbed(odc_ctx* c, const odc_source* src, const odc_grid
         sum.mlp_launches += a.mlp_launches; sum.tc_flops += a.tc_flops; sum.tc_ms += a.tc_ms;
         sum.tc_launches += a.tc_launches; sum.split_flops += a.split_flops; sum.split_ms += a.split_ms;
         sum.split_launches += a.split_launches; sum.n_split += a.n_split;
+        sum.h16_flops += a.h16_flops; sum.h16_ms += a.h16_ms; sum.h16_launches += a.h16_launches;
+        sum.n_h16 += a.n_h16;
         // the next slab's extraction reuses the arenas: the placement must be done
         ODC_CK(cudaStreamSynchronize(st));
     }

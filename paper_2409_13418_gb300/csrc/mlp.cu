@@ -42,6 +42,7 @@ float mlp_logit_threshold(float iso) { return (float)std::log((double)iso / (1.0
 int mlp_precision(const MlpState* st) { return st->precision; }
 int64_t mlp_split_count(const MlpState* st) { return st ? (int64_t)st->hq[1] : 0; }
 int64_t mlp_fp32_requery_count(const MlpState* st) { return st ? (int64_t)st->hq[2] : 0; }
+int64_t mlp_h16_count(const MlpState* st) { return st ? (int64_t)st->hq[3] : 0; }
 
 #define MLP_CK(call)                                                                        \
     do {                                                                                    \
@@ -89,8 +90,8 @@ cudaEvent_t* mlp_ev_pair(MlpState* st, int kind) {
 void mlp_timing_begin(MlpState* st, cudaStream_t s) {
     if (!st) return;
     st->ev_used = 0;
-    st->flops[0] = st->flops[1] = st->flops[2] = 0.0;
-    st->launches[0] = st->launches[1] = st->launches[2] = 0;
+    for (auto& f : st->flops) f = 0.0;
+    for (auto& l : st->launches) l = 0;
     for (auto& v : st->hq) v = 0;
     if (st->dq) cudaMemsetAsync(st->dq, 0, 4 * sizeof(unsigned long long), s);
 }
@@ -115,8 +116,11 @@ void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_
         if (cudaEventElapsedTime(&t, st->ev[2 * i], st->ev[2 * i + 1]) == cudaSuccess) *ms += t;
         else cudaGetLastError();
     }
-    // device-sized lists: hq[0] BF16, hq[1] split-FP16 (three products), hq[2] FP32
-    const double dev = kind == 0 ? (double)st->hq[2] : kind == 1 ? (double)st->hq[0] : 3.0 * (double)st->hq[1];
+    // device-sized lists: hq[0] BF16, hq[1] split-FP16 (three products), hq[2] FP32, hq[3] FP16
+    const double dev = kind == 0   ? (double)st->hq[2]
+                       : kind == 1 ? (double)st->hq[0]
+                       : kind == 2 ? 3.0 * (double)st->hq[1]
+                                   : (double)st->hq[3];
     *flops = st->flops[kind] + kFlopsPerQuery * dev;
     *launches = st->launches[kind];
 }
@@ -164,7 +168,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     }
     {
         const int f = (m->flags >> 8) & 0xf;
-        if ((m->flags & ~(ODC_MLP_REUPLOAD | 0xf00)) || f > kFp32VariantCount) {
+        if ((m->flags & ~(ODC_MLP_REUPLOAD | ODC_MLP_NO_F16_TIER | 0xf00)) || f > kFp32VariantCount) {
             *err = "unknown MLP flags";
             return ODC_ERR_INVALID_ARG;
         }
@@ -173,6 +177,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->precision = m->precision;
     st->band = m->band;
     st->split = m->no_split ? 0 : 1;
+    st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
     st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 4e-5f;
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
     st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
@@ -519,14 +524,18 @@ static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float*
 // Tier of every query: 0 = BF16 tensor-core pass first, 1 = split-FP16 pass
 // first, 2 = FP32 directly.  hint[i] estimates |z_i - zt| (from the logits
 // around the query in its search); no hint routes to the BF16 pass.
+// Tiers: 0 BF16 pass, 1 FP16 tier, 2 split-FP16 tier, 3 FP32.
 struct RouteArgs {
     const float* hint;
-    float zs, zb;
-    int split;
+    float zs, zh, zb;
+    int split, h16;
 };
 __device__ __forceinline__ int route_of(const RouteArgs& ra, int64_t i) {
     const float h = ra.hint ? ra.hint[i] : INFINITY;
-    return h < ra.zs ? 2 : (h < ra.zb ? (ra.split ? 1 : 2) : 0);
+    if (h < ra.zs) return 3;
+    if (h < ra.zh) return ra.split ? 2 : 3;
+    if (h < ra.zb) return ra.h16 ? 1 : (ra.split ? 2 : 3);
+    return 0;
 }
 __global__ void k_route(RouteArgs ra, int64_t n, uint8_t* __restrict__ r) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -582,47 +591,58 @@ __global__ void __launch_bounds__(kTierBlock)
 
 // Tiered evaluation (A.2.2 binary decision at iso): the sign of every logit
 // equals the FP32 plain path's.  A logit of the BF16 pass is kept only
-// outside the band |z - zt| >= zband; the split-FP16 tensor-core network
-// (measured error below zsplit / 3) re-takes the band and keeps |z - zt| >=
-// zsplit; the FP32 SIMT network takes the rest.  Without the split tier the
-// whole band goes to FP32.  With hints, queries predicted inside the band
-// (or inside zsplit) start at the split (or FP32) tier: the tiers' acceptance
-// rules are unchanged, so only the cost depends on the hints.  Each tier's
-// list is built and consumed on the device (its size stays there), so the
-// evaluation needs no host round trip.
+// outside the band |z - zt| >= zband; the single-product FP16 tier (measured
+// error 0.0091, below zh16 / 2) re-takes the band and keeps |z - zt| >= zh16; the
+// split-FP16 tensor-core network (measured error below zsplit / 3) re-takes
+// the rest and keeps |z - zt| >= zsplit; the FP32 SIMT network takes what is
+// left.  A disabled tier passes its queries on with its predecessor's
+// margin.  With hints, a query starts at the tier its predicted |z - zt|
+// points to; the acceptance rules are unchanged, so only the cost depends on
+// the hints.  Each tier's list is built and consumed on the device (its size
+// stays there), so the evaluation needs no host round trip.
 static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float* z, const float* hint, cudaStream_t s,
                               std::string* err) {
     odc_status r;
-    void *pr, *pl0, *pl1, *pl2;
+    void *pr, *pl[4];
     if ((r = mlp_scratch(st, 24, (size_t)n + 64, &pr, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, 25, (size_t)n * 4 + 64, &pl1, err)) != ODC_OK) return r;
-    if ((r = mlp_scratch(st, 26, (size_t)n * 4 + 64, &pl2, err)) != ODC_OK) return r;
     if (Q.idx) { *err = "nested query index"; return ODC_ERR_INTERNAL; }
     uint8_t* route = (uint8_t*)pr;
     unsigned long long* cnt = st->dq + 4;
     const unsigned blocks = (unsigned)((n + kTierBlock - 1) / kTierBlock);
     MLP_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
-    const RouteArgs ra{hint, st->zsplit, st->zband, st->split};
+    const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16};
+    // per tier: its list slot, counters (list size, queries since timing began)
+    const int slot[4] = {27, 28, 25, 26};
+    unsigned long long* tot[4] = {st->dq + 0, st->dq + 3, st->dq + 1, st->dq + 2};
+    auto list_of = [&](int tier) -> odc_status {
+        return mlp_scratch(st, slot[tier], (size_t)n * 4 + 64, &pl[tier], err);
+    };
     if (!hint) {
         k_route<<<blocks, kTierBlock, 0, s>>>(ra, n, route); note_launch();
         if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
     } else {
         // routing and the BF16 pass's list in one pass
-        if ((r = mlp_scratch(st, 27, (size_t)n * 4 + 64, &pl0, err)) != ODC_OK) return r;
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, ra, route, (int*)pl0, cnt + 0, st->dq + 0); note_launch();
-        QuerySrc L0{Q.pts, (const int*)pl0, Q.g, cnt + 0};
+        if ((r = list_of(0)) != ODC_OK) return r;
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, ra, route, (int*)pl[0], cnt + 0, tot[0]); note_launch();
+        QuerySrc L0{Q.pts, (const int*)pl[0], Q.g, cnt + 0};
         if ((r = mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK) return r;
     }
-    if (st->split) {
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, 0, 1, st->zband, ra, route, (int*)pl1, cnt + 1, st->dq + 1); note_launch();
-        QuerySrc L1{Q.pts, (const int*)pl1, Q.g, cnt + 1};
-        if ((r = mlp_tc3_eval(st, L1, n, z, s, err)) != ODC_OK) return r;
+    int from = 0;
+    float thr = st->zband;
+    for (int tier = 1; tier <= 3; ++tier) {
+        const bool on = tier == 1 ? st->h16 != 0 : tier == 2 ? st->split != 0 : true;
+        if (!on) continue;
+        if ((r = list_of(tier)) != ODC_OK) return r;
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, tier, thr, ra, route, (int*)pl[tier],
+                                                  cnt + tier, tot[tier]); note_launch();
+        QuerySrc L{Q.pts, (const int*)pl[tier], Q.g, cnt + tier};
+        r = tier == 1 ? mlp_tc16_eval(st, L, n, z, s, err)
+            : tier == 2 ? mlp_tc3_eval(st, L, n, z, s, err)
+                        : launch_fp32(st, L, n, z, s, err);
+        if (r != ODC_OK) return r;
+        from = tier;
+        thr = tier == 1 ? st->zh16 : st->zsplit;
     }
-    const int from = st->split ? 1 : 0;
-    const float thr = st->split ? st->zsplit : st->zband;
-    k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, 2, thr, ra, route, (int*)pl2, cnt + 2, st->dq + 2); note_launch();
-    QuerySrc L2{Q.pts, (const int*)pl2, Q.g, cnt + 2};
-    if ((r = launch_fp32(st, L2, n, z, s, err)) != ODC_OK) return r;
     MLP_CK(cudaGetLastError());
     return ODC_OK;
 }
@@ -632,6 +652,7 @@ static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int
     if (precision < 0) precision = st->precision;
     if (precision == ODC_PREC_FP32) return launch_fp32(st, Q, n, z, s, err);
     if (precision == ODC_PREC_SPLIT) return mlp_tc3_eval(st, Q, n, z, s, err);
+    if (precision == ODC_PREC_F16) return mlp_tc16_eval(st, Q, n, z, s, err);
     return eval_tiered(st, Q, n, z, hint, s, err);
 }
 

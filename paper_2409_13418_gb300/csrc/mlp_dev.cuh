@@ -61,11 +61,13 @@ struct MlpState {
     MlpTc* tc = nullptr;
     // per-launch CUDA events around the network kernels of one extract
     cudaEvent_t ev[2 * kMaxTimedLaunches] = {};
-    int ev_kind[kMaxTimedLaunches] = {};   // 0: FP32 network, 1: BF16 tensor-core network, 2: split-FP16 network
+    int ev_kind[kMaxTimedLaunches] = {};   // 0: FP32, 1: BF16 pass, 2: split-FP16 tier, 3: FP16 tier
     int ev_used = 0;
-    double flops[3] = {0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
-    int64_t launches[3] = {0, 0, 0};
+    double flops[4] = {0.0, 0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
+    int64_t launches[4] = {0, 0, 0, 0};
     int split = 1;              // use the split-FP16 tier for band re-evaluation
+    int h16 = 1;                // use the single-product FP16 tier between the BF16 pass and the split tier
+    float zh16 = 0.025f;        // |z - zt| below which an FP16-tier decision is re-taken by the split tier
     int fp32_variant = -1;      // FP32 network tile shape picked by the autotuner (-1: not yet)
     int fp32_forced = -1;       // tile shape forced by the source's flags (-1: the autotuner's)
     float zsplit = 4e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
@@ -73,9 +75,9 @@ struct MlpState {
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     int sms = 0;                // SM count of the device
     cudaStream_t stream = nullptr;   // stream of the current call (scratch growth is ordered on it)
-    // device counters: [0..2] queries evaluated from device-sized lists by the
-    // BF16, split-FP16 and FP32 networks since mlp_timing_begin; [4..7] the
-    // list sizes of the current evaluation (tiers 0..2)
+    // device counters: [0..3] queries evaluated from device-sized lists by the
+    // BF16, split-FP16, FP32 and FP16 networks since mlp_timing_begin; [4..7]
+    // the list sizes of the current evaluation
     unsigned long long* dq = nullptr;
     unsigned long long hq[4] = {0, 0, 0, 0};   // host copy of dq[0..3] (mlp_timing_finish)
 };
@@ -88,6 +90,8 @@ constexpr double kFlopsPerQuery = 2.0 * (2.0 * kNF * kH + 3.0 * kH * kH + kH);
 odc_status mlp_tc_prepare(MlpState* st, const float* host_blob, cudaStream_t s, std::string* err);
 struct QuerySrc;
 odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
+// Single-product FP16 network (FP16 activations, the split path's hi weights).
+odc_status mlp_tc16_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 void mlp_tc_destroy(MlpState* st);
 size_t mlp_tc_device_bytes(const MlpState* st);
 // ODC_ERR_TIMEOUT if a tensor-core launch since the last check hit a bounded wait.

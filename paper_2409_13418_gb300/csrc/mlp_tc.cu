@@ -51,6 +51,7 @@ constexpr size_t kSmemBytes = 1024 + kSub * kABytes + kStages * kSliceBytes + 25
 constexpr int kChunks0 = 2 * kNF / kKC;     // layer 0: K = 128
 constexpr int kChunksH = kH / kKC;          // layers 1..3: K = 256
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+constexpr float kF16Safe = 30000.0f;      // FP16 activations kept well inside the FP16 range
 
 // ---------------------------------------------------------------- PTX
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -172,15 +173,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo, uint32_t
 }
 constexpr uint32_t kLayoutSW128 = 2, kLayoutSW64 = 4;
 
-// instruction descriptor: D F32, A/B BF16, both K-major, N = 256, M = 128
+// instruction descriptor: D F32, A/B BF16 (or F16), both K-major, N = 256, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
+constexpr uint32_t kIdescH = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 
+template <bool F16>
 __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+        "l"(a), "l"(b), "r"(F16 ? kIdescH : kIdesc), "r"(acc));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
@@ -274,6 +277,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
 }
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+template <bool F16>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi) {
+    return F16 ? pack_f16(lo, hi) : pack_bf16(lo, hi);
+}
 
 // Byte offset of element (row r, k) in a K-major SWIZZLE_128B operand of K
 // extent 256: four 64-column chunks of 128 rows x 128 B; 16-byte unit u of
@@ -295,6 +306,11 @@ struct TcParams {
     float zt;               // split path: logit written for an out-of-range query (forces re-evaluation)
 };
 
+// F16 = false: the BF16 pass (BF16 weights and activations).  F16 = true: the
+// single-product FP16 tier (FP16 activations and the split tier's hi weights
+// w 2^s_l, unscaled in the epilogue); an activation at or above kF16Safe
+// poisons its row, whose logit is then written as zt (the next tier takes it).
+template <bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_tc(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
              const __grid_constant__ CUtensorMap m2, const __grid_constant__ CUtensorMap m3, TcParams P) {
@@ -395,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 int kg = c * kKC + kk * 16;
                                 uint32_t aaddr = a_base + s * kABytes + (kg >> 6) * (kTileM * 128) + (kg & 63) * 2;
                                 uint32_t baddr = b_base + stage * kSliceBytes + kk * 32;
-                                umma(tmem + s * kH, sdesc(aaddr, 1024, kLayoutSW128), sdesc(baddr, 512, kLayoutSW64),
+                                umma<F16>(tmem + s * kH, sdesc(aaddr, 1024, kLayoutSW128), sdesc(baddr, 512, kLayoutSW64),
                                      (c | kk) != 0);
                             }
                         }
@@ -424,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int64_t q = t * kRows + sub * kTileM + r;
             const bool valid = q < n;
+            bool range_ok = true;
             float3 x = valid ? query_point(P.Q, q) : make_float3(0.f, 0.f, 0.f);
             // Fourier features of this half's frequencies -> A[:, f], A[:, 64 + f]
             for (int j = half * (kNF / kHalves); j < (half + 1) * (kNF / kHalves); j += 8) {
@@ -434,10 +451,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     s[i] = v.x;
                     cs[i] = v.y;
                 }
-                uint4 ps = make_uint4(pack_bf16(s[0], s[1]), pack_bf16(s[2], s[3]), pack_bf16(s[4], s[5]),
-                                      pack_bf16(s[6], s[7]));
-                uint4 pc = make_uint4(pack_bf16(cs[0], cs[1]), pack_bf16(cs[2], cs[3]), pack_bf16(cs[4], cs[5]),
-                                      pack_bf16(cs[6], cs[7]));
+                uint4 ps = make_uint4(pack16<F16>(s[0], s[1]), pack16<F16>(s[2], s[3]), pack16<F16>(s[4], s[5]),
+                                      pack16<F16>(s[6], s[7]));
+                uint4 pc = make_uint4(pack16<F16>(cs[0], cs[1]), pack16<F16>(cs[2], cs[3]),
+                                      pack16<F16>(cs[4], cs[5]), pack16<F16>(cs[6], cs[7]));
                 *reinterpret_cast<uint4*>(As + a_offset(r, j)) = ps;
                 *reinterpret_cast<uint4*>(As + a_offset(r, kNF + j)) = pc;
             }
@@ -451,7 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 acc_phase ^= 1;
                 tc_fence_after();
                 const float* bias = sp + l * kH;
+                // BF16: the weights are unscaled (fmaf(v, 1, b) == v + b); F16: 2^-s_l
+                const float unscale = F16 ? __ldg(P.wsc + l) : 1.0f;
                 if (l < kNL - 1) {
+                    float mx = 0.0f;
                     tmem_row_chunks_serial<kH / 32 / kHalves>(trow + c0, [&](int cb, const uint32_t (&v)[32]) {
                         const int col = c0 + cb * 32;
 #pragma unroll
@@ -461,12 +481,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float4 b1 = *reinterpret_cast<const float4*>(bias + col + u * 8 + 4);
                             const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) h[i] = fmaxf(__uint_as_float(v[u * 8 + i]) + bb[i], 0.f);
-                            uint4 p = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
-                                                 pack_bf16(h[6], h[7]));
+                            for (int i = 0; i < 8; ++i) {
+                                h[i] = fmaxf(fmaf(__uint_as_float(v[u * 8 + i]), unscale, bb[i]), 0.f);
+                                if (F16) mx = fmaxf(mx, h[i]);
+                            }
+                            uint4 p = make_uint4(pack16<F16>(h[0], h[1]), pack16<F16>(h[2], h[3]),
+                                                 pack16<F16>(h[4], h[5]), pack16<F16>(h[6], h[7]));
                             *reinterpret_cast<uint4*>(As + a_offset(r, col + u * 8)) = p;
                         }
                     });
+                    if (F16) {
+                        // a row that left the FP16 range gets an infinite input to
+                        // the last layer: its accumulators turn non-finite
+                        range_ok &= mx < kF16Safe;
+                        if (l == kNL - 2 && !range_ok)
+                            *reinterpret_cast<uint16_t*>(As + a_offset(r, c0)) = (uint16_t)0x7C00u;
+                    }
                     fence_async_smem();
                     tc_fence_before();
                     __syncwarp();
@@ -475,20 +505,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // the 256 -> 1 output layer over all columns (one warp per row group)
                     const float* w4 = sp + 4 * kH;
                     float f = 0.0f;
+                    // F16: the largest exponent field of the row's accumulators;
+                    // all ones (inf or NaN) marks a poisoned row
+                    uint32_t emax = 0;
                     tmem_row_chunks_serial<kH / 32>(trow, [&](int cb, const uint32_t (&v)[32]) {
 #pragma unroll
                         for (int i = 0; i < 32; i += 4) {
                             const float4 b = *reinterpret_cast<const float4*>(bias + cb * 32 + i);
                             const float4 w = *reinterpret_cast<const float4*>(w4 + cb * 32 + i);
-                            f = fmaf(fmaxf(__uint_as_float(v[i]) + b.x, 0.f), w.x, f);
-                            f = fmaf(fmaxf(__uint_as_float(v[i + 1]) + b.y, 0.f), w.y, f);
-                            f = fmaf(fmaxf(__uint_as_float(v[i + 2]) + b.z, 0.f), w.z, f);
-                            f = fmaf(fmaxf(__uint_as_float(v[i + 3]) + b.w, 0.f), w.w, f);
+                            const float bb[4] = {b.x, b.y, b.z, b.w}, ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (F16) emax = max(emax, v[i + j] & 0x7F800000u);
+                                f = fmaf(fmaxf(fmaf(__uint_as_float(v[i + j]), unscale, bb[j]), 0.f), ww[j], f);
+                            }
                         }
                     });
                     tc_fence_before();
                     f += sp[5 * kH];
-                    if (valid) P.z[query_index(P.Q, q)] = envelope_logit(x, f, P.scale, P.radius, P.amp);
+                    const bool fin = !F16 || emax != 0x7F800000u;
+                    if (valid)
+                        P.z[query_index(P.Q, q)] = fin ? envelope_logit(x, f, P.scale, P.radius, P.amp) : P.zt;
                 } else {
                     tc_fence_before();
                 }
@@ -545,7 +582,6 @@ constexpr float kLoUnscale = 1.0f / 2048.0f;
 constexpr size_t kSmemBytes3 =
     1024 + 2 * kABytes + kStages3 * 2 * kHalfSlice + 256 + kGroups3 * kTileM * 4 + (5 * kH + 4) * 4;
 
-constexpr float kF16Safe = 30000.0f;      // activations kept well inside the FP16 range
 // instruction descriptor: D F32, A/B F16, both K-major, N = 256, M = 256 (pair)
 constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kPairRows >> 4) << 24);
 
@@ -822,6 +858,7 @@ struct MlpTc {
     __nv_bfloat16* w = nullptr;     // W_l as BF16 [256][K_l], l = 0..3
     __half* w16 = nullptr;          // split path: fp16 hi parts of W_l 2^s_l, then the lo parts
     CUtensorMap maps[4];            // BF16 weights
+    CUtensorMap maps_h16[4];        // FP16 tier: the split path's hi weights, all 256 rows per box
     CUtensorMap maps_hi_mc[4];      // split path, 128 weight rows per box (each CTA of a pair)
     CUtensorMap maps_lo_mc[4];
     float* wsc = nullptr;           // device [4]: split path weight unscale per layer
@@ -943,6 +980,10 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         cuuint32_t box_mc[2] = {(cuuint32_t)tc::kKC, (cuuint32_t)tc::kBRows};
         if (r == CUDA_SUCCESS)
+            r = fn(&T->maps_h16[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + offs[l]), gdim, gstride, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
             r = fn(&T->maps_hi_mc[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + offs[l]), gdim, gstride,
                    box_mc, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -958,7 +999,9 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(tc::k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
+    if (cudaFuncSetAttribute(tc::k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
             cudaSuccess ||
         cudaFuncSetAttribute(tc::k_mlp_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes3) !=
             cudaSuccess) {
@@ -990,7 +1033,10 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     return ODC_OK;
 }
 
-odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
+// One launch of the single-product network: the BF16 pass (f16 = false,
+// timing kind 1) or the FP16 tier (f16 = true, timing kind 3).
+static odc_status tc_single_eval(MlpState* st, bool f16, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s,
+                                 std::string* err) {
     if (n <= 0) return ODC_OK;
     MlpTc* T = st->tc;
     if (!T || !T->ready) {
@@ -999,10 +1045,16 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
     }
     int64_t tiles = (n + tc::kRows - 1) / tc::kRows;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, nullptr, st->zt};
-    cudaEvent_t* ev = mlp_ev_pair(st, 1);
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, T->wsc, st->zt};
+    const int kind = f16 ? 3 : 1;
+    cudaEvent_t* ev = mlp_ev_pair(st, kind);
     if (ev) cudaEventRecord(ev[0], s);
-    tc::k_mlp_tc<<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2], T->maps[3], P);
+    if (f16)
+        tc::k_mlp_tc<true><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps_h16[0], T->maps_h16[1],
+                                                                     T->maps_h16[2], T->maps_h16[3], P);
+    else
+        tc::k_mlp_tc<false><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2],
+                                                                      T->maps[3], P);
     note_launch();
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = cudaGetLastError();
@@ -1013,10 +1065,18 @@ odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cud
     if (!Q.cnt) {   // device-sized lists are counted on the device
         int64_t real = n;
         if (!Q.pts) real = (int64_t)Q.g.nv[0] * Q.g.nv[1] * Q.g.nv[2];
-        st->flops[1] += kFlopsPerQuery * (double)real;
+        st->flops[kind] += kFlopsPerQuery * (double)real;
     }
-    st->launches[1] += 1;
+    st->launches[kind] += 1;
     return ODC_OK;
+}
+
+odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
+    return tc_single_eval(st, false, Q, n, z, s, err);
+}
+
+odc_status mlp_tc16_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
+    return tc_single_eval(st, true, Q, n, z, s, err);
 }
 
 odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {

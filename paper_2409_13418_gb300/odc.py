@@ -20,8 +20,8 @@ ODC_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
           5: "unsupported", 6: "internal error"}
 SRC_CSG, SRC_MLP, SRC_RESIDENT, SRC_VOXEL = 0, 1, 2, 3
-PREC_FP32, PREC_BF16, PREC_SPLIT = 0, 1, 2
-MLP_REUPLOAD = 1
+PREC_FP32, PREC_BF16, PREC_SPLIT, PREC_F16 = 0, 1, 2, 3
+MLP_REUPLOAD, MLP_NO_F16_TIER = 1, 2
 DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
            cycles=9, vlocal=10, qcase=11, flips=12, search=13)
 _DBG_DTYPE = dict(labels=np.uint32, edges=np.uint32, T=np.uint32, faces=np.uint32, slots=np.uint8,
@@ -70,7 +70,9 @@ class Stats(C.Structure):
                 ("n_launches", C.c_int32), ("mlp_launches", C.c_int64), ("tc_flops", C.c_double),
                 ("tc_ms", C.c_float), ("pad_", C.c_int32), ("tc_launches", C.c_int64),
                 ("split_flops", C.c_double), ("split_ms", C.c_float), ("pad2_", C.c_int32),
-                ("split_launches", C.c_int64), ("n_split", C.c_int64), ("fp32_tile", C.c_int64)]
+                ("split_launches", C.c_int64), ("n_split", C.c_int64), ("fp32_tile", C.c_int64),
+                ("h16_flops", C.c_double), ("h16_ms", C.c_float), ("pad3_", C.c_int32),
+                ("h16_launches", C.c_int64), ("n_h16", C.c_int64)]
 
 
 class SlabC(C.Structure):
@@ -222,7 +224,7 @@ class _SourceHolder:
     """Keeps the numpy buffers behind a Source structure alive."""
 
     def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0, reupload=False,
-                 fp32_tile=None):
+                 fp32_tile=None, h16=True):
         self.keep = []
         self.src = Source()
         if src is None:
@@ -264,7 +266,8 @@ class _SourceHolder:
             m.band = 0.03 if band is None else band
             m.no_split = 0 if split else 1
             m.split_zmargin = split_zmargin
-            m.flags = (MLP_REUPLOAD if reupload else 0) | (((fp32_tile + 1) << 8) if fp32_tile is not None else 0)
+            m.flags = (MLP_REUPLOAD if reupload else 0) | (((fp32_tile + 1) << 8) if fp32_tile is not None else 0) | \
+                (0 if h16 else MLP_NO_F16_TIER)
             self.keep.append(m)
             self.src.kind = SRC_MLP
             self.src.mlp = C.addressof(m)
@@ -372,16 +375,17 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0):
+    def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0, h16=True):
         """Make ``src`` the context's resident source (``extract(None, ...)`` reuses it)."""
-        holder = _SourceHolder(src, precision, band, split, split_zmargin)
+        holder = _SourceHolder(src, precision, band, split, split_zmargin, h16=h16)
         _check(_lib.odc_source_upload(self.h, C.byref(holder.src)))
 
     def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, split=True,
-                split_zmargin=0.0, reupload=False, **kw) -> Mesh:
+                split_zmargin=0.0, reupload=False, h16=True, **kw) -> Mesh:
         """Run ODC; ``src=None`` reuses the resident source.  ``reupload`` forces
-        the network weights to be prepared and copied even if the context holds them."""
-        holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload)
+        the network weights to be prepared and copied even if the context holds them;
+        ``h16=False`` skips the FP16 tier of the BF16 path (same mesh, other cost)."""
+        holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, h16=h16)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
         m = MeshC()

@@ -115,6 +115,28 @@ def test_bf16_logits_within_band_of_fp32(ctx, mlp):
     assert np.array_equal(l16, l32)
 
 
+F16_ZMARGIN = 0.025   # logit margin of the FP16 tier (library constant; measured max error 0.0091)
+
+
+def test_f16_tier_logits_within_half_its_margin_of_fp32(ctx, mlp):
+    """The single-product FP16 tier (FP16 activations, FP16 weights w 2^s,
+    FP32 accumulation) stays within half its 0.02 logit margin of the FP32
+    network (0.025 logit margin), uniformly over the box and on the surface shell where the
+    searches query it."""
+    from paper_2409_13418_gb300 import odc
+    rng = np.random.default_rng(6)
+    u = rng.normal(size=(500000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    shell = u * rng.uniform(0.3, 0.7, (500000, 1))
+    pts = np.concatenate([rng.uniform(-1, 1, (500000, 3)), shell]).astype(np.float32)
+    _, z32 = ctx.eval_points(mlp, pts, precision=0)
+    _, zh = ctx.eval_points(mlp, pts, precision=odc.PREC_F16)
+    d = np.abs(zh.astype(np.float64) - z32)
+    print("fp16 tier |dz| max", d.max(), "median", np.median(d))
+    assert np.isfinite(zh).all()
+    assert d.max() < 0.5 * F16_ZMARGIN
+
+
 def test_split_bf16_logits_within_margin_of_fp32(ctx, mlp):
     """The split tier (FP16 hi + lo operands, three products per layer,
     corrections in their own accumulator) stays within 0.4 of the default
@@ -129,16 +151,18 @@ def test_split_bf16_logits_within_margin_of_fp32(ctx, mlp):
     assert d.max() < 0.4 * 4e-5
 
 
-@pytest.mark.parametrize("n,split", [(48, True), (97, True), (64, False), (131, True), (131, False)])
-def test_bf16_extract_equals_fp32_plain_path(ctx, mlp, n, split):
-    """BF16 tensor cores + tiered re-evaluation in the band (split-BF16, then
-    FP32): every decision, and hence the whole mesh, equals the FP32 plain
-    path's, byte for byte."""
+@pytest.mark.parametrize("n,split,h16", [(48, True, True), (97, True, True), (64, False, True), (131, True, True),
+                                         (131, False, True), (64, True, False), (97, False, False)])
+def test_bf16_extract_equals_fp32_plain_path(ctx, mlp, n, split, h16):
+    """BF16 tensor cores + tiered re-evaluation in the band (FP16 tier,
+    split-FP16 tier, then FP32; with either middle tier switched off):
+    every decision, and hence the whole mesh, equals the FP32 plain path's,
+    byte for byte."""
     g = I.cube_grid(n)
     m32 = ctx.extract(mlp, g, steps_1d=15, precision=0)
     v32, t32 = m32.to_host()
     T32, d32 = ctx.debug("T"), ctx.search_decisions()
-    m16 = ctx.extract(mlp, g, steps_1d=15, precision=1, band=BF16_BAND, split=split)
+    m16 = ctx.extract(mlp, g, steps_1d=15, precision=1, band=BF16_BAND, split=split, h16=h16)
     v16, t16 = m16.to_host()
     assert np.array_equal(ctx.debug("T"), T32)
     d16 = ctx.search_decisions()
@@ -146,6 +170,7 @@ def test_bf16_extract_equals_fp32_plain_path(ctx, mlp, n, split):
         assert np.array_equal(d16[k], d32[k]), k
     assert np.array_equal(t16, t32) and np.array_equal(v16, v32)
     assert m16.stats["n_requeries"] > 0
+    assert (m16.stats["n_h16"] > 0) == h16 and (m16.stats["n_split"] > 0) == split
 
 
 @pytest.mark.parametrize("iso", [0.3, 0.7])
