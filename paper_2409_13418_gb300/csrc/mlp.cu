@@ -603,28 +603,27 @@ __global__ void __launch_bounds__(kTierBlock)
 static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float* z, const float* hint, cudaStream_t s,
                               std::string* err) {
     odc_status r;
-    void *pr, *pl[4];
+    void *pr, *plist;
     if ((r = mlp_scratch(st, 24, (size_t)n + 64, &pr, err)) != ODC_OK) return r;
+    // one list buffer for every tier: a tier's list is consumed (stream order)
+    // before the next tier's list is built into the same buffer
+    if ((r = mlp_scratch(st, 25, (size_t)n * 4 + 64, &plist, err)) != ODC_OK) return r;
     if (Q.idx) { *err = "nested query index"; return ODC_ERR_INTERNAL; }
+    int* list = (int*)plist;
     uint8_t* route = (uint8_t*)pr;
     unsigned long long* cnt = st->dq + 4;
     const unsigned blocks = (unsigned)((n + kTierBlock - 1) / kTierBlock);
     MLP_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
     const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16};
-    // per tier: its list slot, counters (list size, queries since timing began)
-    const int slot[4] = {27, 28, 25, 26};
+    // per tier: queries evaluated since the timing began
     unsigned long long* tot[4] = {st->dq + 0, st->dq + 3, st->dq + 1, st->dq + 2};
-    auto list_of = [&](int tier) -> odc_status {
-        return mlp_scratch(st, slot[tier], (size_t)n * 4 + 64, &pl[tier], err);
-    };
     if (!hint) {
         k_route<<<blocks, kTierBlock, 0, s>>>(ra, n, route); note_launch();
         if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
     } else {
         // routing and the BF16 pass's list in one pass
-        if ((r = list_of(0)) != ODC_OK) return r;
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, ra, route, (int*)pl[0], cnt + 0, tot[0]); note_launch();
-        QuerySrc L0{Q.pts, (const int*)pl[0], Q.g, cnt + 0};
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, ra, route, list, cnt + 0, tot[0]); note_launch();
+        QuerySrc L0{Q.pts, list, Q.g, cnt + 0};
         if ((r = mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK) return r;
     }
     int from = 0;
@@ -632,10 +631,9 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     for (int tier = 1; tier <= 3; ++tier) {
         const bool on = tier == 1 ? st->h16 != 0 : tier == 2 ? st->split != 0 : true;
         if (!on) continue;
-        if ((r = list_of(tier)) != ODC_OK) return r;
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, tier, thr, ra, route, (int*)pl[tier],
-                                                  cnt + tier, tot[tier]); note_launch();
-        QuerySrc L{Q.pts, (const int*)pl[tier], Q.g, cnt + tier};
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, tier, thr, ra, route, list, cnt + tier,
+                                                  tot[tier]); note_launch();
+        QuerySrc L{Q.pts, list, Q.g, cnt + tier};
         r = tier == 1 ? mlp_tc16_eval(st, L, n, z, s, err)
             : tier == 2 ? mlp_tc3_eval(st, L, n, z, s, err)
                         : launch_fp32(st, L, n, z, s, err);
