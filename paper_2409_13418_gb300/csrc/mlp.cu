@@ -521,10 +521,9 @@ static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float*
 }
 
 // ------------------------------------------------------------ band re-eval
-// Tier of every query: 0 = BF16 tensor-core pass first, 1 = split-FP16 pass
-// first, 2 = FP32 directly.  hint[i] estimates |z_i - zt| (from the logits
+// Tiers: 0 BF16 pass, 1 FP16 tier, 2 split-FP16 tier, 3 FP32.  A query's
+// first tier comes from hint[i], an estimate of |z_i - zt| (from the logits
 // around the query in its search); no hint routes to the BF16 pass.
-// Tiers: 0 BF16 pass, 1 FP16 tier, 2 split-FP16 tier, 3 FP32.
 struct RouteArgs {
     const float* hint;
     float zs, zh, zb;
@@ -549,13 +548,14 @@ __global__ void k_route(RouteArgs ra, int64_t n, uint8_t* __restrict__ r) {
 // counted in *cnt and *total.  Launched with kTierBlock threads.
 constexpr int kTierBlock = 256;
 __global__ void __launch_bounds__(kTierBlock)
-    k_tier_list(const float* __restrict__ z, int64_t n, float t, int from, int to, float thr, RouteArgs ra,
-                uint8_t* __restrict__ r, int* __restrict__ list, unsigned long long* __restrict__ cnt,
-                unsigned long long* __restrict__ total) {
+    k_tier_list(const float* __restrict__ z, int64_t n, const unsigned long long* __restrict__ nlim, float t, int from,
+                int to, float thr, RouteArgs ra, uint8_t* __restrict__ r, int* __restrict__ list,
+                unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ total) {
     __shared__ unsigned wbase[kTierBlock / 32];
     __shared__ unsigned long long bbase;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (nlim) n = min(n, (int64_t)*nlim);   // device-sized query list
     bool f = false;
     if (i < n) {
         int ri;
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kTierBlock)
 // the hints.  Each tier's list is built and consumed on the device (its size
 // stays there), so the evaluation needs no host round trip.
 static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float* z, const float* hint, cudaStream_t s,
-                              std::string* err) {
+                              std::string* err, const unsigned long long* nlim = nullptr) {
     odc_status r;
     void *pr, *plist;
     if ((r = mlp_scratch(st, 24, (size_t)n + 64, &pr, err)) != ODC_OK) return r;
@@ -617,12 +617,13 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16};
     // per tier: queries evaluated since the timing began
     unsigned long long* tot[4] = {st->dq + 0, st->dq + 3, st->dq + 1, st->dq + 2};
-    if (!hint) {
+    if (!hint && !nlim) {
         k_route<<<blocks, kTierBlock, 0, s>>>(ra, n, route); note_launch();
         if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
     } else {
-        // routing and the BF16 pass's list in one pass
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, -1, 0, 0.0f, ra, route, list, cnt + 0, tot[0]); note_launch();
+        // routing and the BF16 pass's list in one pass (no hint: every query
+        // starts at the BF16 pass)
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, -1, 0, 0.0f, ra, route, list, cnt + 0, tot[0]); note_launch();
         QuerySrc L0{Q.pts, list, Q.g, cnt + 0};
         if ((r = mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK) return r;
     }
@@ -631,7 +632,7 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     for (int tier = 1; tier <= 3; ++tier) {
         const bool on = tier == 1 ? st->h16 != 0 : tier == 2 ? st->split != 0 : true;
         if (!on) continue;
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, st->zt, from, tier, thr, ra, route, list, cnt + tier,
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, from, tier, thr, ra, route, list, cnt + tier,
                                                   tot[tier]); note_launch();
         QuerySrc L{Q.pts, list, Q.g, cnt + tier};
         r = tier == 1 ? mlp_tc16_eval(st, L, n, z, s, err)
@@ -659,6 +660,26 @@ odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, i
     QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
     st->stream = s;
     return eval(st, Q, n, z, precision, hint, s, err);
+}
+
+// FP32 queries of a device-sized list, counted for the statistics
+__global__ void k_count_add(const unsigned long long* __restrict__ n, int64_t n_max, unsigned long long* total) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *total += min((unsigned long long)n_max, *n);
+}
+
+odc_status mlp_eval_list_dev(MlpState* st, const float3* pts, int64_t n_max, const unsigned long long* n_dev, float* z,
+                             cudaStream_t s, std::string* err, const float* hint) {
+    QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
+    st->stream = s;
+    if (n_max <= 0) return ODC_OK;
+    if (st->precision != ODC_PREC_BF16) {
+        QuerySrc L{pts, nullptr, GridDev{}, n_dev};
+        odc_status r = launch_fp32(st, L, n_max, z, s, err);
+        if (r != ODC_OK) return r;
+        k_count_add<<<1, 32, 0, s>>>(n_dev, n_max, st->dq + 2); note_launch();
+        return ODC_OK;
+    }
+    return eval_tiered(st, Q, n_max, z, hint, s, err, n_dev);
 }
 
 odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, std::string* err) {

@@ -38,6 +38,9 @@ odc_status mlp_scratch(MlpState* st, int slot, size_t bytes, void** out, std::st
 // the cost, never a decision.
 odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, int precision, cudaStream_t s,
                          std::string* err, const float* hint = nullptr);
+// The same over a device-sized list: n_dev (device) queries, at most n_max.
+odc_status mlp_eval_list_dev(MlpState* st, const float3* pts, int64_t n_max, const unsigned long long* n_dev, float* z,
+                             cudaStream_t s, std::string* err, const float* hint = nullptr);
 // Logits at the grid vertices in label-word order (query q -> word q/32, lane q%32).
 odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, std::string* err);
 int mlp_precision(const MlpState* st);

@@ -179,53 +179,115 @@ struct FaceSt {
     float z1a, z1c, z2a, z2c;   // logits at the step-2 bracket ends of both rays
 };
 
+// Routing hint of the midpoint queries m: a chord midpoint lies close to the
+// isocurve through its two 1D points, so |z(m)| falls in the BF16 band for
+// nine in ten faces of the 256^3 envelope network (measured on oracle
+// traces); they start at the FP16 tier.
+constexpr float kHintM = 0.06f;
+
 __global__ void k_face_init(GridDev g, const uint32_t* __restrict__ bits, const uint32_t* __restrict__ flips,
                             const WordInfo* __restrict__ wi, const uint32_t* __restrict__ ebase,
                             const uint32_t* __restrict__ T, const uint32_t* __restrict__ faces,
                             const uint8_t* __restrict__ slots, uint32_t nf, int k, FaceSt* __restrict__ S,
-                            float3* __restrict__ pts) {
+                            float3* __restrict__ pts, float* __restrict__ hint) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     FaceSt st;
     load_face(g, bits, flips, wi, ebase, T, k, faces[i], slots[i], st.F);
     S[i] = st;
     pts[i] = face_world2(g, st.F, st.F.m);
+    if (hint) hint[i] = kHintM;
 }
 
-// label of m -> step-1 ray; queries: the N1 line samples
-__global__ void k_face_m(GridDev g, uint32_t nf, const float* __restrict__ z, float t, SearchParams sp,
-                         FaceSt* __restrict__ S, float3* __restrict__ pts) {
+// Append val to list with one atomic per block; every thread of the block
+// calls it (a block-wide barrier).
+template <int BLOCK>
+__device__ __forceinline__ void block_append(bool f, uint32_t val, uint32_t* __restrict__ list,
+                                             unsigned long long* __restrict__ cnt) {
+    __shared__ unsigned wbase[BLOCK / 32];
+    __shared__ unsigned long long bbase;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wbase[warp] = (unsigned)__popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int w = 0; w < BLOCK / 32; ++w) {
+            const unsigned c = wbase[w];
+            wbase[w] = tot;
+            tot += c;
+        }
+        bbase = tot ? atomicAdd(cnt, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (f) list[bbase + wbase[warp] + __popc(b & ((1u << lane) - 1u))] = val;
+}
+
+__device__ __forceinline__ uint32_t n_of(const unsigned long long* cnt, uint32_t n) {
+    return cnt ? (uint32_t)min((unsigned long long)n, *cnt) : n;
+}
+constexpr int kLinBlock = 128;
+constexpr int kMaxLin = 65;   // line samples per search: at most 64 (odc_params)
+
+// label of m -> step-1 ray.  zc holds the logit of the last line sample
+// taken (m's before the first).
+__global__ void k_face_m(uint32_t nf, const float* __restrict__ z, float t, FaceSt* __restrict__ S) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     FaceSt& st = S[i];
     uint32_t lab_m = z[i] > t;
     st.lab_m = lab_m;
     st.zm = z[i];
-    ff2 d = lab_m ? ff2{ff_neg(st.F.d.u), ff_neg(st.F.d.v)} : st.F.d;
-    st.d = d;
-    for (int j = 1; j <= sp.lin1; ++j)
-        pts[(size_t)(j - 1) * nf + i] =
-            face_world2(g, st.F, ray_point(st.F.m, d, lbs_param(sp.range1, (uint32_t)j << sp.bin1, sp.lin1, sp.bin1)));
+    st.zc = z[i];
+    st.found = 0;
+    st.d = lab_m ? ff2{ff_neg(st.F.d.u), ff_neg(st.F.d.v)} : st.F.d;
 }
 
-// first line sample whose label differs -> bracket; first bisection query
-__global__ void k_face_lin1(GridDev g, uint32_t nf, const float* __restrict__ z, float t, SearchParams sp,
-                            FaceSt* __restrict__ S, float3* __restrict__ pts, HintPar hp, float* __restrict__ hint) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    FaceSt& st = S[i];
-    int first = sp.lin1;
-    st.found = 0;
-    for (int j = 1; j <= sp.lin1; ++j)
-        if ((uint32_t)(z[(size_t)(j - 1) * nf + i] > t) != st.lab_m) { first = j; st.found = 1; break; }
-    st.Ja = (uint32_t)(first - 1) << sp.bin1;
-    st.Jc = (uint32_t)first << sp.bin1;
-    st.za = first > 1 ? z[(size_t)(first - 2) * nf + i] : st.zm;
-    st.zc = z[(size_t)(first - 1) * nf + i];
-    if (sp.bin1 > 0) {
-        pts[i] = face_world2(g, st.F, ray_point(st.F.m, st.d, lbs_param(sp.range1, (st.Ja + st.Jc) >> 1, sp.lin1, sp.bin1)));
-        if (hint) hint[i] = bracket_hint(st.za, st.zc, hp.t, hp.zb, hp.zs);
+// Step-1 line samples one at a time (A.1.3: the first sample whose label
+// differs from m's): round j queries sample j of the faces whose samples
+// 1 .. j-1 kept m's label (list/cnt; every face for j = 1).  The hint of
+// sample j > 1 is the previous sample's |z - t|.
+__global__ void k_lin1_gen(GridDev g, uint32_t nf, int j, const uint32_t* __restrict__ list,
+                           const unsigned long long* __restrict__ cnt, SearchParams sp, const FaceSt* __restrict__ S,
+                           float3* __restrict__ lp, float* __restrict__ lh, float t) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_of(cnt, nf)) return;
+    const FaceSt& st = S[list ? list[k] : k];
+    lp[k] = face_world2(g, st.F, ray_point(st.F.m, st.d, lbs_param(sp.range1, (uint32_t)j << sp.bin1, sp.lin1, sp.bin1)));
+    if (lh) lh[k] = j == 1 ? INFINITY : fabsf(st.zc - t);
+}
+
+// A sample whose label differs from m's (or the last one) closes the bracket
+// [J - 1, J] and queues the first bisection query; the others search on.
+__global__ void __launch_bounds__(kLinBlock)
+    k_lin1_step(GridDev g, uint32_t nf, int j, const uint32_t* __restrict__ list,
+                const unsigned long long* __restrict__ cnt, const float* __restrict__ lz, float t, SearchParams sp,
+                FaceSt* __restrict__ S, float3* __restrict__ pts, HintPar hp, float* __restrict__ hint,
+                uint32_t* __restrict__ list_out, unsigned long long* __restrict__ cnt_out) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    bool more = false;
+    uint32_t i = 0;
+    if (k < n_of(cnt, nf)) {
+        i = list ? list[k] : k;
+        FaceSt& st = S[i];
+        const float zj = lz[k];
+        const bool hit = (uint32_t)(zj > t) != st.lab_m;
+        if (hit || j == sp.lin1) {
+            if (hit) st.found = 1;
+            st.Ja = (uint32_t)(j - 1) << sp.bin1;
+            st.Jc = (uint32_t)j << sp.bin1;
+            st.za = st.zc;
+            st.zc = zj;
+            if (sp.bin1 > 0) {
+                pts[i] = face_world2(g, st.F, ray_point(st.F.m, st.d, lbs_param(sp.range1, (st.Ja + st.Jc) >> 1, sp.lin1, sp.bin1)));
+                if (hint) hint[i] = bracket_hint(st.za, st.zc, hp.t, hp.zb, hp.zs);
+            }
+        } else {
+            st.zc = zj;
+            more = true;
+        }
     }
+    if (list_out) block_append<kLinBlock>(more, i, list_out, cnt_out);
 }
 
 __global__ void k_face_bin1(GridDev g, uint32_t nf, const float* __restrict__ z, float t, SearchParams sp, int step,
@@ -261,6 +323,7 @@ __global__ void k_face_fin1(uint32_t nf, SearchParams sp, FaceSt* __restrict__ S
         active[i] = 0;
     } else {
         st.q = ray_point(st.F.m, st.d, lbs_param(sp.range1, st.Ja, sp.lin1, sp.bin1));
+        st.z1c = st.z2c = st.za;   // logit of the last step-2 line sample of each ray (q's before the first)
         active[i] = 1;
     }
 }
@@ -275,49 +338,65 @@ __device__ __forceinline__ ff2 ray2(const FaceSt& st, int r) {
     return r == 0 ? st.F.u1 : ff2{ff_neg(st.F.u1.u), ff_neg(st.F.u1.v)};
 }
 
-// step 2 line samples of both rays: slot (r * N2 + j - 1) * na + li
-__global__ void k_face_lin2_gen(GridDev g, const uint32_t* __restrict__ list, uint32_t na, SearchParams sp,
-                                const FaceSt* __restrict__ S, float3* __restrict__ pts) {
-    uint32_t li = blockIdx.x * blockDim.x + threadIdx.x;
-    if (li >= na) return;
-    const FaceSt& st = S[list[li]];
-    for (int r = 0; r < 2; ++r) {
-        ff2 d = ray2(st, r);
-        for (int j = 1; j <= sp.lin2; ++j)
-            pts[(size_t)(r * sp.lin2 + j - 1) * na + li] =
-                face_world2(g, st.F, ray_point(st.q, d, lbs_param(sp.range2, (uint32_t)j << sp.bin2, sp.lin2, sp.bin2)));
+// Step-2 line samples of both rays, one at a time per ray: entry e < 2 na is
+// ray r = e / na of active face flist[e % na]; round j queries sample j of
+// the rays whose samples 1 .. j-1 kept m's label.  Hint: the ray leaves the
+// isocurve through q about linearly, so sample 1's |z - t| is estimated as
+// |z(m) - t| scaled by its distance over half the segment, and sample j > 1's
+// as the previous sample's scaled by j / (j - 1).
+__global__ void k_lin2_gen(GridDev g, const uint32_t* __restrict__ flist, uint32_t na, int j,
+                           const uint32_t* __restrict__ list, const unsigned long long* __restrict__ cnt,
+                           SearchParams sp, const FaceSt* __restrict__ S, float3* __restrict__ lp,
+                           float* __restrict__ lh, float t) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_of(cnt, 2 * na)) return;
+    const uint32_t e = list ? list[k] : k;
+    const int r = e >= na;
+    const FaceSt& st = S[flist[e - (uint32_t)r * na]];
+    lp[k] = face_world2(g, st.F, ray_point(st.q, ray2(st, r), lbs_param(sp.range2, (uint32_t)j << sp.bin2, sp.lin2, sp.bin2)));
+    if (lh) {
+        if (j == 1) {
+            const float half = fmaxf(0.5f * hypotf(st.F.p1.x - st.F.p2.x, st.F.p1.y - st.F.p2.y), 0.05f);
+            lh[k] = fabsf(st.zm - t) * (sp.range2 / (float)sp.lin2) / half;
+        } else {
+            lh[k] = fabsf((r ? st.z2c : st.z1c) - t) * (float)j / (float)(j - 1);
+        }
     }
 }
 
-__global__ void k_face_lin2(GridDev g, const uint32_t* __restrict__ list, uint32_t na, const float* __restrict__ z,
-                            float t, SearchParams sp, FaceSt* __restrict__ S, float3* __restrict__ pts, HintPar hp,
-                            float* __restrict__ hint) {
-    uint32_t li = blockIdx.x * blockDim.x + threadIdx.x;
-    if (li >= na) return;
-    FaceSt& st = S[list[li]];
-    uint32_t Ja[2], Jc[2];
-    float za[2], zc[2];
-    for (int r = 0; r < 2; ++r) {
-        int first = sp.lin2;
-        for (int j = 1; j <= sp.lin2; ++j)
-            if ((uint32_t)(z[(size_t)(r * sp.lin2 + j - 1) * na + li] > t) != st.lab_m) {
-                first = j;
-                st.found |= 2u << r;
-                break;
+__global__ void __launch_bounds__(kLinBlock)
+    k_lin2_step(GridDev g, const uint32_t* __restrict__ flist, uint32_t na, int j, const uint32_t* __restrict__ list,
+                const unsigned long long* __restrict__ cnt, const float* __restrict__ lz, float t, SearchParams sp,
+                FaceSt* __restrict__ S, float3* __restrict__ pts, HintPar hp, float* __restrict__ hint,
+                uint32_t* __restrict__ list_out, unsigned long long* __restrict__ cnt_out) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    bool more = false;
+    uint32_t e = 0;
+    if (k < n_of(cnt, 2 * na)) {
+        e = list ? list[k] : k;
+        const int r = e >= na;
+        const uint32_t li = e - (uint32_t)r * na;
+        FaceSt& st = S[flist[li]];   // the two rays of a face write disjoint fields (found: atomically)
+        float* zprev = r ? &st.z2c : &st.z1c;
+        const float zj = lz[k];
+        const bool hit = (uint32_t)(zj > t) != st.lab_m;
+        if (hit || j == sp.lin2) {
+            if (hit) atomicOr(&st.found, 2u << r);
+            const uint32_t Ja = (uint32_t)(j - 1) << sp.bin2, Jc = (uint32_t)j << sp.bin2;
+            const float za = *zprev;
+            if (r == 0) { st.J1a = Ja; st.J1c = Jc; st.z1a = za; st.z1c = zj; }
+            else        { st.J2a = Ja; st.J2c = Jc; st.z2a = za; st.z2c = zj; }
+            if (sp.bin2 > 0) {
+                pts[(size_t)r * na + li] =
+                    face_world2(g, st.F, ray_point(st.q, ray2(st, r), lbs_param(sp.range2, (Ja + Jc) >> 1, sp.lin2, sp.bin2)));
+                if (hint) hint[(size_t)r * na + li] = bracket_hint(za, zj, hp.t, hp.zb, hp.zs);
             }
-        Ja[r] = (uint32_t)(first - 1) << sp.bin2;
-        Jc[r] = (uint32_t)first << sp.bin2;
-        // the rays start at q, the step-1 bracket end Ja, whose logit is za
-        za[r] = first > 1 ? z[(size_t)(r * sp.lin2 + first - 2) * na + li] : st.za;
-        zc[r] = z[(size_t)(r * sp.lin2 + first - 1) * na + li];
-        if (sp.bin2 > 0) {
-            pts[(size_t)r * na + li] =
-                face_world2(g, st.F, ray_point(st.q, ray2(st, r), lbs_param(sp.range2, (Ja[r] + Jc[r]) >> 1, sp.lin2, sp.bin2)));
-            if (hint) hint[(size_t)r * na + li] = bracket_hint(za[r], zc[r], hp.t, hp.zb, hp.zs);
+        } else {
+            *zprev = zj;
+            more = true;
         }
     }
-    st.J1a = Ja[0]; st.J1c = Jc[0]; st.J2a = Ja[1]; st.J2c = Jc[1];
-    st.z1a = za[0]; st.z1c = zc[0]; st.z2a = za[1]; st.z2c = zc[1];
+    if (list_out) block_append<kLinBlock>(more, e, list_out, cnt_out);
 }
 
 __global__ void k_face_bin2(GridDev g, const uint32_t* __restrict__ list, uint32_t na, const float* __restrict__ z,
@@ -368,21 +447,27 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
     const float t = mlp_logit_threshold(iso);
     st->zt = t;
     const HintPar hp{t, st->zband, st->zsplit};
-    size_t nmax = (size_t)nf * std::max(sp.lin1, 2 * sp.lin2);
-    float* hint = nullptr;
+    const size_t n2 = (size_t)nf * 2;   // queries of one wavefront at most (two rays per face)
+    float *hint = nullptr, *lh = nullptr;
     if (mlp_precision(st) == ODC_PREC_BF16) {
-        void* ph;
-        S_TRY(mlp_scratch(st, 36, (size_t)nf * 2 * 4, &ph, err));
+        void *ph, *plh;
+        S_TRY(mlp_scratch(st, 36, n2 * 4, &ph, err));
+        S_TRY(mlp_scratch(st, 17, n2 * 4, &plh, err));
         hint = (float*)ph;
+        lh = (float*)plh;
     }
-    void *pS, *ppts, *pz, *pact, *poff, *plist, *pcnt;
+    void *pS, *ppts, *pz, *pact, *poff, *plist, *pcnt, *plp, *plz, *pll, *plc;
     S_TRY(mlp_scratch(st, 10, (size_t)nf * sizeof(FaceSt), &pS, err));
-    S_TRY(mlp_scratch(st, 2, nmax * 12, &ppts, err));
-    S_TRY(mlp_scratch(st, 3, nmax * 4, &pz, err));
+    S_TRY(mlp_scratch(st, 2, n2 * 12, &ppts, err));
+    S_TRY(mlp_scratch(st, 3, n2 * 4, &pz, err));
     S_TRY(mlp_scratch(st, 11, (size_t)nf * 4, &pact, err));
     S_TRY(mlp_scratch(st, 12, (size_t)nf * 4 + scan_tmp_elems(nf) * 8 + 64, &poff, err));
     S_TRY(mlp_scratch(st, 13, (size_t)nf * 4, &plist, err));
     S_TRY(mlp_scratch(st, 14, 64, &pcnt, err));
+    S_TRY(mlp_scratch(st, 15, n2 * 12, &plp, err));     // line-sample points of a round (compact)
+    S_TRY(mlp_scratch(st, 16, n2 * 4, &plz, err));      // their logits
+    S_TRY(mlp_scratch(st, 18, n2 * 4 * 2, &pll, err));  // two lists of searches still sampling
+    S_TRY(mlp_scratch(st, 19, 2 * kMaxLin * 8, &plc, err));   // their sizes: [j] step 1 round j + 1, [kMaxLin + j] step 2
     FaceSt* S = (FaceSt*)pS;
     float3* pts = (float3*)ppts;
     float* z = (float*)pz;
@@ -391,39 +476,69 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
     uint32_t* tmp = off + ((nf + 63) / 64) * 64;
     uint32_t* list = (uint32_t*)plist;
     uint32_t* cnt = (uint32_t*)pcnt;
+    float3* lp = (float3*)plp;
+    float* lz = (float*)plz;
+    uint32_t* L[2] = {(uint32_t*)pll, (uint32_t*)pll + n2};
+    unsigned long long* C = (unsigned long long*)plc;
+    unsigned long long hc[2 * kMaxLin] = {};
+    S_CK(cudaMemsetAsync(C, 0, 2 * kMaxLin * 8, s));
 
-    // step 1: m, line samples, bisections
-    k_face_init<<<nblk(nf, 128), 128, 0, s>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp.steps_1d, S, pts); note_launch();
-    S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, err));
-    k_face_m<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, S, pts); note_launch();
-    S_TRY(mlp_eval_list(st, pts, (int64_t)nf * sp.lin1, z, -1, s, err));
-    k_face_lin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, S, pts, hp, hint); note_launch();
+    // step 1: m, line samples (one at a time, early exit), bisections
+    k_face_init<<<nblk(nf, 128), 128, 0, s>>>(g, bits, flips, wi, ebase, T, faces, slots, nf, sp.steps_1d, S, pts,
+                                              hint); note_launch();
+    S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, err, hint));
+    k_face_m<<<nblk(nf, 128), 128, 0, s>>>(nf, z, t, S); note_launch();
+    for (int j = 1; j <= sp.lin1; ++j) {
+        const uint32_t* lin = j == 1 ? nullptr : L[j & 1];
+        const unsigned long long* cin = j == 1 ? nullptr : C + (j - 1);
+        uint32_t* lout = j < sp.lin1 ? L[(j + 1) & 1] : nullptr;
+        k_lin1_gen<<<nblk(nf, 128), 128, 0, s>>>(g, nf, j, lin, cin, sp, S, lp, lh, t); note_launch();
+        if (cin) S_TRY(mlp_eval_list_dev(st, lp, nf, cin, lz, s, err, lh));
+        else S_TRY(mlp_eval_list(st, lp, nf, lz, -1, s, err, lh));
+        k_lin1_step<<<nblk(nf, kLinBlock), kLinBlock, 0, s>>>(g, nf, j, lin, cin, lz, t, sp, S, pts, hp, hint, lout,
+                                                             C + j); note_launch();
+    }
     for (int b = 0; b < sp.bin1; ++b) {
         S_TRY(mlp_eval_list(st, pts, nf, z, -1, s, err, hint));
         k_face_bin1<<<nblk(nf, 128), 128, 0, s>>>(g, nf, z, t, sp, b, S, pts, hp, hint); note_launch();
     }
     k_face_fin1<<<nblk(nf), 256, 0, s>>>(nf, sp, S, pf, flags, act, dec); note_launch();
-    *nq += (int64_t)nf * (1 + sp.lin1 + sp.bin1);
     // faces still active after step 1
     exclusive_scan<uint32_t>(act, off, nf, tmp, cnt, s);
     k_list<<<nblk(nf), 256, 0, s>>>(act, off, nf, list); note_launch();
     uint32_t na = 0;
     S_CK(cudaMemcpyAsync(&na, cnt, 4, cudaMemcpyDeviceToHost, s));
+    S_CK(cudaMemcpyAsync(hc, C, kMaxLin * 8, cudaMemcpyDeviceToHost, s));
     S_CK(cudaStreamSynchronize(s));
     S_CK(cudaGetLastError());
+    int64_t lin1_q = nf;
+    for (int j = 1; j < sp.lin1; ++j) lin1_q += (int64_t)hc[j];
+    *nq += (int64_t)nf * (1 + sp.bin1) + lin1_q;
     S_TRY(mlp_tc_check(st, s, err));
     if (!na) return ODC_OK;
-    // step 2: both rays from q, then step 3
-    k_face_lin2_gen<<<nblk(na, 128), 128, 0, s>>>(g, list, na, sp, S, pts); note_launch();
-    S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2 * sp.lin2, z, -1, s, err));
-    k_face_lin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, S, pts, hp, hint); note_launch();
+    // step 2: both rays from q (line samples one at a time per ray), then step 3
+    const uint32_t nr = 2 * na;
+    for (int j = 1; j <= sp.lin2; ++j) {
+        const uint32_t* lin = j == 1 ? nullptr : L[j & 1];
+        const unsigned long long* cin = j == 1 ? nullptr : C + kMaxLin + (j - 1);
+        uint32_t* lout = j < sp.lin2 ? L[(j + 1) & 1] : nullptr;
+        k_lin2_gen<<<nblk(nr, 128), 128, 0, s>>>(g, list, na, j, lin, cin, sp, S, lp, lh, t); note_launch();
+        if (cin) S_TRY(mlp_eval_list_dev(st, lp, nr, cin, lz, s, err, lh));
+        else S_TRY(mlp_eval_list(st, lp, nr, lz, -1, s, err, lh));
+        k_lin2_step<<<nblk(nr, kLinBlock), kLinBlock, 0, s>>>(g, list, na, j, lin, cin, lz, t, sp, S, pts, hp, hint,
+                                                             lout, C + kMaxLin + j); note_launch();
+    }
     for (int b = 0; b < sp.bin2; ++b) {
         S_TRY(mlp_eval_list(st, pts, (int64_t)na * 2, z, -1, s, err, hint));
         k_face_bin2<<<nblk(na, 128), 128, 0, s>>>(g, list, na, z, t, sp, b, S, pts, hp, hint); note_launch();
     }
     k_face_fin2<<<nblk(na, 128), 128, 0, s>>>(list, na, sp, S, pf, flags, dec); note_launch();
     S_CK(cudaGetLastError());
-    *nq += (int64_t)na * 2 * (sp.lin2 + sp.bin2);
+    S_CK(cudaMemcpyAsync(hc + kMaxLin, C + kMaxLin, kMaxLin * 8, cudaMemcpyDeviceToHost, s));
+    S_CK(cudaStreamSynchronize(s));
+    int64_t lin2_q = nr;
+    for (int j = 1; j < sp.lin2; ++j) lin2_q += (int64_t)hc[kMaxLin + j];
+    *nq += (int64_t)na * 2 * sp.bin2 + lin2_q;
     return mlp_tc_check(st, s, err);
 }
 
