@@ -54,15 +54,15 @@ def test_fp32_logits_match_fp64(ctx, mlp):
     assert np.array_equal(lab[sure], (zr > 0)[sure])
 
 
-def replay_parity(ctx, src, grid, k, precision=0, band=None):
-    mesh = ctx.extract(src, grid, steps_1d=k, precision=precision, band=band)
+def replay_parity(ctx, src, grid, k, precision=0, band=None, **search):
+    mesh = ctx.extract(src, grid, steps_1d=k, precision=precision, band=band, **search)
     T = ctx.debug("T").astype(np.int64)
     dec = ctx.search_decisions()
-    ref = oracle.extract(src, grid, steps_1d=k, replay=dict(T=T, **dec), replay_margin=MARGIN)
+    ref = oracle.extract(src, grid, steps_1d=k, replay=dict(T=T, **dec), replay_margin=MARGIN, **search)
     assert ref.stats["edge_violations"] == 0, ref.stats
     assert ref.stats["face_violations"] == 0, ref.stats
     rep, verts, tris = compare(ctx, mesh, ref, margin_eps=0.0)
-    own = oracle.extract(src, grid, steps_1d=k)
+    own = oracle.extract(src, grid, steps_1d=k, **search)
     rep["T_choices_differing_from_fp64"] = int(np.sum(own.T != T)) if own.T.shape == T.shape else None
     return mesh, ref, rep, verts, tris
 
@@ -191,6 +191,20 @@ def test_bf16_extract_equals_fp32_plain_path_off_half_iso(ctx, mlp, iso):
     l16, _ = ctx.eval_points(mlp, pts, iso=iso, precision=1, band=BF16_BAND)
     l32, _ = ctx.eval_points(mlp, pts, iso=iso, precision=0)
     assert np.array_equal(l16, l32)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("search", [dict(lin1=1, bin1=6, lin2=1, bin2=7),
+                                    dict(lin1=7, bin1=8, lin2=6, bin2=9, range1=1.5, range2=1.2)])
+def test_line_search_settings_replay_parity(ctx, mlp, precision, search):
+    """Non-default line-binary searches (one line sample, or many samples
+    over a longer range, where the line phase runs several early-exit rounds
+    and can end without a crossing) match the oracle's by decision replay."""
+    band = BF16_BAND if precision == 1 else None
+    mesh, ref, rep, verts, tris = replay_parity(ctx, mlp, I.cube_grid(24), 12, precision=precision, band=band,
+                                                **search)
+    print(search, rep)
+    assert rep["n_tris"] > 0
 
 
 def test_bf16_extract_replay_parity(ctx, mlp):
