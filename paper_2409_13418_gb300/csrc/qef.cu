@@ -32,16 +32,15 @@ __device__ __forceinline__ void jacobi3(double a[3][3], double V[3][3], double w
                 double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
                 double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                 double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < 3; ++k) {   // A <- A J
-                    double akp = a[k][p], akq = a[k][q];
-                    a[k][p] = c * akp - s * akq;
-                    a[k][q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < 3; ++k) {   // A <- J^T A
-                    double apk = a[p][k], aqk = a[q][k];
-                    a[p][k] = c * apk - s * aqk;
-                    a[q][k] = s * apk + c * aqk;
-                }
+                // A <- J^T A J on the symmetric matrix (Golub & Van Loan, Alg. 8.5.2):
+                // t solves t^2 + 2 theta t - 1 = 0, so the (p, q) entry becomes 0
+                const int r = 3 - p - q;
+                a[p][p] -= t * apq;
+                a[q][q] += t * apq;
+                a[p][q] = a[q][p] = 0.0;
+                const double arp = a[r][p], arq = a[r][q];
+                a[r][p] = a[p][r] = c * arp - s * arq;
+                a[r][q] = a[q][r] = s * arp + c * arq;
                 for (int k = 0; k < 3; ++k) {   // V <- V J
                     double vkp = V[k][p], vkq = V[k][q];
                     V[k][p] = c * vkp - s * vkq;
