@@ -600,7 +600,7 @@ def main():
         line = {"metric": "ODC Mcells/s at 256^3", "value": value, "unit": "Mcells/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if prec == odc.PREC_FP32 else "bf16+f32",
+                "dtype": "f32" if prec == odc.PREC_FP32 else "bf16+f16+f32",
                 "data": "synthetic (seeded random-init MLP weights)",
                 "config": {"workload": f"envelope MLP occupancy, {RES}^3 cells, k={STEPS_1D}, "
                                        f"{args.precision}" + (f" band {args.band}" if prec == odc.PREC_BF16 else ""),
