@@ -28,7 +28,9 @@ Readings where the paper is silent:
 All geometry is in cell-local units (a cell is the unit cube).
 
 Parity unpinned: none of the above readings is printed in the paper; each is
-pinned instead by the closed forms and invariants in tests/test_oracle_pins.py.
+pinned instead by the closed forms and invariants in tests/test_oracle_pins.py,
+and the IC case rule (ic_cases) by the envelope-containment brute force and
+the intersection-free guarantee of A.1.5 in tests/test_oracle_ic.py.
 """
 from __future__ import annotations
 
@@ -300,6 +302,35 @@ def topology_triangles(labels):
             tris += [(ids[0], ids[1], ids[2]), (ids[0], ids[2], ids[3])]
     return np.array(tris, np.int64).reshape(-1, 3), t
 
+
+
+def ic_cases(P, p_in, p_out):
+    """Split case of each quad by the convex/concave analysis (A.1.5).
+
+    P [Q, 4, 3]: the 3D points of cells c1..c4 around a crossing edge, ordered
+    so that the triangle of the cell centres c1, c2, c3 has its normal along
+    v_in -> v_out; p_in, p_out [Q, 3]: the edge's inside and outside ends.
+    Eq. A1: the edge (p_c2, v_out) is concave when p_c2 lies below the oriented
+    triangle (p_c1, p_c3, v_out); Eq. A2: the edge (p_c2, v_in) is concave when
+    p_c2 lies above (p_c1, p_c3, v_in); p_c2 is concave when either is.  The
+    other three vertices take the same tests with their own ring neighbours
+    (c_{k-1}, c_{k+1}) in place of (c1, c3).  Case 1 (diagonal c1 c3) is valid
+    when neither c2 nor c4 is concave, case 2 (diagonal c2 c4) when neither
+    c1 nor c3 is; case 1 when both are valid, case 3 (a fan around p_e) when
+    neither is.  Returns (case [Q], smallest |determinant| over the tests).
+    """
+    Q = P.shape[0]
+    conc = np.zeros((Q, 4), bool)
+    mindet = np.full(Q, np.inf)
+    for kq in range(4):
+        pk, pp, pn = P[:, kq], P[:, (kq - 1) % 4], P[:, (kq + 1) % 4]
+        d_out = np.einsum("ij,ij->i", pk - p_out, np.cross(pp - p_out, pn - p_out))
+        d_in = np.einsum("ij,ij->i", pk - p_in, np.cross(pp - p_in, pn - p_in))
+        conc[:, kq] = (d_out < 0) | (d_in > 0)
+        mindet = np.minimum(mindet, np.minimum(np.abs(d_out), np.abs(d_in)))
+    ok1 = ~(conc[:, 1] | conc[:, 3])
+    ok2 = ~(conc[:, 0] | conc[:, 2])
+    return np.where(ok1, 1, np.where(ok2, 2, 3)), mindet
 
 
 def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12,
@@ -778,17 +809,7 @@ def extract(src, grid, steps_1d=15, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=12
     p_out = np.where(lower_in[:, None], EYE[qa].astype(np.float64), 0.0)
     case = np.ones(Q, np.int64)
     if ic_split and Q:
-        conc = np.zeros((Q, 4), bool)
-        mindet = np.full(Q, np.inf)
-        for kq in range(4):
-            pk, pp, pn = P[:, kq], P[:, (kq - 1) % 4], P[:, (kq + 1) % 4]
-            d_out = np.einsum("ij,ij->i", pk - p_out, np.cross(pp - p_out, pn - p_out))
-            d_in = np.einsum("ij,ij->i", pk - p_in, np.cross(pp - p_in, pn - p_in))
-            conc[:, kq] = (d_out < 0) | (d_in > 0)
-            mindet = np.minimum(mindet, np.minimum(np.abs(d_out), np.abs(d_in)))
-        ok1 = ~(conc[:, 1] | conc[:, 3])
-        ok2 = ~(conc[:, 0] | conc[:, 2])
-        case = np.where(ok1, 1, np.where(ok2, 2, 3))
+        case, mindet = ic_cases(P, p_in, p_out)
         qflag |= mindet < 1e-5
     is3 = case == 3
     pe_id = V3 + np.cumsum(is3) - 1
