@@ -63,7 +63,25 @@ def replay_parity(ctx, src, grid, k, precision=0, band=None, **search):
     assert ref.stats["face_violations"] == 0, ref.stats
     rep, verts, tris = compare(ctx, mesh, ref, margin_eps=0.0)
     own = oracle.extract(src, grid, steps_1d=k, **search)
-    rep["T_choices_differing_from_fp64"] = int(np.sum(own.T != T)) if own.T.shape == T.shape else None
+    # Decisions the GPU took differently from the FP64 network's own choice:
+    # each one sits inside the replay band (the replay above found no
+    # violation), and they must stay a small minority of the searches.
+    assert own.T.shape == T.shape and own.faces.shape == ref.faces.shape
+    rep["T_choices_differing_from_fp64"] = int(np.sum(own.T != T))
+    face_diff = np.zeros(len(own.faces), bool)
+    for key in ("Jq", "J1", "J2", "lab_m"):
+        face_diff |= np.asarray(own.search[key]).astype(np.int64) != np.asarray(dec[key]).astype(np.int64)
+    rep["face_choices_differing_from_fp64"] = int(face_diff.sum())
+    print("decisions differing from the FP64 network's own:", rep["T_choices_differing_from_fp64"], "of", len(T),
+          "edges;", rep["face_choices_differing_from_fp64"], "of", len(face_diff), "faces;",
+          own.stats["queries"], "decisions")
+    # a search that differs differs in at least one decision: at most 1% of all
+    # decisions (measured <= 0.1%), and per search at most 2% of the 1D
+    # searches (measured <= 0.9%) and 8% of the 2D ones (measured <= 4.1%)
+    n_diff = rep["T_choices_differing_from_fp64"] + rep["face_choices_differing_from_fp64"]
+    assert n_diff <= max(2, 0.01 * own.stats["queries"]), rep
+    assert rep["T_choices_differing_from_fp64"] <= max(2, 0.02 * len(T)), rep
+    assert rep["face_choices_differing_from_fp64"] <= max(2, 0.08 * len(face_diff)), rep
     return mesh, ref, rep, verts, tris
 
 
@@ -227,5 +245,5 @@ def test_fp32_tile_shapes_give_identical_bits(ctx, mlp):
     _, z = ctx.eval_points(mlp, pts, precision=0)
     assert z.tobytes() == ref.tobytes()
     m = ctx.extract(mlp, I.cube_grid(24), steps_1d=10, precision=0)
-    assert m.stats["fp32_tile"] in (0, 1, 2, 3)
+    assert m.stats["fp32_tile"] in range(4)
     print("autotuned FP32 tile shape", m.stats["fp32_tile"])
