@@ -140,9 +140,11 @@ extern "C" odc_status odc_compact_edges_noalloc(const uint32_t* d_label_bits, co
     uint32_t* tmp = off + kNoAllocMaxWords;
     uint32_t* total = (uint32_t*)scr + (kNoAllocScratchBytes / 4 - 1);
     if ((size_t)(total - tmp) < scan_tmp_elems(nw)) return na_fail(ODC_ERR_INTERNAL, "scan scratch too small");
-    // the total is the only value read before being written in this call
-    e = cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess) return na_fail(ODC_ERR_CUDA, std::string("memset: ") + cudaGetErrorString(e));
+    // Every scratch word this call reads (counts, offsets, scan partials and
+    // the total, which the scan always writes) is written earlier in the same
+    // call, so no result depends on what an earlier call left in the array.
+    // What the calls share is the array itself: calls that overlap on the GPU
+    // overwrite each other's words.
     k_na_count<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(d, d_label_bits, nw, cnt); note_launch();
     exclusive_scan<uint32_t>(cnt, off, nw, tmp, total, st);
     k_na_emit<<<(unsigned)((nw * 32 + 255) / 256), 256, 0, st>>>(d, d_label_bits, nw, off, d_edges, max_edges); note_launch();

@@ -55,3 +55,29 @@ def test_noalloc_rejects_oversized_grid_and_small_buffer():
     with pytest.raises(odc.OdcError) as e:
         odc.compact_edges_noalloc(d_bits.data_ptr(), (4, 4, 4), d.data_ptr(), 1, d[8:].data_ptr())
     assert e.value.status == 2
+
+
+def test_noalloc_count_stays_on_device_without_host_count():
+    """Without a host count the call only queues its work: the count lands in
+    the caller's device word, stream ordered, and matches odc_extract's."""
+    import torch
+
+    from paper_2409_13418_gb300 import build, inputs as I, odc
+    build.build()
+    ctx = odc.Context(0)
+    try:
+        src, grid = I.random_csg(8), I.cube_grid(72)
+        ctx.extract(src, grid, steps_1d=8)
+        bits, ref = ctx.debug("labels"), ctx.debug("edges")
+        d_bits = torch.from_numpy(bits.view(np.int32).copy()).cuda()
+        d_edges = torch.full((ref.size + 16,), -1, dtype=torch.int32, device="cuda")
+        d_count = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+        for _ in range(2):
+            assert odc.compact_edges_noalloc(d_bits.data_ptr(), grid.res, d_edges.data_ptr(), d_edges.numel(),
+                                             d_count.data_ptr(), stream.cuda_stream, read_count=False) is None
+            stream.synchronize()
+            assert int(d_count.item()) == ref.size
+            assert np.array_equal(d_edges[:ref.size].cpu().numpy().view(np.uint32), ref)
+    finally:
+        ctx.close()
