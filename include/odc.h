@@ -261,6 +261,23 @@ odc_status odc_ctx_create(int device, size_t mem_budget, odc_ctx** out);
  * weights and scratch), for memory accounting. */
 odc_status odc_ctx_memory(odc_ctx* ctx, size_t* bytes);
 
+/* Failure detection of the device pipelines (the paper has no counterpart:
+ * its evaluations have no device-side waits).  ``ns`` limits, in
+ * nanoseconds of device global time, every pipeline wait (an mbarrier
+ * phase: a weight slice landing, an accumulator or activation tile ready)
+ * of this context's single-CTA tensor-core kernels, the BF16 pass and the
+ * FP16 tier of the BF16 path; 0 restores the default of 2 s.  ``d_gate``
+ * (device int32, caller-owned, or NULL for none) holds those kernels
+ * before their first tensor-core operation until *d_gate != 0, waiting
+ * under the same limit: a go signal from other device work.  A wait that
+ * runs out sets the kernel's abort flag: every role of the CTA stops
+ * issuing, the weight loads and tensor-core operations already started are
+ * waited for (shared memory and TMEM are released idle), and the call that
+ * launched the kernel returns ODC_ERR_TIMEOUT with its outputs undefined;
+ * the context stays usable.  A gate that nothing sets is how a test makes
+ * a wait run out without a hung device. */
+odc_status odc_ctx_set_wait_limit(odc_ctx* ctx, uint64_t ns, const int32_t* d_gate);
+
 /* Destroy a context and free its device memory.  NULL is accepted. */
 odc_status odc_ctx_destroy(odc_ctx* ctx);
 

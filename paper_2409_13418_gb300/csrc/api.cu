@@ -60,6 +60,8 @@ struct odc_ctx {
     cudaStream_t own = nullptr;
     Arena A, B, S;              // grid-sized, count-sized, source (prims / weights)
     uint32_t* h_cnt = nullptr;  // pinned host counters
+    unsigned long long wait_ns = 0;   // limit of the tensor-core kernels' pipeline waits (0: default)
+    const int* gate = nullptr;        // device go signal of the tensor-core kernels (NULL: none)
     cudaEvent_t ev[9] = {};
     MlpState* mlp = nullptr;
     // resident source
@@ -361,6 +363,7 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
         return fail(ODC_ERR_INVALID_ARG, "no resident source on this context");
     }
     const int kind = c->res_kind;
+    mlp_set_wait_limit(c->mlp, c->wait_ns, c->gate);
     if ((prm->flags & (ODC_ABL_LINEAR_1D | ODC_ABL_GRADIENT_NORMALS)) && kind != ODC_SRC_CSG)
         return fail(ODC_ERR_UNSUPPORTED, "ablation variants need an implicit with a gradient: CSG sources only");
     const bool linear_1d = (prm->flags & ODC_ABL_LINEAR_1D) != 0;
@@ -989,6 +992,14 @@ odc_status odc_manifold_flips(odc_ctx* c, const odc_grid* grid, const uint32_t* 
     return ODC_OK;
 }
 
+odc_status odc_ctx_set_wait_limit(odc_ctx* c, uint64_t ns, const int32_t* d_gate) {
+    if (!c) return fail(ODC_ERR_INVALID_ARG, "NULL context");
+    c->wait_ns = ns;
+    c->gate = d_gate;
+    mlp_set_wait_limit(c->mlp, ns, d_gate);
+    return ODC_OK;
+}
+
 odc_status odc_ctx_memory(odc_ctx* c, size_t* bytes) {
     if (!c || !bytes) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
     *bytes = c->A.cap + c->B.cap + c->S.cap + c->extra_bytes() + mlp_device_bytes(c->mlp);
@@ -1128,6 +1139,7 @@ odc_status odc_eval_points(odc_ctx* c, const odc_source* src, const float* point
         vox.iso = iso;
         launch_vox_points(vox, dp, n, dl, st);
     } else {
+        mlp_set_wait_limit(c->mlp, c->wait_ns, c->gate);
         s = mlp_points(c->mlp, dp, n, iso, precision, dl, dz, st, &g_err);
         if (s != ODC_OK) return s;
     }

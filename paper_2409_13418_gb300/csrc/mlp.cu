@@ -40,6 +40,11 @@ odc_status mlp_check(const odc_mlp* m, std::string* err) {
 float mlp_logit_threshold(float iso) { return (float)std::log((double)iso / (1.0 - (double)iso)); }
 
 int mlp_precision(const MlpState* st) { return st->precision; }
+void mlp_set_wait_limit(MlpState* st, unsigned long long ns, const int* gate) {
+    if (!st) return;
+    st->wait_ns = ns;
+    st->gate = gate;
+}
 int64_t mlp_split_count(const MlpState* st) { return st ? (int64_t)st->hq[1] : 0; }
 int64_t mlp_fp32_requery_count(const MlpState* st) { return st ? (int64_t)st->hq[2] : 0; }
 int64_t mlp_h16_count(const MlpState* st) { return st ? (int64_t)st->hq[3] : 0; }

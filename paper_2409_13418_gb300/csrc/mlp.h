@@ -44,6 +44,9 @@ odc_status mlp_eval_list_dev(MlpState* st, const float3* pts, int64_t n_max, con
 // Logits at the grid vertices in label-word order (query q -> word q/32, lane q%32).
 odc_status mlp_eval_grid(MlpState* st, const GridDev& g, float* z, cudaStream_t s, std::string* err);
 int mlp_precision(const MlpState* st);
+// Limit of every pipeline wait of the single-CTA tensor-core kernels (the
+// BF16 pass and the FP16 tier), in ns of device global time; 0: 2 s.
+void mlp_set_wait_limit(MlpState* st, unsigned long long ns, const int* gate);
 float mlp_logit_threshold(float iso);
 
 // Grid labels (a1): bit rows as in the CSG path.

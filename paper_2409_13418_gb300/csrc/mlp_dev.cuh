@@ -73,6 +73,8 @@ struct MlpState {
     float zsplit = 4e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
+    unsigned long long wait_ns = 0;   // limit of the single-CTA tensor-core kernels' pipeline waits (0: 2 s)
+    const int* gate = nullptr;        // device go signal of those kernels (NULL: none)
     int sms = 0;                // SM count of the device
     cudaStream_t stream = nullptr;   // stream of the current call (scratch growth is ordered on it)
     // device counters: [0..3] queries evaluated from device-sized lists by the

@@ -80,15 +80,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of parity ``parity``; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+// Bounded wait for the phase of parity ``parity`` (limit_ns of global time);
+// false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort,
+                                          unsigned long long limit_ns = kWaitNs) {
     if (mbar_try(b, parity)) return true;
     unsigned long long t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(b, parity)) return true;
         if ((i & 255) == 0) {
             if (*abort) return false;
-            if (gtimer() - t0 > kWaitNs) {
+            if (gtimer() - t0 > limit_ns) {
                 *abort = 1;
                 return false;
             }
@@ -304,6 +306,8 @@ struct TcParams {
     int* err;
     const float* wsc;       // split path (device [4]): 2^-s_l undoing the weight scale of layer l
     float zt;               // split path: logit written for an out-of-range query (forces re-evaluation)
+    unsigned long long wait_ns;   // single-CTA kernels: limit of each pipeline wait (0: kWaitNs)
+    const volatile int* gate;     // single-CTA kernels: if set, no tensor-core work before *gate != 0
 };
 
 // F16 = false: the BF16 pass (BF16 weights and activations).  F16 = true: the
@@ -323,8 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* empty = bars + kStages;
     uint64_t* acc_full = bars + 2 * kStages;
     uint64_t* act_ready = bars + 2 * kStages + 1;
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 2);
+    uint64_t* mma_drain = bars + 2 * kStages + 2;      // after an abort: the MMAs issued so far have completed
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 3);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
+    static_assert((2 * kStages + 3) * 8 + 8 <= 256, "barrier block");
+    const unsigned long long wlim = P.wait_ns ? P.wait_ns : kWaitNs;
     float* sp = (float*)((uint8_t*)bars + 256);        // biases [4][256], w4 [256], b4, Fourier B [64][3]
     for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sp[i] = P.wblob[kOffb_(i / kH) + (i % kH)];
     for (int i = threadIdx.x; i < kH; i += blockDim.x) sp[4 * kH + i] = P.wblob[kOffW_(kNL) + i];
@@ -343,6 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(acc_full, 1);
         mbar_init(act_ready, kEpiWarps);
+        mbar_init(mma_drain, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&m0) : "memory");
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const CUtensorMap* map = l == 0 ? &m0 : l == 1 ? &m1 : l == 2 ? &m2 : &m3;
                     int nck = l == 0 ? kChunks0 : kChunksH;
                     for (int c = 0; c < nck; ++c) {
-                        if (!mbar_wait(&empty[stage], phase ^ 1, abort)) { ok = false; break; }
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort, wlim)) { ok = false; break; }
                         mbar_expect_tx(&full[stage], kSliceBytes);
                         tma_load_2d(Bring + stage * kSliceBytes, map, c * kKC, 0, &full[stage]);
                         ++issued;
@@ -396,14 +404,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0, act_phase = 0;
             bool ok = true;
             const uint32_t a_base = su32(A), b_base = su32(Bring);
+            if (P.gate) {   // bounded wait for the caller's device-side go signal
+                const unsigned long long t0 = gtimer();
+                while (*P.gate == 0) {
+                    if (*abort) { ok = false; break; }
+                    if (gtimer() - t0 > wlim) { *abort = 1; ok = false; break; }
+                }
+            }
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 for (int l = 0; l < kNL && ok; ++l) {
-                    if (!mbar_wait(act_ready, act_phase, abort)) { ok = false; break; }
+                    if (!mbar_wait(act_ready, act_phase, abort, wlim)) { ok = false; break; }
                     act_phase ^= 1;
                     tc_fence_after();
                     int nck = l == 0 ? kChunks0 : kChunksH;
                     for (int c = 0; c < nck; ++c) {
-                        if (!mbar_wait(&full[stage], phase, abort)) { ok = false; break; }
+                        if (!mbar_wait(&full[stage], phase, abort, wlim)) { ok = false; break; }
                         tc_fence_after();
                         for (int s = 0; s < kSub; ++s) {
 #pragma unroll
@@ -463,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive(act_ready);
             for (int l = 0; l < kNL; ++l) {
                 // every lane waits; the warp proceeds only if all lanes saw the phase
-                bool got = mbar_wait(acc_full, acc_phase, abort);
+                bool got = mbar_wait(acc_full, acc_phase, abort, wlim);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 acc_phase ^= 1;
                 tc_fence_after();
@@ -534,6 +549,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     if (warp == 1) {
+        if (*abort && lane == 0) {
+            // after an expired wait the epilogue may not have waited for the
+            // last MMAs the issuer (this thread) started: let them finish
+            // before TMEM is released
+            umma_commit(mma_drain);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(mma_drain, 0) && gtimer() - t0 < kWaitNs) {}
+        }
+        __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
@@ -1045,7 +1069,7 @@ static odc_status tc_single_eval(MlpState* st, bool f16, const QuerySrc& Q, int6
     }
     int64_t tiles = (n + tc::kRows - 1) / tc::kRows;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, T->wsc, st->zt};
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, T->wsc, st->zt, st->wait_ns, st->gate};
     const int kind = f16 ? 3 : 1;
     cudaEvent_t* ev = mlp_ev_pair(st, kind);
     if (ev) cudaEventRecord(ev[0], s);
@@ -1089,7 +1113,7 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
     // CTA pairs, each pair 256 queries per step
     int64_t steps = (n + tc::kPairRows - 1) / tc::kPairRows;
     int grid = 2 * (int)std::min<int64_t>(steps, (int64_t)T->clusters3);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, nullptr, st->zt};
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, nullptr, st->zt, 0ull, nullptr};
     P.wsc = T->wsc;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];

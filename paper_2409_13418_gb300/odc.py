@@ -147,7 +147,7 @@ EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", 
            "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_compact_edges_noalloc", "odc_status_str",
            "odc_last_error", "odc_server_create", "odc_server_destroy", "odc_submit", "odc_poll", "odc_result_release",
            "odc_server_clock", "odc_mesh_quality", "odc_extract_slab", "odc_slab_place", "odc_extract_slabbed",
-           "odc_ctx_memory", "odc_grid_labels", "odc_manifold_flips"]
+           "odc_ctx_memory", "odc_grid_labels", "odc_manifold_flips", "odc_ctx_set_wait_limit"]
 
 _lib = None
 
@@ -166,6 +166,8 @@ def load(path: str = LIB_PATH):
     lib.odc_extract.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), P, C.POINTER(MeshC)]
     lib.odc_mesh_copy.argtypes = [P, C.POINTER(MeshC), P, P, C.c_int]
     lib.odc_ctx_memory.argtypes = [P, C.POINTER(C.c_size_t)]
+    lib.odc_ctx_set_wait_limit.argtypes = [P, C.c_uint64, P]
+    lib.odc_ctx_set_wait_limit.restype = C.c_int
     lib.odc_grid_labels.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.c_int32, C.c_int32, P,
                                     P]
     lib.odc_manifold_flips.argtypes = [P, C.POINTER(Grid), P, P, C.c_int32, P, C.POINTER(C.c_int64)]
@@ -309,16 +311,19 @@ def make_params(steps_1d=15, iso=0.5, lin1=4, bin1=11, range1=0.8, lin2=3, bin2=
 
 
 def compact_edges_noalloc(d_label_bits: int, res, d_edges: int, max_edges: int, d_count: int,
-                          stream: int | None = None) -> int:
+                          stream: int | None = None, read_count: bool = True) -> int | None:
     """Crossing edges of a device label bitmask with no allocation (odc_compact_edges_noalloc).
 
-    All pointers are device addresses owned by the caller; returns the edge
-    count (the call synchronises ``stream`` to read it back).
+    All pointers are device addresses owned by the caller.  With
+    ``read_count`` the call synchronises ``stream`` and returns the edge
+    count; without it the count is only written to ``d_count`` (stream
+    ordered, no host wait) and None is returned.
     """
     r = (C.c_int32 * 3)(*[int(x) for x in res])
     h = C.c_uint32()
-    _check(load().odc_compact_edges_noalloc(d_label_bits, r, d_edges, max_edges, d_count, C.byref(h), stream))
-    return int(h.value)
+    _check(load().odc_compact_edges_noalloc(d_label_bits, r, d_edges, max_edges, d_count,
+                                            C.byref(h) if read_count else None, stream))
+    return int(h.value) if read_count else None
 
 
 class Mesh:
@@ -375,23 +380,30 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0, h16=True):
+    def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0, h16=True, fp32_tile=None):
         """Make ``src`` the context's resident source (``extract(None, ...)`` reuses it)."""
-        holder = _SourceHolder(src, precision, band, split, split_zmargin, h16=h16)
+        holder = _SourceHolder(src, precision, band, split, split_zmargin, fp32_tile=fp32_tile, h16=h16)
         _check(_lib.odc_source_upload(self.h, C.byref(holder.src)))
 
     def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, split=True,
-                split_zmargin=0.0, reupload=False, h16=True, **kw) -> Mesh:
+                split_zmargin=0.0, reupload=False, h16=True, fp32_tile=None, **kw) -> Mesh:
         """Run ODC; ``src=None`` reuses the resident source.  ``reupload`` forces
         the network weights to be prepared and copied even if the context holds them;
-        ``h16=False`` skips the FP16 tier of the BF16 path (same mesh, other cost)."""
-        holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, h16=h16)
+        ``h16=False`` skips the FP16 tier of the BF16 path (same mesh, other cost);
+        ``fp32_tile`` forces a tile shape of the FP32 network (same bits)."""
+        holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, fp32_tile=fp32_tile, h16=h16)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
         m = MeshC()
         _check(_lib.odc_extract(self.h, C.byref(holder.src), C.byref(g), C.byref(p),
                                 stream if stream else None, C.byref(m)))
         return Mesh(self, m)
+
+    def set_wait_limit(self, ns: int, gate: int | None = None) -> None:
+        """odc_ctx_set_wait_limit: limit of the tensor-core kernels' pipeline
+        waits in ns (0: the default) and an optional device go flag (address
+        of a device int32, None for none)."""
+        _check(_lib.odc_ctx_set_wait_limit(self.h, int(ns), gate))
 
     def device_bytes(self) -> int:
         """odc_ctx_memory: device bytes the context holds."""
