@@ -606,6 +606,7 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
         mlp_timing_collect(c->mlp, 1, &S.tc_ms, &S.tc_flops, &S.tc_launches);
         mlp_timing_collect(c->mlp, 2, &S.split_ms, &S.split_flops, &S.split_launches);
         mlp_timing_collect(c->mlp, 3, &S.h16_ms, &S.h16_flops, &S.h16_launches);
+        mlp_timing_collect(c->mlp, 4, &S.fp8_ms, &S.fp8_flops, &S.fp8_launches);
         S.n_split = mlp_split_count(c->mlp);
         S.n_h16 = mlp_h16_count(c->mlp);
         S.fp32_tile = mlp_fp32_variant(c->mlp);

@@ -29,9 +29,9 @@ odc_status mlp_check(const odc_mlp* m, std::string* err) {
     if (!m->B) { *err = "Fourier matrix missing"; return ODC_ERR_INVALID_ARG; }
     for (int l = 0; l <= kNL; ++l)
         if (!m->W[l] || !m->b[l]) { *err = "weight or bias pointer missing"; return ODC_ERR_INVALID_ARG; }
-    if (m->precision != ODC_PREC_FP32 && m->precision != ODC_PREC_BF16)
-        { *err = "precision must be FP32 or BF16"; return ODC_ERR_INVALID_ARG; }
-    if (m->precision == ODC_PREC_BF16 && !(m->band >= 0.0f && m->band < 0.5f))
+    if (m->precision != ODC_PREC_FP32 && m->precision != ODC_PREC_BF16 && m->precision != ODC_PREC_FP8)
+        { *err = "precision must be FP32, BF16 or FP8"; return ODC_ERR_INVALID_ARG; }
+    if (m->precision != ODC_PREC_FP32 && !(m->band >= 0.0f && m->band < 0.5f))
         { *err = "band must be in [0, 0.5)"; return ODC_ERR_INVALID_ARG; }
     if (!(m->split_zmargin >= 0.0f)) { *err = "split_zmargin must be >= 0"; return ODC_ERR_INVALID_ARG; }
     return ODC_OK;
@@ -48,6 +48,7 @@ void mlp_set_wait_limit(MlpState* st, unsigned long long ns, const int* gate) {
 int64_t mlp_split_count(const MlpState* st) { return st ? (int64_t)st->hq[1] : 0; }
 int64_t mlp_fp32_requery_count(const MlpState* st) { return st ? (int64_t)st->hq[2] : 0; }
 int64_t mlp_h16_count(const MlpState* st) { return st ? (int64_t)st->hq[3] : 0; }
+int64_t mlp_fp8_count(const MlpState* st) { return st ? (int64_t)st->hq[4] : 0; }
 
 #define MLP_CK(call)                                                                        \
     do {                                                                                    \
@@ -98,12 +99,13 @@ void mlp_timing_begin(MlpState* st, cudaStream_t s) {
     for (auto& f : st->flops) f = 0.0;
     for (auto& l : st->launches) l = 0;
     for (auto& v : st->hq) v = 0;
-    if (st->dq) cudaMemsetAsync(st->dq, 0, 4 * sizeof(unsigned long long), s);
+    if (st->dq) cudaMemsetAsync(st->dq, 0, 16 * sizeof(unsigned long long), s);
 }
 
 void mlp_timing_finish(MlpState* st, cudaStream_t s) {
     if (!st || !st->dq) return;
     if (cudaMemcpyAsync(st->hq, st->dq, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(st->hq + 4, st->dq + 10, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         for (auto& v : st->hq) v = 0;
@@ -121,11 +123,12 @@ void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_
         if (cudaEventElapsedTime(&t, st->ev[2 * i], st->ev[2 * i + 1]) == cudaSuccess) *ms += t;
         else cudaGetLastError();
     }
-    // device-sized lists: hq[0] BF16, hq[1] split-FP16 (three products), hq[2] FP32, hq[3] FP16
+    // device-sized lists: hq[0] BF16, hq[1] split-FP16 (three products), hq[2] FP32, hq[3] FP16, hq[4] FP8
     const double dev = kind == 0   ? (double)st->hq[2]
                        : kind == 1 ? (double)st->hq[0]
                        : kind == 2 ? 3.0 * (double)st->hq[1]
-                                   : (double)st->hq[3];
+                       : kind == 3 ? (double)st->hq[3]
+                                   : (double)st->hq[4];
     *flops = st->flops[kind] + kFlopsPerQuery * dev;
     *launches = st->launches[kind];
 }
@@ -167,7 +170,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
         MLP_CK(cudaDeviceGetAttribute(&st->sms, cudaDevAttrMultiProcessorCount, dev));
     }
     if (!st->dq) {
-        MLP_CK(cudaMalloc((void**)&st->dq, 8 * sizeof(unsigned long long)));
+        MLP_CK(cudaMalloc((void**)&st->dq, 16 * sizeof(unsigned long long)));
         odc_status r0 = fp32_kernel_setup(err);
         if (r0 != ODC_OK) return r0;
     }
@@ -179,11 +182,13 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
         }
         st->fp32_forced = f - 1;
     }
-    st->precision = m->precision;
+    // FP8: the BF16 path's tiers behind an FP8 pass
+    st->precision = m->precision == ODC_PREC_FP8 ? ODC_PREC_BF16 : m->precision;
+    st->fp8 = m->precision == ODC_PREC_FP8 ? 1 : 0;
     st->band = m->band;
     st->split = m->no_split ? 0 : 1;
     st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
-    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 4e-5f;
+    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2.5e-5f;
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
     st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
     st->scale = m->env_scale;
@@ -284,7 +289,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // ends with a barrier before the epilogue overwrites the tile.
 template <class T>
 __device__ __forceinline__ void dense_relu(float* act, int K, const float* __restrict__ Wt,
-                                           const float* __restrict__ bias, float* __restrict__ wbuf) {
+                                           const float* __restrict__ bias, float* __restrict__ wbuf,
+                                           const float* const* rowb = nullptr) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = (warp >> 2) * 32 + (lane >> 3) * 8;
     const int col0 = (warp & 3) * 64 + (lane & 7) * 4;
@@ -331,15 +337,30 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
     }
     cp_async_wait<0>();
     __syncthreads();   // every thread has read the last chunk and the whole input tile
+    if (rowb) {   // a bias row per query (rowb[m]: row of tile query m)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int col = col0 + (j < 4 ? j : 28 + j);
-        const float b = bias[col];
-        float* o = act + (size_t)col * T::kActStride + row0;
-        *reinterpret_cast<float4*>(o) = make_float4(fmaxf(acc[0][j] + b, 0.f), fmaxf(acc[1][j] + b, 0.f),
-                                                    fmaxf(acc[2][j] + b, 0.f), fmaxf(acc[3][j] + b, 0.f));
-        *reinterpret_cast<float4*>(o + 4) = make_float4(fmaxf(acc[4][j] + b, 0.f), fmaxf(acc[5][j] + b, 0.f),
-                                                        fmaxf(acc[6][j] + b, 0.f), fmaxf(acc[7][j] + b, 0.f));
+        for (int j = 0; j < 8; ++j) {
+            const int col = col0 + (j < 4 ? j : 28 + j);
+            float* o = act + (size_t)col * T::kActStride + row0;
+            float b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) b[i] = rowb[row0 + i][col];
+            *reinterpret_cast<float4*>(o) = make_float4(fmaxf(acc[0][j] + b[0], 0.f), fmaxf(acc[1][j] + b[1], 0.f),
+                                                        fmaxf(acc[2][j] + b[2], 0.f), fmaxf(acc[3][j] + b[3], 0.f));
+            *reinterpret_cast<float4*>(o + 4) = make_float4(fmaxf(acc[4][j] + b[4], 0.f), fmaxf(acc[5][j] + b[5], 0.f),
+                                                            fmaxf(acc[6][j] + b[6], 0.f), fmaxf(acc[7][j] + b[7], 0.f));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int col = col0 + (j < 4 ? j : 28 + j);
+            const float b = bias[col];
+            float* o = act + (size_t)col * T::kActStride + row0;
+            *reinterpret_cast<float4*>(o) = make_float4(fmaxf(acc[0][j] + b, 0.f), fmaxf(acc[1][j] + b, 0.f),
+                                                        fmaxf(acc[2][j] + b, 0.f), fmaxf(acc[3][j] + b, 0.f));
+            *reinterpret_cast<float4*>(o + 4) = make_float4(fmaxf(acc[4][j] + b, 0.f), fmaxf(acc[5][j] + b, 0.f),
+                                                            fmaxf(acc[6][j] + b, 0.f), fmaxf(acc[7][j] + b, 0.f));
+        }
     }
     __syncthreads();
 }
@@ -355,6 +376,7 @@ __global__ void __launch_bounds__(T::kThreads, 1)
     float* wbuf = sm + kH * T::kActStride;      // kWStages staged weight chunks
     __shared__ float3 xs[T::kTM];
     __shared__ float part[T::kTM][4];
+    __shared__ const float* rowb[T::kTM];   // per-query first-layer bias rows (Q.b0tab)
     const int tid = threadIdx.x;
     const int64_t n = query_count(Q, n_max);
     const float* B = wb + kOffB;
@@ -362,6 +384,7 @@ __global__ void __launch_bounds__(T::kThreads, 1)
         if (tid < T::kTM) {
             int64_t q = base + tid;
             xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
+            if (Q.b0tab) rowb[tid] = q < n ? query_b0(Q, query_index(Q, q)) : wb + kOffb_(0);
         }
         __syncthreads();
         for (int i = tid; i < kNF * T::kTM; i += T::kThreads) {
@@ -372,7 +395,8 @@ __global__ void __launch_bounds__(T::kThreads, 1)
         }
         __syncthreads();
         for (int l = 0; l < kNL; ++l)
-            dense_relu<T>(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf);
+            dense_relu<T>(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf,
+                          l == 0 && Q.b0tab ? rowb : nullptr);
         for (int t = tid; t < 4 * T::kTM; t += T::kThreads) {
             const int m = t % T::kTM, p = t / T::kTM;
             const float* w5 = wb + kOffW[kNL];
@@ -529,13 +553,18 @@ static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float*
 // Tiers: 0 BF16 pass, 1 FP16 tier, 2 split-FP16 tier, 3 FP32.  A query's
 // first tier comes from hint[i], an estimate of |z_i - zt| (from the logits
 // around the query in its search); no hint routes to the BF16 pass.
+// With an FP8 pass, tier 4 comes first: queries predicted at |z - zt| >= z8
+// (and every query without a hint) start there.
 struct RouteArgs {
     const float* hint;
     float zs, zh, zb;
     int split, h16;
+    float z8;
+    int fp8;
 };
 __device__ __forceinline__ int route_of(const RouteArgs& ra, int64_t i) {
     const float h = ra.hint ? ra.hint[i] : INFINITY;
+    if (ra.fp8 && h >= ra.z8) return 4;
     if (h < ra.zs) return 3;
     if (h < ra.zh) return ra.split ? 2 : 3;
     if (h < ra.zb) return ra.h16 ? 1 : (ra.split ? 2 : 3);
@@ -598,7 +627,8 @@ __global__ void __launch_bounds__(kTierBlock)
 // equals the FP32 plain path's.  A logit of the BF16 pass is kept only
 // outside the band |z - zt| >= zband; the single-product FP16 tier (measured
 // error 0.0091, below zh16 / 2) re-takes the band and keeps |z - zt| >= zh16; the
-// split-FP16 tensor-core network (measured error below zsplit / 3) re-takes
+// split-FP16 tensor-core network (largest measured error 0.52 zsplit, about
+// 4.8 standard deviations of its error on near-surface points) re-takes
 // the rest and keeps |z - zt| >= zsplit; the FP32 SIMT network takes what is
 // left.  A disabled tier passes its queries on with its predecessor's
 // margin.  With hints, a query starts at the tier its predicted |z - zt|
@@ -618,18 +648,31 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     uint8_t* route = (uint8_t*)pr;
     unsigned long long* cnt = st->dq + 4;
     const unsigned blocks = (unsigned)((n + kTierBlock - 1) / kTierBlock);
-    MLP_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
-    const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16};
+    MLP_CK(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), s));   // tier lists 0..3, FP8 total and list
+    const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16, st->zb8, st->fp8};
     // per tier: queries evaluated since the timing began
     unsigned long long* tot[4] = {st->dq + 0, st->dq + 3, st->dq + 1, st->dq + 2};
+    unsigned long long* tot8 = st->dq + 10;
+    unsigned long long* cnt8 = st->dq + 9;
+    const int first = st->fp8 ? 4 : 0;
     if (!hint && !nlim) {
         k_route<<<blocks, kTierBlock, 0, s>>>(ra, n, route); note_launch();
-        if ((r = mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK) return r;
+        if ((r = first == 4 ? mlp_tc8_eval(st, Q, n, z, s, err) : mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK)
+            return r;
     } else {
-        // routing and the BF16 pass's list in one pass (no hint: every query
-        // starts at the BF16 pass)
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, -1, 0, 0.0f, ra, route, list, cnt + 0, tot[0]); note_launch();
-        QuerySrc L0{Q.pts, list, Q.g, cnt + 0};
+        // routing and the first pass's list in one pass (no hint: every query
+        // starts at the first pass)
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, -1, first, 0.0f, ra, route, list,
+                                                  first == 4 ? cnt8 : cnt + 0, first == 4 ? tot8 : tot[0]); note_launch();
+        QuerySrc L0{Q.pts, list, Q.g, first == 4 ? cnt8 : cnt + 0, Q.seg, Q.b0tab};
+        if ((r = first == 4 ? mlp_tc8_eval(st, L0, n, z, s, err) : mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK)
+            return r;
+    }
+    if (first == 4) {
+        // the BF16 pass re-takes the FP8 band and the queries routed to it
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, 4, 0, st->zb8, ra, route, list, cnt + 0,
+                                                  tot[0]); note_launch();
+        QuerySrc L0{Q.pts, list, Q.g, cnt + 0, Q.seg, Q.b0tab};
         if ((r = mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK) return r;
     }
     int from = 0;
@@ -639,7 +682,7 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
         if (!on) continue;
         k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, from, tier, thr, ra, route, list, cnt + tier,
                                                   tot[tier]); note_launch();
-        QuerySrc L{Q.pts, list, Q.g, cnt + tier};
+        QuerySrc L{Q.pts, list, Q.g, cnt + tier, Q.seg, Q.b0tab};
         r = tier == 1 ? mlp_tc16_eval(st, L, n, z, s, err)
             : tier == 2 ? mlp_tc3_eval(st, L, n, z, s, err)
                         : launch_fp32(st, L, n, z, s, err);
@@ -657,6 +700,7 @@ static odc_status eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, int
     if (precision == ODC_PREC_FP32) return launch_fp32(st, Q, n, z, s, err);
     if (precision == ODC_PREC_SPLIT) return mlp_tc3_eval(st, Q, n, z, s, err);
     if (precision == ODC_PREC_F16) return mlp_tc16_eval(st, Q, n, z, s, err);
+    if (precision == ODC_PREC_FP8_RAW) return mlp_tc8_eval(st, Q, n, z, s, err);
     return eval_tiered(st, Q, n, z, hint, s, err);
 }
 

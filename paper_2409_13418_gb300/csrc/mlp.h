@@ -72,6 +72,7 @@ void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_
 int64_t mlp_split_count(const MlpState* st);
 int64_t mlp_fp32_requery_count(const MlpState* st);
 int64_t mlp_h16_count(const MlpState* st);   // FP16-tier re-evaluations since the timing began
+int64_t mlp_fp8_count(const MlpState* st);   // FP8-pass evaluations from device-sized lists since the timing began
 
 // Labels (and logits) at explicit points.
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,

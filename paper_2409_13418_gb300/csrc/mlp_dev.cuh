@@ -61,16 +61,19 @@ struct MlpState {
     MlpTc* tc = nullptr;
     // per-launch CUDA events around the network kernels of one extract
     cudaEvent_t ev[2 * kMaxTimedLaunches] = {};
-    int ev_kind[kMaxTimedLaunches] = {};   // 0: FP32, 1: BF16 pass, 2: split-FP16 tier, 3: FP16 tier
+    int ev_kind[kMaxTimedLaunches] = {};   // 0: FP32, 1: BF16 pass, 2: split-FP16 tier, 3: FP16 tier, 4: FP8 pass
     int ev_used = 0;
-    double flops[4] = {0.0, 0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
-    int64_t launches[4] = {0, 0, 0, 0};
+    double flops[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // FLOPs of the network launches per kind (kind 2: tensor-pipe FLOPs)
+    int64_t launches[5] = {0, 0, 0, 0, 0};
     int split = 1;              // use the split-FP16 tier for band re-evaluation
     int h16 = 1;                // use the single-product FP16 tier between the BF16 pass and the split tier
+    int fp8 = 0;                // an FP8 pass ahead of the BF16 pass (source precision ODC_PREC_FP8)
+    float zb8 = 2.5f;           // |z - zt| below which an FP8-pass decision is re-taken by the BF16 pass
+                                // (2.1 times the largest FP8 logit error measured, 1.19)
     float zh16 = 0.025f;        // |z - zt| below which an FP16-tier decision is re-taken by the split tier
     int fp32_variant = -1;      // FP32 network tile shape picked by the autotuner (-1: not yet)
     int fp32_forced = -1;       // tile shape forced by the source's flags (-1: the autotuner's)
-    float zsplit = 4e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
+    float zsplit = 2.5e-5f;     // |z - zt| below which a split-tier decision is re-taken in FP32
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     unsigned long long wait_ns = 0;   // limit of the single-CTA tensor-core kernels' pipeline waits (0: 2 s)
@@ -80,8 +83,9 @@ struct MlpState {
     // device counters: [0..3] queries evaluated from device-sized lists by the
     // BF16, split-FP16, FP32 and FP16 networks since mlp_timing_begin; [4..7]
     // the list sizes of the current evaluation
+    // (FP8 pass: its list size in [9], its total in [10])
     unsigned long long* dq = nullptr;
-    unsigned long long hq[4] = {0, 0, 0, 0};   // host copy of dq[0..3] (mlp_timing_finish)
+    unsigned long long hq[5] = {0, 0, 0, 0, 0};   // host copy of dq[0..3] and dq[10] (mlp_timing_finish)
 };
 
 // Event pair around one network launch of the given kind (none once all are in use).
@@ -94,6 +98,8 @@ struct QuerySrc;
 odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 // Single-product FP16 network (FP16 activations, the split path's hi weights).
 odc_status mlp_tc16_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
+// FP8 pass (E4M3 activations and weights, FP32 accumulation).
+odc_status mlp_tc8_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 void mlp_tc_destroy(MlpState* st);
 size_t mlp_tc_device_bytes(const MlpState* st);
 // ODC_ERR_TIMEOUT if a tensor-core launch since the last check hit a bounded wait.
@@ -134,12 +140,23 @@ __device__ __forceinline__ float envelope_logit(float3 x, float f, float scale, 
 // With idx, query q of a launch is query idx[q] of the source and its logit
 // goes to z[idx[q]]; with cnt, the launch covers min(n, *cnt) queries (a
 // device-side list size, so the host needs no count).
+//
+// seg and b0tab (optional, both set or both null): query q's first-layer
+// bias is row seg[q] of b0tab ([rows][256]) instead of the network's b_0:
+// queries of latent-conditioned shapes of one network (the latent folds into
+// b_0) share one evaluation.
 struct QuerySrc {
     const float3* pts;       // list mode when non-null
     const int* idx;          // optional indices into the source (and the output)
     GridDev g;               // grid mode
     const unsigned long long* cnt;   // optional device-side query count
+    const uint16_t* seg;     // optional per-query row of b0tab (indexed like the output)
+    const float* b0tab;
 };
+// first-layer bias row of source query q (seg and b0tab set)
+__device__ __forceinline__ const float* query_b0(const QuerySrc& Q, int64_t qsrc) {
+    return Q.b0tab + (size_t)Q.seg[qsrc] * 256;
+}
 
 __device__ __forceinline__ int64_t query_count(const QuerySrc& Q, int64_t n) {
     return Q.cnt ? min(n, (int64_t)*Q.cnt) : n;

@@ -20,6 +20,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,6 +53,13 @@ constexpr int kChunks0 = 2 * kNF / kKC;     // layer 0: K = 128
 constexpr int kChunksH = kH / kKC;          // layers 1..3: K = 256
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 constexpr float kF16Safe = 30000.0f;      // FP16 activations kept well inside the FP16 range
+// FP8 pass (E4M3 operands, kind::f8f6f4): activations carried as fp8(h 2^4)
+// (the networks' hidden activations stay below ~7, so they sit at most near
+// 112 of E4M3's 448), weights as fp8(w 2^s8_l) with max |w| 2^s8_l below 256;
+// a scaled activation at or above kF8Safe poisons its row.
+constexpr float kF8ActScale = 16.0f;
+constexpr float kF8Safe = 400.0f;
+constexpr int kKC8 = 64;                    // K per FP8 weight slice (64 bytes a row: the same 16 KB slices)
 
 // ---------------------------------------------------------------- PTX
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -179,6 +187,8 @@ constexpr uint32_t kLayoutSW128 = 2, kLayoutSW64 = 4;
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
 constexpr uint32_t kIdescH = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+// kind::f8f6f4 with A and B E4M3 (format 0), D F32, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc8 = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 
 template <bool F16>
 __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
@@ -186,6 +196,13 @@ __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uin
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(a), "l"(b), "r"(F16 ? kIdescH : kIdesc), "r"(acc));
+}
+// one MMA of K = 32 E4M3 elements (32 bytes a row, as a K = 16 BF16 MMA)
+__device__ __forceinline__ void umma8(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(kIdesc8), "r"(acc));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
@@ -287,12 +304,26 @@ template <bool F16>
 __device__ __forceinline__ uint32_t pack16(float lo, float hi) {
     return F16 ? pack_f16(lo, hi) : pack_bf16(lo, hi);
 }
+// four floats (already scaled) as four E4M3 bytes, saturating to +-448
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
 
 // Byte offset of element (row r, k) in a K-major SWIZZLE_128B operand of K
 // extent 256: four 64-column chunks of 128 rows x 128 B; 16-byte unit u of
 // row r sits at unit u ^ (r % 8).
 __device__ __forceinline__ uint32_t a_offset(int r, int k) {
     int chunk = k >> 6, b = (k & 63) * 2;
+    int u = (b >> 4) ^ (r & 7);
+    return (uint32_t)(chunk * (kTileM * 128) + (r >> 3) * 1024 + (r & 7) * 128 + u * 16 + (b & 15));
+}
+
+// The same for one-byte (E4M3) elements: two 128-column chunks of 128 rows
+// x 128 B.
+__device__ __forceinline__ uint32_t a_offset8(int r, int k) {
+    int chunk = k >> 7, b = k & 127;
     int u = (b >> 4) ^ (r & 7);
     return (uint32_t)(chunk * (kTileM * 128) + (r >> 3) * 1024 + (r & 7) * 128 + u * 16 + (b & 15));
 }
@@ -310,14 +341,21 @@ struct TcParams {
     const volatile int* gate;     // single-CTA kernels: if set, no tensor-core work before *gate != 0
 };
 
-// F16 = false: the BF16 pass (BF16 weights and activations).  F16 = true: the
+// MODE 0: the BF16 pass (BF16 weights and activations).  MODE 1: the
 // single-product FP16 tier (FP16 activations and the split tier's hi weights
 // w 2^s_l, unscaled in the epilogue); an activation at or above kF16Safe
-// poisons its row, whose logit is then written as zt (the next tier takes it).
-template <bool F16>
+// poisons its row, whose logit is then written as zt (the next tier takes
+// it).  MODE 2: the FP8 pass (E4M3 activations fp8(h 2^4) and weights
+// fp8(w 2^s8_l), kind::f8f6f4, FP32 accumulation; the same slices, ring and
+// TMEM accumulators, twice the K per slice), rows poisoned at kF8Safe.
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_tc(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
              const __grid_constant__ CUtensorMap m2, const __grid_constant__ CUtensorMap m3, TcParams P) {
+    constexpr bool F16 = MODE == 1;
+    constexpr bool FP8 = MODE == 2;
+    constexpr int KC = FP8 ? kKC8 : kKC;                 // K per weight slice
+    constexpr int kMmaK = FP8 ? 32 : 16;                 // K per MMA (32 bytes a row either way)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* A = sm;                                   // kSub x 64 KB
@@ -377,11 +415,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 for (int l = 0; l < kNL && ok; ++l) {
                     const CUtensorMap* map = l == 0 ? &m0 : l == 1 ? &m1 : l == 2 ? &m2 : &m3;
-                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    const int nck = (l == 0 ? 2 * kNF : kH) / KC;
                     for (int c = 0; c < nck; ++c) {
                         if (!mbar_wait(&empty[stage], phase ^ 1, abort, wlim)) { ok = false; break; }
                         mbar_expect_tx(&full[stage], kSliceBytes);
-                        tma_load_2d(Bring + stage * kSliceBytes, map, c * kKC, 0, &full[stage]);
+                        tma_load_2d(Bring + stage * kSliceBytes, map, c * KC, 0, &full[stage]);
                         ++issued;
                         if (++stage == kStages) { stage = 0; phase ^= 1; }
                     }
@@ -416,18 +454,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!mbar_wait(act_ready, act_phase, abort, wlim)) { ok = false; break; }
                     act_phase ^= 1;
                     tc_fence_after();
-                    int nck = l == 0 ? kChunks0 : kChunksH;
+                    const int nck = (l == 0 ? 2 * kNF : kH) / KC;
                     for (int c = 0; c < nck; ++c) {
                         if (!mbar_wait(&full[stage], phase, abort, wlim)) { ok = false; break; }
                         tc_fence_after();
                         for (int s = 0; s < kSub; ++s) {
 #pragma unroll
-                            for (int kk = 0; kk < kKC / 16; ++kk) {
-                                int kg = c * kKC + kk * 16;
-                                uint32_t aaddr = a_base + s * kABytes + (kg >> 6) * (kTileM * 128) + (kg & 63) * 2;
-                                uint32_t baddr = b_base + stage * kSliceBytes + kk * 32;
-                                umma<F16>(tmem + s * kH, sdesc(aaddr, 1024, kLayoutSW128), sdesc(baddr, 512, kLayoutSW64),
-                                     (c | kk) != 0);
+                            for (int kk = 0; kk < KC / kMmaK; ++kk) {
+                                const int kg = c * KC + kk * kMmaK;
+                                const uint32_t aaddr = a_base + s * kABytes +
+                                                       (FP8 ? (kg >> 7) * (kTileM * 128) + (kg & 127)
+                                                            : (kg >> 6) * (kTileM * 128) + (kg & 63) * 2);
+                                const uint32_t baddr = b_base + stage * kSliceBytes + kk * 32;
+                                if constexpr (FP8)
+                                    umma8(tmem + s * kH, sdesc(aaddr, 1024, kLayoutSW128),
+                                          sdesc(baddr, 512, kLayoutSW64), (c | kk) != 0);
+                                else
+                                    umma<F16>(tmem + s * kH, sdesc(aaddr, 1024, kLayoutSW128),
+                                              sdesc(baddr, 512, kLayoutSW64), (c | kk) != 0);
                             }
                         }
                         umma_commit(&empty[stage]);
@@ -466,12 +510,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     s[i] = v.x;
                     cs[i] = v.y;
                 }
-                uint4 ps = make_uint4(pack16<F16>(s[0], s[1]), pack16<F16>(s[2], s[3]), pack16<F16>(s[4], s[5]),
-                                      pack16<F16>(s[6], s[7]));
-                uint4 pc = make_uint4(pack16<F16>(cs[0], cs[1]), pack16<F16>(cs[2], cs[3]),
-                                      pack16<F16>(cs[4], cs[5]), pack16<F16>(cs[6], cs[7]));
-                *reinterpret_cast<uint4*>(As + a_offset(r, j)) = ps;
-                *reinterpret_cast<uint4*>(As + a_offset(r, kNF + j)) = pc;
+                if constexpr (FP8) {
+                    const float a = kF8ActScale;
+                    *reinterpret_cast<uint2*>(As + a_offset8(r, j)) =
+                        make_uint2(pack_e4m3x4(a * s[0], a * s[1], a * s[2], a * s[3]),
+                                   pack_e4m3x4(a * s[4], a * s[5], a * s[6], a * s[7]));
+                    *reinterpret_cast<uint2*>(As + a_offset8(r, kNF + j)) =
+                        make_uint2(pack_e4m3x4(a * cs[0], a * cs[1], a * cs[2], a * cs[3]),
+                                   pack_e4m3x4(a * cs[4], a * cs[5], a * cs[6], a * cs[7]));
+                } else {
+                    uint4 ps = make_uint4(pack16<F16>(s[0], s[1]), pack16<F16>(s[2], s[3]), pack16<F16>(s[4], s[5]),
+                                          pack16<F16>(s[6], s[7]));
+                    uint4 pc = make_uint4(pack16<F16>(cs[0], cs[1]), pack16<F16>(cs[2], cs[3]),
+                                          pack16<F16>(cs[4], cs[5]), pack16<F16>(cs[6], cs[7]));
+                    *reinterpret_cast<uint4*>(As + a_offset(r, j)) = ps;
+                    *reinterpret_cast<uint4*>(As + a_offset(r, kNF + j)) = pc;
+                }
             }
             fence_async_smem();
             __syncwarp();
@@ -483,8 +537,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 acc_phase ^= 1;
                 tc_fence_after();
                 const float* bias = sp + l * kH;
-                // BF16: the weights are unscaled (fmaf(v, 1, b) == v + b); F16: 2^-s_l
-                const float unscale = F16 ? __ldg(P.wsc + l) : 1.0f;
+                // BF16: the weights are unscaled (fmaf(v, 1, b) == v + b); F16: 2^-s_l;
+                // FP8: 2^-(4 + s8_l) (activation and weight scales)
+                const float unscale = MODE != 0 ? __ldg(P.wsc + l) : 1.0f;
                 if (l < kNL - 1) {
                     float mx = 0.0f;
                     tmem_row_chunks_serial<kH / 32 / kHalves>(trow + c0, [&](int cb, const uint32_t (&v)[32]) {
@@ -498,19 +553,29 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 h[i] = fmaxf(fmaf(__uint_as_float(v[u * 8 + i]), unscale, bb[i]), 0.f);
-                                if (F16) mx = fmaxf(mx, h[i]);
+                                if (FP8) h[i] *= kF8ActScale;
+                                if (MODE != 0) mx = fmaxf(mx, h[i]);
                             }
-                            uint4 p = make_uint4(pack16<F16>(h[0], h[1]), pack16<F16>(h[2], h[3]),
-                                                 pack16<F16>(h[4], h[5]), pack16<F16>(h[6], h[7]));
-                            *reinterpret_cast<uint4*>(As + a_offset(r, col + u * 8)) = p;
+                            if constexpr (FP8) {
+                                *reinterpret_cast<uint2*>(As + a_offset8(r, col + u * 8)) =
+                                    make_uint2(pack_e4m3x4(h[0], h[1], h[2], h[3]), pack_e4m3x4(h[4], h[5], h[6], h[7]));
+                            } else {
+                                uint4 p = make_uint4(pack16<F16>(h[0], h[1]), pack16<F16>(h[2], h[3]),
+                                                     pack16<F16>(h[4], h[5]), pack16<F16>(h[6], h[7]));
+                                *reinterpret_cast<uint4*>(As + a_offset(r, col + u * 8)) = p;
+                            }
                         }
                     });
-                    if (F16) {
+                    if constexpr (F16) {
                         // a row that left the FP16 range gets an infinite input to
                         // the last layer: its accumulators turn non-finite
                         range_ok &= mx < kF16Safe;
                         if (l == kNL - 2 && !range_ok)
                             *reinterpret_cast<uint16_t*>(As + a_offset(r, c0)) = (uint16_t)0x7C00u;
+                    } else if constexpr (FP8) {
+                        // likewise with an E4M3 NaN (0x7F) as the last layer's input
+                        range_ok &= mx < kF8Safe;
+                        if (l == kNL - 2 && !range_ok) *(As + a_offset8(r, c0)) = (uint8_t)0x7Fu;
                     }
                     fence_async_smem();
                     tc_fence_before();
@@ -531,14 +596,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float bb[4] = {b.x, b.y, b.z, b.w}, ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
-                                if (F16) emax = max(emax, v[i + j] & 0x7F800000u);
+                                if (MODE != 0) emax = max(emax, v[i + j] & 0x7F800000u);
                                 f = fmaf(fmaxf(fmaf(__uint_as_float(v[i + j]), unscale, bb[j]), 0.f), ww[j], f);
                             }
                         }
                     });
                     tc_fence_before();
                     f += sp[5 * kH];
-                    const bool fin = !F16 || emax != 0x7F800000u;
+                    const bool fin = MODE == 0 || emax != 0x7F800000u;
                     if (valid)
                         P.z[query_index(P.Q, q)] = fin ? envelope_logit(x, f, P.scale, P.radius, P.amp) : P.zt;
                 } else {
@@ -885,7 +950,10 @@ struct MlpTc {
     CUtensorMap maps_h16[4];        // FP16 tier: the split path's hi weights, all 256 rows per box
     CUtensorMap maps_hi_mc[4];      // split path, 128 weight rows per box (each CTA of a pair)
     CUtensorMap maps_lo_mc[4];
-    float* wsc = nullptr;           // device [4]: split path weight unscale per layer
+    uint8_t* w8 = nullptr;          // FP8 pass: E4M3 W_l 2^s8_l [256][K_l]
+    CUtensorMap maps8[4];
+    float* wsc = nullptr;           // device: [0..3] split path weight unscale per layer, [4..7] ints (its
+                                    // exponents), [8..11] FP8 pass unscale 2^-(4 + s8_l), [12..15] ints (s8_l)
     int* err = nullptr;
     int sms = 0;
     int clusters3 = 0;              // co-resident CTA pairs of the split kernel
@@ -916,7 +984,8 @@ static EncodeTiledFn encode_fn(std::string* err) {
 // path a power-of-two scale per layer (the largest 2^s keeping |w| 2^s below
 // 2^14) with the FP16 hi and 2^11-scaled lo parts of w 2^s.
 namespace {
-__global__ void k_wprep_scale(const float* __restrict__ blob, float* __restrict__ wsc, int* __restrict__ sexp_out) {
+__global__ void k_wprep_scale(const float* __restrict__ blob, float* __restrict__ wsc, int* __restrict__ sexp_out,
+                              float* __restrict__ wsc8, int* __restrict__ s8_out) {
     const int l = blockIdx.x;
     const size_t K = l == 0 ? 2 * kNF : kH;
     const float* Wt = blob + kOffW_(l);
@@ -935,11 +1004,17 @@ __global__ void k_wprep_scale(const float* __restrict__ blob, float* __restrict_
         while (sexp < 24 && wmax * __int_as_float((127 + sexp + 1) << 23) < 16384.0f) ++sexp;
         wsc[l] = __int_as_float((127 - sexp) << 23);
         sexp_out[l] = sexp;
+        // FP8: the largest 2^s8 keeping |w| 2^s8 below 256 (E4M3 reaches 448)
+        int s8 = -8;
+        while (s8 < 24 && wmax * __int_as_float((127 + s8 + 1) << 23) < 256.0f) ++s8;
+        wsc8[l] = __int_as_float((127 - s8) << 23) / tc::kF8ActScale;
+        s8_out[l] = s8;
     }
 }
 
 __global__ void k_wprep_conv(const float* __restrict__ blob, const int* __restrict__ sexp_in, size_t total,
-                             __nv_bfloat16* __restrict__ wb, __half* __restrict__ w16) {
+                             __nv_bfloat16* __restrict__ wb, __half* __restrict__ w16, const int* __restrict__ s8_in,
+                             uint8_t* __restrict__ w8) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // tile element, layers in order
     if (i >= total) return;
     size_t off = 0;
@@ -957,6 +1032,7 @@ __global__ void k_wprep_conv(const float* __restrict__ blob, const int* __restri
     const __half hi = __float2half_rn(ws);
     w16[i] = hi;
     w16[total + i] = __float2half_rn((ws - __half2float(hi)) * tc::kLoScale);
+    w8[i] = (uint8_t)__nv_cvt_float_to_fp8(w * __int_as_float((127 + s8_in[l]) << 23), __NV_SATFINITE, __NV_E4M3);
 }
 }  // namespace
 
@@ -975,7 +1051,8 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     if (fresh) {
         if (cudaMalloc((void**)&T->w, total * sizeof(__nv_bfloat16)) != cudaSuccess ||
             cudaMalloc((void**)&T->w16, 2 * total * sizeof(__half)) != cudaSuccess ||
-            cudaMalloc((void**)&T->wsc, 4 * sizeof(float) + 4 * sizeof(int)) != cudaSuccess ||
+            cudaMalloc((void**)&T->w8, total) != cudaSuccess ||
+            cudaMalloc((void**)&T->wsc, 8 * sizeof(float) + 8 * sizeof(int)) != cudaSuccess ||
             cudaMalloc((void**)&T->err, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             *err = "tensor-core weight allocation failed";
@@ -983,9 +1060,10 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
         }
     }
     int* sexp = (int*)(T->wsc + 4);
-    k_wprep_scale<<<4, 256, 0, s>>>(st->wblob, T->wsc, sexp);
+    int* s8 = (int*)(T->wsc + 12);
+    k_wprep_scale<<<4, 256, 0, s>>>(st->wblob, T->wsc, sexp, T->wsc + 8, s8);
     note_launch();
-    k_wprep_conv<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(st->wblob, sexp, total, T->w, T->w16);
+    k_wprep_conv<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(st->wblob, sexp, total, T->w, T->w16, s8, T->w8);
     note_launch();
     if (cudaGetLastError() != cudaSuccess || cudaMemsetAsync(T->err, 0, sizeof(int), s) != cudaSuccess) {
         *err = "tensor-core weight preparation failed";
@@ -1015,6 +1093,13 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
             r = fn(&T->maps_lo_mc[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)(T->w16 + total + offs[l]), gdim,
                    gstride, box_mc, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS) {   // E4M3 weights: one byte per element, 64-element slices (the same 16 KB)
+            cuuint64_t gstride8[1] = {(cuuint64_t)K[l]};
+            cuuint32_t box8[2] = {(cuuint32_t)tc::kKC8, (cuuint32_t)kH};
+            r = fn(&T->maps8[l], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)(T->w8 + offs[l]), gdim, gstride8, box8, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
         if (r != CUDA_SUCCESS) {
             *err = "cuTensorMapEncodeTiled failed for layer " + std::to_string(l);
             return ODC_ERR_CUDA;
@@ -1023,9 +1108,11 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&T->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(tc::k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
+    if (cudaFuncSetAttribute(tc::k_mlp_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(tc::k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
+        cudaFuncSetAttribute(tc::k_mlp_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_mlp_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes) !=
             cudaSuccess ||
         cudaFuncSetAttribute(tc::k_mlp_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes3) !=
             cudaSuccess) {
@@ -1057,9 +1144,9 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     return ODC_OK;
 }
 
-// One launch of the single-product network: the BF16 pass (f16 = false,
-// timing kind 1) or the FP16 tier (f16 = true, timing kind 3).
-static odc_status tc_single_eval(MlpState* st, bool f16, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s,
+// One launch of the single-product network: the BF16 pass (mode 0, timing
+// kind 1), the FP16 tier (mode 1, kind 3) or the FP8 pass (mode 2, kind 4).
+static odc_status tc_single_eval(MlpState* st, int mode, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s,
                                  std::string* err) {
     if (n <= 0) return ODC_OK;
     MlpTc* T = st->tc;
@@ -1069,16 +1156,20 @@ static odc_status tc_single_eval(MlpState* st, bool f16, const QuerySrc& Q, int6
     }
     int64_t tiles = (n + tc::kRows - 1) / tc::kRows;
     int grid = (int)std::min<int64_t>(tiles, (int64_t)T->sms);
-    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, T->wsc, st->zt, st->wait_ns, st->gate};
-    const int kind = f16 ? 3 : 1;
+    const float* wsc = mode == 2 ? T->wsc + 8 : T->wsc;
+    tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, wsc, st->zt, st->wait_ns, st->gate};
+    const int kind = mode == 0 ? 1 : mode == 1 ? 3 : 4;
     cudaEvent_t* ev = mlp_ev_pair(st, kind);
     if (ev) cudaEventRecord(ev[0], s);
-    if (f16)
-        tc::k_mlp_tc<true><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps_h16[0], T->maps_h16[1],
-                                                                     T->maps_h16[2], T->maps_h16[3], P);
+    if (mode == 1)
+        tc::k_mlp_tc<1><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps_h16[0], T->maps_h16[1], T->maps_h16[2],
+                                                                  T->maps_h16[3], P);
+    else if (mode == 2)
+        tc::k_mlp_tc<2><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps8[0], T->maps8[1], T->maps8[2],
+                                                                  T->maps8[3], P);
     else
-        tc::k_mlp_tc<false><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2],
-                                                                      T->maps[3], P);
+        tc::k_mlp_tc<0><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(T->maps[0], T->maps[1], T->maps[2], T->maps[3],
+                                                                  P);
     note_launch();
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = cudaGetLastError();
@@ -1096,11 +1187,15 @@ static odc_status tc_single_eval(MlpState* st, bool f16, const QuerySrc& Q, int6
 }
 
 odc_status mlp_tc_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
-    return tc_single_eval(st, false, Q, n, z, s, err);
+    return tc_single_eval(st, 0, Q, n, z, s, err);
 }
 
 odc_status mlp_tc16_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
-    return tc_single_eval(st, true, Q, n, z, s, err);
+    return tc_single_eval(st, 1, Q, n, z, s, err);
+}
+
+odc_status mlp_tc8_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
+    return tc_single_eval(st, 2, Q, n, z, s, err);
 }
 
 odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
@@ -1164,13 +1259,15 @@ size_t mlp_tc_device_bytes(const MlpState* st) {
     const MlpTc* T = st ? st->tc : nullptr;
     if (!T || !T->w) return 0;
     const size_t total = (size_t)kH * (2 * kNF + 3 * kH);
-    return total * sizeof(__nv_bfloat16) + 2 * total * sizeof(__half) + sizeof(int) + 4 * (sizeof(float) + sizeof(int));
+    return total * sizeof(__nv_bfloat16) + 2 * total * sizeof(__half) + total + sizeof(int) +
+           8 * (sizeof(float) + sizeof(int));
 }
 
 void mlp_tc_destroy(MlpState* st) {
     if (!st || !st->tc) return;
     if (st->tc->w) cudaFree(st->tc->w);
     if (st->tc->w16) cudaFree(st->tc->w16);
+    if (st->tc->w8) cudaFree(st->tc->w8);
     if (st->tc->err) cudaFree(st->tc->err);
     if (st->tc->wsc) cudaFree(st->tc->wsc);
     delete st->tc;

@@ -20,7 +20,7 @@ ODC_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
           5: "unsupported", 6: "internal error"}
 SRC_CSG, SRC_MLP, SRC_RESIDENT, SRC_VOXEL = 0, 1, 2, 3
-PREC_FP32, PREC_BF16, PREC_SPLIT, PREC_F16 = 0, 1, 2, 3
+PREC_FP32, PREC_BF16, PREC_SPLIT, PREC_F16, PREC_FP8, PREC_FP8_RAW = 0, 1, 2, 3, 4, 5
 MLP_REUPLOAD, MLP_NO_F16_TIER = 1, 2
 DBG = dict(labels=0, edges=1, T=2, faces=3, slots=4, face_pts=5, face_flags=6, cells=7, configs=8,
            cycles=9, vlocal=10, qcase=11, flips=12, search=13)
@@ -72,7 +72,8 @@ class Stats(C.Structure):
                 ("split_flops", C.c_double), ("split_ms", C.c_float), ("pad2_", C.c_int32),
                 ("split_launches", C.c_int64), ("n_split", C.c_int64), ("fp32_tile", C.c_int64),
                 ("h16_flops", C.c_double), ("h16_ms", C.c_float), ("pad3_", C.c_int32),
-                ("h16_launches", C.c_int64), ("n_h16", C.c_int64)]
+                ("h16_launches", C.c_int64), ("n_h16", C.c_int64), ("fp8_flops", C.c_double),
+                ("fp8_ms", C.c_float), ("pad4_", C.c_int32), ("fp8_launches", C.c_int64)]
 
 
 class SlabC(C.Structure):
