@@ -243,10 +243,12 @@ def slab_scaling(odc, I, r: int = 1024, n_slabs: int = 8):
 def batch_bench(odc, I, n_shapes: int = 64, slots: int = 8, seed: int = 9):
     """The batched workload: n_shapes shapes with resolutions log-uniform in
     64^3..256^3, even ones seeded 64-primitive CSG trees (k = 12), odd ones
-    latent-conditioned envelope MLPs (128-d latent, BF16, k = 15), all
-    submitted at once to the request loop with ``slots`` slots; the rate is
-    the total cells over the wall time from the first submission to the last
-    completion (after one warm-up round of the same shapes)."""
+    latent-conditioned envelope MLPs of one network (128-d latent, BF16,
+    k = 15).  Two ways, each after one warm-up pass over the same shapes:
+    all shapes at once through odc_extract_many, one context per shape, the
+    MLP shapes' search-stage network evaluations merged into shared launches
+    (one batch group); and the request loop with ``slots`` slots, each shape
+    on its own launches.  The rate is the total cells over the wall time."""
     import numpy as np
     rng = np.random.default_rng(seed)
     res = np.round(np.exp(rng.uniform(np.log(64), np.log(256), n_shapes))).astype(int)
@@ -258,19 +260,39 @@ def batch_bench(odc, I, n_shapes: int = 64, slots: int = 8, seed: int = 9):
         else:
             jobs.append((I.with_latent(net, 2000 + i), I.cube_grid(int(r)), dict(steps_1d=15, precision=odc.PREC_BF16)))
     cells = float(np.sum(res.astype(np.float64) ** 3))
+    out = {"workload": f"{n_shapes} shapes, res log-uniform 64^3..256^3 (total {cells / 1e6:.0f} M cells), half "
+                       "64-primitive CSG trees (k=12), half latent-conditioned envelope MLPs of one network "
+                       "(BF16 tiers, k=15)"}
+    ctxs = [odc.Context(0) for _ in jobs]
+    try:
+        with odc.Batch(0) as b:
+            for _ in range(2):
+                b0 = b.stats()
+                t0 = time.perf_counter()
+                odc.extract_many(b, ctxs, jobs)
+                span = time.perf_counter() - t0
+            st = b.stats()
+            rounds, calls = st["rounds"] - b0["rounds"], st["calls"] - b0["calls"]
+            for c in ctxs:
+                c.join_batch(None)
+    finally:
+        for c in ctxs:
+            c.close()
+    out["shared_launches"] = {"contexts": n_shapes, "seconds": round(span, 3), "mcells_per_s": cells / span / 1e6,
+                              "shapes_per_s": n_shapes / span, "merged_rounds": rounds,
+                              "member_calls": calls, "mean_shapes_per_launch": calls / max(rounds, 1)}
     with odc.Server(0, slots=slots, host_copy=False) as srv:
         for _ in range(2):
             t0 = srv.clock()
             ids = [srv.submit(src, g, **kw) for src, g, kw in jobs]
-            out = [srv.poll(i) for i in ids]
+            res_ = [srv.poll(i) for i in ids]
             for i in ids:
                 srv.release(i)
-            span = max(o["t_end"] for o in out) - t0
-    assert all(o["status"] == 0 for o in out)
-    return {"workload": f"{n_shapes} shapes, res log-uniform 64^3..256^3 (total {cells / 1e6:.0f} M cells), half "
-                        "64-primitive CSG trees (k=12), half latent-conditioned envelope MLPs (BF16, k=15)",
-            "slots": slots, "seconds": round(span, 3), "mcells_per_s": cells / span / 1e6,
-            "shapes_per_s": n_shapes / span}
+            span = max(o["t_end"] for o in res_) - t0
+    assert all(o["status"] == 0 for o in res_)
+    out["request_loop"] = {"slots": slots, "seconds": round(span, 3), "mcells_per_s": cells / span / 1e6,
+                           "shapes_per_s": n_shapes / span}
+    return out
 
 
 def ablation_table(odc, I, res: int = 128, seed: int = 1):
@@ -304,11 +326,11 @@ def ablation_table(odc, I, res: int = 128, seed: int = 1):
     return {"workload": f"seeded 64-primitive CSG tree (seed {seed}), {res}^3 cells, k=12", "rows": rows}
 
 
-def serve_arm(odc, I, net, trace, slots, precision, budget):
+def serve_arm(odc, I, net, trace, slots, precision, budget, share=False):
     """Replays an arrival trace through the request loop: a submitter thread
     submits each request at its arrival time, the caller collects them.
     Returns latencies (s), per-request cells and the makespan."""
-    srv = odc.Server(0, slots=slots, mem_budget=budget, host_copy=False)
+    srv = odc.Server(0, slots=slots, mem_budget=budget, host_copy=False, share_network=share)
     try:
         # warm-up: every slot grows its arenas for the largest resolution once
         top = max(r for _, r, _ in trace)
@@ -353,10 +375,12 @@ def serve_bench(odc, I, seconds: float, slots: int, low_rate: float = 2.0, low_s
     queue growth) and at a sub-capacity ``low_rate`` for ``low_seconds``;
     cube resolutions {64, 128, 256, 512} with weights 0.4/0.3/0.2/0.1, each
     request a latent-conditioned envelope MLP (one network, a 128-d latent
-    per shape), 150 GB admission budget.  Three arms on the same traces: our
-    loop (``slots`` slots, FP8 pass + tiers), the same precision one request
-    at a time (1 slot: what the slots and overlap add), and plain
-    one-request-at-a-time GPU ODC (1 slot, FP32 plain network)."""
+    per shape), 150 GB admission budget.  Four arms on the same traces: our
+    loop (``slots`` slots, FP8 pass + tiers, the slots' search-stage network
+    evaluations merged into shared launches), the same without the sharing,
+    the same precision one request at a time (1 slot: what the slots and
+    overlap add), and plain one-request-at-a-time GPU ODC (1 slot, FP32 plain
+    network)."""
     import numpy as np
     net = I.envelope_mlp(11, latent_dim=128)
     budget = 150 * 10 ** 9
@@ -365,15 +389,17 @@ def serve_bench(odc, I, seconds: float, slots: int, low_rate: float = 2.0, low_s
                        f"for {low_seconds:g} s ({len(traces[f'rate_{low_rate:g}'])} requests), cube res "
                        "{64,128,256,512} w 0.4/0.3/0.2/0.1, latent-conditioned envelope MLP (128-d latent), "
                        f"k={STEPS_1D}, 150 GB budget; latency = completion - submission (server clock)"}
-    arms = (("ours", slots, odc.PREC_FP8, "fp8 pass + bf16/fp16/split/fp32 tiers"),
-            ("fifo_same_precision", 1, odc.PREC_FP8, "fp8 pass + bf16/fp16/split/fp32 tiers"),
-            ("plain_fifo_fp32", 1, odc.PREC_FP32, "fp32 plain"))
+    arms = (("ours", slots, odc.PREC_FP8, "fp8 pass + bf16/fp16/split/fp32 tiers", True),
+            ("ours_unshared", slots, odc.PREC_FP8, "fp8 pass + bf16/fp16/split/fp32 tiers", False),
+            ("fifo_same_precision", 1, odc.PREC_FP8, "fp8 pass + bf16/fp16/split/fp32 tiers", False),
+            ("plain_fifo_fp32", 1, odc.PREC_FP32, "fp32 plain", False))
     for tname, trace in traces.items():
         out[tname] = {}
-        for name, sl, prec, pname in arms:
-            lat, cells, span, bad = serve_arm(odc, I, net, trace, sl, prec, budget)
+        for name, sl, prec, pname, share in arms:
+            lat, cells, span, bad = serve_arm(odc, I, net, trace, sl, prec, budget, share)
             lat = np.asarray(lat)
-            out[tname][name] = {"slots": sl, "precision": pname, "requests": len(lat), "failed": int(bad),
+            out[tname][name] = {"slots": sl, "precision": pname, "shared_network_launches": share,
+                                "requests": len(lat), "failed": int(bad),
                                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                                 "mean_s": float(lat.mean()), "makespan_s": span,
                                 "throughput_req_s": len(lat) / span,

@@ -497,7 +497,8 @@ typedef struct {
     int32_t slots;               /* requests on the GPU at once, 1..64 */
     size_t mem_budget;           /* bytes over admitted requests and held results; 0 = no limit */
     int32_t host_copy;           /* nonzero: results also carry host copies of the mesh */
-    int32_t reserved;
+    int32_t share_network;       /* nonzero: the slots' contexts form one batch group, so requests in
+                                    their search stages at the same time share network launches */
 } odc_server_config;
 
 typedef struct {
@@ -529,6 +530,43 @@ odc_status odc_poll(odc_server* srv, uint64_t req_id, int32_t timeout_ms, odc_re
 odc_status odc_result_release(odc_server* srv, uint64_t req_id);
 /* Seconds on the server's monotonic clock (the time base of odc_result). */
 double odc_server_clock(const odc_server* srv);
+
+/* ---- Shared network evaluations (batch groups) ------------------------------
+ * The paper evaluates its network once per search step over all active
+ * edges or faces of one shape (Sec. 5.1, 5.2).  Contexts that join a batch
+ * group share those evaluations across shapes: inside a search stage each
+ * network evaluation waits until every context currently in a search stage
+ * of the group has made one, then all of their queries go through one
+ * merged evaluation (one set of tensor-core and FP32 launches) on the
+ * group's stream, and each context's stream waits for it.  Members must
+ * share one network (the same B, W and b; latents may differ: each shape's
+ * latent, folded into its first-layer bias, travels with its queries) and
+ * one precision; others evaluate on their own.  Every mesh is byte-identical
+ * to the one odc_extract gives without the group.  The grid pass is not
+ * shared (it is one large evaluation per shape already).  A group holds at
+ * most 64 members' bias rows.  Network statistics of members' extractions
+ * then cover their own launches only. */
+typedef struct odc_batch odc_batch;
+
+/* Create / destroy a group on a device.  Destroy after its members have left
+ * it (odc_ctx_join_batch(ctx, NULL)) or been destroyed. */
+odc_status odc_batch_create(int device, odc_batch** out);
+odc_status odc_batch_destroy(odc_batch* b);
+
+/* Join a context to group b (NULL: leave).  Binding happens at the
+ * context's next MLP source upload (odc_extract with an MLP source, or
+ * odc_source_upload). */
+odc_status odc_ctx_join_batch(odc_ctx* ctx, odc_batch* b);
+
+/* Merged evaluation rounds run by the group and the member calls they
+ * served (calls / rounds is the mean number of shapes per launch). */
+odc_status odc_batch_stats(const odc_batch* b, int64_t* rounds, int64_t* calls);
+
+/* Extract n shapes at once, one host thread per context (all distinct), the
+ * contexts joined to group b (NULL: no sharing).  outs[i] and statuses[i]
+ * are shape i's odc_extract result; returns the first failing status. */
+odc_status odc_extract_many(odc_batch* b, int32_t n, odc_ctx* const* ctxs, const odc_source* srcs,
+                            const odc_grid* grids, const odc_params* prms, odc_mesh* outs, odc_status* statuses);
 
 /* List the crossing edges of a label bitmask without allocating any memory.
  * The paper has no counterpart: this serves callers that cannot call

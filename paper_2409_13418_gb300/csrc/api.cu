@@ -14,7 +14,10 @@
 #include <string>
 #include <vector>
 
+#include <thread>
+
 #include "../../include/odc.h"
+#include "batch.h"
 #include "kernels.h"
 #include "mlp.h"
 #include "odc_internal.h"
@@ -62,6 +65,7 @@ struct odc_ctx {
     uint32_t* h_cnt = nullptr;  // pinned host counters
     unsigned long long wait_ns = 0;   // limit of the tensor-core kernels' pipeline waits (0: default)
     const int* gate = nullptr;        // device go signal of the tensor-core kernels (NULL: none)
+    BatchGroup* batch = nullptr;      // shared network evaluations (odc_ctx_join_batch)
     cudaEvent_t ev[9] = {};
     MlpState* mlp = nullptr;
     // resident source
@@ -364,6 +368,10 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
     }
     const int kind = c->res_kind;
     mlp_set_wait_limit(c->mlp, c->wait_ns, c->gate);
+    if (c->mlp) {
+        s = batch_bind(c->mlp, c->batch, src->kind == ODC_SRC_MLP ? src->mlp : nullptr, &g_err);
+        if (s != ODC_OK) return s;
+    }
     if ((prm->flags & (ODC_ABL_LINEAR_1D | ODC_ABL_GRADIENT_NORMALS)) && kind != ODC_SRC_CSG)
         return fail(ODC_ERR_UNSUPPORTED, "ablation variants need an implicit with a gradient: CSG sources only");
     const bool linear_1d = (prm->flags & ODC_ABL_LINEAR_1D) != 0;
@@ -998,6 +1006,78 @@ odc_status odc_ctx_set_wait_limit(odc_ctx* c, uint64_t ns, const int32_t* d_gate
     c->wait_ns = ns;
     c->gate = d_gate;
     mlp_set_wait_limit(c->mlp, ns, d_gate);
+    return ODC_OK;
+}
+
+}  // extern "C"
+
+struct odc_batch {
+    BatchGroup* g = nullptr;
+    int device = 0;
+};
+
+extern "C" {
+
+odc_status odc_batch_create(int device, odc_batch** out) {
+    if (!out) return fail(ODC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    ODC_CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(ODC_ERR_INVALID_ARG, "no such CUDA device");
+    auto* b = new odc_batch();
+    b->device = device;
+    odc_status s = batch_create(device, &b->g, &g_err);
+    if (s != ODC_OK) {
+        delete b;
+        return s;
+    }
+    *out = b;
+    return ODC_OK;
+}
+
+odc_status odc_batch_destroy(odc_batch* b) {
+    if (!b) return ODC_OK;
+    batch_destroy(b->g);
+    delete b;
+    return ODC_OK;
+}
+
+odc_status odc_batch_stats(const odc_batch* b, int64_t* rounds, int64_t* calls) {
+    if (!b || !rounds || !calls) return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    batch_stats(b->g, rounds, calls);
+    return ODC_OK;
+}
+
+odc_status odc_ctx_join_batch(odc_ctx* c, odc_batch* b) {
+    if (!c) return fail(ODC_ERR_INVALID_ARG, "NULL context");
+    if (b && b->device != c->device) return fail(ODC_ERR_INVALID_ARG, "batch and context are on different devices");
+    c->batch = b ? b->g : nullptr;
+    if (!c->batch) batch_unbind(c->mlp);   // a source uploaded later binds at its upload
+    return ODC_OK;
+}
+
+odc_status odc_extract_many(odc_batch* b, int32_t n, odc_ctx* const* ctxs, const odc_source* srcs,
+                            const odc_grid* grids, const odc_params* prms, odc_mesh* outs, odc_status* statuses) {
+    if (n < 0 || (n > 0 && (!ctxs || !srcs || !grids || !prms || !outs || !statuses)))
+        return fail(ODC_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(ODC_ERR_INVALID_ARG, "NULL context");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(ODC_ERR_INVALID_ARG, "a context appears twice");
+        odc_status s = odc_ctx_join_batch(ctxs[i], b);
+        if (s != ODC_OK) return s;
+    }
+    std::vector<std::string> errs(n);
+    std::vector<std::thread> th;
+    th.reserve(n);
+    for (int i = 0; i < n; ++i)
+        th.emplace_back([&, i] {
+            statuses[i] = odc_extract(ctxs[i], &srcs[i], &grids[i], &prms[i], nullptr, &outs[i]);
+            if (statuses[i] != ODC_OK) errs[i] = odc_last_error();
+        });
+    for (auto& t : th) t.join();
+    for (int i = 0; i < n; ++i)
+        if (statuses[i] != ODC_OK) return fail(statuses[i], "shape " + std::to_string(i) + ": " + errs[i]);
     return ODC_OK;
 }
 

@@ -14,6 +14,7 @@
 #include <mutex>
 #include <vector>
 
+#include "batch.h"
 #include "mlp.h"
 #include "mlp_dev.cuh"
 #include "odc_device.cuh"
@@ -135,6 +136,8 @@ void mlp_timing_collect(MlpState* st, int kind, float* ms, double* flops, int64_
 
 void mlp_destroy(MlpState* st) {
     if (!st) return;
+    batch_unbind(st);
+    if (st->bev) cudaEventDestroy(st->bev);
     for (auto& e : st->ev)
         if (e) cudaEventDestroy(e);
     if (st->wblob) cudaFree(st->wblob);
@@ -216,6 +219,8 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
         }
         MLP_CK(cudaMemcpyAsync(st->wblob + kOffb[0], b0.data(), sizeof(float) * kH, cudaMemcpyHostToDevice, s));
         MLP_CK(cudaStreamSynchronize(s));   // b0 is a host temporary
+        st->b0host = b0;
+        st->b0dirty = true;
         return ODC_OK;
     }
     st->wkey.clear();   // set again once the upload below has succeeded
@@ -240,6 +245,8 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
             for (int n = 0; n < kH; ++n) h[kOffW[l] + (size_t)k * kH + n] = W[(size_t)n * kH + k];
         std::memcpy(&h[kOffb[l]], m->b[l], sizeof(float) * kH);
     }
+    st->b0host.assign(h.begin() + kOffb[0], h.begin() + kOffb[0] + kH);
+    st->b0dirty = true;
     std::memcpy(&h[kOffW[kNL]], m->W[kNL], sizeof(float) * kH);
     h[kOffb[kNL]] = m->b[kNL][0];
     if (!st->wblob) MLP_CK(cudaMalloc((void**)&st->wblob, sizeof(float) * kBlobFloats));
@@ -708,6 +715,7 @@ odc_status mlp_eval_list(MlpState* st, const float3* pts, int64_t n, float* z, i
                          std::string* err, const float* hint) {
     QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
     st->stream = s;
+    if (precision < 0 && batch_active(st)) return batch_eval(st, pts, n, nullptr, z, hint, s, err);
     return eval(st, Q, n, z, precision, hint, s, err);
 }
 
@@ -721,6 +729,7 @@ odc_status mlp_eval_list_dev(MlpState* st, const float3* pts, int64_t n_max, con
     QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
     st->stream = s;
     if (n_max <= 0) return ODC_OK;
+    if (batch_active(st)) return batch_eval(st, pts, n_max, n_dev, z, hint, s, err);
     if (st->precision != ODC_PREC_BF16) {
         QuerySrc L{pts, nullptr, GridDev{}, n_dev};
         odc_status r = launch_fp32(st, L, n_max, z, s, err);
@@ -728,6 +737,22 @@ odc_status mlp_eval_list_dev(MlpState* st, const float3* pts, int64_t n_max, con
         k_count_add<<<1, 32, 0, s>>>(n_dev, n_max, st->dq + 2); note_launch();
         return ODC_OK;
     }
+    return eval_tiered(st, Q, n_max, z, hint, s, err, n_dev);
+}
+
+odc_status mlp_eval_merged(MlpState* st, const float3* pts, const float* hint, const uint16_t* seg,
+                           const float* b0tab, int64_t n_max, const unsigned long long* n_dev, float* z,
+                           cudaStream_t s, std::string* err) {
+    st->stream = s;
+    if (n_max <= 0) return ODC_OK;
+    if (st->precision != ODC_PREC_BF16) {
+        QuerySrc L{pts, nullptr, GridDev{}, n_dev, seg, b0tab};
+        odc_status r = launch_fp32(st, L, n_max, z, s, err);
+        if (r != ODC_OK) return r;
+        k_count_add<<<1, 32, 0, s>>>(n_dev, n_max, st->dq + 2); note_launch();
+        return ODC_OK;
+    }
+    QuerySrc Q{pts, nullptr, GridDev{}, nullptr, seg, b0tab};
     return eval_tiered(st, Q, n_max, z, hint, s, err, n_dev);
 }
 

@@ -74,6 +74,13 @@ int64_t mlp_fp32_requery_count(const MlpState* st);
 int64_t mlp_h16_count(const MlpState* st);   // FP16-tier re-evaluations since the timing began
 int64_t mlp_fp8_count(const MlpState* st);   // FP8-pass evaluations from device-sized lists since the timing began
 
+// One evaluation of a merged query list (shared evaluations, batch.cu):
+// n_dev (device) of at most n_max queries at pts with routing hints, query q
+// taking row seg[q] of b0tab as its first-layer bias.
+odc_status mlp_eval_merged(MlpState* st, const float3* pts, const float* hint, const uint16_t* seg,
+                           const float* b0tab, int64_t n_max, const unsigned long long* n_dev, float* z,
+                           cudaStream_t s, std::string* err);
+
 // Labels (and logits) at explicit points.
 odc_status mlp_points(MlpState* st, const float3* pts, int64_t n, float iso, int precision, uint8_t* labels,
                       float* logits, cudaStream_t s, std::string* err);

@@ -47,6 +47,7 @@ constexpr OffW kOffW{};
 constexpr Offb kOffb{};
 
 struct MlpTc;   // tensor-core path state (mlp_tc.cu)
+struct BatchGroup;   // shared evaluations (batch.cu)
 constexpr int kMaxTimedLaunches = 512;
 
 struct MlpState {
@@ -78,6 +79,15 @@ struct MlpState {
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     unsigned long long wait_ns = 0;   // limit of the single-CTA tensor-core kernels' pipeline waits (0: 2 s)
     const int* gate = nullptr;        // device go signal of those kernels (NULL: none)
+    // batch group membership (batch.h): search-stage evaluations shared with
+    // the group's other members when bcompat
+    BatchGroup* group = nullptr;
+    bool bcompat = false;
+    bool bin_stage = false;           // inside a search stage (counted active by the group)
+    int brow = -1;                    // the member's row of the group's first-layer bias table
+    std::vector<float> b0host;        // the folded first-layer bias of the source last uploaded
+    bool b0dirty = false;             // b0host not yet in the group's table
+    cudaEvent_t bev = nullptr;        // the member's queries are ready (recorded per shared call)
     int sms = 0;                // SM count of the device
     cudaStream_t stream = nullptr;   // stream of the current call (scratch growth is ordered on it)
     // device counters: [0..3] queries evaluated from device-sized lists by the
@@ -104,6 +114,8 @@ void mlp_tc_destroy(MlpState* st);
 size_t mlp_tc_device_bytes(const MlpState* st);
 // ODC_ERR_TIMEOUT if a tensor-core launch since the last check hit a bounded wait.
 odc_status mlp_tc_check(MlpState* st, cudaStream_t s, std::string* err);
+// Device error flag of the tensor-core kernels (NULL before their preparation).
+int* mlp_tc_err_flag(MlpState* st);
 // Split-BF16 network (three BF16 products per layer, FP32 accumulation).
 odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 

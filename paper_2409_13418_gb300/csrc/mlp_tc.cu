@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 acc_phase ^= 1;
                 tc_fence_after();
-                const float* bias = sp + l * kH;
+                // first-layer bias: the query's own row when queries carry one
+                const float* bias = (l == 0 && P.Q.b0tab && valid) ? query_b0(P.Q, query_index(P.Q, q)) : sp + l * kH;
                 // BF16: the weights are unscaled (fmaf(v, 1, b) == v + b); F16: 2^-s_l;
                 // FP8: 2^-(4 + s8_l) (activation and weight scales)
                 const float unscale = MODE != 0 ? __ldg(P.wsc + l) : 1.0f;
@@ -860,7 +861,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 acc_phase ^= 1;
                 tc_fence_after();
-                const float* bias = sp + l * kH;
+                const float* bias = (l == 0 && P.Q.b0tab && valid) ? query_b0(P.Q, query_index(P.Q, q)) : sp + l * kH;
                 const float unscale = __ldg(P.wsc + l);
                 if (l < kNL - 1) {
                     // an activation at or above kF16Safe marks the row (poisoned
@@ -1238,6 +1239,8 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
     st->launches[2] += 1;
     return ODC_OK;
 }
+
+int* mlp_tc_err_flag(MlpState* st) { return st && st->tc ? st->tc->err : nullptr; }
 
 odc_status mlp_tc_check(MlpState* st, cudaStream_t s, std::string* err) {
     if (!st || !st->tc || !st->tc->err) return ODC_OK;

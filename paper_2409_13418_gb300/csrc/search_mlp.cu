@@ -7,6 +7,7 @@
 // on the device between steps.
 #include <algorithm>
 
+#include "batch.h"
 #include "kernels.h"
 #include "mlp.h"
 #include "mlp_dev.cuh"
@@ -135,8 +136,8 @@ __global__ void k_bis_upd(GridDev g, const uint32_t* __restrict__ bits, const ui
     }
 }
 
-odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
-                      float iso, uint32_t* T, cudaStream_t s, int64_t* nq, std::string* err) {
+static odc_status bisect_body(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne,
+                              int k, float iso, uint32_t* T, cudaStream_t s, int64_t* nq, std::string* err) {
     if (!ne) return ODC_OK;
     st->stream = s;
     void *plo, *ppts, *pz;
@@ -438,10 +439,10 @@ __global__ void k_face_fin2(const uint32_t* __restrict__ list, uint32_t na, Sear
     flags[i] = (uint8_t)fl;
 }
 
-odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
-                     const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
-                     uint32_t nf, const SearchParams& sp, float iso, float4* pf, uint8_t* flags, FaceDecisions* dec,
-                     cudaStream_t s, int64_t* nq, std::string* err) {
+static odc_status faces_body(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips,
+                             const WordInfo* wi, const uint32_t* ebase, const uint32_t* T, const uint32_t* faces,
+                             const uint8_t* slots, uint32_t nf, const SearchParams& sp, float iso, float4* pf,
+                             uint8_t* flags, FaceDecisions* dec, cudaStream_t s, int64_t* nq, std::string* err) {
     if (!nf) return ODC_OK;
     st->stream = s;
     const float t = mlp_logit_threshold(iso);
@@ -540,6 +541,31 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
     for (int j = 1; j < sp.lin2; ++j) lin2_q += (int64_t)hc[kMaxLin + j];
     *nq += (int64_t)na * 2 * sp.bin2 + lin2_q;
     return mlp_tc_check(st, s, err);
+}
+
+// A search stage is one bracket of a batch group's membership: inside it
+// the network evaluations are shared with the group's other members.
+odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
+                      float iso, uint32_t* T, cudaStream_t s, int64_t* nq, std::string* err) {
+    batch_enter(st);
+    const odc_status r = bisect_body(st, g, bits, edges, ne, k, iso, T, s, nq, err);
+    std::string e2;
+    const odc_status r2 = batch_leave(st, &e2);
+    if (r == ODC_OK && r2 != ODC_OK) *err = e2;
+    return r != ODC_OK ? r : r2;
+}
+
+odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* flips, const WordInfo* wi,
+                     const uint32_t* ebase, const uint32_t* T, const uint32_t* faces, const uint8_t* slots,
+                     uint32_t nf, const SearchParams& sp, float iso, float4* pf, uint8_t* flags, FaceDecisions* dec,
+                     cudaStream_t s, int64_t* nq, std::string* err) {
+    batch_enter(st);
+    const odc_status r = faces_body(st, g, bits, flips, wi, ebase, T, faces, slots, nf, sp, iso, pf, flags, dec, s, nq,
+                                    err);
+    std::string e2;
+    const odc_status r2 = batch_leave(st, &e2);
+    if (r == ODC_OK && r2 != ODC_OK) *err = e2;
+    return r != ODC_OK ? r : r2;
 }
 
 }  // namespace odc

@@ -133,6 +133,7 @@ struct odc_server {
     Clock::time_point t0;
     std::vector<odc_ctx*> ctx;
     std::vector<cudaStream_t> streams;
+    odc_batch* batch = nullptr;  // shared network evaluations of the slots (share_network)
     cudaStream_t free_stream = nullptr;
     std::vector<std::thread> workers;
     std::mutex mu;
@@ -252,6 +253,15 @@ odc_status odc_server_create(const odc_server_config* cfg, odc_server** out) {
             return srv_fail(s, "server slot setup: " + msg);
         }
     }
+    if (cfg->share_network) {
+        odc_status s = odc_batch_create(cfg->device, &srv->batch);
+        for (int i = 0; s == ODC_OK && i < cfg->slots; ++i) s = odc_ctx_join_batch(srv->ctx[i], srv->batch);
+        if (s != ODC_OK) {
+            std::string msg = odc_last_error();
+            odc_server_destroy(srv);
+            return srv_fail(s, "server batch group setup: " + msg);
+        }
+    }
     if (cudaStreamCreateWithFlags(&srv->free_stream, cudaStreamNonBlocking) != cudaSuccess) {
         odc_server_destroy(srv);
         return srv_fail(ODC_ERR_CUDA, "server stream setup failed");
@@ -277,6 +287,7 @@ odc_status odc_server_destroy(odc_server* srv) {
         cudaStreamDestroy(srv->free_stream);
     }
     for (auto* c : srv->ctx) odc_ctx_destroy(c);
+    odc_batch_destroy(srv->batch);   // after its members
     for (auto st : srv->streams) cudaStreamDestroy(st);
     delete srv;
     return ODC_OK;

@@ -130,7 +130,7 @@ Q_OCC, Q_MANIFOLD, Q_SI = 1, 2, 4
 
 class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("mem_budget", C.c_size_t), ("host_copy", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("share_network", C.c_int32)]
 
 
 class ResultC(C.Structure):
@@ -148,7 +148,8 @@ EXPORTS = ["odc_ctx_create", "odc_ctx_destroy", "odc_extract", "odc_mesh_copy", 
            "odc_debug_copy", "odc_eval_points", "odc_source_upload", "odc_launch_count", "odc_compact_edges_noalloc", "odc_status_str",
            "odc_last_error", "odc_server_create", "odc_server_destroy", "odc_submit", "odc_poll", "odc_result_release",
            "odc_server_clock", "odc_mesh_quality", "odc_extract_slab", "odc_slab_place", "odc_extract_slabbed",
-           "odc_ctx_memory", "odc_grid_labels", "odc_manifold_flips", "odc_ctx_set_wait_limit"]
+           "odc_ctx_memory", "odc_grid_labels", "odc_manifold_flips", "odc_ctx_set_wait_limit", "odc_batch_create",
+           "odc_batch_destroy", "odc_batch_stats", "odc_ctx_join_batch", "odc_extract_many"]
 
 _lib = None
 
@@ -168,6 +169,13 @@ def load(path: str = LIB_PATH):
     lib.odc_mesh_copy.argtypes = [P, C.POINTER(MeshC), P, P, C.c_int]
     lib.odc_ctx_memory.argtypes = [P, C.POINTER(C.c_size_t)]
     lib.odc_ctx_set_wait_limit.argtypes = [P, C.c_uint64, P]
+    lib.odc_batch_create.argtypes = [C.c_int, C.POINTER(P)]
+    lib.odc_batch_destroy.argtypes = [P]
+    lib.odc_batch_stats.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.odc_ctx_join_batch.argtypes = [P, P]
+    lib.odc_extract_many.argtypes = [P, C.c_int32, P, P, P, P, P, P]
+    for f in ["odc_batch_create", "odc_batch_destroy", "odc_batch_stats", "odc_ctx_join_batch", "odc_extract_many"]:
+        getattr(lib, f).restype = C.c_int
     lib.odc_ctx_set_wait_limit.restype = C.c_int
     lib.odc_grid_labels.argtypes = [P, C.POINTER(Source), C.POINTER(Grid), C.POINTER(Params), C.c_int32, C.c_int32, P,
                                     P]
@@ -400,6 +408,11 @@ class Context:
                                 stream if stream else None, C.byref(m)))
         return Mesh(self, m)
 
+    def join_batch(self, batch) -> None:
+        """odc_ctx_join_batch: share search-stage network evaluations with the
+        group's other members (None: leave)."""
+        _check(_lib.odc_ctx_join_batch(self.h, batch.h if batch is not None else None))
+
     def set_wait_limit(self, ns: int, gate: int | None = None) -> None:
         """odc_ctx_set_wait_limit: limit of the tensor-core kernels' pipeline
         waits in ns (0: the default) and an optional device go flag (address
@@ -505,14 +518,63 @@ class Context:
         return lab.astype(bool), z
 
 
+class Batch:
+    """A batch group (``odc_batch``): contexts that join it share the network
+    evaluations of their search stages."""
+
+    def __init__(self, device: int = 0):
+        load()
+        h = C.c_void_p()
+        _check(_lib.odc_batch_create(device, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.odc_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stats(self) -> dict:
+        r, c = C.c_int64(), C.c_int64()
+        _check(_lib.odc_batch_stats(self.h, C.byref(r), C.byref(c)))
+        return {"rounds": int(r.value), "calls": int(c.value)}
+
+
+def extract_many(batch, ctxs, jobs) -> list:
+    """odc_extract_many: jobs[i] = (src, grid, kwargs) on ctxs[i] (distinct
+    contexts), one host thread per shape, all joined to ``batch`` (None: no
+    sharing).  Returns the meshes (each valid until its context's next
+    extract)."""
+    n = len(jobs)
+    holders = [_SourceHolder(src, kw.get("precision"), kw.get("band"), kw.get("split", True), kw.get("split_zmargin", 0.0),
+                             kw.get("reupload", False), h16=kw.get("h16", True)) for src, _, kw in jobs]
+    srcs = (Source * n)(*[h.src for h in holders])
+    grids = (Grid * n)(*[make_grid(g) for _, g, _ in jobs])
+    skip = {"precision", "band", "split", "split_zmargin", "reupload", "h16"}
+    prms = (Params * n)(*[make_params(**{k: v for k, v in kw.items() if k not in skip}) for _, _, kw in jobs])
+    outs = (MeshC * n)()
+    sts = (C.c_int * n)()
+    hs = (C.c_void_p * n)(*[c.h.value for c in ctxs])
+    r = _lib.odc_extract_many(batch.h if batch is not None else None, n, hs, srcs, grids, prms, outs, sts)
+    _check(r)
+    return [Mesh(c, outs[i]) for i, c in enumerate(ctxs)]
+
+
 class Server:
     """The library's request loop (``odc_server``): requests of any grid size
     are admitted as slots and memory free up and run concurrently on the GPU."""
 
-    def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0, host_copy: bool = True):
+    def __init__(self, device: int = 0, slots: int = 4, mem_budget: int = 0, host_copy: bool = True,
+                 share_network: bool = False):
         load()
         cfg = ServerConfig()
         cfg.device, cfg.slots, cfg.mem_budget, cfg.host_copy = device, slots, mem_budget, int(bool(host_copy))
+        cfg.share_network = int(bool(share_network))
         h = C.c_void_p()
         _check(_lib.odc_server_create(C.byref(cfg), C.byref(h)))
         self.h = h
