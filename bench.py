@@ -452,6 +452,9 @@ def main():
                     help="profile run: only the CSG pipeline at this resolution (prints its own JSON line)")
     ap.add_argument("--fp32-points", type=int, default=0,
                     help="profile run: only the FP32 network over this many seeded points (list mode, 3 launches)")
+    ap.add_argument("--net-points", type=int, default=0,
+                    help="profile run: only one network tier (--net-tier) over this many seeded points, 3 launches")
+    ap.add_argument("--net-tier", choices=["fp32", "bf16", "f16", "split", "fp8"], default="fp8")
     ap.add_argument("--slab-res", type=int, default=0,
                     help="only the envelope MLP at this resolution in --slab-count z-slabs (prints its own JSON line)")
     ap.add_argument("--slab-count", type=int, default=8)
@@ -480,6 +483,21 @@ def main():
                 ctx.eval_points(mlp, pts, precision=odc.PREC_FP32)
         print(json.dumps({"workload": f"FP32 network over {args.fp32_points} seeded points (list mode)",
                           "launches": 3}), flush=True)
+        return
+    if args.net_points:
+        import numpy as np
+        from paper_2409_13418_gb300 import build, inputs as I, odc
+        build.build()
+        odc.load()
+        prec = {"fp32": odc.PREC_FP32, "bf16": odc.PREC_BF16, "f16": odc.PREC_F16, "split": odc.PREC_SPLIT,
+                "fp8": odc.PREC_FP8_RAW}[args.net_tier]
+        pts = np.random.default_rng(1).uniform(-1, 1, (args.net_points, 3)).astype(np.float32)
+        with odc.Context(0) as ctx:
+            mlp = I.envelope_mlp(0)
+            for _ in range(3):   # bf16 without a band: the raw BF16 pass alone
+                ctx.eval_points(mlp, pts, precision=prec, band=0.0)
+        print(json.dumps({"workload": f"{args.net_tier} network tier over {args.net_points} seeded points "
+                                      f"(list mode)", "launches": 3}), flush=True)
         return
     if args.slab_res:
         from paper_2409_13418_gb300 import build, inputs as I, odc

@@ -508,8 +508,10 @@ class Context:
 
     def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None, split=True,
                     fp32_tile=None):
-        holder = _SourceHolder(src, None if precision < 0 else min(precision, PREC_BF16), band, split,
-                               fp32_tile=fp32_tile)
+        # the source's precision: FP32, BF16 or FP8 tiers; the single-network
+        # overrides (split, FP16, raw FP8) run on a BF16 source's state
+        sp = None if precision < 0 else (precision if precision in (PREC_FP32, PREC_BF16, PREC_FP8) else PREC_BF16)
+        holder = _SourceHolder(src, sp, band, split, fp32_tile=fp32_tile)
         pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
         lab = np.empty(pts.shape[0], np.uint8)
         z = np.empty(pts.shape[0], np.float32)
