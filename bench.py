@@ -130,46 +130,93 @@ def cpu_model() -> str:
     return platform.machine()
 
 
-def cpu_sample(mlp, n_cells: int = 40):
-    """Oracle on an n^3-cell block of the same 256^3 grid crossing the surface shell."""
-    import numpy as np
+def _shell_directions(k: int):
+    """k unit directions spread over the sphere (a Fibonacci lattice)."""
+    import math
+    out = []
+    for i in range(k):
+        zc = 1.0 - 2.0 * (i + 0.5) / k
+        r = math.sqrt(max(0.0, 1.0 - zc * zc))
+        phi = i * math.pi * (3.0 - math.sqrt(5.0))
+        out.append((r * math.cos(phi), r * math.sin(phi), zc))
+    return out
 
+
+def cpu_sample(mlp, n_cells: int = 40, where: int = -1, n_where: int = 16):
+    """Oracle on an n^3-cell block of the same 256^3 grid crossing the surface
+    shell: at x ~ 0.31..0.62 on the x axis (where < 0), else centred on the
+    shell (radius 0.47) in direction ``where`` of ``n_where``."""
     from oracle import odc as oracle
     from paper_2409_13418_gb300 import inputs as I
     h = 2.0 / RES
-    i0 = (RES // 2 + 40, RES // 2 - n_cells // 2, RES // 2 - n_cells // 2)   # x in [0.31, 0.31 + n h]
+    if where < 0:
+        i0 = (RES // 2 + 40, RES // 2 - n_cells // 2, RES // 2 - n_cells // 2)   # x in [0.31, 0.31 + n h]
+    else:
+        d = _shell_directions(n_where)[where]
+        i0 = tuple(int(round((0.47 * d[a] + 1.0) / h)) - n_cells // 2 for a in range(3))
     lo = tuple(-1.0 + i0[a] * h for a in range(3))
     hi = tuple(lo[a] + n_cells * h for a in range(3))
     g = I.Grid(lo, hi, (n_cells, n_cells, n_cells))
     t = time.perf_counter()
     r = oracle.extract(mlp, g, steps_1d=STEPS_1D)
     dt = time.perf_counter() - t
-    del np
     return n_cells ** 3, dt, r.stats
 
 
+def _oracle_block(job):
+    """Process-pool worker: one oracle block (single-threaded numpy)."""
+    n_cells, where, n_where = job
+    mlp, _ = workload(0)
+    return cpu_sample(mlp, n_cells, where, n_where)[:2]
+
+
+def oracle_all_cores(n_cells: int, n_blocks: int, workers: int):
+    """The oracle as it stands on every host core: n_blocks blocks of n_cells^3
+    on the surface shell, one per process of a spawned pool (numpy's BLAS
+    single-threaded in each).  Returns (cells, wall seconds, processes)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    keep = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in keep:
+        os.environ[k] = "1"
+    try:
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_oracle_block, [(8, i, workers) for i in range(workers)]))   # interpreters up, imports done
+            t = time.perf_counter()
+            res = list(ex.map(_oracle_block, [(n_cells, i % n_blocks, n_blocks) for i in range(n_blocks)]))
+            wall = time.perf_counter() - t
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return sum(c for c, _ in res), wall, workers
+
+
 def run_reference(args, rank, world):
-    """The oracle as it stands on the host cores, on a bounded sample per step."""
+    """The oracle as it stands on every host core, on a bounded sample per
+    step: one n^3-cell block of the 256^3 grid on the surface shell per core."""
     if rank != 0:
         return
-    mlp, _ = workload(0)
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_sample(mlp, args.cpu_cells)
+        oracle_all_cores(args.cpu_cells, cores, cores)
     tot_cells, tot_t = 0, 0.0
     for _ in range(args.steps):
-        c, dt, st = cpu_sample(mlp, args.cpu_cells)
+        c, dt, _ = oracle_all_cores(args.cpu_cells, cores, cores)
         tot_cells += c
         tot_t += dt
     v = tot_cells / tot_t / 1e6
-    cores = os.cpu_count()
     line = {"metric": "ODC Mcells/s at 256^3", "value": v, "unit": "Mcells/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"envelope MLP 256^3 (k={STEPS_1D}), sampled as a {args.cpu_cells}^3-cell block "
-                                   f"of the same grid crossing the surface shell"},
+            "config": {"workload": f"envelope MLP 256^3 (k={STEPS_1D}), sampled as {cores} blocks of "
+                                   f"{args.cpu_cells}^3 cells of the same grid on the surface shell per step"},
             "cpu_baseline": {"value": v, "unit": "Mcells/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
-                             "sample": f"{args.cpu_cells}^3-cell block of the 256^3 grid per step"},
+                             "sample": f"{cores} blocks of {args.cpu_cells}^3 cells of the 256^3 grid on the surface "
+                                       f"shell per step, one per process (numpy single-threaded in each)"},
             "e2e": {"value": v, "unit": "Mcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -646,15 +693,15 @@ def main():
         if mlp_launches:
             a = mlp_flops / (mlp_ms * 1e-3) / 1e12
             # DRAM bytes of one launch: ncu on launches of 256 K and 1 M points
-            # (dram__bytes_read + write): 0.95 MB (the weights) + 12.0 B per query
+            # (dram__bytes_read + write): 1.01 MB (the weights) + 12.1 B per query
             q_per_launch = mlp_flops / mlp_launches / 459264.0
             rows.append({"bound": "alu", "kernel": "k_mlp_fp32 (FP32 SIMT network; the plain path and the band "
                                                    "re-evaluation)", "achieved": a, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": a / fp32_peak,
-                         "traffic": 0.95e6 + 12.0 * q_per_launch,
+                         "traffic": 1.01e6 + 12.1 * q_per_launch,
                          "traffic_source": "bytes per launch at this run's mean queries per launch, from ncu "
                                            "dram__bytes_read.sum + dram__bytes_write.sum of launches of 256K and "
-                                           "1M points: 0.95 MB + 12.0 B per query",
+                                           "1M points: 1.01 MB + 12.1 B per query",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock (unit counts)",
                          "ms_per_step": mlp_ms / args.steps, "flops_per_launch": mlp_flops / mlp_launches})
         if tc_launches:
@@ -731,12 +778,18 @@ def main():
             from paper_2409_13418_gb300 import inputs as I
             line["serving"] = serve_bench(odc, I, args.serve_seconds, args.serve_slots)
         if world == 1 and not args.no_cpu_baseline:
-            c, dt, st = cpu_sample(mlp, args.cpu_cells)
-            line["cpu_baseline"] = {"value": c / dt / 1e6, "unit": "Mcells/s", "cores": os.cpu_count(),
+            cores = os.cpu_count() or 1
+            ca, dta, _ = oracle_all_cores(args.cpu_cells, cores, cores)
+            c1, dt1, _ = cpu_sample(mlp, args.cpu_cells)
+            line["cpu_baseline"] = {"value": ca / dta / 1e6, "unit": "Mcells/s", "cores": cores,
                                     "cpu": cpu_model(), "kind": "oracle",
-                                    "sample": f"{args.cpu_cells}^3-cell block of the same 256^3 grid crossing the "
-                                              f"surface shell, FP64 numpy oracle (network products on numpy's "
-                                              f"threaded BLAS, the rest single-threaded Python)"}
+                                    "sample": f"{cores} blocks of {args.cpu_cells}^3 cells of the same 256^3 grid on "
+                                              f"the surface shell, one per process (FP64 numpy oracle, BLAS "
+                                              f"single-threaded in each), {dta:.1f} s wall",
+                                    "single_process": {"value": c1 / dt1 / 1e6, "cores": cores,
+                                                       "sample": f"one {args.cpu_cells}^3 block, one Python "
+                                                                 f"process (numpy's threaded BLAS for the network "
+                                                                 f"products), {dt1:.1f} s"}}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
