@@ -155,6 +155,8 @@ typedef struct {
                                     ODC_MLP_FP32_TILE(v): run the FP32 network with tile shape v
                                     (0..3) instead of the autotuner's pick -- every shape gives the
                                     same bits */
+    float h16_zmargin;           /* logits of the FP16 tier within this of the threshold go on to the
+                                    split tier (0: the default 0.025) */
 } odc_mlp;
 
 /* The FP32 network has four tile shapes (warps x K chunk x chunks in flight:

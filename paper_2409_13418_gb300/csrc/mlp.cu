@@ -35,6 +35,7 @@ odc_status mlp_check(const odc_mlp* m, std::string* err) {
     if (m->precision != ODC_PREC_FP32 && !(m->band >= 0.0f && m->band < 0.5f))
         { *err = "band must be in [0, 0.5)"; return ODC_ERR_INVALID_ARG; }
     if (!(m->split_zmargin >= 0.0f)) { *err = "split_zmargin must be >= 0"; return ODC_ERR_INVALID_ARG; }
+    if (!(m->h16_zmargin >= 0.0f)) { *err = "h16_zmargin must be >= 0"; return ODC_ERR_INVALID_ARG; }
     return ODC_OK;
 }
 
@@ -192,6 +193,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->split = m->no_split ? 0 : 1;
     st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
     st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2.5e-5f;
+    st->zh16 = m->h16_zmargin > 0.0f ? m->h16_zmargin : 0.025f;
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
     st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
     st->scale = m->env_scale;

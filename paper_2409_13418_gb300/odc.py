@@ -40,7 +40,7 @@ class Mlp(C.Structure):
                 ("B", C.c_void_p), ("W", C.c_void_p * 8), ("b", C.c_void_p * 8), ("latent", C.c_void_p),
                 ("env_scale", C.c_float), ("env_radius", C.c_float), ("env_amp", C.c_float),
                 ("precision", C.c_int32), ("band", C.c_float), ("no_split", C.c_int32),
-                ("split_zmargin", C.c_float), ("flags", C.c_int32)]
+                ("split_zmargin", C.c_float), ("flags", C.c_int32), ("h16_zmargin", C.c_float)]
 
 
 class Voxels(C.Structure):
@@ -235,7 +235,7 @@ class _SourceHolder:
     """Keeps the numpy buffers behind a Source structure alive."""
 
     def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0, reupload=False,
-                 fp32_tile=None, h16=True):
+                 fp32_tile=None, h16=True, h16_zmargin=0.0):
         self.keep = []
         self.src = Source()
         if src is None:
@@ -277,6 +277,7 @@ class _SourceHolder:
             m.band = 0.03 if band is None else band
             m.no_split = 0 if split else 1
             m.split_zmargin = split_zmargin
+            m.h16_zmargin = h16_zmargin
             m.flags = (MLP_REUPLOAD if reupload else 0) | (((fp32_tile + 1) << 8) if fp32_tile is not None else 0) | \
                 (0 if h16 else MLP_NO_F16_TIER)
             self.keep.append(m)
@@ -389,18 +390,21 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0, h16=True, fp32_tile=None):
+    def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0, h16=True, fp32_tile=None,
+               h16_zmargin=0.0):
         """Make ``src`` the context's resident source (``extract(None, ...)`` reuses it)."""
-        holder = _SourceHolder(src, precision, band, split, split_zmargin, fp32_tile=fp32_tile, h16=h16)
+        holder = _SourceHolder(src, precision, band, split, split_zmargin, fp32_tile=fp32_tile, h16=h16,
+                               h16_zmargin=h16_zmargin)
         _check(_lib.odc_source_upload(self.h, C.byref(holder.src)))
 
     def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, split=True,
-                split_zmargin=0.0, reupload=False, h16=True, fp32_tile=None, **kw) -> Mesh:
+                split_zmargin=0.0, reupload=False, h16=True, fp32_tile=None, h16_zmargin=0.0, **kw) -> Mesh:
         """Run ODC; ``src=None`` reuses the resident source.  ``reupload`` forces
         the network weights to be prepared and copied even if the context holds them;
         ``h16=False`` skips the FP16 tier of the BF16 path (same mesh, other cost);
         ``fp32_tile`` forces a tile shape of the FP32 network (same bits)."""
-        holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, fp32_tile=fp32_tile, h16=h16)
+        holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, fp32_tile=fp32_tile, h16=h16,
+                               h16_zmargin=h16_zmargin)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
         m = MeshC()
