@@ -670,7 +670,7 @@ constexpr uint32_t kTmemCols3 = 2 * kH;    // main accumulator, then the correct
 constexpr float kLoScale = 2048.0f;        // lo parts carried as fp16((v - hi) 2^11), kept normal
 constexpr float kLoUnscale = 1.0f / 2048.0f;
 constexpr size_t kSmemBytes3 =
-    1024 + 2 * kABytes + kStages3 * 2 * kHalfSlice + 256 + kGroups3 * kTileM * 4 + (5 * kH + 4) * 4;
+    1024 + 2 * kABytes + kStages3 * 2 * kHalfSlice + 256 + kGroups3 * kTileM * 4 + (5 * kH + 4 + 3 * kNF) * 4;
 
 // instruction descriptor: D F32, A/B F16, both K-major, N = 256, M = 256 (pair)
 constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kPairRows >> 4) << 24);
@@ -724,10 +724,11 @@ __global__ void __launch_bounds__(kThreads3, 1)
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages3 + 4);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     float* part = (float*)((uint8_t*)bars + 256);      // [kGroups3][kTileM] partial output sums
-    float* sp = part + kGroups3 * kTileM;              // biases [4][256], w4 [256], b4
+    float* sp = part + kGroups3 * kTileM;              // biases [4][256], w4 [256], b4, Fourier B [64][3]
     for (int i = threadIdx.x; i < 4 * kH; i += blockDim.x) sp[i] = P.wblob[kOffb_(i / kH) + (i % kH)];
     for (int i = threadIdx.x; i < kH; i += blockDim.x) sp[4 * kH + i] = P.wblob[kOffW_(kNL) + i];
     if (threadIdx.x == 0) sp[5 * kH] = P.wblob[kOffb_(kNL)];
+    for (int i = threadIdx.x; i < 3 * kNF; i += blockDim.x) sp[5 * kH + 4 + i] = P.wblob[kOffB + i];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = query_count(P.Q, P.n);
@@ -829,7 +830,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
         const int r = quad * 32 + lane;
         const int c0 = grp * kGCols;
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
-        const float* Bf = P.wblob + kOffB;
+        const float* Bf = sp + 5 * kH + 4;
         const uint32_t ready = cluster_addr(act_ready, 0);   // the leader's barrier
         uint32_t acc_phase = 0, part_phase = 0;
         bool ok = true;
@@ -844,8 +845,7 @@ __global__ void __launch_bounds__(kThreads3, 1)
                 float sv[8], cv[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    float2 v = fourier_sincos(__ldg(Bf + 3 * (j + i)), __ldg(Bf + 3 * (j + i) + 1),
-                                              __ldg(Bf + 3 * (j + i) + 2), x);
+                    float2 v = fourier_sincos(Bf[3 * (j + i)], Bf[3 * (j + i) + 1], Bf[3 * (j + i) + 2], x);
                     sv[i] = v.x;
                     cv[i] = v.y;
                 }
