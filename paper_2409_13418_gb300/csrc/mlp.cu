@@ -374,6 +374,74 @@ __device__ __forceinline__ void dense_relu(float* act, int K, const float* __res
     __syncthreads();
 }
 
+// Small lists: a full tile costs the same whatever its number of real
+// queries (every chunk of every layer runs over all its rows), so a list of
+// a few thousand queries would leave most SMs idle behind one long tile per
+// SM.  Lists of at most kSmallN queries run as tiles of kSM = 32 queries
+// instead, four times as many CTAs for the same list: lane (ty, tx) =
+// (lane / 4, lane % 4) of warp w takes rows ty 4 .. + 3 and columns w 16 +
+// tx 4 .. + 3.  Each output still sums its products in order k = 0..K-1,
+// one rounding per FMA: the same bits as the full tiles.
+constexpr int kSM = 32;                    // queries per small tile
+constexpr int kSmallStride = kSM + 4;      // floats between consecutive k of the small act[k][m]
+template <class T>
+__device__ __forceinline__ void dense_relu_small(float* act, int K, const float* __restrict__ Wt,
+                                                 const float* __restrict__ bias, float* __restrict__ wbuf,
+                                                 const float* const* rowb) {
+    static_assert(T::kWarps == 16, "small tiles: 16 warps x 16 columns");
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row0 = (lane >> 2) * 4;
+    const int col0 = warp * 16 + (lane & 3) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    const int nchunk = K / T::kKC;
+    auto stage = [&](int c) {
+        if (c < nchunk) {
+            const float* src = Wt + (size_t)c * T::kKC * kH;
+            float* dst = wbuf + (c % T::kWStages) * T::kKC * kH;
+#pragma unroll
+            for (int v = tid; v < T::kKC * kH / 4; v += T::kThreads) cp_async16(dst + 4 * v, src + 4 * v);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int c = 0; c < T::kWStages - 1; ++c) stage(c);
+    for (int c = 0; c < nchunk; ++c) {
+        cp_async_wait<T::kWStages - 2>();
+        __syncthreads();
+        stage(c + T::kWStages - 1);
+        const float* w = wbuf + (c % T::kWStages) * T::kKC * kH + col0;
+        const float* a = act + (size_t)(c * T::kKC) * kSmallStride + row0;
+#pragma unroll 8
+        for (int kk = 0; kk < T::kKC; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(a + kk * kSmallStride);
+            const float4 w0 = *reinterpret_cast<const float4*>(w + kk * kH);
+            const float av[4] = {a0.x, a0.y, a0.z, a0.w};
+            const float wv[4] = {w0.x, w0.y, w0.z, w0.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i][j] = fmaf(av[i], wv[j], acc[i][j]);
+        }
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = col0 + j;
+        float b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = rowb ? rowb[row0 + i][col] : bias[col];
+        *reinterpret_cast<float4*>(act + (size_t)col * kSmallStride + row0) =
+            make_float4(fmaxf(acc[0][j] + b[0], 0.f), fmaxf(acc[1][j] + b[1], 0.f), fmaxf(acc[2][j] + b[2], 0.f),
+                        fmaxf(acc[3][j] + b[3], 0.f));
+    }
+    __syncthreads();
+}
+
 // Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // of min(n, *Q.cnt) queries (the tile loop is uniform within a CTA).
 template <class T>
@@ -389,6 +457,41 @@ __global__ void __launch_bounds__(T::kThreads, 1)
     const int tid = threadIdx.x;
     const int64_t n = query_count(Q, n_max);
     const float* B = wb + kOffB;
+    if constexpr (T::kWarps == 16) if (n <= (int64_t)gridDim.x * kSM * 2) {
+        // small list: 32-query tiles (at most two per CTA)
+        for (int64_t base = (int64_t)blockIdx.x * kSM; base < n; base += (int64_t)gridDim.x * kSM) {
+            if (tid < kSM) {
+                int64_t q = base + tid;
+                xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
+                if (Q.b0tab) rowb[tid] = q < n ? query_b0(Q, query_index(Q, q)) : wb + kOffb_(0);
+            }
+            __syncthreads();
+            for (int i = tid; i < kNF * kSM; i += T::kThreads) {
+                int j = i / kSM, m = i % kSM;
+                float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
+                act[j * kSmallStride + m] = sc.x;
+                act[(kNF + j) * kSmallStride + m] = sc.y;
+            }
+            __syncthreads();
+            for (int l = 0; l < kNL; ++l)
+                dense_relu_small<T>(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf,
+                                    l == 0 && Q.b0tab ? rowb : nullptr);
+            for (int t = tid; t < 4 * kSM; t += T::kThreads) {
+                const int m = t % kSM, p = t / kSM;
+                const float* w5 = wb + kOffW[kNL];
+                float s = 0.0f;
+                for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[k * kSmallStride + m], w5[k], s);
+                part[m][p] = s;
+            }
+            __syncthreads();
+            if (tid < kSM && base + tid < n) {
+                float f = ((part[tid][0] + part[tid][1]) + (part[tid][2] + part[tid][3])) + wb[kOffb[kNL]];
+                zout[query_index(Q, base + tid)] = envelope_logit(xs[tid], f, scale, radius, amp);
+            }
+            __syncthreads();   // part and xs are reused by the next tile
+        }
+        return;
+    }
     for (int64_t base = (int64_t)blockIdx.x * T::kTM; base < n; base += (int64_t)gridDim.x * T::kTM) {
         if (tid < T::kTM) {
             int64_t q = base + tid;
@@ -431,7 +534,8 @@ constexpr int kFp32Variants = kFp32VariantCount;
 
 template <class T>
 static void launch_fp32_tile(const MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s) {
-    const int64_t tiles = (n + T::kTM - 1) / T::kTM;
+    // enough CTAs for the small-list path's 32-query tiles when n is small
+    const int64_t tiles = (n + kSM - 1) / kSM;
     const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)std::max(st->sms, 1));
     k_mlp_fp32<T><<<grid, T::kThreads, T::kSmem, s>>>(st->wblob, Q, n, st->scale, st->radius, st->amp, z);
     note_launch();

@@ -237,13 +237,14 @@ def test_fp32_tile_shapes_give_identical_bits(ctx, mlp):
     the same logits bit for bit (same FMA order per output), and the pick is
     one of them."""
     rng = np.random.default_rng(7)
-    pts = rng.uniform(-1, 1, (50000, 3)).astype(np.float32)
-    ref = None
-    for v in range(4):
-        _, z = ctx.eval_points(mlp, pts, precision=0, fp32_tile=v)
-        if ref is None:
-            ref = z
-        assert z.tobytes() == ref.tobytes(), v
+    for npts in (3000, 50000):   # 3000: the 16-warp shapes take their small-list path (32-query tiles)
+        pts = rng.uniform(-1, 1, (npts, 3)).astype(np.float32)
+        ref = None
+        for v in range(4):
+            _, z = ctx.eval_points(mlp, pts, precision=0, fp32_tile=v)
+            if ref is None:
+                ref = z
+            assert z.tobytes() == ref.tobytes(), (npts, v)
     _, z = ctx.eval_points(mlp, pts, precision=0)
     assert z.tobytes() == ref.tobytes()
     m = ctx.extract(mlp, I.cube_grid(24), steps_1d=10, precision=0)
