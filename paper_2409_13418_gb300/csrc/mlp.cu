@@ -457,9 +457,49 @@ __global__ void __launch_bounds__(T::kThreads, 1)
     const int tid = threadIdx.x;
     const int64_t n = query_count(Q, n_max);
     const float* B = wb + kOffB;
-    if constexpr (T::kWarps == 16) if (n <= (int64_t)gridDim.x * kSM * 2) {
-        // small list: 32-query tiles (at most two per CTA)
-        for (int64_t base = (int64_t)blockIdx.x * kSM; base < n; base += (int64_t)gridDim.x * kSM) {
+    // Full tiles cover whole waves of the grid; a remainder of at most three
+    // small-tile rounds (and any list that small) runs as 32-query tiles over
+    // the whole grid instead of a last, partly filled wave of full tiles.
+    int64_t n_big = n;
+    if constexpr (T::kWarps == 16) {
+        const int64_t wave = (int64_t)gridDim.x * T::kTM;
+        const int64_t rem = n % wave;
+        if (rem <= (int64_t)gridDim.x * kSM * 3) n_big = n - rem;
+    }
+    for (int64_t base = (int64_t)blockIdx.x * T::kTM; base < n_big; base += (int64_t)gridDim.x * T::kTM) {
+        if (tid < T::kTM) {
+            int64_t q = base + tid;
+            xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
+            if (Q.b0tab) rowb[tid] = q < n ? query_b0(Q, query_index(Q, q)) : wb + kOffb_(0);
+        }
+        __syncthreads();
+        for (int i = tid; i < kNF * T::kTM; i += T::kThreads) {
+            int j = i / T::kTM, m = i % T::kTM;
+            float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
+            act[j * T::kActStride + m] = sc.x;
+            act[(kNF + j) * T::kActStride + m] = sc.y;
+        }
+        __syncthreads();
+        for (int l = 0; l < kNL; ++l)
+            dense_relu<T>(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf,
+                          l == 0 && Q.b0tab ? rowb : nullptr);
+        for (int t = tid; t < 4 * T::kTM; t += T::kThreads) {
+            const int m = t % T::kTM, p = t / T::kTM;
+            const float* w5 = wb + kOffW[kNL];
+            float s = 0.0f;
+            for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[k * T::kActStride + m], w5[k], s);
+            part[m][p] = s;
+        }
+        __syncthreads();
+        if (tid < T::kTM && base + tid < n) {
+            float f = ((part[tid][0] + part[tid][1]) + (part[tid][2] + part[tid][3])) + wb[kOffb[kNL]];
+            zout[query_index(Q, base + tid)] = envelope_logit(xs[tid], f, scale, radius, amp);
+        }
+    }
+    __syncthreads();   // the small tiles reuse xs, part and the activation buffer
+    if constexpr (T::kWarps == 16) {
+        // the small-tile remainder [n_big, n)
+        for (int64_t base = n_big + (int64_t)blockIdx.x * kSM; base < n; base += (int64_t)gridDim.x * kSM) {
             if (tid < kSM) {
                 int64_t q = base + tid;
                 xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
@@ -489,37 +529,6 @@ __global__ void __launch_bounds__(T::kThreads, 1)
                 zout[query_index(Q, base + tid)] = envelope_logit(xs[tid], f, scale, radius, amp);
             }
             __syncthreads();   // part and xs are reused by the next tile
-        }
-        return;
-    }
-    for (int64_t base = (int64_t)blockIdx.x * T::kTM; base < n; base += (int64_t)gridDim.x * T::kTM) {
-        if (tid < T::kTM) {
-            int64_t q = base + tid;
-            xs[tid] = q < n ? query_point(Q, q) : make_float3(0.f, 0.f, 0.f);
-            if (Q.b0tab) rowb[tid] = q < n ? query_b0(Q, query_index(Q, q)) : wb + kOffb_(0);
-        }
-        __syncthreads();
-        for (int i = tid; i < kNF * T::kTM; i += T::kThreads) {
-            int j = i / T::kTM, m = i % T::kTM;
-            float2 sc = fourier_sincos(B[3 * j], B[3 * j + 1], B[3 * j + 2], xs[m]);
-            act[j * T::kActStride + m] = sc.x;
-            act[(kNF + j) * T::kActStride + m] = sc.y;
-        }
-        __syncthreads();
-        for (int l = 0; l < kNL; ++l)
-            dense_relu<T>(act, l == 0 ? 2 * kNF : kH, wb + kOffW_(l), wb + kOffb_(l), wbuf,
-                          l == 0 && Q.b0tab ? rowb : nullptr);
-        for (int t = tid; t < 4 * T::kTM; t += T::kThreads) {
-            const int m = t % T::kTM, p = t / T::kTM;
-            const float* w5 = wb + kOffW[kNL];
-            float s = 0.0f;
-            for (int k = p * 64; k < p * 64 + 64; ++k) s = fmaf(act[k * T::kActStride + m], w5[k], s);
-            part[m][p] = s;
-        }
-        __syncthreads();
-        if (tid < T::kTM && base + tid < n) {
-            float f = ((part[tid][0] + part[tid][1]) + (part[tid][2] + part[tid][3])) + wb[kOffb[kNL]];
-            zout[query_index(Q, base + tid)] = envelope_logit(xs[tid], f, scale, radius, amp);
         }
     }
 }
