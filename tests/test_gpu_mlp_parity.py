@@ -138,8 +138,8 @@ F16_ZMARGIN = 0.025   # logit margin of the FP16 tier (library constant; measure
 
 def test_f16_tier_logits_within_half_its_margin_of_fp32(ctx, mlp):
     """The single-product FP16 tier (FP16 activations, FP16 weights w 2^s,
-    FP32 accumulation) stays within half its 0.02 logit margin of the FP32
-    network (0.025 logit margin), uniformly over the box and on the surface shell where the
+    FP32 accumulation) stays within half its logit margin (0.025) of the
+    FP32 network, uniformly over the box and on the surface shell where the
     searches query it."""
     from paper_2409_13418_gb300 import odc
     rng = np.random.default_rng(6)
@@ -157,7 +157,7 @@ def test_f16_tier_logits_within_half_its_margin_of_fp32(ctx, mlp):
 
 def test_split_bf16_logits_within_margin_of_fp32(ctx, mlp):
     """The split tier (FP16 hi + lo operands, three products per layer,
-    corrections in their own accumulator) stays within 0.4 of the default
+    corrections in their own accumulator) stays within 0.65 of the default
     re-decision margin (2.5e-5) of the FP32 network, uniformly over the box
     (the near-surface points the searches query show the same largest error,
     1.29e-5, with a median of 1.8e-6)."""
