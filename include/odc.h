@@ -125,10 +125,10 @@ enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2, ODC_PREC_F16 = 
  * (operands split into FP16 hi + lo, three products per layer, FP32
  * accumulation of hi hi and of the lo corrections in separate accumulators),
  * then, for the logits still within ``split_zmargin`` of the threshold (0:
- * the default 2.5e-5: 1.9 times the largest split-tier logit error measured
- * against the FP32 network, 1.29e-5 on 1.45 M near-surface points and
- * 1.34e-5 on 1 M uniform ones, about 9 standard deviations of the
- * near-surface errors), by the FP32 network; ``no_split`` nonzero sends every
+ * the default 2e-5: 2.1 times the largest split-tier logit error measured
+ * against the FP32 network with the default ``split_acc_comp``, 9.5e-6 on
+ * 1 M uniform points and 8.7e-6 on 600 k near-surface ones), by the FP32
+ * network; ``no_split`` nonzero sends every
  * band decision to the FP32 network directly.  A band of 0.03 (|z| < 0.12)
  * covers the measured BF16 logit error (0.063) twice over. */
 typedef struct {
@@ -157,6 +157,12 @@ typedef struct {
                                     same bits */
     float h16_zmargin;           /* logits of the FP16 tier within this of the threshold go on to the
                                     split tier (0: the default 0.025) */
+    float split_acc_comp;        /* split tier: relative scale c (per 256 products of a layer sum) by
+                                    which its layer sums are multiplied, (1 + c K / 256), undoing on
+                                    average the tensor core's accumulation, which rounds every MMA's
+                                    sum toward zero (0: the default 2e-7, measured to leave the split
+                                    tier's mean logit error against the FP32 network within 1e-7 of
+                                    zero; negative: none) */
 } odc_mlp;
 
 /* The FP32 network has four tile shapes (warps x K chunk x chunks in flight:

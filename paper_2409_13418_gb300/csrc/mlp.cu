@@ -36,6 +36,7 @@ odc_status mlp_check(const odc_mlp* m, std::string* err) {
         { *err = "band must be in [0, 0.5)"; return ODC_ERR_INVALID_ARG; }
     if (!(m->split_zmargin >= 0.0f)) { *err = "split_zmargin must be >= 0"; return ODC_ERR_INVALID_ARG; }
     if (!(m->h16_zmargin >= 0.0f)) { *err = "h16_zmargin must be >= 0"; return ODC_ERR_INVALID_ARG; }
+    if (!(m->split_acc_comp < 1e-3f)) { *err = "split_acc_comp must be below 1e-3"; return ODC_ERR_INVALID_ARG; }
     return ODC_OK;
 }
 
@@ -192,8 +193,9 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->band = m->band;
     st->split = m->no_split ? 0 : 1;
     st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
-    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2.5e-5f;
+    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2e-5f;
     st->zh16 = m->h16_zmargin > 0.0f ? m->h16_zmargin : 0.025f;
+    st->split_comp = m->split_acc_comp == 0.0f ? kSplitAccComp : std::max(m->split_acc_comp, 0.0f);
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
     st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
     st->scale = m->env_scale;
@@ -206,6 +208,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     std::vector<float> key;
     key.reserve(kBlobFloats + (size_t)kH * m->latent_dim + 8);
     key.push_back((float)m->latent_dim);
+    key.push_back(st->split_comp);   // part of the prepared split-tier operands
     key.insert(key.end(), m->B, m->B + kNF * 3);
     for (int l = 0; l <= kNL; ++l) {
         size_t rows = l == kNL ? 1 : kH, cols = l == 0 ? (size_t)din : kH;
@@ -749,8 +752,8 @@ __global__ void __launch_bounds__(kTierBlock)
 // equals the FP32 plain path's.  A logit of the BF16 pass is kept only
 // outside the band |z - zt| >= zband; the single-product FP16 tier (measured
 // error 0.0091, below zh16 / 2) re-takes the band and keeps |z - zt| >= zh16; the
-// split-FP16 tensor-core network (largest measured error 0.52 zsplit, about
-// 4.8 standard deviations of its error on near-surface points) re-takes
+// split-FP16 tensor-core network (largest measured error 0.48 zsplit, its
+// accumulation bias compensated) re-takes
 // the rest and keeps |z - zt| >= zsplit; the FP32 SIMT network takes what is
 // left.  A disabled tier passes its queries on with its predecessor's
 // margin.  With hints, a query starts at the tier its predicted |z - zt|

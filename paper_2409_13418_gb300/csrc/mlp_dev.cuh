@@ -15,6 +15,13 @@ constexpr int kNF = 64;    // Fourier frequencies
 constexpr int kH = 256;    // hidden width
 constexpr int kNL = 4;     // hidden layers
 constexpr int kScratchSlots = 40;
+// Split tier: the tensor core rounds each MMA's accumulated sum toward zero,
+// so a layer sum of K products comes out short by a few units in the last
+// place on average; the epilogue multiplies it by (1 + kSplitAccComp K / 256).
+// Measured on GB300 (1.6 M points): mean logit error against the FP32
+// network -9.6e-7 without it, -3.8e-8 with 2e-7; largest error 1.34e-5
+// without, 9.5e-6 with.
+constexpr float kSplitAccComp = 2e-7f;
 
 // FP32 weight blob (floats): B [64][3] (padded to 256), W_l^T [in][out] for
 // l = 0..3, w4 [256], biases b_0..b_3 [256], b_4 [1].
@@ -74,7 +81,8 @@ struct MlpState {
     float zh16 = 0.025f;        // |z - zt| below which an FP16-tier decision is re-taken by the split tier
     int fp32_variant = -1;      // FP32 network tile shape picked by the autotuner (-1: not yet)
     int fp32_forced = -1;       // tile shape forced by the source's flags (-1: the autotuner's)
-    float zsplit = 2.5e-5f;     // |z - zt| below which a split-tier decision is re-taken in FP32
+    float zsplit = 2e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
+    float split_comp = 0.0f;    // split tier: layer sums scaled by (1 + split_comp K / 256)
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     unsigned long long wait_ns = 0;   // limit of the single-CTA tensor-core kernels' pipeline waits (0: 2 s)

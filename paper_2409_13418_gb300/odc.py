@@ -40,7 +40,8 @@ class Mlp(C.Structure):
                 ("B", C.c_void_p), ("W", C.c_void_p * 8), ("b", C.c_void_p * 8), ("latent", C.c_void_p),
                 ("env_scale", C.c_float), ("env_radius", C.c_float), ("env_amp", C.c_float),
                 ("precision", C.c_int32), ("band", C.c_float), ("no_split", C.c_int32),
-                ("split_zmargin", C.c_float), ("flags", C.c_int32), ("h16_zmargin", C.c_float)]
+                ("split_zmargin", C.c_float), ("flags", C.c_int32), ("h16_zmargin", C.c_float),
+                ("split_acc_comp", C.c_float)]
 
 
 class Voxels(C.Structure):
@@ -235,7 +236,7 @@ class _SourceHolder:
     """Keeps the numpy buffers behind a Source structure alive."""
 
     def __init__(self, src, precision=None, band=None, split=True, split_zmargin=0.0, reupload=False,
-                 fp32_tile=None, h16=True, h16_zmargin=0.0):
+                 fp32_tile=None, h16=True, h16_zmargin=0.0, split_acc_comp=0.0):
         self.keep = []
         self.src = Source()
         if src is None:
@@ -278,6 +279,7 @@ class _SourceHolder:
             m.no_split = 0 if split else 1
             m.split_zmargin = split_zmargin
             m.h16_zmargin = h16_zmargin
+            m.split_acc_comp = split_acc_comp
             m.flags = (MLP_REUPLOAD if reupload else 0) | (((fp32_tile + 1) << 8) if fp32_tile is not None else 0) | \
                 (0 if h16 else MLP_NO_F16_TIER)
             self.keep.append(m)
@@ -391,20 +393,21 @@ class Context:
         self.close()
 
     def upload(self, src, precision=None, band=None, split=True, split_zmargin=0.0, h16=True, fp32_tile=None,
-               h16_zmargin=0.0):
+               h16_zmargin=0.0, split_acc_comp=0.0):
         """Make ``src`` the context's resident source (``extract(None, ...)`` reuses it)."""
         holder = _SourceHolder(src, precision, band, split, split_zmargin, fp32_tile=fp32_tile, h16=h16,
-                               h16_zmargin=h16_zmargin)
+                               h16_zmargin=h16_zmargin, split_acc_comp=split_acc_comp)
         _check(_lib.odc_source_upload(self.h, C.byref(holder.src)))
 
     def extract(self, src, grid: I.Grid, steps_1d=15, stream=None, precision=None, band=None, split=True,
-                split_zmargin=0.0, reupload=False, h16=True, fp32_tile=None, h16_zmargin=0.0, **kw) -> Mesh:
+                split_zmargin=0.0, reupload=False, h16=True, fp32_tile=None, h16_zmargin=0.0, split_acc_comp=0.0,
+                **kw) -> Mesh:
         """Run ODC; ``src=None`` reuses the resident source.  ``reupload`` forces
         the network weights to be prepared and copied even if the context holds them;
         ``h16=False`` skips the FP16 tier of the BF16 path (same mesh, other cost);
         ``fp32_tile`` forces a tile shape of the FP32 network (same bits)."""
         holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, fp32_tile=fp32_tile, h16=h16,
-                               h16_zmargin=h16_zmargin)
+                               h16_zmargin=h16_zmargin, split_acc_comp=split_acc_comp)
         g = make_grid(grid)
         p = make_params(steps_1d=steps_1d, **kw)
         m = MeshC()
@@ -511,11 +514,11 @@ class Context:
         return {f: getattr(q, f) for f, _ in QualityC._fields_}
 
     def eval_points(self, src, pts: np.ndarray, iso: float = 0.5, precision: int = -1, band=None, split=True,
-                    fp32_tile=None):
+                    fp32_tile=None, split_acc_comp=0.0):
         # the source's precision: FP32, BF16 or FP8 tiers; the single-network
         # overrides (split, FP16, raw FP8) run on a BF16 source's state
         sp = None if precision < 0 else (precision if precision in (PREC_FP32, PREC_BF16, PREC_FP8) else PREC_BF16)
-        holder = _SourceHolder(src, sp, band, split, fp32_tile=fp32_tile)
+        holder = _SourceHolder(src, sp, band, split, fp32_tile=fp32_tile, split_acc_comp=split_acc_comp)
         pts = np.ascontiguousarray(pts, np.float32).reshape(-1, 3)
         lab = np.empty(pts.shape[0], np.uint8)
         z = np.empty(pts.shape[0], np.float32)
