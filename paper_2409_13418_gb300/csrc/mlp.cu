@@ -702,50 +702,65 @@ __global__ void k_route(RouteArgs ra, int64_t n, uint8_t* __restrict__ r) {
 }
 // Queries of tier `from` whose logit lies within thr of t move to tier `to`
 // (from < 0: every query takes its tier from the hints first); the queries
-// now in tier `to` are appended to list (one atomic per block: the list order
-// varies between runs, the logits written back through it do not) and
-// counted in *cnt and *total.  Launched with kTierBlock threads.
+// now in tier `to` are appended to list (one atomic per block of
+// kTierItems x kTierBlock queries: the list order varies between runs, the
+// logits written back through it do not) and counted in *cnt and *total.
+// Launched with kTierBlock threads.
 constexpr int kTierBlock = 256;
+constexpr int kTierItems = 4;              // queries per thread
 __global__ void __launch_bounds__(kTierBlock)
     k_tier_list(const float* __restrict__ z, int64_t n, const unsigned long long* __restrict__ nlim, float t, int from,
                 int to, float thr, RouteArgs ra, uint8_t* __restrict__ r, int* __restrict__ list,
                 unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ total) {
-    __shared__ unsigned wbase[kTierBlock / 32];
+    constexpr int kWarps = kTierBlock / 32;
+    __shared__ unsigned wbase[kTierItems][kWarps];
     __shared__ unsigned long long bbase;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (nlim) n = min(n, (int64_t)*nlim);   // device-sized query list
-    bool f = false;
-    if (i < n) {
-        int ri;
-        if (from < 0) {
-            ri = route_of(ra, i);
-            r[i] = (uint8_t)ri;
-        } else {
-            ri = r[i];
-            if (ri == from && fabsf(z[i] - t) < thr) {
-                ri = to;
-                r[i] = (uint8_t)to;
+    const int64_t i0 = (int64_t)blockIdx.x * (kTierItems * kTierBlock) + threadIdx.x;
+    uint32_t bal[kTierItems];
+    bool fl[kTierItems];
+#pragma unroll
+    for (int it = 0; it < kTierItems; ++it) {
+        const int64_t i = i0 + it * kTierBlock;
+        bool f = false;
+        if (i < n) {
+            int ri;
+            if (from < 0) {
+                ri = route_of(ra, i);
+                r[i] = (uint8_t)ri;
+            } else {
+                ri = r[i];
+                if (ri == from && fabsf(z[i] - t) < thr) {
+                    ri = to;
+                    r[i] = (uint8_t)to;
+                }
             }
+            f = ri == to;
         }
-        f = ri == to;
+        fl[it] = f;
+        bal[it] = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wbase[it][warp] = (unsigned)__popc(bal[it]);
     }
-    const uint32_t b = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) wbase[warp] = (unsigned)__popc(b);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned tot = 0;
 #pragma unroll
-        for (int w = 0; w < kTierBlock / 32; ++w) {
-            const unsigned c = wbase[w];
-            wbase[w] = tot;
-            tot += c;
-        }
+        for (int it = 0; it < kTierItems; ++it)
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const unsigned c = wbase[it][w];
+                wbase[it][w] = tot;
+                tot += c;
+            }
         bbase = tot ? atomicAdd(cnt, (unsigned long long)tot) : 0ull;
         if (tot) atomicAdd(total, (unsigned long long)tot);
     }
     __syncthreads();
-    if (f) list[bbase + wbase[warp] + __popc(b & ((1u << lane) - 1u))] = (int)i;
+#pragma unroll
+    for (int it = 0; it < kTierItems; ++it)
+        if (fl[it])
+            list[bbase + wbase[it][warp] + __popc(bal[it] & ((1u << lane) - 1u))] = (int)(i0 + it * kTierBlock);
 }
 
 // Tiered evaluation (A.2.2 binary decision at iso): the sign of every logit
@@ -772,7 +787,7 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     int* list = (int*)plist;
     uint8_t* route = (uint8_t*)pr;
     unsigned long long* cnt = st->dq + 4;
-    const unsigned blocks = (unsigned)((n + kTierBlock - 1) / kTierBlock);
+    const unsigned blocks = (unsigned)((n + kTierItems * kTierBlock - 1) / (kTierItems * kTierBlock));
     MLP_CK(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), s));   // tier lists 0..3, FP8 total and list
     const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16, st->zb8, st->fp8};
     // per tier: queries evaluated since the timing began
@@ -781,7 +796,7 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     unsigned long long* cnt8 = st->dq + 9;
     const int first = st->fp8 ? 4 : 0;
     if (!hint && !nlim) {
-        k_route<<<blocks, kTierBlock, 0, s>>>(ra, n, route); note_launch();
+        k_route<<<(unsigned)((n + kTierBlock - 1) / kTierBlock), kTierBlock, 0, s>>>(ra, n, route); note_launch();
         if ((r = first == 4 ? mlp_tc8_eval(st, Q, n, z, s, err) : mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK)
             return r;
     } else {
