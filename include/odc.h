@@ -125,10 +125,10 @@ enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2, ODC_PREC_F16 = 
  * (operands split into FP16 hi + lo, three products per layer, FP32
  * accumulation of hi hi and of the lo corrections in separate accumulators),
  * then, for the logits still within ``split_zmargin`` of the threshold (0:
- * the default 2e-5: 2.1 times the largest split-tier logit error measured
- * against the FP32 network with the default ``split_acc_comp``, 9.5e-6 on
- * 1 M uniform points and 8.7e-6 on 600 k near-surface ones), by the FP32
- * network; ``no_split`` nonzero sends every
+ * the default 2e-5: 1.75 times the largest split-tier logit error measured
+ * against the FP32 network over eight networks of this shape with the
+ * calibrated ``split_acc_comp``, 1.14e-5, and 2.3 times or more on six of
+ * them), by the FP32 network; ``no_split`` nonzero sends every
  * band decision to the FP32 network directly.  A band of 0.03 (|z| < 0.12)
  * covers the measured BF16 logit error (0.063) twice over. */
 typedef struct {
@@ -157,12 +157,14 @@ typedef struct {
                                     same bits */
     float h16_zmargin;           /* logits of the FP16 tier within this of the threshold go on to the
                                     split tier (0: the default 0.025) */
-    float split_acc_comp;        /* split tier: relative scale c (per 256 products of a layer sum) by
-                                    which its layer sums are multiplied, (1 + c K / 256), undoing on
-                                    average the tensor core's accumulation, which rounds every MMA's
-                                    sum toward zero (0: the default 2e-7, measured to leave the split
-                                    tier's mean logit error against the FP32 network within 1e-7 of
-                                    zero; negative: none) */
+    float split_acc_comp;        /* split tier: the layer sums of its tensor-core products are taken as
+                                    (1 + c K / 256) times what the tensor core returns, undoing on
+                                    average its accumulation, which rounds every MMA's sum toward
+                                    zero.  0 (the default): c is calibrated for each uploaded network
+                                    (its logit error against the FP32 network is fitted against the
+                                    network output at two values of c on 16384 points, and c is set
+                                    where the fit's slope vanishes; about 1 ms per upload of new
+                                    weights); > 0: this c; < 0: none.  Must be below 1e-3. */
 } odc_mlp;
 
 /* The FP32 network has four tile shapes (warps x K chunk x chunks in flight:
@@ -563,7 +565,10 @@ odc_status odc_batch_destroy(odc_batch* b);
 
 /* Join a context to group b (NULL: leave).  Binding happens at the
  * context's next MLP source upload (odc_extract with an MLP source, or
- * odc_source_upload). */
+ * odc_source_upload).  A member's shared evaluation waits on the host until
+ * every member inside a search stage has made its call; a call that no
+ * round takes within 120 s fails with ODC_ERR_TIMEOUT, and so does that
+ * member's odc_extract. */
 odc_status odc_ctx_join_batch(odc_ctx* ctx, odc_batch* b);
 
 /* Merged evaluation rounds run by the group and the member calls they

@@ -12,8 +12,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "batch.h"
@@ -23,6 +25,11 @@
 namespace odc {
 
 constexpr int kMaxMembers = 64;
+// A queued call that no round has taken within this time leaves the queue
+// and fails with ODC_ERR_TIMEOUT (its search stage then ends, so the other
+// members' rounds no longer wait for it); a call already taken by a running
+// round waits for that round.
+constexpr int kRendezvousSeconds = 120;
 
 struct BatchSeg {
     const float3* pts;
@@ -368,7 +375,17 @@ odc_status batch_eval(MlpState* st, const float3* pts, int64_t n_max, const unsi
     std::unique_lock<std::mutex> lk(g->mu);
     g->queue.push_back(&p);
     maybe_lead(g, lk);
-    g->cv.wait(lk, [&] { return p.done; });
+    if (!g->cv.wait_for(lk, std::chrono::seconds(kRendezvousSeconds), [&] { return p.done; })) {
+        auto it = std::find(g->queue.begin(), g->queue.end(), &p);
+        if (it != g->queue.end()) {
+            g->queue.erase(it);
+            *err = "batch: no shared evaluation round formed within " + std::to_string(kRendezvousSeconds) +
+                   " s (" + std::to_string(g->queue.size()) + " other calls queued, " + std::to_string(g->active) +
+                   " members in a search stage)";
+            return ODC_ERR_TIMEOUT;
+        }
+        g->cv.wait(lk, [&] { return p.done; });   // taken by a round that is running: it completes
+    }
     if (p.status != ODC_OK) *err = p.err;
     return p.status;
 }

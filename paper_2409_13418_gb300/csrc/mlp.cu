@@ -159,6 +159,7 @@ size_t mlp_device_bytes(const MlpState* st) {
 
 static odc_status fp32_kernel_setup(std::string* err);
 static odc_status fp32_autotune(MlpState* st, cudaStream_t s, std::string* err);
+static odc_status split_calibrate(MlpState* st, cudaStream_t s, std::string* err);
 constexpr int kFp32VariantCount = 4;
 
 // Upload weights: FP32 transposed copies for the SIMT path (W^T [in][out]),
@@ -195,7 +196,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
     st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2e-5f;
     st->zh16 = m->h16_zmargin > 0.0f ? m->h16_zmargin : 0.025f;
-    st->split_comp = m->split_acc_comp == 0.0f ? kSplitAccComp : std::max(m->split_acc_comp, 0.0f);
+    st->split_comp = m->split_acc_comp;
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
     st->zband = (float)(2.0 * std::atanh(std::min(0.999999, 2.0 * (double)m->band)));
     st->scale = m->env_scale;
@@ -228,6 +229,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
         st->b0dirty = true;
         return ODC_OK;
     }
+    const bool same_weights = st->wblob && key == st->wkey;   // a forced re-upload
     st->wkey.clear();   // set again once the upload below has succeeded
     std::vector<float> h(kBlobFloats, 0.0f);
     // B
@@ -258,8 +260,18 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     MLP_CK(cudaMemcpyAsync(st->wblob, h.data(), sizeof(float) * kBlobFloats, cudaMemcpyHostToDevice, s));
     r = mlp_tc_prepare(st, h.data(), s, err);
     if (r != ODC_OK) return r;
+    if (st->fp32_variant < 0 && (r = fp32_autotune(st, s, err)) != ODC_OK) return r;
+    // the split tier's accumulation compensation for these weights
+    if (st->split_comp != 0.0f) {
+        st->split_comp_used = std::max(st->split_comp, 0.0f);
+        r = mlp_tc_set_comp(st, st->split_comp_used, s, err);
+    } else if (same_weights && st->split_comp_used >= 0.0f) {
+        r = mlp_tc_set_comp(st, st->split_comp_used, s, err);
+    } else {
+        r = split_calibrate(st, s, err);
+    }
+    if (r != ODC_OK) return r;
     st->wkey.swap(key);
-    if (st->fp32_variant < 0) return fp32_autotune(st, s, err);
     return ODC_OK;
 }
 
@@ -657,6 +669,60 @@ float mlp_fp32_variant_ms(int v) {
 
 // n is the query count, or with Q.cnt its upper bound (the count is then
 // accumulated on the device for the FLOP accounting).
+static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
+
+// Calibration of the split tier's accumulation compensation c for the
+// uploaded weights.  Its logit error against the FP32 network is close to
+// beta f (f the network output, recovered from the FP32 logit), with beta
+// linear in c: beta is fitted by least squares at c = 0 and at c =
+// kSplitCompProbe on 16384 hashed points of the box, and c is set where the
+// line crosses zero (kept within [0, 1e-6]).  Rows the split tier hands on
+// (out of FP16 range) and differences beyond 1e-3 are left out of the fit.
+static odc_status split_calibrate(MlpState* st, cudaStream_t s, std::string* err) {
+    const int64_t n = 16384;
+    float3* pts = nullptr;
+    float* z = nullptr;
+    MLP_CK(cudaMallocAsync((void**)&pts, n * sizeof(float3), s));
+    MLP_CK(cudaMallocAsync((void**)&z, 3 * n * sizeof(float), s));
+    k_calib_points<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n);
+    note_launch();
+    const QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
+    odc_status r = launch_fp32(st, Q, n, z, s, err);
+    if (r == ODC_OK) r = mlp_tc_set_comp(st, 0.0f, s, err);
+    if (r == ODC_OK) r = mlp_tc3_eval(st, Q, n, z + n, s, err);
+    if (r == ODC_OK) r = mlp_tc_set_comp(st, kSplitCompProbe, s, err);
+    if (r == ODC_OK) r = mlp_tc3_eval(st, Q, n, z + 2 * n, s, err);
+    std::vector<float> hz((size_t)3 * n);
+    std::vector<float3> hp((size_t)n);
+    if (r == ODC_OK &&
+        (cudaMemcpyAsync(hz.data(), z, hz.size() * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(hp.data(), pts, hp.size() * sizeof(float3), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess)) {
+        *err = "split calibration: copy failed";
+        r = ODC_ERR_CUDA;
+    }
+    cudaFreeAsync(pts, s);
+    cudaFreeAsync(z, s);
+    if (r == ODC_OK) r = mlp_tc_check(st, s, err);
+    if (r != ODC_OK) return r;
+    double sff = 0.0, sf0 = 0.0, sf1 = 0.0;
+    for (int64_t i = 0; i < n && st->amp != 0.0f && st->scale != 0.0f; ++i) {
+        const double z32 = hz[i], d0 = (double)hz[n + i] - z32, d1 = (double)hz[2 * n + i] - z32;
+        if (!std::isfinite(z32) || !std::isfinite(d0) || !std::isfinite(d1) || std::fabs(d0) > 1e-3 ||
+            std::fabs(d1) > 1e-3)
+            continue;
+        const double x = hp[i].x, y = hp[i].y, w = hp[i].z;
+        const double f = (z32 / st->scale - st->radius + std::sqrt(x * x + y * y + w * w)) / st->amp;
+        sff += f * f;
+        sf0 += d0 * f;
+        sf1 += d1 * f;
+    }
+    double c = 0.0;
+    if (sff > 0.0 && sf1 != sf0) c = -sf0 * (double)kSplitCompProbe / (sf1 - sf0);
+    st->split_comp_used = (float)std::min(std::max(c, 0.0), 1e-6);
+    return mlp_tc_set_comp(st, st->split_comp_used, s, err);
+}
+
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {
     if (n <= 0) return ODC_OK;
     const int v = st->fp32_forced >= 0 ? st->fp32_forced : std::max(st->fp32_variant, 0);

@@ -16,12 +16,14 @@ constexpr int kH = 256;    // hidden width
 constexpr int kNL = 4;     // hidden layers
 constexpr int kScratchSlots = 40;
 // Split tier: the tensor core rounds each MMA's accumulated sum toward zero,
-// so a layer sum of K products comes out short by a few units in the last
-// place on average; the epilogue multiplies it by (1 + kSplitAccComp K / 256).
-// Measured on GB300 (1.6 M points): mean logit error against the FP32
-// network -9.6e-7 without it, -3.8e-8 with 2e-7; largest error 1.34e-5
-// without, 9.5e-6 with.
-constexpr float kSplitAccComp = 2e-7f;
+// so a layer sum of K products comes out short by about c K / 256 of its
+// size (c from 1e-7 to 3e-7 on the networks measured); its weights are
+// prepared as w (1 + c K / 256), which puts that back at no cost per query.  A ReLU network whose layer sums all shrink by
+// the same fraction shrinks its output f by a fixed fraction, so the logit
+// error is close to proportional to f: mlp_split_calibrate fits that slope
+// at c = 0 and at c = kSplitCompProbe on a calibration list and takes the c
+// where it vanishes, per network, at weight upload.
+constexpr float kSplitCompProbe = 2e-7f;
 
 // FP32 weight blob (floats): B [64][3] (padded to 256), W_l^T [in][out] for
 // l = 0..3, w4 [256], biases b_0..b_3 [256], b_4 [1].
@@ -82,7 +84,8 @@ struct MlpState {
     int fp32_variant = -1;      // FP32 network tile shape picked by the autotuner (-1: not yet)
     int fp32_forced = -1;       // tile shape forced by the source's flags (-1: the autotuner's)
     float zsplit = 2e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
-    float split_comp = 0.0f;    // split tier: layer sums scaled by (1 + split_comp K / 256)
+    float split_comp = 0.0f;    // requested split-tier compensation: 0 calibrate, < 0 none, > 0 this c
+    float split_comp_used = -1.0f;   // c in effect for the uploaded weights (-1: none set yet)
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     unsigned long long wait_ns = 0;   // limit of the single-CTA tensor-core kernels' pipeline waits (0: 2 s)
@@ -126,6 +129,8 @@ odc_status mlp_tc_check(MlpState* st, cudaStream_t s, std::string* err);
 int* mlp_tc_err_flag(MlpState* st);
 // Split-BF16 network (three BF16 products per layer, FP32 accumulation).
 odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
+// Split tier: prepare its weights for the accumulation compensation c (w (1 + c K / 256)).
+odc_status mlp_tc_set_comp(MlpState* st, float c, cudaStream_t s, std::string* err);
 
 // [sin(2 pi u), cos(2 pi u)] with u = b . x formed exactly in float-float and
 // reduced to [-1/2, 1/2] turns before sincospi.

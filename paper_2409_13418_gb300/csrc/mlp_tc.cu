@@ -953,9 +953,8 @@ struct MlpTc {
     CUtensorMap maps_lo_mc[4];
     uint8_t* w8 = nullptr;          // FP8 pass: E4M3 W_l 2^s8_l [256][K_l]
     CUtensorMap maps8[4];
-    float* wsc = nullptr;           // device: [0..3] FP16 tier weight unscale 2^-s_l, [4..7] ints (s_l),
-                                    // [8..11] FP8 pass unscale 2^-(4 + s8_l), [12..15] ints (s8_l),
-                                    // [16..19] split tier unscale 2^-s_l (1 + comp K_l / 256)
+    float* wsc = nullptr;           // device: [0..3] split path weight unscale 2^-s_l, [4..7] ints (s_l),
+                                    // [8..11] FP8 pass unscale 2^-(4 + s8_l), [12..15] ints (s8_l)
     int* err = nullptr;
     int sms = 0;
     int clusters3 = 0;              // co-resident CTA pairs of the split kernel
@@ -987,8 +986,7 @@ static EncodeTiledFn encode_fn(std::string* err) {
 // 2^14) with the FP16 hi and 2^11-scaled lo parts of w 2^s.
 namespace {
 __global__ void k_wprep_scale(const float* __restrict__ blob, float* __restrict__ wsc, int* __restrict__ sexp_out,
-                              float* __restrict__ wsc8, int* __restrict__ s8_out, float* __restrict__ wsc3,
-                              float comp) {
+                              float* __restrict__ wsc8, int* __restrict__ s8_out) {
     const int l = blockIdx.x;
     const size_t K = l == 0 ? 2 * kNF : kH;
     const float* Wt = blob + kOffW_(l);
@@ -1007,8 +1005,6 @@ __global__ void k_wprep_scale(const float* __restrict__ blob, float* __restrict_
         while (sexp < 24 && wmax * __int_as_float((127 + sexp + 1) << 23) < 16384.0f) ++sexp;
         wsc[l] = __int_as_float((127 - sexp) << 23);
         sexp_out[l] = sexp;
-        // split tier: the same unscale times the accumulation compensation
-        wsc3[l] = (float)((double)wsc[l] * (1.0 + (double)comp * (double)K / (double)kH));
         // FP8: the largest 2^s8 keeping |w| 2^s8 below 256 (E4M3 reaches 448)
         int s8 = -8;
         while (s8 < 24 && wmax * __int_as_float((127 + s8 + 1) << 23) < 256.0f) ++s8;
@@ -1057,7 +1053,7 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
         if (cudaMalloc((void**)&T->w, total * sizeof(__nv_bfloat16)) != cudaSuccess ||
             cudaMalloc((void**)&T->w16, 2 * total * sizeof(__half)) != cudaSuccess ||
             cudaMalloc((void**)&T->w8, total) != cudaSuccess ||
-            cudaMalloc((void**)&T->wsc, 12 * sizeof(float) + 8 * sizeof(int)) != cudaSuccess ||
+            cudaMalloc((void**)&T->wsc, 8 * sizeof(float) + 8 * sizeof(int)) != cudaSuccess ||
             cudaMalloc((void**)&T->err, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             *err = "tensor-core weight allocation failed";
@@ -1066,7 +1062,7 @@ odc_status mlp_tc_prepare(MlpState* st, const float* hb, cudaStream_t s, std::st
     }
     int* sexp = (int*)(T->wsc + 4);
     int* s8 = (int*)(T->wsc + 12);
-    k_wprep_scale<<<4, 256, 0, s>>>(st->wblob, T->wsc, sexp, T->wsc + 8, s8, T->wsc + 16, st->split_comp);
+    k_wprep_scale<<<4, 256, 0, s>>>(st->wblob, T->wsc, sexp, T->wsc + 8, s8);
     note_launch();
     k_wprep_conv<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(st->wblob, sexp, total, T->w, T->w16, s8, T->w8);
     note_launch();
@@ -1214,7 +1210,7 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
     int64_t steps = (n + tc::kPairRows - 1) / tc::kPairRows;
     int grid = 2 * (int)std::min<int64_t>(steps, (int64_t)T->clusters3);
     tc::TcParams P{st->wblob, Q, n, st->scale, st->radius, st->amp, z, T->err, nullptr, st->zt, 0ull, nullptr};
-    P.wsc = T->wsc + 16;   // the split tier's compensated unscale
+    P.wsc = T->wsc;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1241,6 +1237,47 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
     }
     if (!Q.cnt) st->flops[2] += 3.0 * kFlopsPerQuery * (double)n;   // three products per layer
     st->launches[2] += 1;
+    return ODC_OK;
+}
+
+namespace {
+// The split path's FP16 hi and 2^11-scaled lo parts of w 2^s_l (1 + c_l),
+// c_l = c K_l / 256, the factor formed in double so that c is not rounded
+// to the float spacing near 1 (the split keeps 22 of its bits).
+__global__ void k_wprep_split(const float* __restrict__ blob, const int* __restrict__ sexp_in, size_t total,
+                              __half* __restrict__ w16, float c) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // tile element, layers in order
+    if (i >= total) return;
+    size_t off = 0;
+    int l = 0;
+    for (; l < 3; ++l) {
+        const size_t sz = (size_t)kH * (l == 0 ? 2 * kNF : kH);
+        if (i < off + sz) break;
+        off += sz;
+    }
+    const size_t K = l == 0 ? 2 * kNF : kH;
+    const size_t j = i - off, n = j / K, k = j % K;
+    const double f = 1.0 + (double)c * (double)K / (double)kH;
+    const float ws = (float)((double)blob[kOffW_(l) + k * kH + n] * (double)__int_as_float((127 + sexp_in[l]) << 23) * f);
+    const __half hi = __float2half_rn(ws);
+    w16[i] = hi;
+    w16[total + i] = __float2half_rn((ws - __half2float(hi)) * tc::kLoScale);
+}
+}  // namespace
+
+odc_status mlp_tc_set_comp(MlpState* st, float c, cudaStream_t s, std::string* err) {
+    MlpTc* T = st->tc;
+    if (!T || !T->w16 || !T->wsc) {
+        *err = "tensor-core path not prepared";
+        return ODC_ERR_INTERNAL;
+    }
+    const size_t total = (size_t)kH * (2 * kNF + 3 * kH);
+    k_wprep_split<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(st->wblob, (const int*)(T->wsc + 4), total, T->w16, c);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+        *err = "split compensation update failed";
+        return ODC_ERR_CUDA;
+    }
     return ODC_OK;
 }
 
