@@ -405,7 +405,9 @@ class Context:
         """Run ODC; ``src=None`` reuses the resident source.  ``reupload`` forces
         the network weights to be prepared and copied even if the context holds them;
         ``h16=False`` skips the FP16 tier of the BF16 path (same mesh, other cost);
-        ``fp32_tile`` forces a tile shape of the FP32 network (same bits)."""
+        ``fp32_tile`` forces a tile shape of the FP32 network (same bits);
+        ``split_acc_comp`` sets the split tier's accumulation compensation (0:
+        calibrated per network at upload, negative: none; same mesh, other cost)."""
         holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, fp32_tile=fp32_tile, h16=h16,
                                h16_zmargin=h16_zmargin, split_acc_comp=split_acc_comp)
         g = make_grid(grid)
