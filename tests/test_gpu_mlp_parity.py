@@ -371,3 +371,23 @@ def test_fp8_saturated_rows_are_handed_on(ctx):
     v32, t32 = ctx.extract(src, g, steps_1d=12, precision=0).to_host()
     v8, t8 = ctx.extract(src, g, steps_1d=12, precision=odc.PREC_FP8, band=BF16_BAND).to_host()
     assert np.array_equal(t8, t32) and np.array_equal(v8, v32)
+
+
+def test_split_calibration_is_deterministic(mlp):
+    """The calibrated compensation is a function of the weights alone: two
+    contexts, and a forced re-upload of the same weights, give the split
+    tier the same logits bit for bit, and so the same tiered mesh."""
+    from paper_2409_13418_gb300 import odc
+    rng = np.random.default_rng(12)
+    pts = rng.uniform(-1, 1, (200000, 3)).astype(np.float32)
+    g = I.cube_grid(40)
+    out = []
+    for reupload in (False, True):
+        with odc.Context(0) as c:
+            _, zs = c.eval_points(mlp, pts, precision=2)
+            v, t = c.extract(mlp, g, steps_1d=15, precision=odc.PREC_BF16, reupload=reupload).to_host()
+            _, zs2 = c.eval_points(mlp, pts, precision=2)
+            out.append((zs, zs2, v, t))
+    (a, a2, va, ta), (b, b2, vb, tb) = out
+    assert a.tobytes() == a2.tobytes() == b.tobytes() == b2.tobytes()
+    assert va.tobytes() == vb.tobytes() and np.array_equal(ta, tb)
