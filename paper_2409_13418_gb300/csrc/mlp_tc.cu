@@ -641,7 +641,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // the corrections (the scheme of Ootomo and Yokota, 2022, for FP32 GEMM on
 // FP16 tensor cores); the epilogue forms main + corr 2^-11 in FP32 and undoes
 // the 2^s weight scale exactly.  The dropped A_lo W_lo term is ~2^-22
-// relative.  An activation beyond the FP16 range marks its query (logit zt)
+// relative.  The weights are split from w 2^s (1 + c K / 256), c the
+// network's calibrated compensation of the tensor core's accumulation,
+// which rounds every MMA's sum toward zero (mlp_tc_set_comp).  An activation beyond the FP16 range marks its query (logit zt)
 // so that the FP32 tier re-evaluates it.
 //
 // CTA pairs (clusters of two) run the 2-SM form of the MMA (cta_group::2,
