@@ -1245,7 +1245,9 @@ odc_status mlp_tc3_eval(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cu
 namespace {
 // The split path's FP16 hi and 2^11-scaled lo parts of w 2^s_l (1 + c_l),
 // c_l = c K_l / 256, the factor formed in double so that c is not rounded
-// to the float spacing near 1 (the split keeps 22 of its bits).
+// to the float spacing near 1 (the split keeps 22 of its bits).  The FP16
+// tier reads the same hi parts; the factor (below 1e-6) is far inside its
+// FP16 rounding.
 __global__ void k_wprep_split(const float* __restrict__ blob, const int* __restrict__ sexp_in, size_t total,
                               __half* __restrict__ w16, float c) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // tile element, layers in order
