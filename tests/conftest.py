@@ -11,3 +11,18 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (run with -m gpu)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+# A GPU test that stalls ends as a failure with every thread's stack dumped,
+# instead of holding the run (and the GPU) until an outer limit kills it.
+# Uses pytest-timeout where it is installed; the longest GPU test takes
+# well under a minute.
+GPU_TEST_TIMEOUT_S = 600
+
+
+def pytest_collection_modifyitems(config, items):
+    if not config.pluginmanager.hasplugin("timeout"):
+        return
+    for item in items:
+        if item.get_closest_marker("gpu") and not item.get_closest_marker("timeout"):
+            item.add_marker(pytest.mark.timeout(GPU_TEST_TIMEOUT_S, method="thread"))
