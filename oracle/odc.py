@@ -27,8 +27,8 @@ Readings where the paper is silent:
     are valid; concavity for c1, c3, c4 by cyclic relabelling of Eqs. A1/A2.
 All geometry is in cell-local units (a cell is the unit cube).
 
-Parity unpinned: none of the above readings is printed in the paper; each is
-pinned instead by the closed forms and invariants in tests/test_oracle_pins.py,
+Pins: the paper prints none of the above readings, so each is pinned by
+the closed forms and invariants in tests/test_oracle_pins.py,
 and the IC case rule (ic_cases) by the envelope-containment brute force and
 the intersection-free guarantee of A.1.5 in tests/test_oracle_ic.py.
 """
