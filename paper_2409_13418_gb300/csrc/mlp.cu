@@ -96,8 +96,20 @@ cudaEvent_t* mlp_ev_pair(MlpState* st, int kind) {
     return p;
 }
 
+// The FP16 tier costs each search round a launch of ~25 us even when its
+// list is short, and saves (1.33 - 0.65) ns per query it takes from the split
+// tier: with fewer crossing edges than this (about a 128^3 surface of the
+// envelope networks) its launches cost more than they save, and its queries
+// go to the split tier instead (the same decisions; measured 64^3: 47 FP16
+// launches, 1.17 ms of a 12.1 ms extraction).
+constexpr int64_t kH16MinEdges = 250000;
+void mlp_size_tiers(MlpState* st, int64_t n_edges) {
+    if (st) st->h16_run = st->h16 && n_edges >= kH16MinEdges;
+}
+
 void mlp_timing_begin(MlpState* st, cudaStream_t s) {
     if (!st) return;
+    st->h16_run = st->h16;
     st->ev_used = 0;
     for (auto& f : st->flops) f = 0.0;
     for (auto& l : st->launches) l = 0;
@@ -194,6 +206,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->band = m->band;
     st->split = m->no_split ? 0 : 1;
     st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
+    st->h16_run = st->h16;
     st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2e-5f;
     st->zh16 = m->h16_zmargin > 0.0f ? m->h16_zmargin : 0.025f;
     st->split_comp = m->split_acc_comp;
@@ -855,7 +868,7 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     unsigned long long* cnt = st->dq + 4;
     const unsigned blocks = (unsigned)((n + kTierItems * kTierBlock - 1) / (kTierItems * kTierBlock));
     MLP_CK(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), s));   // tier lists 0..3, FP8 total and list
-    const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16, st->zb8, st->fp8};
+    const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16_run, st->zb8, st->fp8};
     // per tier: queries evaluated since the timing began
     unsigned long long* tot[4] = {st->dq + 0, st->dq + 3, st->dq + 1, st->dq + 2};
     unsigned long long* tot8 = st->dq + 10;
@@ -884,7 +897,7 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     int from = 0;
     float thr = st->zband;
     for (int tier = 1; tier <= 3; ++tier) {
-        const bool on = tier == 1 ? st->h16 != 0 : tier == 2 ? st->split != 0 : true;
+        const bool on = tier == 1 ? st->h16_run != 0 : tier == 2 ? st->split != 0 : true;
         if (!on) continue;
         k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, from, tier, thr, ra, route, list, cnt + tier,
                                                   tot[tier]); note_launch();

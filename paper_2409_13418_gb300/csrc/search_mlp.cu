@@ -547,6 +547,7 @@ static odc_status faces_body(MlpState* st, const GridDev& g, const uint32_t* bit
 // the network evaluations are shared with the group's other members.
 odc_status mlp_bisect(MlpState* st, const GridDev& g, const uint32_t* bits, const uint32_t* edges, uint32_t ne, int k,
                       float iso, uint32_t* T, cudaStream_t s, int64_t* nq, std::string* err) {
+    mlp_size_tiers(st, (int64_t)ne);
     batch_enter(st);
     const odc_status r = bisect_body(st, g, bits, edges, ne, k, iso, T, s, nq, err);
     std::string e2;
