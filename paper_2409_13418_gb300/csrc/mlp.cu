@@ -96,20 +96,25 @@ cudaEvent_t* mlp_ev_pair(MlpState* st, int kind) {
     return p;
 }
 
-// The FP16 tier costs each search round a launch of ~25 us even when its
-// list is short, and saves (1.33 - 0.65) ns per query it takes from the split
-// tier: with fewer crossing edges than this (about a 128^3 surface of the
-// envelope networks) its launches cost more than they save, and its queries
-// go to the split tier instead (the same decisions; measured 64^3: 47 FP16
-// launches, 1.17 ms of a 12.1 ms extraction).
-constexpr int64_t kH16MinEdges = 250000;
+// Each tensor-core pass costs a search round a launch of ~25 us even when
+// its list is short (one tile's chain of weight slices and four layers);
+// per query the FP16 tier saves (1.33 - 0.65) ns and the BF16 pass (1.33 -
+// 0.56) ns against the split tier.  With fewer crossing edges than this
+// (about a 128^3 surface of the envelope networks) their search-round
+// launches cost more than they save: the search queries then start at the
+// split tier (or the FP32 tier) instead, with the same decisions.  The grid
+// pass keeps every tier.
+constexpr int64_t kSmallSurfaceEdges = 250000;
 void mlp_size_tiers(MlpState* st, int64_t n_edges) {
-    if (st) st->h16_run = st->h16 && n_edges >= kH16MinEdges;
+    if (!st) return;
+    st->h16_run = st->h16 && n_edges >= kSmallSurfaceEdges;
+    st->first_run = n_edges >= kSmallSurfaceEdges;
 }
 
 void mlp_timing_begin(MlpState* st, cudaStream_t s) {
     if (!st) return;
     st->h16_run = st->h16;
+    st->first_run = 1;
     st->ev_used = 0;
     for (auto& f : st->flops) f = 0.0;
     for (auto& l : st->launches) l = 0;
@@ -207,6 +212,7 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->split = m->no_split ? 0 : 1;
     st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
     st->h16_run = st->h16;
+    st->first_run = 1;
     st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2e-5f;
     st->zh16 = m->h16_zmargin > 0.0f ? m->h16_zmargin : 0.025f;
     st->split_comp = m->split_acc_comp;
@@ -765,14 +771,17 @@ struct RouteArgs {
     int split, h16;
     float z8;
     int fp8;
+    int first;   // the FP8 / BF16 passes take queries (0: every query starts at a later tier)
 };
 __device__ __forceinline__ int route_of(const RouteArgs& ra, int64_t i) {
     const float h = ra.hint ? ra.hint[i] : INFINITY;
-    if (ra.fp8 && h >= ra.z8) return 4;
+    if (ra.first) {
+        if (ra.fp8 && h >= ra.z8) return 4;
+        if (h >= ra.zb) return 0;
+    }
     if (h < ra.zs) return 3;
     if (h < ra.zh) return ra.split ? 2 : 3;
-    if (h < ra.zb) return ra.h16 ? 1 : (ra.split ? 2 : 3);
-    return 0;
+    return ra.h16 ? 1 : (ra.split ? 2 : 3);
 }
 __global__ void k_route(RouteArgs ra, int64_t n, uint8_t* __restrict__ r) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -868,7 +877,11 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     unsigned long long* cnt = st->dq + 4;
     const unsigned blocks = (unsigned)((n + kTierItems * kTierBlock - 1) / (kTierItems * kTierBlock));
     MLP_CK(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), s));   // tier lists 0..3, FP8 total and list
-    const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16_run, st->zb8, st->fp8};
+    // small surfaces: the search queries skip the FP8 / BF16 passes (their
+    // launches would cost more than they save, mlp_size_tiers)
+    const bool first_on = !hint || st->first_run;
+    const RouteArgs ra{hint, st->zsplit, st->zh16, st->zband, st->split, st->h16_run, st->zb8, st->fp8,
+                       first_on ? 1 : 0};
     // per tier: queries evaluated since the timing began
     unsigned long long* tot[4] = {st->dq + 0, st->dq + 3, st->dq + 1, st->dq + 2};
     unsigned long long* tot8 = st->dq + 10;
@@ -884,10 +897,11 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
         k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, -1, first, 0.0f, ra, route, list,
                                                   first == 4 ? cnt8 : cnt + 0, first == 4 ? tot8 : tot[0]); note_launch();
         QuerySrc L0{Q.pts, list, Q.g, first == 4 ? cnt8 : cnt + 0, Q.seg, Q.b0tab};
-        if ((r = first == 4 ? mlp_tc8_eval(st, L0, n, z, s, err) : mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK)
+        if (first_on &&
+            (r = first == 4 ? mlp_tc8_eval(st, L0, n, z, s, err) : mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK)
             return r;
     }
-    if (first == 4) {
+    if (first == 4 && first_on) {
         // the BF16 pass re-takes the FP8 band and the queries routed to it
         k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, 4, 0, st->zb8, ra, route, list, cnt + 0,
                                                   tot[0]); note_launch();

@@ -78,6 +78,7 @@ struct MlpState {
     int split = 1;              // use the split-FP16 tier for band re-evaluation
     int h16 = 1;                // use the single-product FP16 tier between the BF16 pass and the split tier
     int h16_run = 1;            // ... in the current extraction (off for small surfaces, mlp_size_tiers)
+    int first_run = 1;          // search queries may start at the FP8 / BF16 passes (off for small surfaces)
     int fp8 = 0;                // an FP8 pass ahead of the BF16 pass (source precision ODC_PREC_FP8)
     float zb8 = 2.5f;           // |z - zt| below which an FP8-pass decision is re-taken by the BF16 pass
                                 // (2.1 times the largest FP8 logit error measured, 1.19)
