@@ -505,6 +505,9 @@ def main():
     ap.add_argument("--slab-res", type=int, default=0,
                     help="only the envelope MLP at this resolution in --slab-count z-slabs (prints its own JSON line)")
     ap.add_argument("--slab-count", type=int, default=8)
+    ap.add_argument("--mlp-res", type=int, default=0,
+                    help="profile run: only whole envelope-MLP extractions at this resolution (resident BF16 "
+                         "source, --warmup untimed, --steps timed; prints its own JSON line)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -545,6 +548,28 @@ def main():
                 ctx.eval_points(mlp, pts, precision=prec, band=0.0)
         print(json.dumps({"workload": f"{args.net_tier} network tier over {args.net_points} seeded points "
                                       f"(list mode)", "launches": 3}), flush=True)
+        return
+    if args.mlp_res:
+        import torch
+        from paper_2409_13418_gb300 import build, inputs as I, odc
+        build.build()
+        odc.load()
+        g = I.cube_grid(args.mlp_res)
+        with odc.Context(0) as ctx:
+            ctx.upload(I.envelope_mlp(0), precision=odc.PREC_BF16)
+            for _ in range(args.warmup):
+                ctx.extract(None, g, steps_1d=15)
+            torch.cuda.synchronize()
+            l0, t0 = odc.launch_total(), time.perf_counter()
+            for _ in range(args.steps):
+                ctx.extract(None, g, steps_1d=15)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / max(args.steps, 1)
+            launches = (odc.launch_total() - l0) / max(args.steps, 1)
+        print(json.dumps({"workload": f"envelope MLP occupancy, {args.mlp_res}^3 cells, k=15, bf16 band 0.03, "
+                                      f"resident source", "ms_per_extraction": dt * 1e3,
+                          "launches_per_extraction": launches, "steps": args.steps, "warmup": args.warmup}),
+              flush=True)
         return
     if args.slab_res:
         from paper_2409_13418_gb300 import build, inputs as I, odc
