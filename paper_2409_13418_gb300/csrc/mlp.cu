@@ -887,6 +887,9 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     unsigned long long* tot8 = st->dq + 10;
     unsigned long long* cnt8 = st->dq + 9;
     const int first = st->fp8 ? 4 : 0;
+    // without the first passes the routing pass builds the first active
+    // tier's list directly
+    const int start = first_on ? first : (st->h16_run ? 1 : (st->split ? 2 : 3));
     if (!hint && !nlim) {
         k_route<<<(unsigned)((n + kTierBlock - 1) / kTierBlock), kTierBlock, 0, s>>>(ra, n, route); note_launch();
         if ((r = first == 4 ? mlp_tc8_eval(st, Q, n, z, s, err) : mlp_tc_eval(st, Q, n, z, s, err)) != ODC_OK)
@@ -894,8 +897,9 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     } else {
         // routing and the first pass's list in one pass (no hint: every query
         // starts at the first pass)
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, -1, first, 0.0f, ra, route, list,
-                                                  first == 4 ? cnt8 : cnt + 0, first == 4 ? tot8 : tot[0]); note_launch();
+        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, -1, start, 0.0f, ra, route, list,
+                                                  start == 4 ? cnt8 : cnt + start, start == 4 ? tot8 : tot[start]);
+        note_launch();
         QuerySrc L0{Q.pts, list, Q.g, first == 4 ? cnt8 : cnt + 0, Q.seg, Q.b0tab};
         if (first_on &&
             (r = first == 4 ? mlp_tc8_eval(st, L0, n, z, s, err) : mlp_tc_eval(st, L0, n, z, s, err)) != ODC_OK)
@@ -913,8 +917,11 @@ static odc_status eval_tiered(MlpState* st, const QuerySrc& Q, int64_t n, float*
     for (int tier = 1; tier <= 3; ++tier) {
         const bool on = tier == 1 ? st->h16_run != 0 : tier == 2 ? st->split != 0 : true;
         if (!on) continue;
-        k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, from, tier, thr, ra, route, list, cnt + tier,
-                                                  tot[tier]); note_launch();
+        if (tier != start) {   // else the routing pass built this list
+            k_tier_list<<<blocks, kTierBlock, 0, s>>>(z, n, nlim, st->zt, from, tier, thr, ra, route, list,
+                                                      cnt + tier, tot[tier]);
+            note_launch();
+        }
         QuerySrc L{Q.pts, list, Q.g, cnt + tier, Q.seg, Q.b0tab};
         r = tier == 1 ? mlp_tc16_eval(st, L, n, z, s, err)
             : tier == 2 ? mlp_tc3_eval(st, L, n, z, s, err)
