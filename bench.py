@@ -782,6 +782,8 @@ def main():
                            "requeries_split_fp16": stats["n_split"],
                            "requeries_fp32": stats["n_requeries"],
                            "fp32_tile_autotuned": stats["fp32_tile"],
+                           "split_margin": stats.get("split_zmargin"),
+                           "split_acc_comp": stats.get("split_acc_comp"),
                            "stage_ms": [round(x, 3) for x in stats["stage_ms"]]},
                 "e2e": {"value": e2e, "unit": "Mcells/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(vbytes + tbytes)},

@@ -125,10 +125,11 @@ enum { ODC_PREC_FP32 = 0, ODC_PREC_BF16 = 1, ODC_PREC_SPLIT = 2, ODC_PREC_F16 = 
  * (operands split into FP16 hi + lo, three products per layer, FP32
  * accumulation of hi hi and of the lo corrections in separate accumulators),
  * then, for the logits still within ``split_zmargin`` of the threshold (0:
- * the default 2e-5: 1.75 times the largest split-tier logit error measured
- * against the FP32 network over eight networks of this shape with the
- * calibrated ``split_acc_comp``, 1.14e-5, and 2.3 times or more on six of
- * them), by the FP32 network; ``no_split`` nonzero sends every
+ * calibrated for each uploaded network, 2.5 times the largest split-tier
+ * logit difference against the FP32 network on 65536 calibration points and
+ * at least 1.2e-5; over eight networks of this shape that is about twice
+ * the largest difference seen on 3 M points), by the FP32 network;
+ * ``no_split`` nonzero sends every
  * band decision to the FP32 network directly.  A band of 0.03 (|z| < 0.12)
  * covers the measured BF16 logit error (0.063) twice over. */
 typedef struct {
@@ -162,9 +163,10 @@ typedef struct {
                                     average its accumulation, which rounds every MMA's sum toward
                                     zero.  0 (the default): c is calibrated for each uploaded network
                                     (its logit error against the FP32 network is fitted against the
-                                    network output at two values of c on 16384 points, and c is set
-                                    where the fit's slope vanishes; about 1 ms per upload of new
-                                    weights); > 0: this c; < 0: none.  Must be below 1e-3. */
+                                    network output at two values of c on 65536 points, half of them
+                                    on the surface shell 0.3 <= |x| <= 0.7, and c is set where the
+                                    fit's slope vanishes; a few ms per upload of new weights); > 0:
+                                    this c; < 0: none.  Must be below 1e-3. */
 } odc_mlp;
 
 /* The FP32 network has four tile shapes (warps x K chunk x chunks in flight:
@@ -267,6 +269,8 @@ typedef struct {
     float fp8_ms;                /* CUDA-event time of the FP8-pass launches */
     int32_t pad4_;
     int64_t fp8_launches;
+    float split_zmargin;         /* the split tier's logit margin in this extract (MLP sources) */
+    float split_acc_comp;        /* its accumulation compensation c (MLP sources) */
 } odc_stats;
 
 typedef struct {

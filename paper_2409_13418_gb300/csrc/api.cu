@@ -618,8 +618,10 @@ static odc_status extract_impl(odc_ctx* c, const odc_source* src, const std::vec
         S.n_split = mlp_split_count(c->mlp);
         S.n_h16 = mlp_h16_count(c->mlp);
         S.fp32_tile = mlp_fp32_variant(c->mlp);
+        mlp_split_settings(c->mlp, &S.split_zmargin, &S.split_acc_comp);
     } else {
         S.fp32_tile = -1;
+        S.split_zmargin = S.split_acc_comp = 0.0f;
     }
     return ODC_OK;
 }
@@ -939,6 +941,8 @@ odc_status odc_extract_slabbed(odc_ctx* c, const odc_source* src, const odc_grid
         sum.split_launches += a.split_launches; sum.n_split += a.n_split;
         sum.h16_flops += a.h16_flops; sum.h16_ms += a.h16_ms; sum.h16_launches += a.h16_launches;
         sum.n_h16 += a.n_h16;
+        sum.split_zmargin = a.split_zmargin;
+        sum.split_acc_comp = a.split_acc_comp;
         // the next slab's extraction reuses the arenas: the placement must be done
         ODC_CK(cudaStreamSynchronize(st));
     }

@@ -213,7 +213,8 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     st->h16 = (m->flags & ODC_MLP_NO_F16_TIER) ? 0 : 1;
     st->h16_run = st->h16;
     st->first_run = 1;
-    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : 2e-5f;
+    st->zsplit_user = m->split_zmargin;
+    st->zsplit = m->split_zmargin > 0.0f ? m->split_zmargin : (st->zsplit_cal > 0.0f ? st->zsplit_cal : 2e-5f);
     st->zh16 = m->h16_zmargin > 0.0f ? m->h16_zmargin : 0.025f;
     st->split_comp = m->split_acc_comp;
     // |occ - 1/2| < band  <=>  |z| < 2 atanh(2 band)
@@ -280,16 +281,14 @@ odc_status mlp_prepare(MlpState** pst, const odc_mlp* m, cudaStream_t s, std::st
     r = mlp_tc_prepare(st, h.data(), s, err);
     if (r != ODC_OK) return r;
     if (st->fp32_variant < 0 && (r = fp32_autotune(st, s, err)) != ODC_OK) return r;
-    // the split tier's accumulation compensation for these weights
-    if (st->split_comp != 0.0f) {
-        st->split_comp_used = std::max(st->split_comp, 0.0f);
-        r = mlp_tc_set_comp(st, st->split_comp_used, s, err);
-    } else if (same_weights && st->split_comp_used >= 0.0f) {
+    // the split tier's accumulation compensation and margin for these weights
+    if (same_weights && st->split_comp_used >= 0.0f && st->zsplit_cal > 0.0f) {
         r = mlp_tc_set_comp(st, st->split_comp_used, s, err);
     } else {
         r = split_calibrate(st, s, err);
     }
     if (r != ODC_OK) return r;
+    st->zsplit = st->zsplit_user > 0.0f ? st->zsplit_user : st->zsplit_cal;
     st->wkey.swap(key);
     return ODC_OK;
 }
@@ -690,56 +689,115 @@ float mlp_fp32_variant_ms(int v) {
 // accumulated on the device for the FLOP accounting).
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err);
 
-// Calibration of the split tier's accumulation compensation c for the
-// uploaded weights.  Its logit error against the FP32 network is close to
-// beta f (f the network output, recovered from the FP32 logit), with beta
-// linear in c: beta is fitted by least squares at c = 0 and at c =
-// kSplitCompProbe on 16384 hashed points of the box, and c is set where the
-// line crosses zero (kept within [0, 1e-6]).  Rows the split tier hands on
-// (out of FP16 range) and differences beyond 1e-3 are left out of the fit.
+// Half of the split tier's calibration list: points on the shell 0.3 <=
+// |x| <= 0.7 where the envelope networks' surfaces lie (hashed directions
+// from a cube, rejected outside the unit ball, and radii).
+__global__ void k_shell_points(float3* p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t h = (uint64_t)(i + 0x5D1) * 0xD1B54A32D192ED03ull + 0x8CB92BA72F3D8DD7ull;
+    auto next = [&]() {
+        h ^= h >> 29;
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 32;
+        return (float)(h >> 40) * (1.0f / 16777216.0f);
+    };
+    float d[3], q = 0.0f;
+    for (int t = 0; t < 16; ++t) {
+        for (int a = 0; a < 3; ++a) d[a] = 2.0f * next() - 1.0f;
+        q = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (q > 1e-4f && q <= 1.0f) break;
+    }
+    if (!(q > 1e-4f)) { d[0] = 1.0f; d[1] = d[2] = 0.0f; q = 1.0f; }
+    const float r = (0.3f + 0.4f * next()) * rsqrtf(q);
+    p[i] = make_float3(d[0] * r, d[1] * r, d[2] * r);
+}
+
+// Calibration of the split tier for the uploaded weights, on 65536 points
+// (half hashed over the box, half on the surface shell).
+//  * Accumulation compensation c (unless the source fixes it): the split
+//    tier's logit error against the FP32 network is close to beta f (f the
+//    network output, recovered from the FP32 logit), with beta linear in c;
+//    beta is fitted by least squares at c = 0 and at c = kSplitCompProbe, and
+//    c is set where the line crosses zero (kept within [0, 1e-6]).
+//  * Margin: kSplitMarginFactor times the largest |split - FP32| logit
+//    difference on the list at that c, and at least kSplitMarginFloor; on
+//    eight networks of this shape the largest difference over 3 M points was
+//    1.0 to 1.4 times the list's, so the margin is about twice the
+//    large-sample error of each network.
+// Rows the split tier hands on (out of FP16 range) and differences beyond
+// 1e-3 are left out.
+constexpr float kSplitMarginFactor = 2.5f;
+constexpr float kSplitMarginFloor = 1.2e-5f;
 static odc_status split_calibrate(MlpState* st, cudaStream_t s, std::string* err) {
-    const int64_t n = 16384;
+    const int64_t n = 65536;
     float3* pts = nullptr;
     float* z = nullptr;
     MLP_CK(cudaMallocAsync((void**)&pts, n * sizeof(float3), s));
     MLP_CK(cudaMallocAsync((void**)&z, 3 * n * sizeof(float), s));
-    k_calib_points<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pts, n);
+    k_calib_points<<<(unsigned)((n / 2 + 255) / 256), 256, 0, s>>>(pts, n / 2);
+    note_launch();
+    k_shell_points<<<(unsigned)((n / 2 + 255) / 256), 256, 0, s>>>(pts + n / 2, n / 2);
     note_launch();
     const QuerySrc Q{pts, nullptr, GridDev{}, nullptr};
+    const bool fit = st->split_comp == 0.0f;
     odc_status r = launch_fp32(st, Q, n, z, s, err);
-    if (r == ODC_OK) r = mlp_tc_set_comp(st, 0.0f, s, err);
-    if (r == ODC_OK) r = mlp_tc3_eval(st, Q, n, z + n, s, err);
-    if (r == ODC_OK) r = mlp_tc_set_comp(st, kSplitCompProbe, s, err);
-    if (r == ODC_OK) r = mlp_tc3_eval(st, Q, n, z + 2 * n, s, err);
+    if (fit) {
+        if (r == ODC_OK) r = mlp_tc_set_comp(st, 0.0f, s, err);
+        if (r == ODC_OK) r = mlp_tc3_eval(st, Q, n, z + n, s, err);
+        if (r == ODC_OK) r = mlp_tc_set_comp(st, kSplitCompProbe, s, err);
+        if (r == ODC_OK) r = mlp_tc3_eval(st, Q, n, z + 2 * n, s, err);
+    }
     std::vector<float> hz((size_t)3 * n);
     std::vector<float3> hp((size_t)n);
-    if (r == ODC_OK &&
-        (cudaMemcpyAsync(hz.data(), z, hz.size() * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaMemcpyAsync(hp.data(), pts, hp.size() * sizeof(float3), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaStreamSynchronize(s) != cudaSuccess)) {
-        *err = "split calibration: copy failed";
-        r = ODC_ERR_CUDA;
+    auto fetch = [&](size_t count) {
+        if (r == ODC_OK &&
+            (cudaMemcpyAsync(hz.data(), z, count * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+             cudaMemcpyAsync(hp.data(), pts, hp.size() * sizeof(float3), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+             cudaStreamSynchronize(s) != cudaSuccess)) {
+            *err = "split calibration: copy failed";
+            r = ODC_ERR_CUDA;
+        }
+        if (r == ODC_OK) r = mlp_tc_check(st, s, err);
+    };
+    auto usable = [&](double z32, double d) { return std::isfinite(z32) && std::isfinite(d) && std::fabs(d) <= 1e-3; };
+    double c = std::max(st->split_comp, 0.0f);
+    if (fit) {
+        fetch(hz.size());
+        double sff = 0.0, sf0 = 0.0, sf1 = 0.0;
+        for (int64_t i = 0; r == ODC_OK && i < n && st->amp != 0.0f && st->scale != 0.0f; ++i) {
+            const double z32 = hz[i], d0 = (double)hz[n + i] - z32, d1 = (double)hz[2 * n + i] - z32;
+            if (!usable(z32, d0) || !usable(z32, d1)) continue;
+            const double x = hp[i].x, y = hp[i].y, w = hp[i].z;
+            const double f = (z32 / st->scale - st->radius + std::sqrt(x * x + y * y + w * w)) / st->amp;
+            sff += f * f;
+            sf0 += d0 * f;
+            sf1 += d1 * f;
+        }
+        c = 0.0;
+        if (sff > 0.0 && sf1 != sf0) c = -sf0 * (double)kSplitCompProbe / (sf1 - sf0);
+        c = std::min(std::max(c, 0.0), 1e-6);
     }
+    // the margin, from the split tier at the compensation it keeps
+    if (r == ODC_OK) r = mlp_tc_set_comp(st, (float)c, s, err);
+    if (r == ODC_OK) r = mlp_tc3_eval(st, Q, n, z + n, s, err);
+    fetch((size_t)2 * n);
     cudaFreeAsync(pts, s);
     cudaFreeAsync(z, s);
-    if (r == ODC_OK) r = mlp_tc_check(st, s, err);
     if (r != ODC_OK) return r;
-    double sff = 0.0, sf0 = 0.0, sf1 = 0.0;
-    for (int64_t i = 0; i < n && st->amp != 0.0f && st->scale != 0.0f; ++i) {
-        const double z32 = hz[i], d0 = (double)hz[n + i] - z32, d1 = (double)hz[2 * n + i] - z32;
-        if (!std::isfinite(z32) || !std::isfinite(d0) || !std::isfinite(d1) || std::fabs(d0) > 1e-3 ||
-            std::fabs(d1) > 1e-3)
-            continue;
-        const double x = hp[i].x, y = hp[i].y, w = hp[i].z;
-        const double f = (z32 / st->scale - st->radius + std::sqrt(x * x + y * y + w * w)) / st->amp;
-        sff += f * f;
-        sf0 += d0 * f;
-        sf1 += d1 * f;
+    double emax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double z32 = hz[i], d = (double)hz[n + i] - z32;
+        if (usable(z32, d)) emax = std::max(emax, std::fabs(d));
     }
-    double c = 0.0;
-    if (sff > 0.0 && sf1 != sf0) c = -sf0 * (double)kSplitCompProbe / (sf1 - sf0);
-    st->split_comp_used = (float)std::min(std::max(c, 0.0), 1e-6);
-    return mlp_tc_set_comp(st, st->split_comp_used, s, err);
+    st->split_comp_used = (float)c;
+    st->zsplit_cal = std::max(kSplitMarginFloor, (float)(kSplitMarginFactor * emax));
+    return ODC_OK;
+}
+
+void mlp_split_settings(const MlpState* st, float* zmargin, float* comp) {
+    *zmargin = st ? st->zsplit : 0.0f;
+    *comp = st ? std::max(st->split_comp_used, 0.0f) : 0.0f;
 }
 
 static odc_status launch_fp32(MlpState* st, const QuerySrc& Q, int64_t n, float* z, cudaStream_t s, std::string* err) {

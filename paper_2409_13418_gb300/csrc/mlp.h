@@ -65,6 +65,8 @@ odc_status mlp_faces(MlpState* st, const GridDev& g, const uint32_t* bits, const
 void mlp_timing_begin(MlpState* st, cudaStream_t s);
 // Per-extraction tier choice from the surface size (crossing edges).
 void mlp_size_tiers(MlpState* st, int64_t n_edges);
+// The split tier's margin and accumulation compensation in use.
+void mlp_split_settings(const MlpState* st, float* zmargin, float* comp);
 // Reads the device-side query counters (synchronises the stream).
 void mlp_timing_finish(MlpState* st, cudaStream_t s);
 // Per kind (0: FP32 SIMT network, 1: tensor-core network).

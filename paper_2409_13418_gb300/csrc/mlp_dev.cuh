@@ -88,6 +88,8 @@ struct MlpState {
     float zsplit = 2e-5f;       // |z - zt| below which a split-tier decision is re-taken in FP32
     float split_comp = 0.0f;    // requested split-tier compensation: 0 calibrate, < 0 none, > 0 this c
     float split_comp_used = -1.0f;   // c in effect for the uploaded weights (-1: none set yet)
+    float zsplit_user = 0.0f;   // the source's split_zmargin (0: calibrated per network)
+    float zsplit_cal = 0.0f;    // the calibrated margin of the uploaded weights (0: none yet)
     float zt = 0.0f;            // decision threshold logit(iso) of the current extract
     const float* zgrid = nullptr;   // grid logits of the current extract (label-word order)
     unsigned long long wait_ns = 0;   // limit of the single-CTA tensor-core kernels' pipeline waits (0: 2 s)

@@ -74,7 +74,8 @@ class Stats(C.Structure):
                 ("split_launches", C.c_int64), ("n_split", C.c_int64), ("fp32_tile", C.c_int64),
                 ("h16_flops", C.c_double), ("h16_ms", C.c_float), ("pad3_", C.c_int32),
                 ("h16_launches", C.c_int64), ("n_h16", C.c_int64), ("fp8_flops", C.c_double),
-                ("fp8_ms", C.c_float), ("pad4_", C.c_int32), ("fp8_launches", C.c_int64)]
+                ("fp8_ms", C.c_float), ("pad4_", C.c_int32), ("fp8_launches", C.c_int64),
+                ("split_zmargin", C.c_float), ("split_acc_comp", C.c_float)]
 
 
 class SlabC(C.Structure):
