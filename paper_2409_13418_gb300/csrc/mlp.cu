@@ -913,8 +913,8 @@ __global__ void __launch_bounds__(kTierBlock)
 // equals the FP32 plain path's.  A logit of the BF16 pass is kept only
 // outside the band |z - zt| >= zband; the single-product FP16 tier (measured
 // error 0.0091, below zh16 / 2) re-takes the band and keeps |z - zt| >= zh16; the
-// split-FP16 tensor-core network (largest measured error 0.48 zsplit, its
-// accumulation bias compensated) re-takes
+// split-FP16 tensor-core network (its accumulation bias compensated; zsplit
+// calibrated per network at about twice its largest error) re-takes
 // the rest and keeps |z - zt| >= zsplit; the FP32 SIMT network takes what is
 // left.  A disabled tier passes its queries on with its predecessor's
 // margin.  With hints, a query starts at the tier its predicted |z - zt|
