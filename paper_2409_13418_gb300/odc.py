@@ -408,7 +408,9 @@ class Context:
         ``h16=False`` skips the FP16 tier of the BF16 path (same mesh, other cost);
         ``fp32_tile`` forces a tile shape of the FP32 network (same bits);
         ``split_acc_comp`` sets the split tier's accumulation compensation (0:
-        calibrated per network at upload, negative: none; same mesh, other cost)."""
+        calibrated per network at upload, negative: none) and ``split_zmargin``
+        its margin (0: calibrated per network at upload); the margin in use is
+        ``Mesh.stats["split_zmargin"]``."""
         holder = _SourceHolder(src, precision, band, split, split_zmargin, reupload, fp32_tile=fp32_tile, h16=h16,
                                h16_zmargin=h16_zmargin, split_acc_comp=split_acc_comp)
         g = make_grid(grid)
